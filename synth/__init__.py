@@ -1,0 +1,4 @@
+"""Seeded synthetic inputs (meshes and fixations) shared by the oracle tests, the GPU tests and
+the benchmark. Data only: nothing here performs the gaze-mapping computation."""
+from .workloads import (Mesh, Fixations, Params, Workload, tiny_sphere, paper_scene, session,
+                        batched_sessions, city_block, flatten, identity, scale_translate)
