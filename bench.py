@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Throughput of the gaze-mapping hot path: sample x fixation pairs per second.
+
+One step = the whole path on one synthetic workload: scene build (world transform + BVH),
+area-weighted sampling, fixation prep, the fused cone/occlusion/Gaussian accumulation and the
+max-normalisation, through the C ABI. `value` times steps with inputs already resident in
+HBM (CUDA events, L2 flushed between steps); `e2e` times the same call from pinned host
+buffers with the copies in and the map copy out inside the timed region.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl gazemap|reference] [--workload ...]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload (weak scaling:
+the path shards by sample or by session with no data-path exchange); timing is the max over
+ranks. `--impl reference` times the FP64 CPU oracle on this host's cores on a bounded sample
+of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sample×fixation pairs/s at ≤1e-4 rel err"
+FP32_INSTR_PER_PAIR = 18          # algorithmic FP32 work of the cone test per pair
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gazemap", "reference"], default="gazemap")
+    ap.add_argument("--workload", choices=["paper_scene", "tiny_sphere"], default="paper_scene")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    import synth
+    return synth.paper_scene() if name == "paper_scene" else synth.tiny_sphere()
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 10:
+                    continue
+                if self.uuid and self.uuid not in p[1]:
+                    continue
+                rows.append(p)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[6:10]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------------------------
+def oracle_sample_run(w, n_samples, nthreads):
+    """The oracle as it stands: world triangles, areas and counts for the whole scene, then
+    the sample positions and brute-force accumulation of `n_samples` evenly strided samples
+    over every fixation. Returns (seconds, pairs)."""
+    import oracle
+    t0 = time.perf_counter()
+    tri = oracle.world_triangles(w)
+    off = oracle.tri_offsets(oracle.areas(tri), oracle.tri_density(w))
+    n = int(off[-1])
+    which = np.unique(np.linspace(0, n - 1, max(1, min(n_samples, n))).astype(np.int64))
+    s = oracle.samples(tri, off, w.seed, w.session, which)
+    oracle.accumulate(tri, s.xyz, s.tri, w.fixations, w.params, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return dt, len(which) * w.fixations.n
+
+
+def calibrated_oracle(w, target_s, nthreads):
+    dt, _ = oracle_sample_run(w, 8, nthreads)
+    # scale the sample count so one run takes about target_s seconds
+    n = int(max(8, min(20000, 8 * target_s / max(dt, 1e-3))))
+    dt, pairs = oracle_sample_run(w, n, nthreads)
+    return dt, pairs, n
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = make_workload(args.workload)
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    per_step = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    dt, _ = oracle_sample_run(w, 8, cores)
+    n = int(max(8, min(20000, 8 * per_step / max(dt, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_sample_run(w, n, cores)
+    tot_t, tot_p = 0.0, 0
+    for _ in range(args.steps):
+        dt, p = oracle_sample_run(w, n, cores)
+        tot_t += dt
+        tot_p += p
+    v = tot_p / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "fixations": w.fixations.n},
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} evenly strided samples x all {w.fixations.n} fixations per step, "
+                                       f"whole-scene transform/areas/counts included"},
+            "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2601_07571_gb300 import build as B
+    B.build()
+    import paper_2601_07571_gb300 as G
+    from paper_2601_07571_gb300 import pipeline
+
+    w = make_workload(args.workload)
+    ctx = G.gm_create(local)
+    stream = torch.cuda.current_stream()
+    dev_meshes = pipeline.mesh_args(w, to_device=True)
+    dev_fix = pipeline.fixation_args(w.fixations, to_device=True)
+    dens = [m.density for m in w.meshes]
+    prm = pipeline.params_of(w, flags=G.GM_F_TIMING, normalize=True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(meshes, fix):
+        sc = G.gm_build_scene(ctx, meshes, stream)
+        sm = G.gm_sample_surface(sc, dens, w.seed, w.session, stream)
+        mp = G.gm_accumulate_fixations(sc, sm, *fix, prm, stream)
+        return sc, sm, mp
+
+    def release(h):
+        sc, sm, mp = h
+        G.gm_map_free(mp)
+        G.gm_samples_free(sm)
+        G.gm_scene_free(sc)
+
+    for _ in range(args.warmup):
+        h = step(dev_meshes, dev_fix)
+        G.gm_map_info(h[2])
+        release(h)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    times, acc_ms, prep_ms, norm_ms, launches = [], [], [], [], 0
+    stats = None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = G.gm_ctx_launches(ctx)
+        e0.record(stream)
+        h = step(dev_meshes, dev_fix)
+        e1.record(stream)
+        launches += G.gm_ctx_launches(ctx) - l0
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        _, ns, stats, _ = G.gm_map_info(h[2])
+        acc_ms.append(stats["accumulate_ms"])
+        prep_ms.append(stats["prep_ms"])
+        norm_ms.append(stats["normalize_ms"])
+        release(h)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = sum(times) / len(times)
+    if dist:
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    pairs = stats["pairs"]
+    value = world * pairs / (step_ms * 1e-3)
+
+    # ---- end to end from pinned host buffers -------------------------------------------------
+    host_meshes = [(torch.from_numpy(np.ascontiguousarray(v)).pin_memory(),
+                    torch.from_numpy(np.ascontiguousarray(f).view(np.int32)).pin_memory(), xf, o)
+                   for v, f, xf, o in pipeline.mesh_args(w)]
+    host_fix = [torch.from_numpy(a).pin_memory() for a in pipeline.fixation_args(w.fixations)]
+    out = torch.empty(int(stats["pairs"] // max(1, stats["n_fixations_used"])) if stats["n_fixations_used"] else 1,
+                      dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() + f.numel() * f.element_size() for v, f, _, _ in host_meshes)
+    h2d += sum(a.numel() * a.element_size() for a in host_fix)
+    e2e_t = []
+    for i in range(args.warmup + max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = step(host_meshes, host_fix)
+        G.gm_map_copy(h[2], 0, out, stream)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_t.append(t1 - t0)
+        release(h)
+    e2e_s = statistics.mean(e2e_t)
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # ---- roofline of the dominant kernel (the fused accumulate) ------------------------------
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    acc = sum(acc_ms) / len(acc_ms)
+    achieved = FP32_INSTR_PER_PAIR * pairs / (acc * 1e-3) / 1e12
+    peak = n_sm * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s (FP32)", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_accumulate",
+            "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz",
+            "work_basis": f"{FP32_INSTR_PER_PAIR} FP32 instructions per sample x fixation pair (cone test)",
+            "kernel_ms": acc}
+    if clk and clk.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (n_sm * FP32_LANES_PER_SM * clk["sm_mhz"] * 1e6 / 1e12)
+
+    line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "triangles": w.n_tris, "samples": int(ns),
+                       "fixations": w.fixations.n, "pairs_per_step": int(pairs),
+                       "l2": "flushed between steps (256 MiB write)", "inputs": "device-resident",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "stages_ms": {"accumulate": acc, "fixation_prep": sum(prep_ms) / len(prep_ms),
+                          "normalize": sum(norm_ms) / len(norm_ms),
+                          "build_and_sample": step_ms - acc - sum(prep_ms) / len(prep_ms) - sum(norm_ms) / len(norm_ms)},
+            "in_cone_pairs": int(stats["in_cone"]), "visible_pairs": int(stats["visible"]),
+            "roofline": roof,
+            "e2e": {"value": world * pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(out.numel() * 4), "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        dt, p, n = calibrated_oracle(w, args.cpu_seconds, cores)
+        line["cpu_baseline"] = {"value": p / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{n} evenly strided samples x all {w.fixations.n} fixations, "
+                                          f"whole-scene transform/areas/counts included ({dt:.1f} s)"}
+    G.gm_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

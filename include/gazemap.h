@@ -1,0 +1,199 @@
+/*
+ * gazemap.h -- C ABI of libgazemap, a GB300 (sm_103a) implementation of surface-based
+ * fixation density maps (Javerliat & Lavoue, "GPU accelerated surface-based gaze mapping
+ * for XR experiences").
+ *
+ * The method (Section 3): sample mesh surfaces at a chosen density (samples per m^2); for
+ * every sample x fixation pair, keep the pair when the sample lies inside the gaze cone cut
+ * at 4 sigma and is visible from the eye, and add the duration-weighted angular Gaussian of
+ * Section 3.2.1 to the sample; finally divide every value by the maximum (Section 3.2.3).
+ *
+ * Conventions for every call:
+ *  - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream). All device work
+ *    is enqueued on it; calls return once the work is enqueued unless stated otherwise.
+ *  - Pointers marked "host or device" are classified with cudaPointerGetAttributes; host
+ *    memory is copied to the device inside the call (synchronously for pageable memory).
+ *    Input buffers are borrowed for the duration of the call only.
+ *  - Handles (gm_ctx, gm_scene, gm_samples, gm_map, gm_field) own their device memory and are
+ *    released by the matching gm_*_free / gm_destroy. A handle must outlive every handle built
+ *    from it (samples need their scene; maps need their samples).
+ *  - Errors: every call returns a gm_status; gm_last_error() returns a thread-local message
+ *    for the last failing call on this thread. Kernel-side faults detected by the library
+ *    (a BVH deeper than the traversal stack) are reported by the next gm_sync / info call.
+ *  - Nothing here falls back to the CPU: without a usable sm_103a device, gm_create fails.
+ */
+#ifndef GAZEMAP_H
+#define GAZEMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gm_ctx gm_ctx;
+typedef struct gm_scene gm_scene;
+typedef struct gm_samples gm_samples;
+typedef struct gm_map gm_map;
+typedef struct gm_field gm_field;
+typedef void* gm_stream; /* cudaStream_t */
+
+typedef enum {
+    GM_OK = 0,
+    GM_ERR_INVALID_ARG = 1,  /* bad pointer, size, NaN/Inf input, theta <= 0, ... */
+    GM_ERR_CUDA = 2,         /* a CUDA runtime call failed (message has the CUDA error) */
+    GM_ERR_OOM = 3,          /* device allocation failed */
+    GM_ERR_TIMEOUT = 4,      /* a bounded device wait ran out */
+    GM_ERR_UNSUPPORTED = 5,  /* no sm_103a device, or a size beyond a documented limit */
+    GM_ERR_INTERNAL = 6,     /* a device-side consistency check failed */
+    GM_WARN_EMPTY = 100      /* success, but a map's maximum is 0 (all values 0) */
+} gm_status;
+
+/* One mesh of the scene. Section 3.3.4: the sampling density may differ per mesh. */
+typedef struct {
+    const float* vertices;     /* n_verts x 3 FP32, mesh-local (host or device) */
+    const uint32_t* indices;   /* n_tris x 3 vertex indices (host or device) */
+    uint32_t n_verts;
+    uint32_t n_tris;
+    double transform[16];      /* row-major 4x4 local -> world (metres), applied in FP64 */
+    uint32_t object_id;        /* reported per sample (Section 3.3.3 export format) */
+} gm_mesh_desc;
+
+/* Fixations, structure of arrays (host or device). */
+typedef struct {
+    const float* eye_xyz;      /* n x 3, world-space eye position */
+    const float* gaze_xyz;     /* n x 3, gaze direction (any non-zero length) */
+    const float* duration_s;   /* n, fixation duration t in seconds (weights g, Section 3.2.1) */
+    const double* timestamp_s; /* n, fixation start time (windowing, Section 3.3.4) */
+    uint32_t n;
+} gm_fixations;
+
+/* Generation parameters (Section 3.3.4 lists theta, per-mesh density and the time interval). */
+typedef struct {
+    float theta_rad;      /* angular deviation theta = one standard deviation (> 0) */
+    float cutoff_sigmas;  /* cone cut-off in sigmas; 4 in the paper (Fig. 4, Section 3.3.2) */
+    float eps_rel;        /* occlusion segment stops (1 - eps_rel) of the way to the sample */
+    double t_begin;       /* fixations with t_begin <= timestamp < t_end are used */
+    double t_end;
+    double window_s;      /* > 0: one map per window of this length from t_begin; else one map */
+    int32_t normalize;    /* non-zero: divide each map by its maximum in place (Section 3.2.3) */
+    int32_t flags;        /* GM_F_* below */
+    uint64_t debug_pair_cap; /* > 0 with GM_F_DEBUG_PAIRS: record up to this many in-cone pairs */
+} gm_params;
+
+enum {
+    GM_F_TIMING = 1,        /* record CUDA events around each stage (gm_map_stats.*_ms) */
+    GM_F_DEBUG_PAIRS = 2,   /* record in-cone pairs (sample, fixation, visible, weight) */
+    GM_F_NO_REORDER = 4     /* process samples in stored order (no spatial work order) */
+};
+
+typedef struct {
+    uint64_t pairs;           /* nominal sample x fixation pairs (valid fixations only) */
+    uint64_t in_cone;         /* pairs inside the cut-off cone = occlusion rays traced */
+    uint64_t visible;         /* in-cone pairs whose ray reached the sample */
+    uint32_t n_windows;
+    uint32_t n_fixations_used;
+    float prep_ms;            /* fixation prep + window sort (GM_F_TIMING) */
+    float accumulate_ms;      /* cone + occlusion + Gaussian + store + max kernel */
+    float normalize_ms;
+    uint32_t launches;        /* kernels this call launched */
+} gm_map_stats;
+
+/* ---- context ------------------------------------------------------------------------ */
+
+/* Bind `device` (must be compute capability 10.3) and create a context. */
+gm_status gm_create(int device, gm_ctx** out);
+void gm_destroy(gm_ctx* ctx);
+const char* gm_last_error(void);
+/* Wait for `stream`, then report any device-side fault recorded by library kernels. */
+gm_status gm_sync(gm_ctx* ctx, gm_stream stream);
+/* Number of kernels this context has launched so far (every library launch site counts). */
+gm_status gm_ctx_launches(const gm_ctx* ctx, uint64_t* kernel_launches);
+
+/* ---- scene (meshes -> world triangles -> BVH) ----------------------------------------- */
+
+/* Transform every mesh to world space (FP64, rounded to FP32), then build a linear BVH over
+ * all triangles (Morton codes of centroids, LSD radix sort, Karras' HPG 2012 hierarchy,
+ * bottom-up box refit). The BVH replaces the per-view z-buffer of Section 3.2.2 as the
+ * occlusion structure. Meshes are concatenated in order; global triangle ids follow that
+ * order. Synchronises `stream` once (to check the tree depth). */
+gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes,
+                         gm_stream stream, gm_scene** out);
+gm_status gm_scene_info(const gm_scene* scene, uint32_t* n_tris, uint32_t* bvh_depth);
+/* Copy the world triangles (n_tris x 9 FP32, v0 v1 v2) to `dst` (host or device). */
+gm_status gm_scene_triangles(const gm_scene* scene, float* dst, gm_stream stream);
+void gm_scene_free(gm_scene* scene);
+
+/* ---- samples (Section 3.1) ----------------------------------------------------------- */
+
+/* Area-weighted surface sampling. Triangle i of mesh m gets count_i samples with
+ * |count_i - k_m A_i| < 1 (A_i its FP64 world area): counts are differences of the rounded
+ * running total of k_m A_i in 32.32 fixed point. Global sample j (mesh order, triangle order,
+ * then j) is placed from Philox4x32-10(key = seed, counter = (j lo, j hi, session, 0)) words
+ * w0, w1: u = ((w >> 9) + 1/2) 2^-23, barycentrics (1 - sqrt u1, sqrt u1 (1 - u2), sqrt u1 u2).
+ * density_per_mesh: n_meshes samples-per-m^2 values (host memory). Synchronises `stream`
+ * once (to read the sample count). Fails with GM_ERR_UNSUPPORTED beyond 2^31 - 1 samples. */
+gm_status gm_sample_surface(gm_scene* scene, const double* density_per_mesh, uint64_t seed,
+                            uint32_t session, gm_stream stream, gm_samples** out);
+/* Explicit query points (n x 3 FP32 world positions, each on triangle tri[i], which is
+ * excluded from its occlusion test), host or device. Used for GM_Q_PLAIN queries. */
+gm_status gm_samples_from_points(gm_scene* scene, const float* xyz, const uint32_t* tri,
+                                 uint64_t n, gm_stream stream, gm_samples** out);
+gm_status gm_samples_info(const gm_samples* s, uint64_t* n_samples);
+/* Copy the per-triangle start offsets (n_tris + 1 int64) to `dst` (host or device). */
+gm_status gm_samples_offsets(const gm_samples* s, int64_t* dst, gm_stream stream);
+/* Copy sample data in stored order; any destination may be NULL (host or device):
+ * xyz n x 3 FP32, tri n global triangle ids, bary2 n x 2 FP32 (b1, b2; b0 = 1 - b1 - b2),
+ * obj n object ids (Section 3.3.3 export fields). */
+gm_status gm_samples_copy(const gm_samples* s, float* xyz, uint32_t* tri, float* bary2,
+                          uint32_t* obj, gm_stream stream);
+void gm_samples_free(gm_samples* s);
+
+/* ---- accumulation (Section 3.2) -------------------------------------------------------- */
+
+/* For every sample s and every fixation f whose timestamp lies in [t_begin, t_end):
+ *   p = s - e_f, r^ = r_f/|r_f|, d1 = p.r^, d2 = |p x r^|, sigma = tan(theta);
+ *   the pair counts when d1 > 0, d2/d1 <= cutoff * sigma (the 4 sigma cone), and the segment
+ *   from e_f to e_f + (1 - eps_rel) p meets no triangle but the sample's own;
+ *   then value[window(f)][s] += t_f / (sigma sqrt(2 pi)) exp(-(d2/d1)^2 / (2 sigma^2)).
+ * Sums are compensated (Kahan) FP32 in fixation order. The maximum of each window's map is
+ * kept; with params->normalize the map is divided by it in place (max 0 => map stays 0 and
+ * the call returns GM_WARN_EMPTY at gm_map_info). */
+gm_status gm_accumulate_fixations(gm_scene* scene, gm_samples* samples, const gm_fixations* fix,
+                                  const gm_params* params, gm_stream stream, gm_map** out);
+/* Number of windows, samples and statistics; waits for the map's work to finish. */
+gm_status gm_map_info(gm_map* map, uint32_t* n_windows, uint64_t* n_samples, gm_map_stats* stats);
+/* Copy window `window` (n_samples FP32 values in stored sample order) to `dst` (host or
+ * device), and its maximum to *max_out (may be NULL). Values are normalised iff the map was
+ * accumulated with params->normalize. */
+gm_status gm_map_copy(const gm_map* map, uint32_t window, float* dst, float* max_out, gm_stream stream);
+/* Device pointer to the map values (n_windows x n_samples FP32, window-major), owned by map. */
+const float* gm_map_device_values(const gm_map* map);
+/* Recorded in-cone pairs (GM_F_DEBUG_PAIRS), in no particular order: sample index (stored
+ * order), fixation index (input order), visible flag, weight g. Host arrays of `cap`
+ * entries; *n returns how many pairs were found (may exceed cap). */
+gm_status gm_map_debug_pairs(const gm_map* map, uint32_t* sample, uint32_t* fix, uint8_t* visible,
+                             float* g, uint64_t cap, uint64_t* n);
+void gm_map_free(gm_map* map);
+
+/* ---- queries -------------------------------------------------------------------------- */
+
+typedef enum {
+    GM_Q_SAMPLE = 0,  /* gather: out[i] = map value of sample idx[i] (window `window`) */
+    GM_Q_PLAIN = 1,   /* evaluate the plain accumulation at explicit points (see below) */
+    GM_Q_FIELD = 2    /* evaluate a trained neural density field at explicit points */
+} gm_query_mode;
+
+/* GM_Q_SAMPLE: `map` and `sample_idx` (n indices, host or device) are used.
+ * GM_Q_PLAIN: unused here; build points with gm_samples_from_points and accumulate them.
+ * GM_Q_FIELD: `field` and `xyz` (n x 3 FP32 world points, host or device) are used.
+ * out: n FP32 values (host or device). */
+gm_status gm_query_density(const gm_map* map, const gm_field* field, gm_query_mode mode,
+                           uint32_t window, const uint32_t* sample_idx, const float* xyz,
+                           uint64_t n, float* out, gm_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GAZEMAP_H */

@@ -1,0 +1,661 @@
+// gm_accum.cu -- gm_accumulate_fixations: Section 3.2 of the paper on one GPU.
+//
+// Per fixation (prep kernel): r^ = r / |r|, weight t / (sigma sqrt(2 pi)), window id
+// floor((ts - t_begin) / window_s); fixations outside [t_begin, t_end) are dropped and the
+// rest are stably sorted by window (radix sort on the window id), so every window is one
+// contiguous run of the fixation list.
+//
+// Accumulation (one fused kernel, sample-stationary): every thread owns SPT samples taken in
+// spatial (Morton) work order and keeps their compensated FP32 sums in registers. The block
+// streams the fixation list through shared memory in tiles; for each fixation every thread
+// runs the 4-sigma cone test on its samples (p = s - e, d1 = p.r^, c = p x r^,
+// in-cone <=> d1 > 0 and |c|^2 <= (cutoff tan theta)^2 d1^2, about 20 FP32 instructions per
+// pair) and, for in-cone pairs only, traces the occlusion segment e -> e + (1 - eps) p through
+// the BVH (any-hit, early exit, the sample's own triangle skipped) with the watertight
+// ray/triangle test of Woop, Benthin and Wald (JCGT 2013). A visible pair adds
+// g = w exp(-(|c|/d1)^2 / (2 tan^2 theta)), i.e. the paper's t/(sigma sqrt(2 pi)) *
+// exp(-sigma_k^2 / (2 sigma^2)) with sigma_k = d2 / d1, d2 = |c|, in fixation order (Kahan).
+// When the window id of the next fixation changes (block-uniform), the block stores its sums
+// for the finished window and folds its maximum into that window's max with one atomicMax on
+// the float's bit pattern (values are >= 0) -- the paper keeps this running maximum under a
+// mutex (Section 3.3.1); here no lock is needed.
+// Normalisation (Section 3.2.3) is a separate streaming kernel: v / max per window.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gm_internal.cuh"
+
+namespace {
+
+constexpr int ACC_THREADS = 256;
+constexpr int SPT = 4;            // samples per thread
+constexpr int FIX_TILE = 256;     // fixations per shared-memory tile (8 KB)
+constexpr int STACK = 64;         // traversal stack entries (BVH depth is checked at build)
+
+struct AccParams {
+    float C2;     // log2(e) / (2 tan^2 theta)
+    float K;      // (cutoff tan theta)^2
+    float tmax;   // 1 - eps_rel
+    uint32_t ns;
+    uint32_t W;
+    uint32_t nt;
+    uint64_t dbg_cap;
+};
+
+struct DebugOut {
+    uint32_t* sample;
+    uint32_t* fix;
+    uint8_t* vis;
+    float* g;
+    const uint32_t* fix_orig;
+};
+
+// ------------------------------------------------------------------------------------------
+// fixation prep
+// ------------------------------------------------------------------------------------------
+__global__ void k_fix_keys(const double* __restrict__ ts, const float* __restrict__ eye,
+                           const float* __restrict__ gaze, const float* __restrict__ dur, uint32_t nf,
+                           double t_begin, double t_end, double window_s, uint32_t W,
+                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                           uint32_t* __restrict__ n_valid, int* __restrict__ err) {
+    uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    double t = ts[f];
+    uint32_t key = W;
+    if (t >= t_begin && t < t_end) {
+        // the window bucket of a FP64 timestamp (one division per fixation)
+        double w = window_s > 0.0 ? floor((t - t_begin) / window_s) : 0.0;
+        if (w >= 0.0 && w < (double)W) key = (uint32_t)w;
+    }
+    float gx = gaze[3 * f], gy = gaze[3 * f + 1], gz = gaze[3 * f + 2];
+    float ex = eye[3 * f], ey = eye[3 * f + 1], ez = eye[3 * f + 2];
+    float d = dur[f];
+    bool finite = isfinite(gx) && isfinite(gy) && isfinite(gz) && isfinite(ex) && isfinite(ey) && isfinite(ez) &&
+                  isfinite(d) && (gx != 0.f || gy != 0.f || gz != 0.f);
+    if (!finite || !(d >= 0.f) || isnan(t)) {
+        atomicCAS(err, 0, 3);
+        key = W;
+    }
+    keys[f] = key;
+    vals[f] = f;
+    if (key < W) atomicAdd(n_valid, 1u);
+}
+
+__global__ void k_fix_pack(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                           const float* __restrict__ eye, const float* __restrict__ gaze,
+                           const float* __restrict__ dur, uint32_t nf, float wnorm,
+                           float4* __restrict__ packed, uint32_t* __restrict__ orig) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    uint32_t f = vals[i];
+    float rx = gaze[3 * f], ry = gaze[3 * f + 1], rz = gaze[3 * f + 2];
+    float rn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(rx, rx), __fmul_rn(ry, ry)), __fmul_rn(rz, rz)));
+    rx = __fdiv_rn(rx, rn);
+    ry = __fdiv_rn(ry, rn);
+    rz = __fdiv_rn(rz, rn);
+    packed[2 * i + 0] = make_float4(eye[3 * f], eye[3 * f + 1], eye[3 * f + 2], __fmul_rn(dur[f], wnorm));
+    packed[2 * i + 1] = make_float4(rx, ry, rz, __uint_as_float(keys[i]));
+    orig[i] = f;
+}
+
+// ------------------------------------------------------------------------------------------
+// occlusion: BVH any-hit with a watertight segment/triangle test
+// ------------------------------------------------------------------------------------------
+struct Ray {
+    float3 o, d;
+    float3 idir, oidir;   // slab test: t = lo * idir - o * idir
+    float tmax, tmax_box;
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ float comp(const float3& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+__device__ __forceinline__ void make_ray(Ray& R, float3 o, float3 d, float tmax) {
+    R.o = o;
+    R.d = d;
+    R.tmax = tmax;
+    R.tmax_box = tmax * 1.0001f;
+    const float tiny = 1e-20f;
+    float dx = fabsf(d.x) < tiny ? copysignf(tiny, d.x) : d.x;
+    float dy = fabsf(d.y) < tiny ? copysignf(tiny, d.y) : d.y;
+    float dz = fabsf(d.z) < tiny ? copysignf(tiny, d.z) : d.z;
+    R.idir = make_float3(1.f / dx, 1.f / dy, 1.f / dz);
+    R.oidir = make_float3(o.x * R.idir.x, o.y * R.idir.y, o.z * R.idir.z);
+    float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    if (comp(d, kz) < 0.f) {
+        int t = kx;
+        kx = ky;
+        ky = t;
+    }
+    R.kx = kx;
+    R.ky = ky;
+    R.kz = kz;
+    float dkz = comp(d, kz);
+    R.Sx = comp(d, kx) / dkz;
+    R.Sy = comp(d, ky) / dkz;
+    R.Sz = 1.0f / dkz;
+}
+
+__device__ __forceinline__ bool slab(const Ray& R, float lx, float ly, float lz, float hx, float hy, float hz) {
+    float t0x = fmaf(lx, R.idir.x, -R.oidir.x), t1x = fmaf(hx, R.idir.x, -R.oidir.x);
+    float t0y = fmaf(ly, R.idir.y, -R.oidir.y), t1y = fmaf(hy, R.idir.y, -R.oidir.y);
+    float t0z = fmaf(lz, R.idir.z, -R.oidir.z), t1z = fmaf(hz, R.idir.z, -R.oidir.z);
+    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.f));
+    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), R.tmax_box));
+    return tn <= tf;
+}
+
+// Woop, Benthin, Wald, "Watertight ray/triangle intersection", JCGT 2(1), 2013. Edge functions
+// are evaluated without fused multiply-add so that a shared edge gives exactly opposite values
+// in its two triangles (no ray slips between them).
+__device__ __forceinline__ bool tri_hit(const Ray& R, float4 a, float4 b, float4 c) {
+    float3 A = make_float3(a.x - R.o.x, a.y - R.o.y, a.z - R.o.z);
+    float3 B = make_float3(b.x - R.o.x, b.y - R.o.y, b.z - R.o.z);
+    float3 C = make_float3(c.x - R.o.x, c.y - R.o.y, c.z - R.o.z);
+    float Akz = comp(A, R.kz), Bkz = comp(B, R.kz), Ckz = comp(C, R.kz);
+    float Ax = __fsub_rn(comp(A, R.kx), __fmul_rn(R.Sx, Akz));
+    float Ay = __fsub_rn(comp(A, R.ky), __fmul_rn(R.Sy, Akz));
+    float Bx = __fsub_rn(comp(B, R.kx), __fmul_rn(R.Sx, Bkz));
+    float By = __fsub_rn(comp(B, R.ky), __fmul_rn(R.Sy, Bkz));
+    float Cx = __fsub_rn(comp(C, R.kx), __fmul_rn(R.Sx, Ckz));
+    float Cy = __fsub_rn(comp(C, R.ky), __fmul_rn(R.Sy, Ckz));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return false;
+    float det = U + V + W;
+    if (det == 0.f) return false;
+    float T = U * (R.Sz * Akz) + V * (R.Sz * Bkz) + W * (R.Sz * Ckz);
+    return det > 0.f ? (T > 0.f && T < R.tmax * det) : (T < 0.f && T > R.tmax * det);
+}
+
+__device__ __forceinline__ bool leaf_hit(const Ray& R, const float4* __restrict__ tris, int slot, uint32_t own) {
+    float4 a = __ldg(&tris[3 * slot]);
+    if (__float_as_uint(a.w) == own) return false;
+    return tri_hit(R, a, __ldg(&tris[3 * slot + 1]), __ldg(&tris[3 * slot + 2]));
+}
+
+__device__ bool occluded(const Ray& R, uint32_t own, const float4* __restrict__ nodes,
+                         const float4* __restrict__ tris, uint32_t nt, int* __restrict__ err) {
+    if (nt < 2) return nt == 1 ? leaf_hit(R, tris, 0, own) : false;
+    int stack[STACK];
+    int sp = 0;
+    int node = 0;
+    for (;;) {
+        float4 n0 = __ldg(&nodes[4 * node + 0]);
+        float4 n1 = __ldg(&nodes[4 * node + 1]);
+        float4 n2 = __ldg(&nodes[4 * node + 2]);
+        float4 n3 = __ldg(&nodes[4 * node + 3]);
+        bool hl = slab(R, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
+        bool hr = slab(R, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
+        int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
+        if (hl && cl < 0) {
+            if (leaf_hit(R, tris, ~cl, own)) return true;
+            hl = false;
+        }
+        if (hr && cr < 0) {
+            if (leaf_hit(R, tris, ~cr, own)) return true;
+            hr = false;
+        }
+        if (hl && hr) {
+            if (sp >= STACK) {
+                atomicCAS(err, 0, GM_DEV_STACK_OVERFLOW);
+                return true;
+            }
+            stack[sp++] = cr;
+            node = cl;
+        } else if (hl) {
+            node = cl;
+        } else if (hr) {
+            node = cr;
+        } else {
+            if (sp == 0) return false;
+            node = stack[--sp];
+        }
+    }
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <bool DEBUG>
+__global__ void __launch_bounds__(ACC_THREADS) k_accumulate(
+    const float4* __restrict__ spos, const uint32_t* __restrict__ sidx, const float4* __restrict__ fix,
+    const uint32_t* __restrict__ n_fix_dev, const float4* __restrict__ nodes, const float4* __restrict__ tris,
+    AccParams P, float* __restrict__ out, unsigned int* __restrict__ max_bits,
+    unsigned long long* __restrict__ counters, int* __restrict__ err, DebugOut dbg) {
+    __shared__ float4 sfix[2 * FIX_TILE];
+    __shared__ float wmax[ACC_THREADS / 32];
+
+    const uint32_t nf = *n_fix_dev;
+    const uint32_t base = blockIdx.x * (uint32_t)(ACC_THREADS * SPT) + threadIdx.x;
+
+    float sx[SPT], sy[SPT], sz[SPT], sum[SPT], cmp[SPT];
+    uint32_t own[SPT];
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+        uint32_t j = base + k * ACC_THREADS;
+        // padding lanes hold NaN positions: every cone test on them is false
+        float4 p = j < P.ns ? spos[j] : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, __uint_as_float(0xffffffffu));
+        sx[k] = p.x;
+        sy[k] = p.y;
+        sz[k] = p.z;
+        own[k] = __float_as_uint(p.w);
+        sum[k] = 0.f;
+        cmp[k] = 0.f;
+    }
+    unsigned long long n_in = 0, n_vis = 0;
+    uint32_t cur = 0xffffffffu;
+
+    auto flush = [&](uint32_t w) {
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+            uint32_t j = base + k * ACC_THREADS;
+            if (j < P.ns && (P.W == 1 || sum[k] != 0.f)) out[(size_t)w * P.ns + sidx[j]] = sum[k];
+            m = fmaxf(m, sum[k]);
+            sum[k] = 0.f;
+            cmp[k] = 0.f;
+        }
+        m = warp_max(m);
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            float v = threadIdx.x < ACC_THREADS / 32 ? wmax[threadIdx.x] : 0.f;
+            v = warp_max(v);
+            if (threadIdx.x == 0 && v > 0.f) atomicMax(&max_bits[w], __float_as_uint(v));
+        }
+        __syncthreads();
+    };
+
+    for (uint32_t t0 = 0; t0 < nf; t0 += FIX_TILE) {
+        const uint32_t cnt = min((uint32_t)FIX_TILE, nf - t0);
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < 2 * cnt; i += ACC_THREADS) sfix[i] = fix[2 * t0 + i];
+        __syncthreads();
+        for (uint32_t i = 0; i < cnt; ++i) {
+            const float4 F0 = sfix[2 * i], F1 = sfix[2 * i + 1];
+            const uint32_t win = __float_as_uint(F1.w);
+            if (win != cur) {
+                if (cur != 0xffffffffu) flush(cur);
+                cur = win;
+            }
+#pragma unroll
+            for (int k = 0; k < SPT; ++k) {
+                const float px = sx[k] - F0.x, py = sy[k] - F0.y, pz = sz[k] - F0.z;
+                const float d1 = fmaf(px, F1.x, fmaf(py, F1.y, pz * F1.z));
+                const float cx = fmaf(py, F1.z, -pz * F1.y);
+                const float cy = fmaf(pz, F1.x, -px * F1.z);
+                const float cz = fmaf(px, F1.y, -py * F1.x);
+                const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+                const float d1s = d1 * d1;
+                if (d1 > 0.f && c2 <= P.K * d1s) {
+                    ++n_in;
+                    Ray R;
+                    make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(px, py, pz), P.tmax);
+                    const bool vis = !occluded(R, own[k], nodes, tris, P.nt, err);
+                    const float g = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
+                    if (vis) {
+                        ++n_vis;
+                        const float y = g - cmp[k];
+                        const float t = sum[k] + y;
+                        cmp[k] = (t - sum[k]) - y;
+                        sum[k] = t;
+                    }
+                    if (DEBUG) {
+                        unsigned long long slot = atomicAdd(&counters[2], 1ull);
+                        if (slot < P.dbg_cap) {
+                            dbg.sample[slot] = sidx[base + k * ACC_THREADS];
+                            dbg.fix[slot] = dbg.fix_orig[t0 + i];
+                            dbg.vis[slot] = vis ? 1 : 0;
+                            dbg.g[slot] = g;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (cur != 0xffffffffu) flush(cur);
+    else if (P.W == 1) flush(0);   // no fixation at all: window 0 is written as zeros
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n_in += __shfl_xor_sync(0xffffffffu, n_in, o);
+        n_vis += __shfl_xor_sync(0xffffffffu, n_vis, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (n_in | n_vis)) {
+        atomicAdd(&counters[0], n_in);
+        atomicAdd(&counters[1], n_vis);
+    }
+}
+
+__global__ void k_normalize(float* __restrict__ v, uint64_t ns, uint32_t W, const unsigned int* __restrict__ max_bits) {
+    const uint64_t total = ns * W;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        float m = __uint_as_float(max_bits[i / ns]);
+        v[i] = m > 0.f ? __fdiv_rn(v[i], m) : 0.f;
+    }
+}
+
+__global__ void k_iota(uint32_t* p, uint32_t n) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = i;
+}
+
+__global__ void k_gather_values(const float* __restrict__ v, uint64_t ns, uint32_t w, const uint32_t* __restrict__ idx,
+                                uint64_t n, float* __restrict__ out, int* __restrict__ err) {
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t j = idx[i];
+    if (j >= ns) {
+        atomicCAS(err, 0, GM_DEV_BAD_INDEX);
+        out[i] = 0.f;
+        return;
+    }
+    out[i] = v[(size_t)w * ns + j];
+}
+
+}  // namespace
+
+extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const gm_fixations* fx,
+                                             const gm_params* prm, gm_stream stream, gm_map** out) {
+    if (!sc || !sm || !fx || !prm || !out) return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: null argument");
+    *out = nullptr;
+    if (sm->scene != sc) return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: samples belong to another scene");
+    if (!(prm->theta_rad > 0.f) || !(prm->theta_rad < 1.5f))
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: theta must be in (0, 1.5) rad");
+    if (!(prm->cutoff_sigmas > 0.f) || !std::isfinite(prm->cutoff_sigmas))
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: cutoff must be > 0");
+    if (!(prm->eps_rel >= 0.f && prm->eps_rel < 1.f))
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: eps_rel must be in [0, 1)");
+    if (std::isnan(prm->t_begin) || std::isnan(prm->t_end) || !(prm->t_begin < prm->t_end))
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: need t_begin < t_end");
+    if (fx->n > 0 && (!fx->eye_xyz || !fx->gaze_xyz || !fx->duration_s || !fx->timestamp_s))
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: null fixation array");
+    uint64_t W = 1;
+    if (prm->window_s > 0.0) {
+        if (!std::isfinite(prm->t_begin) || !std::isfinite(prm->t_end) || !std::isfinite(prm->window_s))
+            return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: windows need a finite interval");
+        W = (uint64_t)std::ceil((prm->t_end - prm->t_begin) / prm->window_s);
+        if (W == 0) W = 1;
+        if (W > (1u << 24)) return gm_set_error(GM_ERR_UNSUPPORTED, "gm_accumulate_fixations: more than 2^24 windows");
+    }
+    const bool debug = (prm->flags & GM_F_DEBUG_PAIRS) && prm->debug_pair_cap > 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    gm_ctx* ctx = sc->ctx;
+    GM_TRY_CUDA(cudaSetDevice(ctx->device));
+    const uint64_t ns = sm->n;
+    const uint32_t nf = fx->n;
+
+    gm_map* mp = new gm_map();
+    mp->ctx = ctx;
+    mp->W = (uint32_t)W;
+    mp->ns = ns;
+    mp->stream = s;
+    mp->timing = (prm->flags & GM_F_TIMING) != 0;
+    mp->stats.n_windows = (uint32_t)W;
+    std::vector<void*> tmp;
+    auto fail = [&](gm_status st) {
+        for (void* p : tmp) cudaFreeAsync(p, s);
+        gm_map_free(mp);
+        return st;
+    };
+    gm_status st;
+#define TMP_ALLOC(ptr, bytes)                                                          \
+    do {                                                                               \
+        if ((st = gm_alloc((void**)&(ptr), (bytes), s)) != GM_OK) return fail(st);     \
+        tmp.push_back((void*)(ptr));                                                   \
+    } while (0)
+#define MAP_ALLOC(ptr, bytes) \
+    if ((st = gm_alloc((void**)&(ptr), (bytes), s)) != GM_OK) return fail(st)
+
+    if (mp->timing) {
+        for (int i = 0; i < 4; ++i) {
+            cudaError_t e = cudaEventCreate(&mp->ev[i]);
+            if (e != cudaSuccess) return fail(gm_cuda_error(e, "cudaEventCreate"));
+        }
+        cudaEventRecord(mp->ev[0], s);
+    }
+    MAP_ALLOC(mp->values, sizeof(float) * W * ns);
+    MAP_ALLOC(mp->max_bits, sizeof(unsigned int) * W);
+    MAP_ALLOC(mp->counters, sizeof(unsigned long long) * 4);
+    GM_TRY_CUDA(cudaMemsetAsync(mp->max_bits, 0, sizeof(unsigned int) * W, s));
+    GM_TRY_CUDA(cudaMemsetAsync(mp->counters, 0, sizeof(unsigned long long) * 4, s));
+    if (W > 1) GM_TRY_CUDA(cudaMemsetAsync(mp->values, 0, sizeof(float) * W * ns, s));
+    if (debug) {
+        mp->dbg_cap = prm->debug_pair_cap;
+        MAP_ALLOC(mp->dbg_sample, sizeof(uint32_t) * mp->dbg_cap);
+        MAP_ALLOC(mp->dbg_fix, sizeof(uint32_t) * mp->dbg_cap);
+        MAP_ALLOC(mp->dbg_vis, mp->dbg_cap);
+        MAP_ALLOC(mp->dbg_g, sizeof(float) * mp->dbg_cap);
+    }
+    int launches = 0;
+
+    // ---- fixation prep --------------------------------------------------------------------
+    void *d_eye = nullptr, *d_gaze = nullptr, *d_dur = nullptr, *d_ts = nullptr;
+    bool o1, o2, o3, o4;
+    if ((st = gm_stage_to_device(fx->eye_xyz, sizeof(float) * 3 * (size_t)nf, s, &d_eye, &o1)) != GM_OK) return fail(st);
+    if (o1) tmp.push_back(d_eye);
+    if ((st = gm_stage_to_device(fx->gaze_xyz, sizeof(float) * 3 * (size_t)nf, s, &d_gaze, &o2)) != GM_OK) return fail(st);
+    if (o2) tmp.push_back(d_gaze);
+    if ((st = gm_stage_to_device(fx->duration_s, sizeof(float) * (size_t)nf, s, &d_dur, &o3)) != GM_OK) return fail(st);
+    if (o3) tmp.push_back(d_dur);
+    if ((st = gm_stage_to_device(fx->timestamp_s, sizeof(double) * (size_t)nf, s, &d_ts, &o4)) != GM_OK) return fail(st);
+    if (o4) tmp.push_back(d_ts);
+    uint32_t *keys = nullptr, *vals = nullptr, *n_valid = nullptr, *orig = nullptr;
+    float4* packed = nullptr;
+    TMP_ALLOC(keys, sizeof(uint32_t) * (nf ? nf : 1));
+    TMP_ALLOC(vals, sizeof(uint32_t) * (nf ? nf : 1));
+    TMP_ALLOC(orig, sizeof(uint32_t) * (nf ? nf : 1));
+    TMP_ALLOC(packed, sizeof(float4) * 2 * (nf ? nf : 1));
+    MAP_ALLOC(n_valid, sizeof(uint32_t));
+    tmp.push_back(n_valid);
+    GM_TRY_CUDA(cudaMemsetAsync(n_valid, 0, sizeof(uint32_t), s));
+    const double tan_t = std::tan((double)prm->theta_rad);
+    const float wnorm = (float)(1.0 / (tan_t * std::sqrt(2.0 * 3.14159265358979323846)));
+    if (nf > 0) {
+        k_fix_keys<<<gm_div_up(nf, 256), 256, 0, s>>>((const double*)d_ts, (const float*)d_eye, (const float*)d_gaze,
+                                                      (const float*)d_dur, nf, prm->t_begin, prm->t_end,
+                                                      prm->window_s > 0.0 ? prm->window_s : 0.0, (uint32_t)W, keys, vals,
+                                                      n_valid, ctx->dev_err);
+        ++launches;
+        int bits = 1;
+        while (bits < 32 && (1ull << bits) <= W) ++bits;
+        if ((st = gm_radix_sort_u32(keys, vals, nf, bits, s, &launches)) != GM_OK) return fail(st);
+        k_fix_pack<<<gm_div_up(nf, 256), 256, 0, s>>>(keys, vals, (const float*)d_eye, (const float*)d_gaze,
+                                                      (const float*)d_dur, nf, wnorm, packed, orig);
+        ++launches;
+    }
+    if (mp->timing) cudaEventRecord(mp->ev[1], s);
+
+    // ---- accumulate -----------------------------------------------------------------------
+    AccParams P;
+    P.C2 = (float)(1.4426950408889634 / (2.0 * tan_t * tan_t));
+    P.K = (float)((double)prm->cutoff_sigmas * tan_t * (double)prm->cutoff_sigmas * tan_t);
+    P.tmax = 1.0f - prm->eps_rel;
+    P.ns = (uint32_t)ns;
+    P.W = (uint32_t)W;
+    P.nt = sc->n_tris;
+    P.dbg_cap = mp->dbg_cap;
+    DebugOut dbg{mp->dbg_sample, mp->dbg_fix, mp->dbg_vis, mp->dbg_g, orig};
+    const bool reorder = !(prm->flags & GM_F_NO_REORDER) && sm->work_pos;
+    uint32_t* ident = nullptr;
+    const float4* spos = reorder ? sm->work_pos : sm->pos;
+    const uint32_t* sidx = reorder ? sm->work_idx : nullptr;
+    if (!sidx) TMP_ALLOC(ident, sizeof(uint32_t) * (ns ? ns : 1));
+    if (ns > 0) {
+        if (!sidx) {
+            k_iota<<<gm_div_up(ns, 256), 256, 0, s>>>(ident, (uint32_t)ns);
+            ++launches;
+            sidx = ident;
+        }
+        const uint32_t grid = gm_div_up(ns, (uint64_t)ACC_THREADS * SPT);
+        if (debug)
+            k_accumulate<true><<<grid, ACC_THREADS, 0, s>>>(spos, sidx, packed, n_valid, sc->nodes, sc->bvh_tris, P,
+                                                            mp->values, mp->max_bits, mp->counters, ctx->dev_err, dbg);
+        else
+            k_accumulate<false><<<grid, ACC_THREADS, 0, s>>>(spos, sidx, packed, n_valid, sc->nodes, sc->bvh_tris, P,
+                                                             mp->values, mp->max_bits, mp->counters, ctx->dev_err, dbg);
+        ++launches;
+    }
+    if (mp->timing) cudaEventRecord(mp->ev[2], s);
+    if (prm->normalize && ns > 0) {
+        uint64_t total = ns * W;
+        uint32_t grid = (uint32_t)std::min<uint64_t>(gm_div_up(total, 256), (uint64_t)ctx->n_sm * 16);
+        k_normalize<<<grid, 256, 0, s>>>(mp->values, ns, (uint32_t)W, mp->max_bits);
+        ++launches;
+    }
+    if (mp->timing) cudaEventRecord(mp->ev[3], s);
+    // keep the valid-fixation count with the map for gm_map_info
+    GM_TRY_CUDA(cudaMemcpyAsync(&mp->counters[3], n_valid, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_accumulate_fixations launch"));
+    for (void* p : tmp) cudaFreeAsync(p, s);
+    mp->stats.launches = (uint32_t)launches;
+    ctx->launches += launches;
+    *out = mp;
+    return GM_OK;
+#undef TMP_ALLOC
+#undef MAP_ALLOC
+}
+
+extern "C" gm_status gm_map_info(gm_map* mp, uint32_t* n_windows, uint64_t* n_samples, gm_map_stats* stats) {
+    if (!mp) return gm_set_error(GM_ERR_INVALID_ARG, "gm_map_info: null map");
+    GM_TRY_CUDA(cudaStreamSynchronize(mp->stream));
+    int err = 0;
+    unsigned long long c[4] = {0, 0, 0, 0};
+    GM_TRY_CUDA(cudaMemcpy(&err, mp->ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    GM_TRY_CUDA(cudaMemcpy(c, mp->counters, sizeof(c), cudaMemcpyDeviceToHost));
+    if (err) {
+        cudaMemset(mp->ctx->dev_err, 0, sizeof(int));
+        if (err == 3) return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: non-finite fixation, zero gaze or negative duration");
+        if (err == GM_DEV_STACK_OVERFLOW) return gm_set_error(GM_ERR_INTERNAL, "BVH traversal stack overflow");
+        return gm_set_error(GM_ERR_INTERNAL, "device consistency check failed (" + std::to_string(err) + ")");
+    }
+    uint32_t nvalid = (uint32_t)(c[3] & 0xffffffffu);
+    mp->stats.in_cone = c[0];
+    mp->stats.visible = c[1];
+    mp->stats.n_fixations_used = nvalid;
+    mp->stats.pairs = (uint64_t)nvalid * mp->ns;
+    if (mp->timing) {
+        float a = 0, b = 0, d = 0;
+        cudaEventElapsedTime(&a, mp->ev[0], mp->ev[1]);
+        cudaEventElapsedTime(&b, mp->ev[1], mp->ev[2]);
+        cudaEventElapsedTime(&d, mp->ev[2], mp->ev[3]);
+        mp->stats.prep_ms = a;
+        mp->stats.accumulate_ms = b;
+        mp->stats.normalize_ms = d;
+    }
+    if (n_windows) *n_windows = mp->W;
+    if (n_samples) *n_samples = mp->ns;
+    if (stats) *stats = mp->stats;
+    // any window whose maximum is 0 -> warning
+    std::vector<unsigned int> mx(mp->W);
+    GM_TRY_CUDA(cudaMemcpy(mx.data(), mp->max_bits, sizeof(unsigned int) * mp->W, cudaMemcpyDeviceToHost));
+    for (unsigned int m : mx)
+        if (m == 0) return GM_WARN_EMPTY;
+    return GM_OK;
+}
+
+extern "C" gm_status gm_map_copy(const gm_map* mp, uint32_t window, float* dst, float* max_out, gm_stream stream) {
+    if (!mp || !dst) return gm_set_error(GM_ERR_INVALID_ARG, "gm_map_copy: null argument");
+    if (window >= mp->W) return gm_set_error(GM_ERR_INVALID_ARG, "gm_map_copy: window out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    GM_TRY(gm_copy_out(dst, mp->values + (size_t)window * mp->ns, sizeof(float) * mp->ns, s));
+    if (max_out) {
+        unsigned int b = 0;
+        GM_TRY_CUDA(cudaMemcpyAsync(&b, mp->max_bits + window, sizeof(b), cudaMemcpyDeviceToHost, s));
+        GM_TRY_CUDA(cudaStreamSynchronize(s));
+        memcpy(max_out, &b, sizeof(float));
+    }
+    return GM_OK;
+}
+
+extern "C" const float* gm_map_device_values(const gm_map* mp) { return mp ? mp->values : nullptr; }
+
+extern "C" gm_status gm_map_debug_pairs(const gm_map* mp, uint32_t* sample, uint32_t* fix, uint8_t* vis, float* g,
+                                        uint64_t cap, uint64_t* n) {
+    if (!mp || !n) return gm_set_error(GM_ERR_INVALID_ARG, "gm_map_debug_pairs: null argument");
+    GM_TRY_CUDA(cudaStreamSynchronize(mp->stream));
+    unsigned long long cnt = 0;
+    if (mp->counters) GM_TRY_CUDA(cudaMemcpy(&cnt, &mp->counters[2], sizeof(cnt), cudaMemcpyDeviceToHost));
+    *n = cnt;
+    uint64_t k = std::min<uint64_t>(std::min<uint64_t>(cnt, cap), mp->dbg_cap);
+    if (k == 0) return GM_OK;
+    if (!sample || !fix || !vis || !g) return gm_set_error(GM_ERR_INVALID_ARG, "gm_map_debug_pairs: null output");
+    GM_TRY_CUDA(cudaMemcpy(sample, mp->dbg_sample, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost));
+    GM_TRY_CUDA(cudaMemcpy(fix, mp->dbg_fix, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost));
+    GM_TRY_CUDA(cudaMemcpy(vis, mp->dbg_vis, k, cudaMemcpyDeviceToHost));
+    GM_TRY_CUDA(cudaMemcpy(g, mp->dbg_g, sizeof(float) * k, cudaMemcpyDeviceToHost));
+    return GM_OK;
+}
+
+extern "C" void gm_map_free(gm_map* mp) {
+    if (!mp) return;
+    cudaFree(mp->values);
+    cudaFree(mp->max_bits);
+    cudaFree(mp->counters);
+    cudaFree(mp->dbg_sample);
+    cudaFree(mp->dbg_fix);
+    cudaFree(mp->dbg_vis);
+    cudaFree(mp->dbg_g);
+    for (auto& e : mp->ev)
+        if (e) cudaEventDestroy(e);
+    delete mp;
+}
+
+extern "C" gm_status gm_query_density(const gm_map* mp, const gm_field* field, gm_query_mode mode, uint32_t window,
+                                      const uint32_t* sample_idx, const float* xyz, uint64_t n, float* out,
+                                      gm_stream stream) {
+    (void)xyz;
+    if (!out && n > 0) return gm_set_error(GM_ERR_INVALID_ARG, "gm_query_density: null output");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mode == GM_Q_SAMPLE) {
+        if (!mp || (!sample_idx && n > 0)) return gm_set_error(GM_ERR_INVALID_ARG, "gm_query_density: map and indices required");
+        if (window >= mp->W) return gm_set_error(GM_ERR_INVALID_ARG, "gm_query_density: window out of range");
+        if (n == 0) return GM_OK;
+        void* di = nullptr;
+        bool oi = false;
+        GM_TRY(gm_stage_to_device(sample_idx, sizeof(uint32_t) * n, s, &di, &oi));
+        bool dev_out = gm_is_device_ptr(out);
+        float* dout = out;
+        if (!dev_out) GM_TRY(gm_alloc((void**)&dout, sizeof(float) * n, s));
+        k_gather_values<<<gm_div_up(n, 256), 256, 0, s>>>(mp->values, mp->ns, window, (const uint32_t*)di, n, dout,
+                                                          mp->ctx->dev_err);
+        mp->ctx->launches += 1;
+        gm_status st = GM_OK;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) st = gm_cuda_error(e, "gm_query_density launch");
+        if (!dev_out) {
+            if (st == GM_OK) st = gm_copy_out(out, dout, sizeof(float) * n, s);
+            cudaFreeAsync(dout, s);
+        }
+        if (oi) cudaFreeAsync(di, s);
+        return st;
+    }
+    if (mode == GM_Q_PLAIN)
+        return gm_set_error(GM_ERR_INVALID_ARG,
+                            "gm_query_density: GM_Q_PLAIN points are accumulated with gm_samples_from_points + "
+                            "gm_accumulate_fixations");
+    if (mode == GM_Q_FIELD) {
+        if (!field) return gm_set_error(GM_ERR_INVALID_ARG, "gm_query_density: GM_Q_FIELD needs a field");
+        return gm_set_error(GM_ERR_UNSUPPORTED, "gm_query_density: neural field queries are not built in this library");
+    }
+    return gm_set_error(GM_ERR_INVALID_ARG, "gm_query_density: unknown mode");
+}

@@ -1,0 +1,419 @@
+// gm_scene.cu -- gm_build_scene: meshes -> world triangles -> linear BVH.
+//
+// The paper tests occlusion with a z-buffer rendered per point of view (Section 3.2.2); here
+// occlusion is an exact segment test against every triangle, accelerated by a binary BVH
+// built on the GPU in five data-parallel steps (Karras, "Maximizing parallelism in the
+// construction of BVHs, octrees, and k-d trees", HPG 2012):
+//   1. world vertices: FP64 transform per vertex, rounded to FP32 (same operation order as
+//      the FP64 reference: ((m0 x + m1 y) + m2 z) + m3, no fused multiply-add);
+//   2. 63-bit Morton code of each triangle centroid in the centroid bounds;
+//   3. stable radix sort of the codes (leaf order);
+//   4. one thread per internal node finds its key range and split (longest common prefix,
+//      ties between equal codes broken by leaf index);
+//   5. bottom-up refit: the second child to arrive at a node writes the node's union box.
+// Node layout (64 B): the boxes of both children plus the two child links, so one node fetch
+// decides both children. A child link >= 0 is an internal node, < 0 is leaf ~link (one
+// triangle). Boxes are widened by 2^-19 of the scene's largest coordinate so that the FP32
+// slab test never rejects a triangle the watertight triangle test would hit.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gm_internal.cuh"
+
+namespace {
+
+struct Mat16 {
+    double m[16];
+};
+
+__global__ void k_transform(const float* __restrict__ v, uint32_t nv, Mat16 M, float* __restrict__ out) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    double x = v[3 * i], y = v[3 * i + 1], z = v[3 * i + 2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        double s = __dadd_rn(__dmul_rn(M.m[4 * r + 0], x), __dmul_rn(M.m[4 * r + 1], y));
+        s = __dadd_rn(s, __dmul_rn(M.m[4 * r + 2], z));
+        s = __dadd_rn(s, M.m[4 * r + 3]);
+        out[3 * i + r] = __double2float_rn(s);
+    }
+}
+
+__device__ __forceinline__ unsigned int f2ord(float f) {
+    unsigned int b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(unsigned int o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// bounds layout (ordered-uint encoded floats): [0..2] centroid min, [3..5] centroid max,
+// [6..8] vertex min, [9..11] vertex max.
+__global__ void k_bounds_init(unsigned int* b) {
+    int i = threadIdx.x;
+    if (i < 12) b[i] = ((i / 3) % 2 == 0) ? 0xffffffffu : 0u;
+}
+
+__global__ void k_gather(const float* __restrict__ wv, const uint32_t* __restrict__ idx, uint32_t nt,
+                         uint32_t nv, uint32_t tri_base, uint32_t mesh, float4* __restrict__ tri_canon,
+                         uint32_t* __restrict__ tri_mesh, unsigned int* __restrict__ bounds,
+                         int* __restrict__ err) {
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    float lo[6], hi[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) { lo[c] = INFINITY; hi[c] = -INFINITY; }
+    if (t < nt) {
+        float3 v[3];
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint32_t vi = idx[3 * t + k];
+            if (vi >= nv) { bad = true; vi = 0; }
+            v[k] = make_float3(wv[3 * vi], wv[3 * vi + 1], wv[3 * vi + 2]);
+        }
+        if (bad) atomicCAS(err, 0, GM_DEV_BAD_INDEX);
+        uint32_t g = tri_base + t;
+        tri_canon[3 * g + 0] = make_float4(v[0].x, v[0].y, v[0].z, 0.f);
+        tri_canon[3 * g + 1] = make_float4(v[1].x, v[1].y, v[1].z, 0.f);
+        tri_canon[3 * g + 2] = make_float4(v[2].x, v[2].y, v[2].z, 0.f);
+        tri_mesh[g] = mesh;
+        float c[3] = {(v[0].x + v[1].x + v[2].x) * (1.f / 3.f), (v[0].y + v[1].y + v[2].y) * (1.f / 3.f),
+                      (v[0].z + v[1].z + v[2].z) * (1.f / 3.f)};
+        const float* vf = &v[0].x;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = hi[a] = c[a];
+            lo[3 + a] = fminf(fminf(vf[a], vf[3 + a]), vf[6 + a]);
+            hi[3 + a] = fmaxf(fmaxf(vf[a], vf[3 + a]), vf[6 + a]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0 && blockIdx.x * blockDim.x + (threadIdx.x & ~31u) < nt) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&bounds[a], f2ord(lo[a]));
+            atomicMax(&bounds[3 + a], f2ord(hi[a]));
+            atomicMin(&bounds[6 + a], f2ord(lo[3 + a]));
+            atomicMax(&bounds[9 + a], f2ord(hi[3 + a]));
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t spread3_21(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t quant21(float c, float lo, float hi) {
+    float ext = hi - lo;
+    if (!(ext > 0.f)) return 0u;
+    float q = (c - lo) / ext * 2097152.f;
+    q = fminf(fmaxf(q, 0.f), 2097151.f);
+    return (uint32_t)q;
+}
+
+__global__ void k_morton(const float4* __restrict__ tri, uint32_t nt, const unsigned int* __restrict__ bounds,
+                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    float4 a = tri[3 * t], b = tri[3 * t + 1], c = tri[3 * t + 2];
+    float cx = (a.x + b.x + c.x) * (1.f / 3.f), cy = (a.y + b.y + c.y) * (1.f / 3.f),
+          cz = (a.z + b.z + c.z) * (1.f / 3.f);
+    uint32_t qx = quant21(cx, ord2f(bounds[0]), ord2f(bounds[3]));
+    uint32_t qy = quant21(cy, ord2f(bounds[1]), ord2f(bounds[4]));
+    uint32_t qz = quant21(cz, ord2f(bounds[2]), ord2f(bounds[5]));
+    keys[t] = (spread3_21(qx) << 2) | (spread3_21(qy) << 1) | spread3_21(qz);
+    vals[t] = t;
+}
+
+__device__ __forceinline__ int lcp(const uint64_t* __restrict__ keys, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    uint64_t a = keys[i], b = keys[j];
+    if (a != b) return __clzll((long long)(a ^ b));
+    return 64 + __clz(i ^ j);
+}
+
+__global__ void k_hierarchy(const uint64_t* __restrict__ keys, int n, float4* __restrict__ nodes,
+                            int* __restrict__ parent_node, int* __restrict__ parent_leaf) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (lcp(keys, n, i, i + 1) - lcp(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = lcp(keys, n, i, i - d);
+    int lmax = 2;
+    while (lcp(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (lcp(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = lcp(keys, n, i, j);
+    int s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (lcp(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int split = i + s * d + min(d, 0);
+    int lo = min(i, j), hi = max(i, j);
+    int left = (lo == split) ? ~split : split;
+    int right = (hi == split + 1) ? ~(split + 1) : split + 1;
+    nodes[4 * i + 3] = make_float4(__int_as_float(left), __int_as_float(right), 0.f, 0.f);
+    if (left < 0) parent_leaf[~left] = i; else parent_node[left] = i;
+    if (right < 0) parent_leaf[~right] = i; else parent_node[right] = i;
+    if (i == 0) parent_node[0] = -1;
+}
+
+__device__ __forceinline__ void store_child_box(float* node, int side, const float lo[3], const float hi[3]) {
+    // side 0: floats 0..5 = Lmin xyz, Lmax xyz; side 1: floats 6..11 = Rmin xyz, Rmax xyz
+    float* p = node + 6 * side;
+    p[0] = lo[0]; p[1] = lo[1]; p[2] = lo[2];
+    p[3] = hi[0]; p[4] = hi[1]; p[5] = hi[2];
+}
+
+__global__ void k_refit(const float4* __restrict__ tri_canon, const uint32_t* __restrict__ order, int n,
+                        float4* __restrict__ nodes, const int* __restrict__ parent_node,
+                        const int* __restrict__ parent_leaf, unsigned int* __restrict__ flags,
+                        const unsigned int* __restrict__ bounds, float4* __restrict__ bvh_tris) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t t = order[i];
+    float4 a = tri_canon[3 * t], b = tri_canon[3 * t + 1], c = tri_canon[3 * t + 2];
+    bvh_tris[3 * i + 0] = make_float4(a.x, a.y, a.z, __uint_as_float(t));
+    bvh_tris[3 * i + 1] = b;
+    bvh_tris[3 * i + 2] = c;
+    if (n == 1) return;
+    float big = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) big = fmaxf(big, fmaxf(fabsf(ord2f(bounds[6 + k])), fabsf(ord2f(bounds[9 + k]))));
+    const float margin = big * (1.0f / 524288.0f) + 1e-30f;
+    float lo[3] = {fminf(fminf(a.x, b.x), c.x) - margin, fminf(fminf(a.y, b.y), c.y) - margin,
+                   fminf(fminf(a.z, b.z), c.z) - margin};
+    float hi[3] = {fmaxf(fmaxf(a.x, b.x), c.x) + margin, fmaxf(fmaxf(a.y, b.y), c.y) + margin,
+                   fmaxf(fmaxf(a.z, b.z), c.z) + margin};
+    int p = parent_leaf[i];
+    int self = ~i;
+    while (p >= 0) {
+        float* node = reinterpret_cast<float*>(nodes + 4 * p);
+        int left = __float_as_int(node[12]);
+        store_child_box(node, left == self ? 0 : 1, lo, hi);
+        __threadfence();
+        if (atomicAdd(&flags[p], 1u) == 0u) return;  // the sibling finishes this node
+        __threadfence();
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fminf(__ldcg(node + k), __ldcg(node + 6 + k));
+            hi[k] = fmaxf(__ldcg(node + 3 + k), __ldcg(node + 9 + k));
+        }
+        self = p;
+        p = parent_node[p];
+    }
+}
+
+__global__ void k_depth(const int* __restrict__ parent_node, const int* __restrict__ parent_leaf, int n,
+                        unsigned int* __restrict__ depth) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || n < 2) return;
+    unsigned int d = 1;
+    int p = parent_leaf[i];
+    while (p > 0 && d < 4096u) {
+        p = parent_node[p];
+        ++d;
+    }
+    atomicMax(depth, d);
+}
+
+}  // namespace
+
+extern "C" gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes,
+                                    gm_stream stream, gm_scene** out) {
+    if (!ctx || !meshes || !out || n_meshes == 0)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene: null argument or no meshes");
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t nt64 = 0;
+    for (uint32_t m = 0; m < n_meshes; ++m) {
+        const gm_mesh_desc& d = meshes[m];
+        if (d.n_tris > 0 && (!d.vertices || !d.indices || d.n_verts == 0))
+            return gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene: mesh " + std::to_string(m) + " has triangles but no vertices/indices");
+        for (int k = 0; k < 16; ++k)
+            if (!std::isfinite(d.transform[k]))
+                return gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene: non-finite transform");
+        nt64 += d.n_tris;
+    }
+    if (nt64 == 0) return gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene: the scene has no triangles");
+    if (nt64 > 0x7fffffffu) return gm_set_error(GM_ERR_UNSUPPORTED, "gm_build_scene: more than 2^31-1 triangles");
+    GM_TRY_CUDA(cudaSetDevice(ctx->device));
+    const uint32_t nt = (uint32_t)nt64;
+
+    gm_scene* sc = new gm_scene();
+    sc->ctx = ctx;
+    sc->n_tris = nt;
+    sc->n_meshes = n_meshes;
+    std::vector<void*> tmp;
+    auto fail = [&](gm_status st) {
+        for (void* p : tmp) cudaFreeAsync(p, s);
+        gm_scene_free(sc);
+        return st;
+    };
+    gm_status st;
+#define SC_ALLOC(ptr, bytes) \
+    if ((st = gm_alloc((void**)&(ptr), (bytes), s)) != GM_OK) return fail(st)
+#define TMP_ALLOC(ptr, bytes)                                          \
+    do {                                                               \
+        if ((st = gm_alloc((void**)&(ptr), (bytes), s)) != GM_OK) return fail(st); \
+        tmp.push_back((void*)(ptr));                                   \
+    } while (0)
+
+    SC_ALLOC(sc->tri_canon, sizeof(float4) * 3 * (size_t)nt);
+    SC_ALLOC(sc->tri_mesh, sizeof(uint32_t) * (size_t)nt);
+    SC_ALLOC(sc->mesh_object, sizeof(uint32_t) * n_meshes);
+    SC_ALLOC(sc->bvh_tris, sizeof(float4) * 3 * (size_t)nt);
+    if (nt > 1) SC_ALLOC(sc->nodes, sizeof(float4) * 4 * (size_t)(nt - 1));
+    unsigned int* bounds = nullptr;
+    int* err = nullptr;
+    TMP_ALLOC(bounds, sizeof(unsigned int) * 16);
+    err = ctx->dev_err;
+    k_bounds_init<<<1, 32, 0, s>>>(bounds);
+    int launches = 1;
+
+    std::vector<uint32_t> objs(n_meshes);
+    uint32_t base = 0;
+    for (uint32_t m = 0; m < n_meshes; ++m) {
+        const gm_mesh_desc& d = meshes[m];
+        objs[m] = d.object_id;
+        if (d.n_tris == 0) continue;
+        void *dv = nullptr, *di = nullptr;
+        bool ov = false, oi = false;
+        if ((st = gm_stage_to_device(d.vertices, sizeof(float) * 3 * (size_t)d.n_verts, s, &dv, &ov)) != GM_OK) return fail(st);
+        if (ov) tmp.push_back(dv);
+        if ((st = gm_stage_to_device(d.indices, sizeof(uint32_t) * 3 * (size_t)d.n_tris, s, &di, &oi)) != GM_OK) return fail(st);
+        if (oi) tmp.push_back(di);
+        float* wv = nullptr;
+        TMP_ALLOC(wv, sizeof(float) * 3 * (size_t)d.n_verts);
+        Mat16 M;
+        memcpy(M.m, d.transform, sizeof(M.m));
+        k_transform<<<gm_div_up(d.n_verts, 256), 256, 0, s>>>((const float*)dv, d.n_verts, M, wv);
+        k_gather<<<gm_div_up(d.n_tris, 256), 256, 0, s>>>(wv, (const uint32_t*)di, d.n_tris, d.n_verts, base, m,
+                                                          sc->tri_canon, sc->tri_mesh, bounds, err);
+        launches += 2;
+        base += d.n_tris;
+    }
+    GM_TRY_CUDA(cudaMemcpyAsync(sc->mesh_object, objs.data(), sizeof(uint32_t) * n_meshes, cudaMemcpyHostToDevice, s));
+
+    uint64_t* keys = nullptr;
+    uint32_t* order = nullptr;
+    int *parent_node = nullptr, *parent_leaf = nullptr;
+    unsigned int *flags = nullptr, *depth = nullptr;
+    TMP_ALLOC(keys, sizeof(uint64_t) * nt);
+    TMP_ALLOC(order, sizeof(uint32_t) * nt);
+    TMP_ALLOC(parent_leaf, sizeof(int) * nt);
+    TMP_ALLOC(parent_node, sizeof(int) * (nt > 1 ? nt - 1 : 1));
+    TMP_ALLOC(flags, sizeof(unsigned int) * (nt > 1 ? nt - 1 : 1));
+    TMP_ALLOC(depth, sizeof(unsigned int));
+    GM_TRY_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned int) * (nt > 1 ? nt - 1 : 1), s));
+    // -1 everywhere: a link the hierarchy step did not write stops the refit instead of escaping
+    GM_TRY_CUDA(cudaMemsetAsync(parent_leaf, 0xff, sizeof(int) * nt, s));
+    GM_TRY_CUDA(cudaMemsetAsync(parent_node, 0xff, sizeof(int) * (nt > 1 ? nt - 1 : 1), s));
+    GM_TRY_CUDA(cudaMemsetAsync(depth, 0, sizeof(unsigned int), s));
+    k_morton<<<gm_div_up(nt, 256), 256, 0, s>>>(sc->tri_canon, nt, bounds, keys, order);
+    if ((st = gm_radix_sort_u64(keys, order, nt, 63, s, &launches)) != GM_OK) return fail(st);
+    if (nt > 1) k_hierarchy<<<gm_div_up(nt - 1, 256), 256, 0, s>>>(keys, (int)nt, sc->nodes, parent_node, parent_leaf);
+    k_refit<<<gm_div_up(nt, 256), 256, 0, s>>>(sc->tri_canon, order, (int)nt, sc->nodes, parent_node, parent_leaf,
+                                                flags, bounds, sc->bvh_tris);
+    k_depth<<<gm_div_up(nt, 256), 256, 0, s>>>(parent_node, parent_leaf, (int)nt, depth);
+    launches += (nt > 1 ? 4 : 3);
+    ctx->launches += launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_build_scene launch"));
+    unsigned int hb[16] = {0};
+    unsigned int hdepth = 0;
+    int herr = 0;
+    if ((e = cudaMemcpyAsync(hb, bounds, sizeof(unsigned int) * 12, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&hdepth, depth, sizeof(unsigned int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return fail(gm_cuda_error(e, "gm_build_scene"));
+    for (void* p : tmp) cudaFreeAsync(p, s);
+    tmp.clear();
+    if (herr == GM_DEV_BAD_INDEX) {
+        cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), s);
+        return fail(gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene: a vertex index is out of range"));
+    }
+    auto dec = [](unsigned int o) {
+        unsigned int b = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+        float f;
+        memcpy(&f, &b, 4);
+        return f;
+    };
+    for (int k = 0; k < 3; ++k) {
+        sc->box_lo[k] = dec(hb[6 + k]);
+        sc->box_hi[k] = dec(hb[9 + k]);
+        if (!std::isfinite(sc->box_lo[k]) || !std::isfinite(sc->box_hi[k]))
+            return fail(gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene: non-finite vertex"));
+    }
+    sc->depth = nt > 1 ? hdepth : 0;
+    *out = sc;
+    return GM_OK;
+#undef SC_ALLOC
+#undef TMP_ALLOC
+}
+
+extern "C" gm_status gm_scene_info(const gm_scene* sc, uint32_t* n_tris, uint32_t* bvh_depth) {
+    if (!sc) return gm_set_error(GM_ERR_INVALID_ARG, "gm_scene_info: null scene");
+    if (n_tris) *n_tris = sc->n_tris;
+    if (bvh_depth) *bvh_depth = sc->depth;
+    return GM_OK;
+}
+
+namespace {
+__global__ void k_unpack_tris(const float4* __restrict__ t, uint32_t nt, float* __restrict__ out) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float4 v = t[3 * i + k];
+        out[9 * i + 3 * k + 0] = v.x;
+        out[9 * i + 3 * k + 1] = v.y;
+        out[9 * i + 3 * k + 2] = v.z;
+    }
+}
+}  // namespace
+
+extern "C" gm_status gm_scene_triangles(const gm_scene* sc, float* dst, gm_stream stream) {
+    if (!sc || !dst) return gm_set_error(GM_ERR_INVALID_ARG, "gm_scene_triangles: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = sizeof(float) * 9 * (size_t)sc->n_tris;
+    bool dev = gm_is_device_ptr(dst);
+    float* tmp = dst;
+    if (!dev) GM_TRY(gm_alloc((void**)&tmp, bytes, s));
+    k_unpack_tris<<<gm_div_up(sc->n_tris, 256), 256, 0, s>>>(sc->tri_canon, sc->n_tris, tmp);
+    sc->ctx->launches += 1;
+    if (!dev) {
+        gm_status st = gm_copy_out(dst, tmp, bytes, s);
+        cudaFreeAsync(tmp, s);
+        return st;
+    }
+    GM_TRY_CUDA(cudaGetLastError());
+    return GM_OK;
+}
+
+extern "C" void gm_scene_free(gm_scene* sc) {
+    if (!sc) return;
+    cudaFree(sc->tri_canon);
+    cudaFree(sc->tri_mesh);
+    cudaFree(sc->mesh_object);
+    cudaFree(sc->nodes);
+    cudaFree(sc->bvh_tris);
+    delete sc;
+}

@@ -1,0 +1,274 @@
+"""Thin ctypes binding of libgazemap (include/gazemap.h): same names, argument marshalling only.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA); every computation
+runs in the library's CUDA kernels. There is no CPU fallback: if the library is not built or
+no sm_103a GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from .build import LIB
+
+GM_OK, GM_ERR_INVALID_ARG, GM_ERR_CUDA, GM_ERR_OOM, GM_ERR_TIMEOUT = 0, 1, 2, 3, 4
+GM_ERR_UNSUPPORTED, GM_ERR_INTERNAL, GM_WARN_EMPTY = 5, 6, 100
+GM_F_TIMING, GM_F_DEBUG_PAIRS, GM_F_NO_REORDER = 1, 2, 4
+GM_Q_SAMPLE, GM_Q_PLAIN, GM_Q_FIELD = 0, 1, 2
+
+
+class GazeMapError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[gm status {status}] {msg}")
+        self.status = status
+
+
+class gm_mesh_desc(C.Structure):
+    _fields_ = [("vertices", C.c_void_p), ("indices", C.c_void_p), ("n_verts", C.c_uint32),
+                ("n_tris", C.c_uint32), ("transform", C.c_double * 16), ("object_id", C.c_uint32)]
+
+
+class gm_fixations(C.Structure):
+    _fields_ = [("eye_xyz", C.c_void_p), ("gaze_xyz", C.c_void_p), ("duration_s", C.c_void_p),
+                ("timestamp_s", C.c_void_p), ("n", C.c_uint32)]
+
+
+class gm_params(C.Structure):
+    _fields_ = [("theta_rad", C.c_float), ("cutoff_sigmas", C.c_float), ("eps_rel", C.c_float),
+                ("t_begin", C.c_double), ("t_end", C.c_double), ("window_s", C.c_double),
+                ("normalize", C.c_int32), ("flags", C.c_int32), ("debug_pair_cap", C.c_uint64)]
+
+
+class gm_map_stats(C.Structure):
+    _fields_ = [("pairs", C.c_uint64), ("in_cone", C.c_uint64), ("visible", C.c_uint64),
+                ("n_windows", C.c_uint32), ("n_fixations_used", C.c_uint32), ("prep_ms", C.c_float),
+                ("accumulate_ms", C.c_float), ("normalize_ms", C.c_float), ("launches", C.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_P = C.c_void_p
+
+_SIGS = {
+    "gm_create": (C.c_int, [C.c_int, C.POINTER(_P)]),
+    "gm_destroy": (None, [_P]),
+    "gm_last_error": (C.c_char_p, []),
+    "gm_sync": (C.c_int, [_P, _P]),
+    "gm_ctx_launches": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
+    "gm_build_scene": (C.c_int, [_P, C.POINTER(gm_mesh_desc), C.c_uint32, _P, C.POINTER(_P)]),
+    "gm_scene_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
+    "gm_scene_triangles": (C.c_int, [_P, _P, _P]),
+    "gm_scene_free": (None, [_P]),
+    "gm_sample_surface": (C.c_int, [_P, _P, C.c_uint64, C.c_uint32, _P, C.POINTER(_P)]),
+    "gm_samples_from_points": (C.c_int, [_P, _P, _P, C.c_uint64, _P, C.POINTER(_P)]),
+    "gm_samples_info": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
+    "gm_samples_offsets": (C.c_int, [_P, _P, _P]),
+    "gm_samples_copy": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "gm_samples_free": (None, [_P]),
+    "gm_accumulate_fixations": (C.c_int, [_P, _P, C.POINTER(gm_fixations), C.POINTER(gm_params), _P,
+                                          C.POINTER(_P)]),
+    "gm_map_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(gm_map_stats)]),
+    "gm_map_copy": (C.c_int, [_P, C.c_uint32, _P, C.POINTER(C.c_float), _P]),
+    "gm_map_device_values": (_P, [_P]),
+    "gm_map_debug_pairs": (C.c_int, [_P, _P, _P, _P, _P, C.c_uint64, C.POINTER(C.c_uint64)]),
+    "gm_map_free": (None, [_P]),
+    "gm_query_density": (C.c_int, [_P, _P, C.c_int, C.c_uint32, _P, _P, C.c_uint64, _P, _P]),
+}
+
+
+def lib():
+    """Load libgazemap.so (built by paper_2601_07571_gb300.build.build()); raise if missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"libgazemap.so is not built ({LIB}); run paper_2601_07571_gb300.build.build()")
+        L = C.CDLL(LIB)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> Sequence[str]:
+    L = lib()
+    return [n for n in _SIGS if hasattr(L, n)]
+
+
+def _check(st: int, allow_empty: bool = False) -> int:
+    if st == GM_OK or (allow_empty and st == GM_WARN_EMPTY):
+        return st
+    raise GazeMapError(st, lib().gm_last_error().decode(errors="replace"))
+
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream or None
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream or None
+    return int(stream) or None
+
+
+# ---- context ---------------------------------------------------------------------------------
+def gm_create(device: int = 0):
+    h = _P()
+    _check(lib().gm_create(device, C.byref(h)))
+    return h
+
+
+def gm_destroy(ctx) -> None:
+    lib().gm_destroy(ctx)
+
+
+def gm_sync(ctx, stream=None) -> None:
+    _check(lib().gm_sync(ctx, _stream(stream)))
+
+
+def gm_ctx_launches(ctx) -> int:
+    n = C.c_uint64()
+    _check(lib().gm_ctx_launches(ctx, C.byref(n)))
+    return n.value
+
+
+# ---- scene -----------------------------------------------------------------------------------
+def gm_build_scene(ctx, meshes, stream=None):
+    """meshes: sequence of (vertices (nv,3) f32, indices (nt,3) u32, transform (4,4) f64, object_id)."""
+    descs = (gm_mesh_desc * len(meshes))()
+    keep = []
+    for d, (v, f, xf, obj) in zip(descs, meshes):
+        keep += [v, f]
+        d.vertices = _ptr(v)
+        d.indices = _ptr(f)
+        d.n_verts = int(v.shape[0])
+        d.n_tris = int(f.shape[0])
+        d.transform = (C.c_double * 16)(*np.asarray(xf, np.float64).reshape(16).tolist())
+        d.object_id = int(obj)
+    h = _P()
+    _check(lib().gm_build_scene(ctx, descs, len(meshes), _stream(stream), C.byref(h)))
+    return h
+
+
+def gm_scene_info(scene):
+    nt, depth = C.c_uint32(), C.c_uint32()
+    _check(lib().gm_scene_info(scene, C.byref(nt), C.byref(depth)))
+    return nt.value, depth.value
+
+
+def gm_scene_triangles(scene, out, stream=None) -> None:
+    _check(lib().gm_scene_triangles(scene, _ptr(out), _stream(stream)))
+
+
+def gm_scene_free(scene) -> None:
+    lib().gm_scene_free(scene)
+
+
+# ---- samples ---------------------------------------------------------------------------------
+def gm_sample_surface(scene, density_per_mesh, seed: int, session: int = 0, stream=None):
+    dens = np.ascontiguousarray(density_per_mesh, np.float64)
+    h = _P()
+    _check(lib().gm_sample_surface(scene, _ptr(dens), C.c_uint64(seed), C.c_uint32(session), _stream(stream),
+                                   C.byref(h)))
+    return h
+
+
+def gm_samples_from_points(scene, xyz, tri, stream=None):
+    h = _P()
+    _check(lib().gm_samples_from_points(scene, _ptr(xyz), _ptr(tri), C.c_uint64(int(xyz.shape[0])),
+                                        _stream(stream), C.byref(h)))
+    return h
+
+
+def gm_samples_info(samples) -> int:
+    n = C.c_uint64()
+    _check(lib().gm_samples_info(samples, C.byref(n)))
+    return n.value
+
+
+def gm_samples_offsets(samples, out, stream=None) -> None:
+    _check(lib().gm_samples_offsets(samples, _ptr(out), _stream(stream)))
+
+
+def gm_samples_copy(samples, xyz=None, tri=None, bary2=None, obj=None, stream=None) -> None:
+    _check(lib().gm_samples_copy(samples, _ptr(xyz), _ptr(tri), _ptr(bary2), _ptr(obj), _stream(stream)))
+
+
+def gm_samples_free(samples) -> None:
+    lib().gm_samples_free(samples)
+
+
+# ---- accumulation ----------------------------------------------------------------------------
+def make_params(theta_rad, cutoff_sigmas=4.0, eps_rel=1e-5, t_begin=-np.inf, t_end=np.inf, window_s=0.0,
+                normalize=True, flags=0, debug_pair_cap=0) -> gm_params:
+    return gm_params(float(theta_rad), float(cutoff_sigmas), float(eps_rel), float(t_begin), float(t_end),
+                     float(window_s), int(bool(normalize)), int(flags), int(debug_pair_cap))
+
+
+def gm_accumulate_fixations(scene, samples, eye, gaze, duration_s, timestamp_s, params: gm_params, stream=None):
+    fx = gm_fixations(_ptr(eye), _ptr(gaze), _ptr(duration_s), _ptr(timestamp_s), int(eye.shape[0]))
+    h = _P()
+    _check(lib().gm_accumulate_fixations(scene, samples, C.byref(fx), C.byref(params), _stream(stream), C.byref(h)))
+    return h
+
+
+def gm_map_info(m):
+    W, ns, st = C.c_uint32(), C.c_uint64(), gm_map_stats()
+    status = _check(lib().gm_map_info(m, C.byref(W), C.byref(ns), C.byref(st)), allow_empty=True)
+    return W.value, ns.value, st.as_dict(), status
+
+
+def gm_map_copy(m, window: int, out, stream=None) -> float:
+    mx = C.c_float()
+    _check(lib().gm_map_copy(m, int(window), _ptr(out), C.byref(mx), _stream(stream)))
+    return mx.value
+
+
+def gm_map_device_values(m) -> int:
+    return lib().gm_map_device_values(m)
+
+
+def gm_map_debug_pairs(m, cap: int):
+    s = np.empty(cap, np.uint32)
+    f = np.empty(cap, np.uint32)
+    v = np.empty(cap, np.uint8)
+    g = np.empty(cap, np.float32)
+    n = C.c_uint64()
+    _check(lib().gm_map_debug_pairs(m, _ptr(s), _ptr(f), _ptr(v), _ptr(g), C.c_uint64(cap), C.byref(n)))
+    k = min(n.value, cap)
+    return dict(sample=s[:k], fix=f[:k], visible=v[:k], g=g[:k], n=n.value)
+
+
+def gm_map_free(m) -> None:
+    lib().gm_map_free(m)
+
+
+def gm_query_density(m, field, mode: int, window: int, sample_idx, xyz, n: int, out, stream=None) -> None:
+    _check(lib().gm_query_density(m, field, int(mode), int(window), _ptr(sample_idx), _ptr(xyz), C.c_uint64(n),
+                                  _ptr(out), _stream(stream)))

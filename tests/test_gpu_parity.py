@@ -1,0 +1,300 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element.
+
+Bars (see the oracle for the readings of the paper):
+  - world triangles, per-triangle offsets, sample triangle ids: bit-exact;
+  - barycentrics within 2^-21, positions within 8 ulp of the triangle's largest coordinate;
+  - in-cone pairs identical except at the cone edge; visibility identical except where the
+    oracle marks the pair ambiguous (grazing within delta metres);
+  - densities: |gpu - oracle| <= 1e-4 * oracle + amb (+ sens * position error when the GPU
+    places its own samples), with amb and sens from the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.parity_utils import compare_pairs, tri_max_coord, ulp32
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2601_07571_gb300 import build
+    build.build()
+    import paper_2601_07571_gb300 as G
+    return G
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    c = G.gm_create(0)
+    yield c
+    G.gm_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def pipe(G):
+    from paper_2601_07571_gb300 import pipeline
+    return pipeline
+
+
+def _shared_inputs(w):
+    """Oracle sample positions rounded to FP32: the same points go to both sides."""
+    tri = oracle.world_triangles(w)
+    off = oracle.tri_offsets(oracle.areas(tri), oracle.tri_density(w))
+    s = oracle.samples(tri, off, w.seed, w.session)
+    return tri, s.xyz.astype(np.float32), s.tri.astype(np.uint32)
+
+
+def _run_shared(G, ctx, pipe, w, delta, band=1e-5, record=True):
+    tri, pts, stri = _shared_inputs(w)
+    ora = oracle.accumulate(tri, pts.astype(np.float64), stri.astype(np.int64), w.fixations, w.params,
+                            delta_abs=delta, cone_band=band, record=record)
+    cap = 4 * max(1, len(ora["pairs"]["sample"])) + 1024 if record else 0
+    h = pipe.run(ctx, w, points=(pts, stri), normalize=False, flags=G.GM_F_DEBUG_PAIRS if record else 0,
+                 debug_pair_cap=cap)
+    return tri, pts, stri, ora, h
+
+
+def _check_density(gpu, ora, amb, extra=0.0):
+    tol = REL * ora + amb + extra + 1e-30
+    err = np.abs(gpu.astype(np.float64) - ora)
+    bad = err > tol
+    assert not bad.any(), (f"{bad.sum()} samples off; worst rel "
+                           f"{(err / np.maximum(ora, 1e-30))[bad].max():.3e}")
+
+
+# ---------------------------------------------------------------------------------------------
+def test_world_triangles_bit_exact(G, ctx, pipe):
+    for w in (synth.tiny_sphere(), synth.paper_scene()):
+        sc = G.gm_build_scene(ctx, pipe.mesh_args(w))
+        nt, depth = G.gm_scene_info(sc)
+        ref = oracle.world_triangles(w)
+        out = np.empty((nt, 9), np.float32)
+        G.gm_scene_triangles(sc, out)
+        G.gm_scene_free(sc)
+        assert nt == len(ref) and 0 < depth <= 64
+        assert np.array_equal(out.view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("which", ["tiny", "paper"])
+def test_sampler_parity(G, ctx, pipe, which):
+    w = synth.tiny_sphere() if which == "tiny" else synth.paper_scene()
+    tri = oracle.world_triangles(w)
+    off = oracle.tri_offsets(oracle.areas(tri), oracle.tri_density(w))
+    sc = G.gm_build_scene(ctx, pipe.mesh_args(w))
+    sm = G.gm_sample_surface(sc, [m.density for m in w.meshes], w.seed, w.session)
+    n = G.gm_samples_info(sm)
+    goff = np.empty(len(tri) + 1, np.int64)
+    G.gm_samples_offsets(sm, goff)
+    assert n == off[-1]
+    assert np.array_equal(goff, off)
+    xyz = np.empty((n, 3), np.float32)
+    st = np.empty(n, np.uint32)
+    b2 = np.empty((n, 2), np.float32)
+    obj = np.empty(n, np.uint32)
+    G.gm_samples_copy(sm, xyz, st, b2, obj)
+    G.gm_samples_free(sm)
+    G.gm_scene_free(sc)
+    s = oracle.samples(tri, off, w.seed, w.session)
+    assert np.array_equal(st.astype(np.int64), s.tri)
+    assert np.array_equal(obj, oracle.tri_object(w)[s.tri])
+    assert np.abs(b2.astype(np.float64) - s.bary[:, 1:]).max() <= 2.0 ** -21
+    M = tri_max_coord(tri, s.tri)
+    assert np.all(np.abs(xyz.astype(np.float64) - s.xyz) <= 8 * ulp32(M)[:, None])
+
+
+def test_accumulate_shared_inputs_tiny(G, ctx, pipe):
+    w = synth.tiny_sphere()
+    tri, pts, stri, ora, h = _run_shared(G, ctx, pipe, w, delta=4e-6)
+    W, ns, stats, status = G.gm_map_info(h.map)
+    gpu, _ = pipe.map_array(h)
+    gp = G.gm_map_debug_pairs(h.map, 200000)
+    h.free()
+    assert ns == len(pts) and W == 1
+    assert stats["pairs"] == ns * w.fixations.n
+    assert gp["n"] == len(gp["sample"]) == stats["in_cone"]
+    c = compare_pairs(gp, ora["pairs"], w.fixations.n)
+    assert c["gpu"] > 10000
+    assert stats["visible"] == int(gp["visible"].sum())
+    _check_density(gpu, ora["density"][0], ora["amb"][0])
+    # per-pair weights: g on the GPU within the Gaussian's FP32 error of the oracle's
+    key_o = ora["pairs"]["sample"] * w.fixations.n + ora["pairs"]["fix"]
+    key_g = gp["sample"].astype(np.int64) * w.fixations.n + gp["fix"]
+    idx = np.searchsorted(key_o, key_g)
+    go = ora["pairs"]["g"][idx]
+    assert np.all(np.abs(gp["g"] - go) <= 5e-5 * go)
+
+
+@pytest.mark.parametrize("theta_deg", [0.5, 2.0])
+def test_accumulate_theta_variants(G, ctx, pipe, theta_deg):
+    w = synth.tiny_sphere()
+    w.params = synth.Params(theta_rad=math.radians(theta_deg))
+    tri, pts, stri, ora, h = _run_shared(G, ctx, pipe, w, delta=4e-6)
+    gpu, _ = pipe.map_array(h)
+    gp = G.gm_map_debug_pairs(h.map, 400000)
+    h.free()
+    compare_pairs(gp, ora["pairs"], w.fixations.n)
+    _check_density(gpu, ora["density"][0], ora["amb"][0])
+
+
+def test_accumulate_windows_and_interval(G, ctx, pipe):
+    w = synth.tiny_sphere(n_fix=300)
+    ts = w.fixations.timestamp_s
+    w.params = synth.Params(t_begin=2.0, t_end=float(ts.max()) * 0.9, window_s=5.0)
+    tri, pts, stri, ora, h = _run_shared(G, ctx, pipe, w, delta=4e-6, record=False)
+    W, ns, stats, status = G.gm_map_info(h.map)
+    assert W == ora["density"].shape[0] > 5
+    keep = (ts >= 2.0) & (ts < float(ts.max()) * 0.9)
+    assert stats["n_fixations_used"] == keep.sum()
+    for k in range(W):
+        gpu, mx = pipe.map_array(h, k)
+        _check_density(gpu, ora["density"][k], ora["amb"][k])
+        assert mx == gpu.max()
+    h.free()
+
+
+def test_end_to_end_tiny_with_normalisation(G, ctx, pipe):
+    w = synth.tiny_sphere()
+    r = oracle.run(w, delta_abs=2e-5, cone_band=1e-4)
+    tri = r["tri"]
+    h = pipe.run(ctx, w, normalize=False)
+    gpu, mx = pipe.map_array(h)
+    h.free()
+    dpos = 8 * ulp32(tri_max_coord(tri, r["samples"].tri))
+    ora = r["density"][0]
+    _check_density(gpu, ora, r["amb"][0], r["sens"][0] * dpos)
+    # normalised map: divide by the maximum (Section 3.2.3)
+    h = pipe.run(ctx, w, normalize=True)
+    gn, mxn = pipe.map_array(h)
+    W, ns, stats, status = G.gm_map_info(h.map)
+    h.free()
+    assert gn.max() == 1.0 and gn.min() >= 0.0
+    assert mxn == mx
+    on, omax = oracle.normalize(ora)
+    assert abs(mx - omax) <= REL * omax
+    tol = (REL * ora + r["amb"][0] + r["sens"][0] * dpos) / omax + 2 * REL
+    assert np.all(np.abs(gn - on) <= tol)
+
+
+def test_device_inputs_match_host_inputs_and_rerun_is_bit_identical(G, ctx, pipe):
+    w = synth.tiny_sphere()
+    a = pipe.run(ctx, w, normalize=False)
+    b = pipe.run(ctx, w, normalize=False, device_inputs=True)
+    c = pipe.run(ctx, w, normalize=False)
+    va, vb, vc = (pipe.map_array(x)[0] for x in (a, b, c))
+    for x in (a, b, c):
+        x.free()
+    assert np.array_equal(va.view(np.uint32), vb.view(np.uint32))
+    assert np.array_equal(va.view(np.uint32), vc.view(np.uint32))
+
+
+def test_sample_query_gathers_map_values(G, ctx, pipe):
+    w = synth.tiny_sphere()
+    h = pipe.run(ctx, w)
+    v, _ = pipe.map_array(h)
+    idx = np.random.default_rng(0).integers(0, h.n_samples, 1000).astype(np.uint32)
+    out = np.empty(1000, np.float32)
+    G.gm_query_density(h.map, None, G.GM_Q_SAMPLE, 0, idx, None, 1000, out)
+    h.free()
+    assert np.array_equal(out, v[idx])
+
+
+def test_edge_cases(G, ctx, pipe):
+    w = synth.tiny_sphere()
+    # no fixation at all: an all-zero map and the empty-map warning
+    w0 = synth.tiny_sphere(n_fix=1)
+    w0.fixations = w0.fixations.subset(slice(0, 0))
+    h = pipe.run(ctx, w0)
+    W, ns, stats, status = G.gm_map_info(h.map)
+    v, mx = pipe.map_array(h)
+    h.free()
+    assert status == G.GM_WARN_EMPTY and mx == 0.0 and not v.any() and stats["pairs"] == 0
+    # an interval that excludes every fixation behaves the same
+    w1 = synth.tiny_sphere()
+    w1.params = synth.Params(t_begin=1e6, t_end=2e6)
+    h = pipe.run(ctx, w1)
+    W, ns, stats, status = G.gm_map_info(h.map)
+    v, mx = pipe.map_array(h)
+    h.free()
+    assert status == G.GM_WARN_EMPTY and not v.any() and stats["n_fixations_used"] == 0
+    # zero density: no samples, still a valid (empty) map
+    w2 = synth.tiny_sphere()
+    for m in w2.meshes:
+        m.density = 0.0
+    h = pipe.run(ctx, w2)
+    assert h.n_samples == 0
+    h.free()
+    # a one-triangle scene: its samples can only see (own triangle excluded)
+    v1 = np.array([[-1, -1, 0], [1.3, -0.9, 0.2], [-0.7, 1.1, -0.1]], np.float32)
+    w3 = synth.Workload("one", [synth.Mesh(v1, np.array([[0, 1, 2]], np.uint32), synth.identity(), 7, 5000.0)],
+                        synth.Fixations(np.array([[0.1, 0.2, 3.0]], np.float32), np.array([[0, 0, -1]], np.float32),
+                                        np.array([0.3], np.float32), np.array([0.0])),
+                        synth.Params(theta_rad=math.radians(8.0), eps_rel=0.0), seed=3)
+    r = oracle.run(w3)
+    h = pipe.run(ctx, w3, normalize=False)
+    v, _ = pipe.map_array(h)
+    xyz, tri, b2, obj = pipe.samples_arrays(h)
+    h.free()
+    assert np.all(obj == 7) and len(v) == len(r["density"][0])
+    _check_density(v, r["density"][0], r["amb"][0], r["sens"][0] * 8 * ulp32(1.3))
+    # degenerate triangles get no samples and never occlude
+    vd = np.array([[0, 0, 1], [0, 0, 1], [0, 0, 1]], np.float32)
+    w4 = synth.tiny_sphere()
+    w4.meshes.append(synth.Mesh(vd, np.array([[0, 1, 2]], np.uint32), synth.identity(), 9, 500.0))
+    ra = pipe.run(ctx, synth.tiny_sphere(), normalize=False)
+    rb = pipe.run(ctx, w4, normalize=False)
+    va, vb = pipe.map_array(ra)[0], pipe.map_array(rb)[0]
+    ra.free()
+    rb.free()
+    assert np.array_equal(va, vb)
+    # invalid arguments are reported, not computed
+    bad = synth.tiny_sphere()
+    bad.params = synth.Params(theta_rad=0.0)
+    with pytest.raises(G.GazeMapError):
+        pipe.run(ctx, bad)
+    bad = synth.tiny_sphere()
+    bad.meshes[0].indices = bad.meshes[0].indices.copy()
+    bad.meshes[0].indices[5, 1] = 10 ** 6
+    with pytest.raises(G.GazeMapError):
+        G.gm_build_scene(ctx, pipe.mesh_args(bad))
+
+
+def test_paper_scene_full_size_sampled(G, ctx, pipe):
+    """The paper-shaped scene at full size (800k tris, ~2M samples, 6000 fixations), in the
+    launch configuration the benchmark times; the oracle recomputes a seeded selection of
+    samples one by one (brute force over every triangle)."""
+    w = synth.paper_scene()
+    tri = oracle.world_triangles(w)
+    off = oracle.tri_offsets(oracle.areas(tri), oracle.tri_density(w))
+    s_all = oracle.samples(tri, off, w.seed, w.session)
+    rng = np.random.default_rng(99)
+    # half uniform over all samples, half the nearest samples to a few gaze rays (non-zero)
+    pick = set(rng.choice(len(s_all.tri), 40, replace=False).tolist())
+    fx = w.fixations
+    for f in rng.choice(fx.n, 20, replace=False):
+        p = s_all.xyz - fx.eye[f].astype(np.float64)
+        r = fx.gaze[f].astype(np.float64) / np.linalg.norm(fx.gaze[f])
+        d1 = p @ r
+        ang = np.linalg.norm(np.cross(p, r), axis=1) / np.maximum(d1, 1e-9)
+        ang[d1 <= 0] = np.inf
+        pick.update(np.argsort(ang)[:3].tolist())
+    which = np.array(sorted(pick), np.int64)
+    s = oracle.samples(tri, off, w.seed, w.session, which)
+    ora = oracle.accumulate(tri, s.xyz, s.tri, w.fixations, w.params, delta_abs=3e-5, cone_band=1e-4)
+    h = pipe.run(ctx, w, normalize=False)
+    W, ns, stats, status = G.gm_map_info(h.map)
+    gpu, _ = pipe.map_array(h)
+    h.free()
+    assert ns == off[-1] and stats["pairs"] == ns * fx.n
+    d = ora["density"][0]
+    assert (d > 0).sum() >= 30
+    dpos = 8 * ulp32(tri_max_coord(tri, s.tri))
+    _check_density(gpu[which], d, ora["amb"][0], ora["sens"][0] * dpos)
