@@ -44,14 +44,18 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gazemap", "reference"], default="gazemap")
     ap.add_argument("--workload", choices=["paper_scene", "tiny_sphere"], default="paper_scene")
+    ap.add_argument("--fixations", type=int, default=0, help="use only the first N fixations (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     return ap.parse_args()
 
 
-def make_workload(name):
+def make_workload(name, n_fix=0):
     import synth
-    return synth.paper_scene() if name == "paper_scene" else synth.tiny_sphere()
+    w = synth.paper_scene() if name == "paper_scene" else synth.tiny_sphere()
+    if n_fix:
+        w.fixations = w.fixations.subset(slice(0, n_fix))
+    return w
 
 
 # ---------------------------------------------------------------------------------------------
@@ -124,9 +128,10 @@ def oracle_sample_run(w, n_samples, nthreads):
 
 
 def calibrated_oracle(w, target_s, nthreads):
-    dt, _ = oracle_sample_run(w, 8, nthreads)
-    # scale the sample count so one run takes about target_s seconds
-    n = int(max(8, min(20000, 8 * target_s / max(dt, 1e-3))))
+    n0 = nthreads
+    dt, _ = oracle_sample_run(w, n0, nthreads)
+    # scale the sample count so one run takes about target_s seconds (at least one per thread)
+    n = int(max(n0, min(20000, n0 * target_s / max(dt, 1e-3))))
     dt, pairs = oracle_sample_run(w, n, nthreads)
     return dt, pairs, n
 
@@ -135,13 +140,13 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.fixations)
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
     per_step = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
-    dt, _ = oracle_sample_run(w, 8, cores)
-    n = int(max(8, min(20000, 8 * per_step / max(dt, 1e-3))))
+    dt, _ = oracle_sample_run(w, cores, cores)
+    n = int(max(cores, min(20000, cores * per_step / max(dt, 1e-3))))
     for _ in range(args.warmup):
         oracle_sample_run(w, n, cores)
     tot_t, tot_p = 0.0, 0
@@ -154,7 +159,7 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "fixations": w.fixations.n},
-            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": min(cores, n), "kind": "oracle",
                              "sample": f"{n} evenly strided samples x all {w.fixations.n} fixations per step, "
                                        f"whole-scene transform/areas/counts included"},
             "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -183,7 +188,7 @@ def main():
     import paper_2601_07571_gb300 as G
     from paper_2601_07571_gb300 import pipeline
 
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.fixations)
     ctx = G.gm_create(local)
     stream = torch.cuda.current_stream()
     dev_meshes = pipeline.mesh_args(w, to_device=True)
@@ -305,7 +310,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         dt, p, n = calibrated_oracle(w, args.cpu_seconds, cores)
-        line["cpu_baseline"] = {"value": p / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+        line["cpu_baseline"] = {"value": p / dt, "unit": "pairs/s", "cores": min(cores, n), "kind": "oracle",
                                 "sample": f"{n} evenly strided samples x all {w.fixations.n} fixations, "
                                           f"whole-scene transform/areas/counts included ({dt:.1f} s)"}
     G.gm_destroy(ctx)
