@@ -143,13 +143,14 @@ __device__ __forceinline__ void make_ray(Ray& R, float3 o, float3 d, float tmax)
     R.Sz = 1.0f / dkz;
 }
 
-__device__ __forceinline__ bool slab(const Ray& R, float lx, float ly, float lz, float hx, float hy, float hz) {
+// Entry distance of the segment into the box, or +inf when it misses.
+__device__ __forceinline__ float slab(const Ray& R, float lx, float ly, float lz, float hx, float hy, float hz) {
     float t0x = fmaf(lx, R.idir.x, -R.oidir.x), t1x = fmaf(hx, R.idir.x, -R.oidir.x);
     float t0y = fmaf(ly, R.idir.y, -R.oidir.y), t1y = fmaf(hy, R.idir.y, -R.oidir.y);
     float t0z = fmaf(lz, R.idir.z, -R.oidir.z), t1z = fmaf(hz, R.idir.z, -R.oidir.z);
     float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.f));
     float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), R.tmax_box));
-    return tn <= tf;
+    return tn <= tf ? tn : INFINITY;
 }
 
 // Woop, Benthin, Wald, "Watertight ray/triangle intersection", JCGT 2(1), 2013. Edge functions
@@ -182,6 +183,8 @@ __device__ __forceinline__ bool leaf_hit(const Ray& R, const float4* __restrict_
     return tri_hit(R, a, __ldg(&tris[3 * slot + 1]), __ldg(&tris[3 * slot + 2]));
 }
 
+// Any-hit traversal of the segment: stack of deferred subtrees, nearer child first (an occluder
+// between the eye and the sample is met sooner), leaves tested as soon as they are reached.
 __device__ bool occluded(const Ray& R, uint32_t own, const float4* __restrict__ nodes,
                          const float4* __restrict__ tris, uint32_t nt, int* __restrict__ err) {
     if (nt < 2) return nt == 1 ? leaf_hit(R, tris, 0, own) : false;
@@ -189,31 +192,32 @@ __device__ bool occluded(const Ray& R, uint32_t own, const float4* __restrict__ 
     int sp = 0;
     int node = 0;
     for (;;) {
-        float4 n0 = __ldg(&nodes[4 * node + 0]);
-        float4 n1 = __ldg(&nodes[4 * node + 1]);
-        float4 n2 = __ldg(&nodes[4 * node + 2]);
-        float4 n3 = __ldg(&nodes[4 * node + 3]);
-        bool hl = slab(R, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
-        bool hr = slab(R, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
-        int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
-        if (hl && cl < 0) {
+        const float4 n0 = __ldg(&nodes[4 * node + 0]);
+        const float4 n1 = __ldg(&nodes[4 * node + 1]);
+        const float4 n2 = __ldg(&nodes[4 * node + 2]);
+        const float4 n3 = __ldg(&nodes[4 * node + 3]);
+        float tl = slab(R, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
+        float tr = slab(R, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
+        const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
+        if (tl < INFINITY && cl < 0) {
             if (leaf_hit(R, tris, ~cl, own)) return true;
-            hl = false;
+            tl = INFINITY;
         }
-        if (hr && cr < 0) {
+        if (tr < INFINITY && cr < 0) {
             if (leaf_hit(R, tris, ~cr, own)) return true;
-            hr = false;
+            tr = INFINITY;
         }
-        if (hl && hr) {
+        if (tl < INFINITY && tr < INFINITY) {
             if (sp >= STACK) {
                 atomicCAS(err, 0, GM_DEV_STACK_OVERFLOW);
                 return true;
             }
-            stack[sp++] = cr;
+            const bool left_first = tl <= tr;
+            stack[sp++] = left_first ? cr : cl;
+            node = left_first ? cl : cr;
+        } else if (tl < INFINITY) {
             node = cl;
-        } else if (hl) {
-            node = cl;
-        } else if (hr) {
+        } else if (tr < INFINITY) {
             node = cr;
         } else {
             if (sp == 0) return false;
@@ -234,16 +238,29 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-template <bool DEBUG>
+// COMPACT = false: every lane traces the rays of its own in-cone samples (lanes whose samples
+// are outside the cone idle meanwhile).
+// COMPACT = true: per fixation, the warp gathers its in-cone (sample, weight) pairs into a
+// shared-memory queue and traces them 32 at a time, so every lane works on a ray from the same
+// eye; the compensated sums live in shared memory, one slot per sample, and each slot receives
+// at most one addition per fixation, in fixation order -- the result is bit-identical.
+template <bool DEBUG, bool COMPACT>
 __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(
     const float4* __restrict__ spos, const uint32_t* __restrict__ sidx, const float4* __restrict__ fix,
     const uint32_t* __restrict__ n_fix_dev, const float4* __restrict__ nodes, const float4* __restrict__ tris,
     AccParams P, float* __restrict__ out, unsigned int* __restrict__ max_bits,
     unsigned long long* __restrict__ counters, int* __restrict__ err, DebugOut dbg) {
+    constexpr int QN = COMPACT ? ACC_THREADS * SPT : 1;
     __shared__ float4 sfix[2 * FIX_TILE];
     __shared__ float wmax[ACC_THREADS / 32];
+    __shared__ float4 wsmp[QN];     // per warp: its 32*SPT samples (x, y, z, own triangle)
+    __shared__ float2 wacc[QN];     // per warp: (sum, compensation) of each sample
+    __shared__ uint16_t qslot[QN];  // per warp: queue of in-cone sample slots
+    __shared__ float qg[QN];        // per warp: their weights
 
     const uint32_t nf = *n_fix_dev;
+    const int lane = threadIdx.x & 31;
+    const int wb = (threadIdx.x >> 5) * 32 * SPT;   // this warp's region in the per-warp arrays
     const uint32_t base = blockIdx.x * (uint32_t)(ACC_THREADS * SPT) + threadIdx.x;
 
     float sx[SPT], sy[SPT], sz[SPT], sum[SPT], cmp[SPT];
@@ -259,6 +276,10 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(
         own[k] = __float_as_uint(p.w);
         sum[k] = 0.f;
         cmp[k] = 0.f;
+        if (COMPACT) {
+            wsmp[wb + k * 32 + lane] = p;
+            wacc[wb + k * 32 + lane] = make_float2(0.f, 0.f);
+        }
     }
     unsigned long long n_in = 0, n_vis = 0;
     uint32_t cur = 0xffffffffu;
@@ -267,6 +288,11 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(
         float m = 0.f;
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {
+            if (COMPACT) {
+                __syncwarp();
+                sum[k] = wacc[wb + k * 32 + lane].x;
+                wacc[wb + k * 32 + lane] = make_float2(0.f, 0.f);
+            }
             uint32_t j = base + k * ACC_THREADS;
             if (j < P.ns && (P.W == 1 || sum[k] != 0.f)) out[(size_t)w * P.ns + sidx[j]] = sum[k];
             m = fmaxf(m, sum[k]);
@@ -274,7 +300,7 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(
             cmp[k] = 0.f;
         }
         m = warp_max(m);
-        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+        if (lane == 0) wmax[threadIdx.x >> 5] = m;
         __syncthreads();
         if (threadIdx.x < 32) {
             float v = threadIdx.x < ACC_THREADS / 32 ? wmax[threadIdx.x] : 0.f;
@@ -296,35 +322,92 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(
                 if (cur != 0xffffffffu) flush(cur);
                 cur = win;
             }
+            if (COMPACT) {
+                int tot = 0;
 #pragma unroll
-            for (int k = 0; k < SPT; ++k) {
-                const float px = sx[k] - F0.x, py = sy[k] - F0.y, pz = sz[k] - F0.z;
-                const float d1 = fmaf(px, F1.x, fmaf(py, F1.y, pz * F1.z));
-                const float cx = fmaf(py, F1.z, -pz * F1.y);
-                const float cy = fmaf(pz, F1.x, -px * F1.z);
-                const float cz = fmaf(px, F1.y, -py * F1.x);
-                const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-                const float d1s = d1 * d1;
-                if (d1 > 0.f && c2 <= P.K * d1s) {
-                    ++n_in;
-                    Ray R;
-                    make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(px, py, pz), P.tmax);
-                    const bool vis = !occluded(R, own[k], nodes, tris, P.nt, err);
-                    const float g = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
-                    if (vis) {
-                        ++n_vis;
-                        const float y = g - cmp[k];
-                        const float t = sum[k] + y;
-                        cmp[k] = (t - sum[k]) - y;
-                        sum[k] = t;
+                for (int k = 0; k < SPT; ++k) {
+                    const float px = sx[k] - F0.x, py = sy[k] - F0.y, pz = sz[k] - F0.z;
+                    const float d1 = fmaf(px, F1.x, fmaf(py, F1.y, pz * F1.z));
+                    const float cx = fmaf(py, F1.z, -pz * F1.y);
+                    const float cy = fmaf(pz, F1.x, -px * F1.z);
+                    const float cz = fmaf(px, F1.y, -py * F1.x);
+                    const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+                    const float d1s = d1 * d1;
+                    const bool in = d1 > 0.f && c2 <= P.K * d1s;
+                    const unsigned m = __ballot_sync(0xffffffffu, in);
+                    if (in) {
+                        const int pos = tot + __popc(m & gm_lanemask_lt());
+                        qslot[wb + pos] = (uint16_t)(k * 32 + lane);
+                        qg[wb + pos] = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
                     }
-                    if (DEBUG) {
-                        unsigned long long slot = atomicAdd(&counters[2], 1ull);
-                        if (slot < P.dbg_cap) {
-                            dbg.sample[slot] = sidx[base + k * ACC_THREADS];
-                            dbg.fix[slot] = dbg.fix_orig[t0 + i];
-                            dbg.vis[slot] = vis ? 1 : 0;
-                            dbg.g[slot] = g;
+                    tot += __popc(m);
+                }
+                if (tot == 0) continue;
+                __syncwarp();
+                for (int b = 0; b < tot; b += 32) {
+                    const int e = b + lane;
+                    if (e < tot) {
+                        const int slot = qslot[wb + e];
+                        const float4 sp = wsmp[wb + slot];
+                        const float g = qg[wb + e];
+                        ++n_in;
+                        Ray R;
+                        make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(sp.x - F0.x, sp.y - F0.y, sp.z - F0.z),
+                                 P.tmax);
+                        const bool vis = !occluded(R, __float_as_uint(sp.w), nodes, tris, P.nt, err);
+                        if (vis) {
+                            ++n_vis;
+                            float2 a = wacc[wb + slot];
+                            const float y = g - a.y;
+                            const float t = a.x + y;
+                            a.y = (t - a.x) - y;
+                            a.x = t;
+                            wacc[wb + slot] = a;
+                        }
+                        if (DEBUG) {
+                            unsigned long long q = atomicAdd(&counters[2], 1ull);
+                            if (q < P.dbg_cap) {
+                                dbg.sample[q] = sidx[blockIdx.x * (uint32_t)(ACC_THREADS * SPT) + (slot >> 5) * ACC_THREADS +
+                                                     (threadIdx.x & ~31) + (slot & 31)];
+                                dbg.fix[q] = dbg.fix_orig[t0 + i];
+                                dbg.vis[q] = vis ? 1 : 0;
+                                dbg.g[q] = g;
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+            } else {
+#pragma unroll
+                for (int k = 0; k < SPT; ++k) {
+                    const float px = sx[k] - F0.x, py = sy[k] - F0.y, pz = sz[k] - F0.z;
+                    const float d1 = fmaf(px, F1.x, fmaf(py, F1.y, pz * F1.z));
+                    const float cx = fmaf(py, F1.z, -pz * F1.y);
+                    const float cy = fmaf(pz, F1.x, -px * F1.z);
+                    const float cz = fmaf(px, F1.y, -py * F1.x);
+                    const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+                    const float d1s = d1 * d1;
+                    if (d1 > 0.f && c2 <= P.K * d1s) {
+                        ++n_in;
+                        Ray R;
+                        make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(px, py, pz), P.tmax);
+                        const bool vis = !occluded(R, own[k], nodes, tris, P.nt, err);
+                        const float g = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
+                        if (vis) {
+                            ++n_vis;
+                            const float y = g - cmp[k];
+                            const float t = sum[k] + y;
+                            cmp[k] = (t - sum[k]) - y;
+                            sum[k] = t;
+                        }
+                        if (DEBUG) {
+                            unsigned long long q = atomicAdd(&counters[2], 1ull);
+                            if (q < P.dbg_cap) {
+                                dbg.sample[q] = sidx[base + k * ACC_THREADS];
+                                dbg.fix[q] = dbg.fix_orig[t0 + i];
+                                dbg.vis[q] = vis ? 1 : 0;
+                                dbg.g[q] = g;
+                            }
                         }
                     }
                 }
@@ -338,7 +421,7 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(
         n_in += __shfl_xor_sync(0xffffffffu, n_in, o);
         n_vis += __shfl_xor_sync(0xffffffffu, n_vis, o);
     }
-    if ((threadIdx.x & 31) == 0 && (n_in | n_vis)) {
+    if (lane == 0 && (n_in | n_vis)) {
         atomicAdd(&counters[0], n_in);
         atomicAdd(&counters[1], n_vis);
     }
@@ -506,12 +589,15 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
             sidx = ident;
         }
         const uint32_t grid = gm_div_up(ns, (uint64_t)ACC_THREADS * SPT);
-        if (debug)
-            k_accumulate<true><<<grid, ACC_THREADS, 0, s>>>(spos, sidx, packed, n_valid, sc->nodes, sc->bvh_tris, P,
-                                                            mp->values, mp->max_bits, mp->counters, ctx->dev_err, dbg);
-        else
-            k_accumulate<false><<<grid, ACC_THREADS, 0, s>>>(spos, sidx, packed, n_valid, sc->nodes, sc->bvh_tris, P,
-                                                             mp->values, mp->max_bits, mp->counters, ctx->dev_err, dbg);
+        const bool compact = !(prm->flags & GM_F_NO_COMPACT);
+#define GM_LAUNCH_ACC(D, Cm)                                                                                 \
+    k_accumulate<D, Cm><<<grid, ACC_THREADS, 0, s>>>(spos, sidx, packed, n_valid, sc->nodes, sc->bvh_tris, P, \
+                                                    mp->values, mp->max_bits, mp->counters, ctx->dev_err, dbg)
+        if (debug && compact) GM_LAUNCH_ACC(true, true);
+        else if (debug) GM_LAUNCH_ACC(true, false);
+        else if (compact) GM_LAUNCH_ACC(false, true);
+        else GM_LAUNCH_ACC(false, false);
+#undef GM_LAUNCH_ACC
         ++launches;
     }
     if (mp->timing) cudaEventRecord(mp->ev[2], s);

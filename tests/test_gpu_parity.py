@@ -298,3 +298,21 @@ def test_paper_scene_full_size_sampled(G, ctx, pipe):
     assert (d > 0).sum() >= 30
     dpos = 8 * ulp32(tri_max_coord(tri, s.tri))
     _check_density(gpu[which], d, ora["amb"][0], ora["sens"][0] * dpos)
+
+
+def test_compacted_and_in_place_tracing_agree_bit_for_bit(G, ctx, pipe):
+    """The per-warp ray queue only reorders which lane traces which ray; each sample still gets
+    its additions in fixation order, so maps and recorded pairs are identical."""
+    for w in (synth.tiny_sphere(), synth.session(5)):
+        a = pipe.run(ctx, w, normalize=False, flags=G.GM_F_DEBUG_PAIRS, debug_pair_cap=2_000_000)
+        b = pipe.run(ctx, w, normalize=False, flags=G.GM_F_DEBUG_PAIRS | G.GM_F_NO_COMPACT,
+                     debug_pair_cap=2_000_000)
+        va, vb = pipe.map_array(a)[0], pipe.map_array(b)[0]
+        pa, pb = G.gm_map_debug_pairs(a.map, 2_000_000), G.gm_map_debug_pairs(b.map, 2_000_000)
+        a.free()
+        b.free()
+        assert np.array_equal(va.view(np.uint32), vb.view(np.uint32))
+        assert pa["n"] == pb["n"] > 0
+        ka = np.sort(pa["sample"].astype(np.int64) * (1 << 32) + pa["fix"])
+        kb = np.sort(pb["sample"].astype(np.int64) * (1 << 32) + pb["fix"])
+        assert np.array_equal(ka, kb)
