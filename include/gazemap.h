@@ -151,6 +151,28 @@ gm_status gm_samples_copy(const gm_samples* s, float* xyz, uint32_t* tri, float*
                           uint32_t* obj, gm_stream stream);
 void gm_samples_free(gm_samples* s);
 
+/* Allocation-free per-triangle sample offsets. The paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory when they need the offsets -- an engine
+ * plugin whose host application owns all device memory through its own allocator, or a
+ * real-time (per-frame) thread on which cudaMalloc may stall or fail. It computes exactly the
+ * offsets gm_sample_surface computes (FP64 area, rint(k A 2^32), int64 prefix, rounded starts;
+ * bit-identical) and calls no allocator.
+ *   tri_xyz:         n_tris x 9 FP32 world vertices (v0 v1 v2), device memory
+ *   density_per_tri: n_tris FP64 samples per m^2, device memory
+ *   offsets:         n_tris + 1 int64 output, device memory (also used as the prefix buffer)
+ * Scratch: the per-block partial sums live in a file-scope __device__ array of 65 536 int64
+ * (512 KiB) that every GPU loading this library holds until the process exits, so n_tris is
+ * limited to 65 536 * 2 048 = 134 217 728; larger inputs return GM_ERR_UNSUPPORTED without
+ * launching anything. Every call shares that array and it keeps the last call's contents;
+ * nothing in it needs to start at zero (each call writes every partial it reads), but calls
+ * that overlap on the GPU (different streams, or other threads) race on it and must be
+ * serialised by the caller. The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before any stream
+ * capture. Densities that are negative, NaN or give a triangle 2^31 or more samples set that
+ * triangle's count to 0 and are reported by the next gm_sync. */
+gm_status gm_tri_offsets_noalloc(gm_ctx* ctx, const float* tri_xyz, const double* density_per_tri,
+                                 uint32_t n_tris, int64_t* offsets, gm_stream stream);
+
 /* ---- accumulation (Section 3.2) -------------------------------------------------------- */
 
 /* For every sample s and every fixation f whose timestamp lies in [t_begin, t_end):

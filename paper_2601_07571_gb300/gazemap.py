@@ -70,6 +70,7 @@ _SIGS = {
     "gm_samples_offsets": (C.c_int, [_P, _P, _P]),
     "gm_samples_copy": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "gm_samples_free": (None, [_P]),
+    "gm_tri_offsets_noalloc": (C.c_int, [_P, _P, _P, C.c_uint32, _P, _P]),
     "gm_accumulate_fixations": (C.c_int, [_P, _P, C.POINTER(gm_fixations), C.POINTER(gm_params), _P,
                                           C.POINTER(_P)]),
     "gm_map_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(gm_map_stats)]),
@@ -222,6 +223,12 @@ def gm_samples_copy(samples, xyz=None, tri=None, bary2=None, obj=None, stream=No
 
 def gm_samples_free(samples) -> None:
     lib().gm_samples_free(samples)
+
+
+def gm_tri_offsets_noalloc(ctx, tri_xyz, density_per_tri, n_tris: int, offsets, stream=None) -> None:
+    """Per-triangle offsets from caller-owned device buffers, allocating nothing (see the header)."""
+    _check(lib().gm_tri_offsets_noalloc(ctx, _ptr(tri_xyz), _ptr(density_per_tri), C.c_uint32(n_tris),
+                                        _ptr(offsets), _stream(stream)))
 
 
 # ---- accumulation ----------------------------------------------------------------------------
