@@ -303,6 +303,9 @@ def main():
                           "normalize": sum(norm_ms) / len(norm_ms),
                           "build_and_sample": step_ms - acc - sum(prep_ms) / len(prep_ms) - sum(norm_ms) / len(norm_ms)},
             "in_cone_pairs": int(stats["in_cone"]), "visible_pairs": int(stats["visible"]),
+            "rays_per_s": stats["in_cone"] / (acc * 1e-3),
+            "nodes_per_ray": stats["nodes_visited"] / max(1, stats["in_cone"]),
+            "tris_per_ray": stats["tris_tested"] / max(1, stats["in_cone"]),
             "roofline": roof,
             "e2e": {"value": world * pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(out.numel() * 4), "ms_per_step": e2e_s * 1e3},

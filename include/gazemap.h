@@ -99,6 +99,8 @@ typedef struct {
     float accumulate_ms;      /* cone + occlusion + Gaussian + store + max kernel */
     float normalize_ms;
     uint32_t launches;        /* kernels this call launched */
+    uint64_t nodes_visited;   /* BVH nodes fetched by all occlusion rays */
+    uint64_t tris_tested;     /* ray/triangle tests performed by all occlusion rays */
 } gm_map_stats;
 
 /* ---- context ------------------------------------------------------------------------ */

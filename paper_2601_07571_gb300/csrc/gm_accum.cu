@@ -177,7 +177,9 @@ __device__ __forceinline__ bool tri_hit(const Ray& R, float4 a, float4 b, float4
     return det > 0.f ? (T > 0.f && T < R.tmax * det) : (T < 0.f && T > R.tmax * det);
 }
 
-__device__ __forceinline__ bool leaf_hit(const Ray& R, const float4* __restrict__ tris, int slot, uint32_t own) {
+__device__ __forceinline__ bool leaf_hit(const Ray& R, const float4* __restrict__ tris, int slot, uint32_t own,
+                                         uint32_t& n_tri) {
+    ++n_tri;
     float4 a = __ldg(&tris[3 * slot]);
     if (__float_as_uint(a.w) == own) return false;
     return tri_hit(R, a, __ldg(&tris[3 * slot + 1]), __ldg(&tris[3 * slot + 2]));
@@ -186,12 +188,14 @@ __device__ __forceinline__ bool leaf_hit(const Ray& R, const float4* __restrict_
 // Any-hit traversal of the segment: stack of deferred subtrees, nearer child first (an occluder
 // between the eye and the sample is met sooner), leaves tested as soon as they are reached.
 __device__ bool occluded(const Ray& R, uint32_t own, const float4* __restrict__ nodes,
-                         const float4* __restrict__ tris, uint32_t nt, int* __restrict__ err) {
-    if (nt < 2) return nt == 1 ? leaf_hit(R, tris, 0, own) : false;
+                         const float4* __restrict__ tris, uint32_t nt, int* __restrict__ err, uint32_t& n_node,
+                         uint32_t& n_tri) {
+    if (nt < 2) return nt == 1 ? leaf_hit(R, tris, 0, own, n_tri) : false;
     int stack[STACK];
     int sp = 0;
     int node = 0;
     for (;;) {
+        ++n_node;
         const float4 n0 = __ldg(&nodes[4 * node + 0]);
         const float4 n1 = __ldg(&nodes[4 * node + 1]);
         const float4 n2 = __ldg(&nodes[4 * node + 2]);
@@ -200,11 +204,11 @@ __device__ bool occluded(const Ray& R, uint32_t own, const float4* __restrict__ 
         float tr = slab(R, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
         const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
         if (tl < INFINITY && cl < 0) {
-            if (leaf_hit(R, tris, ~cl, own)) return true;
+            if (leaf_hit(R, tris, ~cl, own, n_tri)) return true;
             tl = INFINITY;
         }
         if (tr < INFINITY && cr < 0) {
-            if (leaf_hit(R, tris, ~cr, own)) return true;
+            if (leaf_hit(R, tris, ~cr, own, n_tri)) return true;
             tr = INFINITY;
         }
         if (tl < INFINITY && tr < INFINITY) {
@@ -282,6 +286,7 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(
         }
     }
     unsigned long long n_in = 0, n_vis = 0;
+    uint32_t n_node = 0, n_tri = 0;   // traversal work of this thread (wraps only past 4e9)
     uint32_t cur = 0xffffffffu;
 
     auto flush = [&](uint32_t w) {
@@ -354,7 +359,7 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(
                         Ray R;
                         make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(sp.x - F0.x, sp.y - F0.y, sp.z - F0.z),
                                  P.tmax);
-                        const bool vis = !occluded(R, __float_as_uint(sp.w), nodes, tris, P.nt, err);
+                        const bool vis = !occluded(R, __float_as_uint(sp.w), nodes, tris, P.nt, err, n_node, n_tri);
                         if (vis) {
                             ++n_vis;
                             float2 a = wacc[wb + slot];
@@ -391,7 +396,7 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(
                         ++n_in;
                         Ray R;
                         make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(px, py, pz), P.tmax);
-                        const bool vis = !occluded(R, own[k], nodes, tris, P.nt, err);
+                        const bool vis = !occluded(R, own[k], nodes, tris, P.nt, err, n_node, n_tri);
                         const float g = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
                         if (vis) {
                             ++n_vis;
@@ -416,14 +421,19 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(
     }
     if (cur != 0xffffffffu) flush(cur);
     else if (P.W == 1) flush(0);   // no fixation at all: window 0 is written as zeros
+    unsigned long long n_nd = n_node, n_tr = n_tri;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         n_in += __shfl_xor_sync(0xffffffffu, n_in, o);
         n_vis += __shfl_xor_sync(0xffffffffu, n_vis, o);
+        n_nd += __shfl_xor_sync(0xffffffffu, n_nd, o);
+        n_tr += __shfl_xor_sync(0xffffffffu, n_tr, o);
     }
     if (lane == 0 && (n_in | n_vis)) {
         atomicAdd(&counters[0], n_in);
         atomicAdd(&counters[1], n_vis);
+        atomicAdd(&counters[4], n_nd);
+        atomicAdd(&counters[5], n_tr);
     }
 }
 
@@ -517,9 +527,9 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
     }
     MAP_ALLOC(mp->values, sizeof(float) * W * ns);
     MAP_ALLOC(mp->max_bits, sizeof(unsigned int) * W);
-    MAP_ALLOC(mp->counters, sizeof(unsigned long long) * 4);
+    MAP_ALLOC(mp->counters, sizeof(unsigned long long) * 8);
     GM_TRY_CUDA(cudaMemsetAsync(mp->max_bits, 0, sizeof(unsigned int) * W, s));
-    GM_TRY_CUDA(cudaMemsetAsync(mp->counters, 0, sizeof(unsigned long long) * 4, s));
+    GM_TRY_CUDA(cudaMemsetAsync(mp->counters, 0, sizeof(unsigned long long) * 8, s));
     if (W > 1) GM_TRY_CUDA(cudaMemsetAsync(mp->values, 0, sizeof(float) * W * ns, s));
     if (debug) {
         mp->dbg_cap = prm->debug_pair_cap;
@@ -625,7 +635,7 @@ extern "C" gm_status gm_map_info(gm_map* mp, uint32_t* n_windows, uint64_t* n_sa
     if (!mp) return gm_set_error(GM_ERR_INVALID_ARG, "gm_map_info: null map");
     GM_TRY_CUDA(cudaStreamSynchronize(mp->stream));
     int err = 0;
-    unsigned long long c[4] = {0, 0, 0, 0};
+    unsigned long long c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     GM_TRY_CUDA(cudaMemcpy(&err, mp->ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
     GM_TRY_CUDA(cudaMemcpy(c, mp->counters, sizeof(c), cudaMemcpyDeviceToHost));
     if (err) {
@@ -639,6 +649,8 @@ extern "C" gm_status gm_map_info(gm_map* mp, uint32_t* n_windows, uint64_t* n_sa
     mp->stats.visible = c[1];
     mp->stats.n_fixations_used = nvalid;
     mp->stats.pairs = (uint64_t)nvalid * mp->ns;
+    mp->stats.nodes_visited = c[4];
+    mp->stats.tris_tested = c[5];
     if (mp->timing) {
         float a = 0, b = 0, d = 0;
         cudaEventElapsedTime(&a, mp->ev[0], mp->ev[1]);

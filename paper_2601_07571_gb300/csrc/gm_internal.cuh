@@ -66,7 +66,8 @@ struct gm_map {
     uint64_t ns = 0;
     float* values = nullptr;           // W x ns
     unsigned int* max_bits = nullptr;  // W (bit pattern of a non-negative float)
-    unsigned long long* counters = nullptr;  // [0] in_cone [1] visible [2] debug cursor
+    unsigned long long* counters = nullptr;  // [0] in_cone [1] visible [2] debug cursor [3] fixations used
+                                             // [4] BVH nodes visited [5] triangles tested
     uint32_t* dbg_sample = nullptr;
     uint32_t* dbg_fix = nullptr;
     uint8_t* dbg_vis = nullptr;

@@ -45,7 +45,8 @@ class gm_params(C.Structure):
 class gm_map_stats(C.Structure):
     _fields_ = [("pairs", C.c_uint64), ("in_cone", C.c_uint64), ("visible", C.c_uint64),
                 ("n_windows", C.c_uint32), ("n_fixations_used", C.c_uint32), ("prep_ms", C.c_float),
-                ("accumulate_ms", C.c_float), ("normalize_ms", C.c_float), ("launches", C.c_uint32)]
+                ("accumulate_ms", C.c_float), ("normalize_ms", C.c_float), ("launches", C.c_uint32),
+                ("nodes_visited", C.c_uint64), ("tris_tested", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

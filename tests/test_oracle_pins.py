@@ -486,7 +486,7 @@ def test_plane_head_on_closed_form():
     assert np.all(np.abs(dens[~edge] - expect[~edge]) <= 1e-12 * expect[~edge])
     integral = t / (sg * math.sqrt(2 * math.pi)) * 2 * math.pi * sg * sg * D * D * (1 - math.exp(-8))
     assert abs(dens.sum() / k - integral) / integral < 0.02
-    # 4 sigma holds 1 - e^-8 of the radial Gaussian: "approximately 100%" (Fig. 4 caption)
+    # 4 sigma holds 1 - e^-8 of the radial Gaussian, nearly all of it (Fig. 4 caption)
     assert 1 - math.exp(-8) > 0.9996
 
 
