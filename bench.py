@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", choices=["gazemap", "reference"], default="gazemap")
     ap.add_argument("--workload", choices=["paper_scene", "tiny_sphere"], default="paper_scene")
     ap.add_argument("--fixations", type=int, default=0, help="use only the first N fixations (profiling)")
+    ap.add_argument("--flags", type=int, default=0, help="extra GM_F_* accumulation flags (variant A/B runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     return ap.parse_args()
@@ -194,7 +195,7 @@ def main():
     dev_meshes = pipeline.mesh_args(w, to_device=True)
     dev_fix = pipeline.fixation_args(w.fixations, to_device=True)
     dens = [m.density for m in w.meshes]
-    prm = pipeline.params_of(w, flags=G.GM_F_TIMING, normalize=True)
+    prm = pipeline.params_of(w, flags=G.GM_F_TIMING | args.flags, normalize=True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def step(meshes, fix):
@@ -298,7 +299,8 @@ def main():
             "config": {"workload": w.name, "triangles": w.n_tris, "samples": int(ns),
                        "fixations": w.fixations.n, "pairs_per_step": int(pairs),
                        "l2": "flushed between steps (256 MiB write)", "inputs": "device-resident",
-                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "accumulate_flags": args.flags},
             "stages_ms": {"accumulate": acc, "fixation_prep": sum(prep_ms) / len(prep_ms),
                           "normalize": sum(norm_ms) / len(norm_ms),
                           "build_and_sample": step_ms - acc - sum(prep_ms) / len(prep_ms) - sum(norm_ms) / len(norm_ms)},

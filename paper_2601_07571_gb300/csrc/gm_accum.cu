@@ -32,8 +32,9 @@ namespace {
 
 constexpr int ACC_THREADS = 256;
 constexpr int SPT = 4;            // samples per thread
-constexpr int FIX_TILE = 256;     // fixations per shared-memory tile (8 KB)
-constexpr int STACK = 64;         // traversal stack entries (BVH depth is checked at build)
+constexpr int STACK = 64;         // binary traversal stack (the build refuses trees deeper than 64)
+constexpr int STACK4 = 96;        // 4-wide traversal stack: at most 3 pushes per level, <= 32 levels
+constexpr int LINK_EMPTY = (int)0x80000000;
 
 struct AccParams {
     float C2;     // log2(e) / (2 tan^2 theta)
@@ -230,6 +231,61 @@ __device__ bool occluded(const Ray& R, uint32_t own, const float4* __restrict__ 
     }
 }
 
+__device__ __forceinline__ void cswap(float& ta, int& la, float& tb, int& lb) {
+    const bool sw = tb < ta;
+    const float t = sw ? tb : ta;
+    const int l = sw ? lb : la;
+    tb = sw ? ta : tb;
+    lb = sw ? la : lb;
+    ta = t;
+    la = l;
+}
+
+// Any-hit traversal of the 4-wide tree: one 128-byte node fetch tests four child boxes; leaf
+// children are tested at once; internal children are visited nearest first (a five-exchange
+// sorting network on the entry distances), the others pushed far-to-near.
+__device__ bool occluded4(const Ray& R, uint32_t own, const float4* __restrict__ nodes4,
+                          const float4* __restrict__ tris, int* __restrict__ err, uint32_t& n_node,
+                          uint32_t& n_tri) {
+    int stack[STACK4];
+    int sp = 0;
+    int node = 0;
+    for (;;) {
+        ++n_node;
+        const float4* N = nodes4 + 8 * node;
+        const float4 lx = __ldg(N + 0), hx = __ldg(N + 1), ly = __ldg(N + 2), hy = __ldg(N + 3);
+        const float4 lz = __ldg(N + 4), hz = __ldg(N + 5), L = __ldg(N + 6);
+        float t0 = slab(R, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x);
+        float t1 = slab(R, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y);
+        float t2 = slab(R, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z);
+        float t3 = slab(R, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w);
+        int c0 = __float_as_int(L.x), c1 = __float_as_int(L.y), c2 = __float_as_int(L.z), c3 = __float_as_int(L.w);
+        if (t0 < INFINITY && c0 < 0) { if (c0 != LINK_EMPTY && leaf_hit(R, tris, ~c0, own, n_tri)) return true; t0 = INFINITY; }
+        if (t1 < INFINITY && c1 < 0) { if (c1 != LINK_EMPTY && leaf_hit(R, tris, ~c1, own, n_tri)) return true; t1 = INFINITY; }
+        if (t2 < INFINITY && c2 < 0) { if (c2 != LINK_EMPTY && leaf_hit(R, tris, ~c2, own, n_tri)) return true; t2 = INFINITY; }
+        if (t3 < INFINITY && c3 < 0) { if (c3 != LINK_EMPTY && leaf_hit(R, tris, ~c3, own, n_tri)) return true; t3 = INFINITY; }
+        cswap(t0, c0, t1, c1);
+        cswap(t2, c2, t3, c3);
+        cswap(t0, c0, t2, c2);
+        cswap(t1, c1, t3, c3);
+        cswap(t1, c1, t2, c2);
+        if (t0 == INFINITY) {
+            if (sp == 0) return false;
+            node = stack[--sp];
+            continue;
+        }
+        const int np = (t1 < INFINITY) + (t2 < INFINITY) + (t3 < INFINITY);
+        if (sp + np > STACK4) {
+            atomicCAS(err, 0, GM_DEV_STACK_OVERFLOW);
+            return true;
+        }
+        if (t3 < INFINITY) stack[sp++] = c3;
+        if (t2 < INFINITY) stack[sp++] = c2;
+        if (t1 < INFINITY) stack[sp++] = c1;
+        node = c0;
+    }
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -242,21 +298,26 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
+// Warps run independently: fixations are read from global memory (every lane reads the same
+// 32 bytes, served by L1 as a broadcast; the next fixation is fetched while the current one is
+// processed), window maxima are folded per warp, and no block-wide barrier is ever taken, so a
+// warp that traces many rays never holds up the others.
 // COMPACT = false: every lane traces the rays of its own in-cone samples (lanes whose samples
 // are outside the cone idle meanwhile).
 // COMPACT = true: per fixation, the warp gathers its in-cone (sample, weight) pairs into a
 // shared-memory queue and traces them 32 at a time, so every lane works on a ray from the same
 // eye; the compensated sums live in shared memory, one slot per sample, and each slot receives
 // at most one addition per fixation, in fixation order -- the result is bit-identical.
-template <bool DEBUG, bool COMPACT>
-__global__ void __launch_bounds__(ACC_THREADS) k_accumulate(
+// WIDE selects the 4-wide tree (occluded4) or the binary one (occluded). MINB is the minimum
+// number of resident blocks per SM the register allocation must allow (3: up to 80 registers,
+// 4: up to 64).
+template <bool DEBUG, bool COMPACT, bool WIDE, int MINB>
+__global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate(
     const float4* __restrict__ spos, const uint32_t* __restrict__ sidx, const float4* __restrict__ fix,
     const uint32_t* __restrict__ n_fix_dev, const float4* __restrict__ nodes, const float4* __restrict__ tris,
     AccParams P, float* __restrict__ out, unsigned int* __restrict__ max_bits,
     unsigned long long* __restrict__ counters, int* __restrict__ err, DebugOut dbg) {
     constexpr int QN = COMPACT ? ACC_THREADS * SPT : 1;
-    __shared__ float4 sfix[2 * FIX_TILE];
-    __shared__ float wmax[ACC_THREADS / 32];
     __shared__ float4 wsmp[QN];     // per warp: its 32*SPT samples (x, y, z, own triangle)
     __shared__ float2 wacc[QN];     // per warp: (sum, compensation) of each sample
     __shared__ uint16_t qslot[QN];  // per warp: queue of in-cone sample slots
@@ -285,16 +346,17 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(
             wacc[wb + k * 32 + lane] = make_float2(0.f, 0.f);
         }
     }
+    __syncwarp();
     unsigned long long n_in = 0, n_vis = 0;
     uint32_t n_node = 0, n_tri = 0;   // traversal work of this thread (wraps only past 4e9)
     uint32_t cur = 0xffffffffu;
 
     auto flush = [&](uint32_t w) {
         float m = 0.f;
+        if (COMPACT) __syncwarp();
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {
             if (COMPACT) {
-                __syncwarp();
                 sum[k] = wacc[wb + k * 32 + lane].x;
                 wacc[wb + k * 32 + lane] = make_float2(0.f, 0.f);
             }
@@ -304,115 +366,111 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accumulate(
             sum[k] = 0.f;
             cmp[k] = 0.f;
         }
+        if (COMPACT) __syncwarp();
         m = warp_max(m);
-        if (lane == 0) wmax[threadIdx.x >> 5] = m;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            float v = threadIdx.x < ACC_THREADS / 32 ? wmax[threadIdx.x] : 0.f;
-            v = warp_max(v);
-            if (threadIdx.x == 0 && v > 0.f) atomicMax(&max_bits[w], __float_as_uint(v));
-        }
-        __syncthreads();
+        if (lane == 0 && m > 0.f) atomicMax(&max_bits[w], __float_as_uint(m));
     };
 
-    for (uint32_t t0 = 0; t0 < nf; t0 += FIX_TILE) {
-        const uint32_t cnt = min((uint32_t)FIX_TILE, nf - t0);
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < 2 * cnt; i += ACC_THREADS) sfix[i] = fix[2 * t0 + i];
-        __syncthreads();
-        for (uint32_t i = 0; i < cnt; ++i) {
-            const float4 F0 = sfix[2 * i], F1 = sfix[2 * i + 1];
-            const uint32_t win = __float_as_uint(F1.w);
-            if (win != cur) {
-                if (cur != 0xffffffffu) flush(cur);
-                cur = win;
+    float4 nF0 = nf > 0 ? __ldg(&fix[0]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 nF1 = nf > 0 ? __ldg(&fix[1]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (uint32_t i = 0; i < nf; ++i) {
+        const float4 F0 = nF0, F1 = nF1;
+        if (i + 1 < nf) {
+            nF0 = __ldg(&fix[2 * (i + 1)]);
+            nF1 = __ldg(&fix[2 * (i + 1) + 1]);
+        }
+        const uint32_t win = __float_as_uint(F1.w);
+        if (win != cur) {
+            if (cur != 0xffffffffu) flush(cur);
+            cur = win;
+        }
+        if (COMPACT) {
+            int tot = 0;
+#pragma unroll
+            for (int k = 0; k < SPT; ++k) {
+                const float px = sx[k] - F0.x, py = sy[k] - F0.y, pz = sz[k] - F0.z;
+                const float d1 = fmaf(px, F1.x, fmaf(py, F1.y, pz * F1.z));
+                const float cx = fmaf(py, F1.z, -pz * F1.y);
+                const float cy = fmaf(pz, F1.x, -px * F1.z);
+                const float cz = fmaf(px, F1.y, -py * F1.x);
+                const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+                const float d1s = d1 * d1;
+                const bool in = d1 > 0.f && c2 <= P.K * d1s;
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                if (in) {
+                    const int pos = tot + __popc(m & gm_lanemask_lt());
+                    qslot[wb + pos] = (uint16_t)(k * 32 + lane);
+                    qg[wb + pos] = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
+                }
+                tot += __popc(m);
             }
-            if (COMPACT) {
-                int tot = 0;
-#pragma unroll
-                for (int k = 0; k < SPT; ++k) {
-                    const float px = sx[k] - F0.x, py = sy[k] - F0.y, pz = sz[k] - F0.z;
-                    const float d1 = fmaf(px, F1.x, fmaf(py, F1.y, pz * F1.z));
-                    const float cx = fmaf(py, F1.z, -pz * F1.y);
-                    const float cy = fmaf(pz, F1.x, -px * F1.z);
-                    const float cz = fmaf(px, F1.y, -py * F1.x);
-                    const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-                    const float d1s = d1 * d1;
-                    const bool in = d1 > 0.f && c2 <= P.K * d1s;
-                    const unsigned m = __ballot_sync(0xffffffffu, in);
-                    if (in) {
-                        const int pos = tot + __popc(m & gm_lanemask_lt());
-                        qslot[wb + pos] = (uint16_t)(k * 32 + lane);
-                        qg[wb + pos] = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
+            if (tot == 0) continue;
+            __syncwarp();
+            for (int b = 0; b < tot; b += 32) {
+                const int e = b + lane;
+                if (e < tot) {
+                    const int slot = qslot[wb + e];
+                    const float4 sp = wsmp[wb + slot];
+                    const float g = qg[wb + e];
+                    ++n_in;
+                    Ray R;
+                    make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(sp.x - F0.x, sp.y - F0.y, sp.z - F0.z),
+                             P.tmax);
+                    const bool vis = WIDE ? !occluded4(R, __float_as_uint(sp.w), nodes, tris, err, n_node, n_tri)
+                                          : !occluded(R, __float_as_uint(sp.w), nodes, tris, P.nt, err, n_node, n_tri);
+                    if (vis) {
+                        ++n_vis;
+                        float2 a = wacc[wb + slot];
+                        const float y = g - a.y;
+                        const float t = a.x + y;
+                        a.y = (t - a.x) - y;
+                        a.x = t;
+                        wacc[wb + slot] = a;
                     }
-                    tot += __popc(m);
-                }
-                if (tot == 0) continue;
-                __syncwarp();
-                for (int b = 0; b < tot; b += 32) {
-                    const int e = b + lane;
-                    if (e < tot) {
-                        const int slot = qslot[wb + e];
-                        const float4 sp = wsmp[wb + slot];
-                        const float g = qg[wb + e];
-                        ++n_in;
-                        Ray R;
-                        make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(sp.x - F0.x, sp.y - F0.y, sp.z - F0.z),
-                                 P.tmax);
-                        const bool vis = !occluded(R, __float_as_uint(sp.w), nodes, tris, P.nt, err, n_node, n_tri);
-                        if (vis) {
-                            ++n_vis;
-                            float2 a = wacc[wb + slot];
-                            const float y = g - a.y;
-                            const float t = a.x + y;
-                            a.y = (t - a.x) - y;
-                            a.x = t;
-                            wacc[wb + slot] = a;
-                        }
-                        if (DEBUG) {
-                            unsigned long long q = atomicAdd(&counters[2], 1ull);
-                            if (q < P.dbg_cap) {
-                                dbg.sample[q] = sidx[blockIdx.x * (uint32_t)(ACC_THREADS * SPT) + (slot >> 5) * ACC_THREADS +
-                                                     (threadIdx.x & ~31) + (slot & 31)];
-                                dbg.fix[q] = dbg.fix_orig[t0 + i];
-                                dbg.vis[q] = vis ? 1 : 0;
-                                dbg.g[q] = g;
-                            }
+                    if (DEBUG) {
+                        unsigned long long q = atomicAdd(&counters[2], 1ull);
+                        if (q < P.dbg_cap) {
+                            dbg.sample[q] = sidx[blockIdx.x * (uint32_t)(ACC_THREADS * SPT) + (slot >> 5) * ACC_THREADS +
+                                                 (threadIdx.x & ~31) + (slot & 31)];
+                            dbg.fix[q] = dbg.fix_orig[i];
+                            dbg.vis[q] = vis ? 1 : 0;
+                            dbg.g[q] = g;
                         }
                     }
                 }
-                __syncwarp();
-            } else {
+            }
+            __syncwarp();
+        } else {
 #pragma unroll
-                for (int k = 0; k < SPT; ++k) {
-                    const float px = sx[k] - F0.x, py = sy[k] - F0.y, pz = sz[k] - F0.z;
-                    const float d1 = fmaf(px, F1.x, fmaf(py, F1.y, pz * F1.z));
-                    const float cx = fmaf(py, F1.z, -pz * F1.y);
-                    const float cy = fmaf(pz, F1.x, -px * F1.z);
-                    const float cz = fmaf(px, F1.y, -py * F1.x);
-                    const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-                    const float d1s = d1 * d1;
-                    if (d1 > 0.f && c2 <= P.K * d1s) {
-                        ++n_in;
-                        Ray R;
-                        make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(px, py, pz), P.tmax);
-                        const bool vis = !occluded(R, own[k], nodes, tris, P.nt, err, n_node, n_tri);
-                        const float g = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
-                        if (vis) {
-                            ++n_vis;
-                            const float y = g - cmp[k];
-                            const float t = sum[k] + y;
-                            cmp[k] = (t - sum[k]) - y;
-                            sum[k] = t;
-                        }
-                        if (DEBUG) {
-                            unsigned long long q = atomicAdd(&counters[2], 1ull);
-                            if (q < P.dbg_cap) {
-                                dbg.sample[q] = sidx[base + k * ACC_THREADS];
-                                dbg.fix[q] = dbg.fix_orig[t0 + i];
-                                dbg.vis[q] = vis ? 1 : 0;
-                                dbg.g[q] = g;
-                            }
+            for (int k = 0; k < SPT; ++k) {
+                const float px = sx[k] - F0.x, py = sy[k] - F0.y, pz = sz[k] - F0.z;
+                const float d1 = fmaf(px, F1.x, fmaf(py, F1.y, pz * F1.z));
+                const float cx = fmaf(py, F1.z, -pz * F1.y);
+                const float cy = fmaf(pz, F1.x, -px * F1.z);
+                const float cz = fmaf(px, F1.y, -py * F1.x);
+                const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+                const float d1s = d1 * d1;
+                if (d1 > 0.f && c2 <= P.K * d1s) {
+                    ++n_in;
+                    Ray R;
+                    make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(px, py, pz), P.tmax);
+                    const bool vis = WIDE ? !occluded4(R, own[k], nodes, tris, err, n_node, n_tri)
+                                          : !occluded(R, own[k], nodes, tris, P.nt, err, n_node, n_tri);
+                    const float g = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
+                    if (vis) {
+                        ++n_vis;
+                        const float y = g - cmp[k];
+                        const float t = sum[k] + y;
+                        cmp[k] = (t - sum[k]) - y;
+                        sum[k] = t;
+                    }
+                    if (DEBUG) {
+                        unsigned long long q = atomicAdd(&counters[2], 1ull);
+                        if (q < P.dbg_cap) {
+                            dbg.sample[q] = sidx[base + k * ACC_THREADS];
+                            dbg.fix[q] = dbg.fix_orig[i];
+                            dbg.vis[q] = vis ? 1 : 0;
+                            dbg.g[q] = g;
                         }
                     }
                 }
@@ -600,13 +658,33 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
         }
         const uint32_t grid = gm_div_up(ns, (uint64_t)ACC_THREADS * SPT);
         const bool compact = !(prm->flags & GM_F_NO_COMPACT);
-#define GM_LAUNCH_ACC(D, Cm)                                                                                 \
-    k_accumulate<D, Cm><<<grid, ACC_THREADS, 0, s>>>(spos, sidx, packed, n_valid, sc->nodes, sc->bvh_tris, P, \
-                                                    mp->values, mp->max_bits, mp->counters, ctx->dev_err, dbg)
-        if (debug && compact) GM_LAUNCH_ACC(true, true);
-        else if (debug) GM_LAUNCH_ACC(true, false);
-        else if (compact) GM_LAUNCH_ACC(false, true);
-        else GM_LAUNCH_ACC(false, false);
+        const bool wide = !(prm->flags & GM_F_BINARY_BVH) && sc->nodes4;
+        const bool occ4 = (prm->flags & GM_F_REGCAP64) != 0;
+        const float4* tree = wide ? sc->nodes4 : sc->nodes;
+#define GM_LAUNCH_ACC(D, Cm, Wd, Mb)                                                                          \
+    k_accumulate<D, Cm, Wd, Mb><<<grid, ACC_THREADS, 0, s>>>(spos, sidx, packed, n_valid, tree, sc->bvh_tris, \
+                                                            P, mp->values, mp->max_bits, mp->counters,        \
+                                                            ctx->dev_err, dbg)
+        const int code = (compact ? 1 : 0) | (wide ? 2 : 0) | (occ4 ? 4 : 0);
+        if (debug) {
+            switch (code & 3) {
+                case 0: GM_LAUNCH_ACC(true, false, false, 3); break;
+                case 1: GM_LAUNCH_ACC(true, true, false, 3); break;
+                case 2: GM_LAUNCH_ACC(true, false, true, 3); break;
+                default: GM_LAUNCH_ACC(true, true, true, 3); break;
+            }
+        } else {
+            switch (code) {
+                case 0: GM_LAUNCH_ACC(false, false, false, 3); break;
+                case 1: GM_LAUNCH_ACC(false, true, false, 3); break;
+                case 2: GM_LAUNCH_ACC(false, false, true, 3); break;
+                case 3: GM_LAUNCH_ACC(false, true, true, 3); break;
+                case 4: GM_LAUNCH_ACC(false, false, false, 4); break;
+                case 5: GM_LAUNCH_ACC(false, true, false, 4); break;
+                case 6: GM_LAUNCH_ACC(false, false, true, 4); break;
+                default: GM_LAUNCH_ACC(false, true, true, 4); break;
+            }
+        }
 #undef GM_LAUNCH_ACC
         ++launches;
     }

@@ -46,6 +46,11 @@ struct gm_scene {
     float4* nodes = nullptr;         // (n_tris - 1) x 4 float4: child boxes + child links
     float4* bvh_tris = nullptr;      // n_tris x 3 float4 in leaf order, v0.w = global tri id
     uint32_t depth = 0;
+    // 4-wide collapse of the binary tree: the binary nodes at even depth, each holding up to four
+    // children (its grandchildren) as 8 float4: lo.x[4] hi.x[4] lo.y[4] hi.y[4] lo.z[4] hi.z[4]
+    // links[4] (int bits; >= 0 node, < 0 leaf ~slot, INT_MIN empty) and one spare float4
+    float4* nodes4 = nullptr;
+    uint32_t n4 = 0;
     float box_lo[3], box_hi[3];      // world bounds of all vertices
 };
 

@@ -233,6 +233,67 @@ __global__ void k_depth(const int* __restrict__ parent_node, const int* __restri
     atomicMax(depth, d);
 }
 
+// Depth of every internal node (root 0); even-depth nodes become 4-wide nodes.
+__global__ void k_node_depth(const int* __restrict__ parent_node, int n_int, int64_t* __restrict__ flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    int d = 0, p = i;
+    while (p > 0 && d < 4096) {
+        p = parent_node[p];
+        ++d;
+    }
+    flag[i] = (d & 1) == 0 ? 1 : 0;
+}
+
+constexpr int LINK_EMPTY = (int)0x80000000;
+
+__device__ __forceinline__ void child_box(const float* node, int side, float lo[3], float hi[3]) {
+    const float* p = node + 6 * side;
+    lo[0] = p[0]; lo[1] = p[1]; lo[2] = p[2];
+    hi[0] = p[3]; hi[1] = p[4]; hi[2] = p[5];
+}
+
+__global__ void k_collapse4(const float4* __restrict__ nodes, int n_int, const int64_t* __restrict__ incl,
+                            float4* __restrict__ nodes4) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    const int64_t before = i > 0 ? incl[i - 1] : 0;
+    if (incl[i] == before) return;                    // odd depth: absorbed by its parent
+    const int j = (int)before;                        // index of this 4-wide node
+    const float* bn = reinterpret_cast<const float*>(nodes + 4 * i);
+    float lo[4][3], hi[4][3];
+    int link[4];
+    int m = 0;
+    for (int side = 0; side < 2; ++side) {
+        const int c = __float_as_int(bn[12 + side]);
+        if (c < 0) {
+            child_box(bn, side, lo[m], hi[m]);
+            link[m++] = c;
+        } else {
+            const float* cn = reinterpret_cast<const float*>(nodes + 4 * c);
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const int g = __float_as_int(cn[12 + s2]);
+                child_box(cn, s2, lo[m], hi[m]);
+                link[m++] = g < 0 ? g : (int)(g > 0 ? incl[g - 1] : 0);
+            }
+        }
+    }
+    for (; m < 4; ++m) {
+        for (int k = 0; k < 3; ++k) lo[m][k] = hi[m][k] = 1e30f;   // a box no segment reaches
+        link[m] = LINK_EMPTY;
+    }
+    float4* o = nodes4 + 8 * (size_t)j;
+    o[0] = make_float4(lo[0][0], lo[1][0], lo[2][0], lo[3][0]);
+    o[1] = make_float4(hi[0][0], hi[1][0], hi[2][0], hi[3][0]);
+    o[2] = make_float4(lo[0][1], lo[1][1], lo[2][1], lo[3][1]);
+    o[3] = make_float4(hi[0][1], hi[1][1], hi[2][1], hi[3][1]);
+    o[4] = make_float4(lo[0][2], lo[1][2], lo[2][2], lo[3][2]);
+    o[5] = make_float4(hi[0][2], hi[1][2], hi[2][2], hi[3][2]);
+    o[6] = make_float4(__int_as_float(link[0]), __int_as_float(link[1]), __int_as_float(link[2]),
+                       __int_as_float(link[3]));
+    o[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 }  // namespace
 
 extern "C" gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes,
@@ -344,8 +405,7 @@ extern "C" gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uin
         (e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return fail(gm_cuda_error(e, "gm_build_scene"));
-    for (void* p : tmp) cudaFreeAsync(p, s);
-    tmp.clear();
+    int* parent_node_keep = parent_node;
     if (herr == GM_DEV_BAD_INDEX) {
         cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), s);
         return fail(gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene: a vertex index is out of range"));
@@ -363,6 +423,30 @@ extern "C" gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uin
             return fail(gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene: non-finite vertex"));
     }
     sc->depth = nt > 1 ? hdepth : 0;
+    if (sc->depth > 64)
+        return fail(gm_set_error(GM_ERR_UNSUPPORTED, "gm_build_scene: BVH deeper than 64 levels (" +
+                                                         std::to_string(sc->depth) + ")"));
+    if (nt > 1) {
+        const uint32_t n_int = nt - 1;
+        int64_t* incl = nullptr;
+        TMP_ALLOC(incl, sizeof(int64_t) * n_int);
+        k_node_depth<<<gm_div_up(n_int, 256), 256, 0, s>>>(parent_node_keep, (int)n_int, incl);
+        launches = 1;
+        if ((st = gm_inclusive_scan_i64(incl, n_int, s, &launches)) != GM_OK) return fail(st);
+        int64_t n4 = 0;
+        if ((e = cudaMemcpyAsync(&n4, incl + (n_int - 1), sizeof(int64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return fail(gm_cuda_error(e, "gm_build_scene (4-wide count)"));
+        sc->n4 = (uint32_t)n4;
+        SC_ALLOC(sc->nodes4, sizeof(float4) * 8 * (size_t)sc->n4);
+        k_collapse4<<<gm_div_up(n_int, 256), 256, 0, s>>>(sc->nodes, (int)n_int, incl, sc->nodes4);
+        ++launches;
+        ctx->launches += launches;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_build_scene collapse"));
+    }
+    for (void* p : tmp) cudaFreeAsync(p, s);
+    tmp.clear();
     *out = sc;
     return GM_OK;
 #undef SC_ALLOC
@@ -414,6 +498,7 @@ extern "C" void gm_scene_free(gm_scene* sc) {
     cudaFree(sc->tri_mesh);
     cudaFree(sc->mesh_object);
     cudaFree(sc->nodes);
+    cudaFree(sc->nodes4);
     cudaFree(sc->bvh_tris);
     delete sc;
 }

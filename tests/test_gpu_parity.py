@@ -300,15 +300,19 @@ def test_paper_scene_full_size_sampled(G, ctx, pipe):
     _check_density(gpu[which], d, ora["amb"][0], ora["sens"][0] * dpos)
 
 
-def test_compacted_and_in_place_tracing_agree_bit_for_bit(G, ctx, pipe):
-    """The per-warp ray queue only reorders which lane traces which ray; each sample still gets
-    its additions in fixation order, so maps and recorded pairs are identical."""
+@pytest.mark.parametrize("other", ["in_place", "binary_tree"])
+def test_accumulate_variants_agree_bit_for_bit(G, ctx, pipe, other):
+    """The per-warp ray queue only reorders which lane traces which ray, and the 4-wide tree
+    only skips intermediate boxes (every box is conservative, so every hitting triangle is
+    reached either way); each sample still gets its additions in fixation order, so maps and
+    recorded pairs are identical."""
+    flag = G.GM_F_NO_COMPACT if other == "in_place" else G.GM_F_BINARY_BVH
     s5 = synth.session(5)
     s5.fixations = s5.fixations.subset(slice(0, 150))
     cap = 4_000_000
     for w in (synth.tiny_sphere(), s5):
         a = pipe.run(ctx, w, normalize=False, flags=G.GM_F_DEBUG_PAIRS, debug_pair_cap=cap)
-        b = pipe.run(ctx, w, normalize=False, flags=G.GM_F_DEBUG_PAIRS | G.GM_F_NO_COMPACT, debug_pair_cap=cap)
+        b = pipe.run(ctx, w, normalize=False, flags=G.GM_F_DEBUG_PAIRS | flag, debug_pair_cap=cap)
         va, vb = pipe.map_array(a)[0], pipe.map_array(b)[0]
         pa, pb = G.gm_map_debug_pairs(a.map, cap), G.gm_map_debug_pairs(b.map, cap)
         a.free()
