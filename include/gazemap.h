@@ -87,7 +87,7 @@ enum {
     GM_F_DEBUG_PAIRS = 2,   /* record in-cone pairs (sample, fixation, visible, weight) */
     GM_F_NO_REORDER = 4,    /* process samples in stored order (no spatial work order) */
     GM_F_NO_COMPACT = 8,    /* trace each lane's in-cone rays in place (no per-warp ray queue) */
-    GM_F_BINARY_BVH = 16,   /* traverse the binary tree instead of its 4-wide collapse */
+    GM_F_WIDE_BVH = 16,     /* traverse the 4-wide collapse of the tree instead of the binary tree */
     GM_F_REGCAP64 = 32      /* cap the accumulation kernel at 64 registers (4 blocks per SM) */
 };
 

@@ -28,31 +28,9 @@
 
 #include "gm_internal.cuh"
 
+#include "gm_trace.cuh"
+
 namespace {
-
-constexpr int ACC_THREADS = 256;
-constexpr int SPT = 4;            // samples per thread
-constexpr int STACK = 64;         // binary traversal stack (the build refuses trees deeper than 64)
-constexpr int STACK4 = 96;        // 4-wide traversal stack: at most 3 pushes per level, <= 32 levels
-constexpr int LINK_EMPTY = (int)0x80000000;
-
-struct AccParams {
-    float C2;     // log2(e) / (2 tan^2 theta)
-    float K;      // (cutoff tan theta)^2
-    float tmax;   // 1 - eps_rel
-    uint32_t ns;
-    uint32_t W;
-    uint32_t nt;
-    uint64_t dbg_cap;
-};
-
-struct DebugOut {
-    uint32_t* sample;
-    uint32_t* fix;
-    uint8_t* vis;
-    float* g;
-    const uint32_t* fix_orig;
-};
 
 // ------------------------------------------------------------------------------------------
 // fixation prep
@@ -102,215 +80,8 @@ __global__ void k_fix_pack(const uint32_t* __restrict__ keys, const uint32_t* __
     orig[i] = f;
 }
 
-// ------------------------------------------------------------------------------------------
-// occlusion: BVH any-hit with a watertight segment/triangle test
-// ------------------------------------------------------------------------------------------
-struct Ray {
-    float3 o, d;
-    float3 idir, oidir;   // slab test: t = lo * idir - o * idir
-    float tmax, tmax_box;
-    int kx, ky, kz;
-    float Sx, Sy, Sz;
-};
-
-__device__ __forceinline__ float comp(const float3& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
-
-__device__ __forceinline__ void make_ray(Ray& R, float3 o, float3 d, float tmax) {
-    R.o = o;
-    R.d = d;
-    R.tmax = tmax;
-    R.tmax_box = tmax * 1.0001f;
-    const float tiny = 1e-20f;
-    float dx = fabsf(d.x) < tiny ? copysignf(tiny, d.x) : d.x;
-    float dy = fabsf(d.y) < tiny ? copysignf(tiny, d.y) : d.y;
-    float dz = fabsf(d.z) < tiny ? copysignf(tiny, d.z) : d.z;
-    R.idir = make_float3(1.f / dx, 1.f / dy, 1.f / dz);
-    R.oidir = make_float3(o.x * R.idir.x, o.y * R.idir.y, o.z * R.idir.z);
-    float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
-    int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
-    int kx = kz == 2 ? 0 : kz + 1;
-    int ky = kx == 2 ? 0 : kx + 1;
-    if (comp(d, kz) < 0.f) {
-        int t = kx;
-        kx = ky;
-        ky = t;
-    }
-    R.kx = kx;
-    R.ky = ky;
-    R.kz = kz;
-    float dkz = comp(d, kz);
-    R.Sx = comp(d, kx) / dkz;
-    R.Sy = comp(d, ky) / dkz;
-    R.Sz = 1.0f / dkz;
-}
-
-// Entry distance of the segment into the box, or +inf when it misses.
-__device__ __forceinline__ float slab(const Ray& R, float lx, float ly, float lz, float hx, float hy, float hz) {
-    float t0x = fmaf(lx, R.idir.x, -R.oidir.x), t1x = fmaf(hx, R.idir.x, -R.oidir.x);
-    float t0y = fmaf(ly, R.idir.y, -R.oidir.y), t1y = fmaf(hy, R.idir.y, -R.oidir.y);
-    float t0z = fmaf(lz, R.idir.z, -R.oidir.z), t1z = fmaf(hz, R.idir.z, -R.oidir.z);
-    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.f));
-    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), R.tmax_box));
-    return tn <= tf ? tn : INFINITY;
-}
-
-// Woop, Benthin, Wald, "Watertight ray/triangle intersection", JCGT 2(1), 2013. Edge functions
-// are evaluated without fused multiply-add so that a shared edge gives exactly opposite values
-// in its two triangles (no ray slips between them).
-__device__ __forceinline__ bool tri_hit(const Ray& R, float4 a, float4 b, float4 c) {
-    float3 A = make_float3(a.x - R.o.x, a.y - R.o.y, a.z - R.o.z);
-    float3 B = make_float3(b.x - R.o.x, b.y - R.o.y, b.z - R.o.z);
-    float3 C = make_float3(c.x - R.o.x, c.y - R.o.y, c.z - R.o.z);
-    float Akz = comp(A, R.kz), Bkz = comp(B, R.kz), Ckz = comp(C, R.kz);
-    float Ax = __fsub_rn(comp(A, R.kx), __fmul_rn(R.Sx, Akz));
-    float Ay = __fsub_rn(comp(A, R.ky), __fmul_rn(R.Sy, Akz));
-    float Bx = __fsub_rn(comp(B, R.kx), __fmul_rn(R.Sx, Bkz));
-    float By = __fsub_rn(comp(B, R.ky), __fmul_rn(R.Sy, Bkz));
-    float Cx = __fsub_rn(comp(C, R.kx), __fmul_rn(R.Sx, Ckz));
-    float Cy = __fsub_rn(comp(C, R.ky), __fmul_rn(R.Sy, Ckz));
-    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
-    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
-    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
-    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return false;
-    float det = U + V + W;
-    if (det == 0.f) return false;
-    float T = U * (R.Sz * Akz) + V * (R.Sz * Bkz) + W * (R.Sz * Ckz);
-    return det > 0.f ? (T > 0.f && T < R.tmax * det) : (T < 0.f && T > R.tmax * det);
-}
-
-__device__ __forceinline__ bool leaf_hit(const Ray& R, const float4* __restrict__ tris, int slot, uint32_t own,
-                                         uint32_t& n_tri) {
-    ++n_tri;
-    float4 a = __ldg(&tris[3 * slot]);
-    if (__float_as_uint(a.w) == own) return false;
-    return tri_hit(R, a, __ldg(&tris[3 * slot + 1]), __ldg(&tris[3 * slot + 2]));
-}
-
-// Any-hit traversal of the segment: stack of deferred subtrees, nearer child first (an occluder
-// between the eye and the sample is met sooner), leaves tested as soon as they are reached.
-__device__ bool occluded(const Ray& R, uint32_t own, const float4* __restrict__ nodes,
-                         const float4* __restrict__ tris, uint32_t nt, int* __restrict__ err, uint32_t& n_node,
-                         uint32_t& n_tri) {
-    if (nt < 2) return nt == 1 ? leaf_hit(R, tris, 0, own, n_tri) : false;
-    int stack[STACK];
-    int sp = 0;
-    int node = 0;
-    for (;;) {
-        ++n_node;
-        const float4 n0 = __ldg(&nodes[4 * node + 0]);
-        const float4 n1 = __ldg(&nodes[4 * node + 1]);
-        const float4 n2 = __ldg(&nodes[4 * node + 2]);
-        const float4 n3 = __ldg(&nodes[4 * node + 3]);
-        float tl = slab(R, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
-        float tr = slab(R, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
-        const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
-        if (tl < INFINITY && cl < 0) {
-            if (leaf_hit(R, tris, ~cl, own, n_tri)) return true;
-            tl = INFINITY;
-        }
-        if (tr < INFINITY && cr < 0) {
-            if (leaf_hit(R, tris, ~cr, own, n_tri)) return true;
-            tr = INFINITY;
-        }
-        if (tl < INFINITY && tr < INFINITY) {
-            if (sp >= STACK) {
-                atomicCAS(err, 0, GM_DEV_STACK_OVERFLOW);
-                return true;
-            }
-            const bool left_first = tl <= tr;
-            stack[sp++] = left_first ? cr : cl;
-            node = left_first ? cl : cr;
-        } else if (tl < INFINITY) {
-            node = cl;
-        } else if (tr < INFINITY) {
-            node = cr;
-        } else {
-            if (sp == 0) return false;
-            node = stack[--sp];
-        }
-    }
-}
-
-__device__ __forceinline__ void cswap(float& ta, int& la, float& tb, int& lb) {
-    const bool sw = tb < ta;
-    const float t = sw ? tb : ta;
-    const int l = sw ? lb : la;
-    tb = sw ? ta : tb;
-    lb = sw ? la : lb;
-    ta = t;
-    la = l;
-}
-
-// Any-hit traversal of the 4-wide tree: one 128-byte node fetch tests four child boxes; leaf
-// children are tested at once; internal children are visited nearest first (a five-exchange
-// sorting network on the entry distances), the others pushed far-to-near.
-__device__ bool occluded4(const Ray& R, uint32_t own, const float4* __restrict__ nodes4,
-                          const float4* __restrict__ tris, int* __restrict__ err, uint32_t& n_node,
-                          uint32_t& n_tri) {
-    int stack[STACK4];
-    int sp = 0;
-    int node = 0;
-    for (;;) {
-        ++n_node;
-        const float4* N = nodes4 + 8 * node;
-        const float4 lx = __ldg(N + 0), hx = __ldg(N + 1), ly = __ldg(N + 2), hy = __ldg(N + 3);
-        const float4 lz = __ldg(N + 4), hz = __ldg(N + 5), L = __ldg(N + 6);
-        float t0 = slab(R, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x);
-        float t1 = slab(R, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y);
-        float t2 = slab(R, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z);
-        float t3 = slab(R, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w);
-        int c0 = __float_as_int(L.x), c1 = __float_as_int(L.y), c2 = __float_as_int(L.z), c3 = __float_as_int(L.w);
-        if (t0 < INFINITY && c0 < 0) { if (c0 != LINK_EMPTY && leaf_hit(R, tris, ~c0, own, n_tri)) return true; t0 = INFINITY; }
-        if (t1 < INFINITY && c1 < 0) { if (c1 != LINK_EMPTY && leaf_hit(R, tris, ~c1, own, n_tri)) return true; t1 = INFINITY; }
-        if (t2 < INFINITY && c2 < 0) { if (c2 != LINK_EMPTY && leaf_hit(R, tris, ~c2, own, n_tri)) return true; t2 = INFINITY; }
-        if (t3 < INFINITY && c3 < 0) { if (c3 != LINK_EMPTY && leaf_hit(R, tris, ~c3, own, n_tri)) return true; t3 = INFINITY; }
-        cswap(t0, c0, t1, c1);
-        cswap(t2, c2, t3, c3);
-        cswap(t0, c0, t2, c2);
-        cswap(t1, c1, t3, c3);
-        cswap(t1, c1, t2, c2);
-        if (t0 == INFINITY) {
-            if (sp == 0) return false;
-            node = stack[--sp];
-            continue;
-        }
-        const int np = (t1 < INFINITY) + (t2 < INFINITY) + (t3 < INFINITY);
-        if (sp + np > STACK4) {
-            atomicCAS(err, 0, GM_DEV_STACK_OVERFLOW);
-            return true;
-        }
-        if (t3 < INFINITY) stack[sp++] = c3;
-        if (t2 < INFINITY) stack[sp++] = c2;
-        if (t1 < INFINITY) stack[sp++] = c1;
-        node = c0;
-    }
-}
-
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// Warps run independently: fixations are read from global memory (every lane reads the same
-// 32 bytes, served by L1 as a broadcast; the next fixation is fetched while the current one is
-// processed), window maxima are folded per warp, and no block-wide barrier is ever taken, so a
-// warp that traces many rays never holds up the others.
-// COMPACT = false: every lane traces the rays of its own in-cone samples (lanes whose samples
-// are outside the cone idle meanwhile).
-// COMPACT = true: per fixation, the warp gathers its in-cone (sample, weight) pairs into a
-// shared-memory queue and traces them 32 at a time, so every lane works on a ray from the same
-// eye; the compensated sums live in shared memory, one slot per sample, and each slot receives
-// at most one addition per fixation, in fixation order -- the result is bit-identical.
-// WIDE selects the 4-wide tree (occluded4) or the binary one (occluded). MINB is the minimum
-// number of resident blocks per SM the register allocation must allow (3: up to 80 registers,
-// 4: up to 64).
+// One block = ACC_THREADS / 32 independent warp tiles (see warp_tile). MINB is the minimum number
+// of resident blocks per SM the register allocation must allow (3: up to 80 registers, 4: 64).
 template <bool DEBUG, bool COMPACT, bool WIDE, int MINB>
 __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate(
     const float4* __restrict__ spos, const uint32_t* __restrict__ sidx, const float4* __restrict__ fix,
@@ -318,181 +89,17 @@ __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate(
     AccParams P, float* __restrict__ out, unsigned int* __restrict__ max_bits,
     unsigned long long* __restrict__ counters, int* __restrict__ err, DebugOut dbg) {
     constexpr int QN = COMPACT ? ACC_THREADS * SPT : 1;
-    __shared__ float4 wsmp[QN];     // per warp: its 32*SPT samples (x, y, z, own triangle)
+    __shared__ float4 wsmp[QN];     // per warp: its WARP_TILE samples (x, y, z, own triangle)
     __shared__ float2 wacc[QN];     // per warp: (sum, compensation) of each sample
     __shared__ uint16_t qslot[QN];  // per warp: queue of in-cone sample slots
     __shared__ float qg[QN];        // per warp: their weights
-
-    const uint32_t nf = *n_fix_dev;
-    const int lane = threadIdx.x & 31;
-    const int wb = (threadIdx.x >> 5) * 32 * SPT;   // this warp's region in the per-warp arrays
-    const uint32_t base = blockIdx.x * (uint32_t)(ACC_THREADS * SPT) + threadIdx.x;
-
-    float sx[SPT], sy[SPT], sz[SPT], sum[SPT], cmp[SPT];
-    uint32_t own[SPT];
-#pragma unroll
-    for (int k = 0; k < SPT; ++k) {
-        uint32_t j = base + k * ACC_THREADS;
-        // padding lanes hold NaN positions: every cone test on them is false
-        float4 p = j < P.ns ? spos[j] : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, __uint_as_float(0xffffffffu));
-        sx[k] = p.x;
-        sy[k] = p.y;
-        sz[k] = p.z;
-        own[k] = __float_as_uint(p.w);
-        sum[k] = 0.f;
-        cmp[k] = 0.f;
-        if (COMPACT) {
-            wsmp[wb + k * 32 + lane] = p;
-            wacc[wb + k * 32 + lane] = make_float2(0.f, 0.f);
-        }
-    }
-    __syncwarp();
-    unsigned long long n_in = 0, n_vis = 0;
-    uint32_t n_node = 0, n_tri = 0;   // traversal work of this thread (wraps only past 4e9)
-    uint32_t cur = 0xffffffffu;
-
-    auto flush = [&](uint32_t w) {
-        float m = 0.f;
-        if (COMPACT) __syncwarp();
-#pragma unroll
-        for (int k = 0; k < SPT; ++k) {
-            if (COMPACT) {
-                sum[k] = wacc[wb + k * 32 + lane].x;
-                wacc[wb + k * 32 + lane] = make_float2(0.f, 0.f);
-            }
-            uint32_t j = base + k * ACC_THREADS;
-            if (j < P.ns && (P.W == 1 || sum[k] != 0.f)) out[(size_t)w * P.ns + sidx[j]] = sum[k];
-            m = fmaxf(m, sum[k]);
-            sum[k] = 0.f;
-            cmp[k] = 0.f;
-        }
-        if (COMPACT) __syncwarp();
-        m = warp_max(m);
-        if (lane == 0 && m > 0.f) atomicMax(&max_bits[w], __float_as_uint(m));
-    };
-
-    float4 nF0 = nf > 0 ? __ldg(&fix[0]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 nF1 = nf > 0 ? __ldg(&fix[1]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (uint32_t i = 0; i < nf; ++i) {
-        const float4 F0 = nF0, F1 = nF1;
-        if (i + 1 < nf) {
-            nF0 = __ldg(&fix[2 * (i + 1)]);
-            nF1 = __ldg(&fix[2 * (i + 1) + 1]);
-        }
-        const uint32_t win = __float_as_uint(F1.w);
-        if (win != cur) {
-            if (cur != 0xffffffffu) flush(cur);
-            cur = win;
-        }
-        if (COMPACT) {
-            int tot = 0;
-#pragma unroll
-            for (int k = 0; k < SPT; ++k) {
-                const float px = sx[k] - F0.x, py = sy[k] - F0.y, pz = sz[k] - F0.z;
-                const float d1 = fmaf(px, F1.x, fmaf(py, F1.y, pz * F1.z));
-                const float cx = fmaf(py, F1.z, -pz * F1.y);
-                const float cy = fmaf(pz, F1.x, -px * F1.z);
-                const float cz = fmaf(px, F1.y, -py * F1.x);
-                const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-                const float d1s = d1 * d1;
-                const bool in = d1 > 0.f && c2 <= P.K * d1s;
-                const unsigned m = __ballot_sync(0xffffffffu, in);
-                if (in) {
-                    const int pos = tot + __popc(m & gm_lanemask_lt());
-                    qslot[wb + pos] = (uint16_t)(k * 32 + lane);
-                    qg[wb + pos] = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
-                }
-                tot += __popc(m);
-            }
-            if (tot == 0) continue;
-            __syncwarp();
-            for (int b = 0; b < tot; b += 32) {
-                const int e = b + lane;
-                if (e < tot) {
-                    const int slot = qslot[wb + e];
-                    const float4 sp = wsmp[wb + slot];
-                    const float g = qg[wb + e];
-                    ++n_in;
-                    Ray R;
-                    make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(sp.x - F0.x, sp.y - F0.y, sp.z - F0.z),
-                             P.tmax);
-                    const bool vis = WIDE ? !occluded4(R, __float_as_uint(sp.w), nodes, tris, err, n_node, n_tri)
-                                          : !occluded(R, __float_as_uint(sp.w), nodes, tris, P.nt, err, n_node, n_tri);
-                    if (vis) {
-                        ++n_vis;
-                        float2 a = wacc[wb + slot];
-                        const float y = g - a.y;
-                        const float t = a.x + y;
-                        a.y = (t - a.x) - y;
-                        a.x = t;
-                        wacc[wb + slot] = a;
-                    }
-                    if (DEBUG) {
-                        unsigned long long q = atomicAdd(&counters[2], 1ull);
-                        if (q < P.dbg_cap) {
-                            dbg.sample[q] = sidx[blockIdx.x * (uint32_t)(ACC_THREADS * SPT) + (slot >> 5) * ACC_THREADS +
-                                                 (threadIdx.x & ~31) + (slot & 31)];
-                            dbg.fix[q] = dbg.fix_orig[i];
-                            dbg.vis[q] = vis ? 1 : 0;
-                            dbg.g[q] = g;
-                        }
-                    }
-                }
-            }
-            __syncwarp();
-        } else {
-#pragma unroll
-            for (int k = 0; k < SPT; ++k) {
-                const float px = sx[k] - F0.x, py = sy[k] - F0.y, pz = sz[k] - F0.z;
-                const float d1 = fmaf(px, F1.x, fmaf(py, F1.y, pz * F1.z));
-                const float cx = fmaf(py, F1.z, -pz * F1.y);
-                const float cy = fmaf(pz, F1.x, -px * F1.z);
-                const float cz = fmaf(px, F1.y, -py * F1.x);
-                const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-                const float d1s = d1 * d1;
-                if (d1 > 0.f && c2 <= P.K * d1s) {
-                    ++n_in;
-                    Ray R;
-                    make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(px, py, pz), P.tmax);
-                    const bool vis = WIDE ? !occluded4(R, own[k], nodes, tris, err, n_node, n_tri)
-                                          : !occluded(R, own[k], nodes, tris, P.nt, err, n_node, n_tri);
-                    const float g = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
-                    if (vis) {
-                        ++n_vis;
-                        const float y = g - cmp[k];
-                        const float t = sum[k] + y;
-                        cmp[k] = (t - sum[k]) - y;
-                        sum[k] = t;
-                    }
-                    if (DEBUG) {
-                        unsigned long long q = atomicAdd(&counters[2], 1ull);
-                        if (q < P.dbg_cap) {
-                            dbg.sample[q] = sidx[base + k * ACC_THREADS];
-                            dbg.fix[q] = dbg.fix_orig[i];
-                            dbg.vis[q] = vis ? 1 : 0;
-                            dbg.g[q] = g;
-                        }
-                    }
-                }
-            }
-        }
-    }
-    if (cur != 0xffffffffu) flush(cur);
-    else if (P.W == 1) flush(0);   // no fixation at all: window 0 is written as zeros
-    unsigned long long n_nd = n_node, n_tr = n_tri;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        n_in += __shfl_xor_sync(0xffffffffu, n_in, o);
-        n_vis += __shfl_xor_sync(0xffffffffu, n_vis, o);
-        n_nd += __shfl_xor_sync(0xffffffffu, n_nd, o);
-        n_tr += __shfl_xor_sync(0xffffffffu, n_tr, o);
-    }
-    if (lane == 0 && (n_in | n_vis)) {
-        atomicAdd(&counters[0], n_in);
-        atomicAdd(&counters[1], n_vis);
-        atomicAdd(&counters[4], n_nd);
-        atomicAdd(&counters[5], n_tr);
-    }
+    const int warp = threadIdx.x >> 5;
+    const int wb = COMPACT ? warp * WARP_TILE : 0;
+    TileStats st;
+    warp_tile<DEBUG, COMPACT, WIDE>(blockIdx.x * (ACC_THREADS / 32) + warp, spos, sidx, fix, *n_fix_dev, nodes, tris,
+                                    P, out, max_bits, wsmp + wb, wacc + wb, qslot + wb, qg + wb, &counters[2], dbg,
+                                    err, st);
+    warp_stats_commit(st, counters);
 }
 
 __global__ void k_normalize(float* __restrict__ v, uint64_t ns, uint32_t W, const unsigned int* __restrict__ max_bits) {
@@ -658,7 +265,7 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
         }
         const uint32_t grid = gm_div_up(ns, (uint64_t)ACC_THREADS * SPT);
         const bool compact = !(prm->flags & GM_F_NO_COMPACT);
-        const bool wide = !(prm->flags & GM_F_BINARY_BVH) && sc->nodes4;
+        const bool wide = (prm->flags & GM_F_WIDE_BVH) && sc->nodes4;
         const bool occ4 = (prm->flags & GM_F_REGCAP64) != 0;
         const float4* tree = wide ? sc->nodes4 : sc->nodes;
 #define GM_LAUNCH_ACC(D, Cm, Wd, Mb)                                                                          \

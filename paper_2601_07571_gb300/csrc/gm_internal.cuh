@@ -104,6 +104,11 @@ gm_status gm_radix_sort_u64(uint64_t* keys, uint32_t* vals, uint32_t n, int bits
                             int* launches);
 gm_status gm_radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t n, int bits, cudaStream_t s,
                             int* launches);
+// The same sort with caller-provided temporaries: tmp_keys/tmp_vals of n entries and a histogram
+// table of gm_radix_sort_u32_hist_words(n) words. Allocates nothing (usable under graph capture).
+size_t gm_radix_sort_u32_hist_words(uint32_t n);
+gm_status gm_radix_sort_u32_prealloc(uint32_t* keys, uint32_t* vals, uint32_t n, int bits, uint32_t* tmp_keys,
+                                     uint32_t* tmp_vals, uint32_t* hist, cudaStream_t s, int* launches);
 // Inclusive prefix sum of int64 values in place.
 gm_status gm_inclusive_scan_i64(int64_t* data, uint32_t n, cudaStream_t s, int* launches);
 

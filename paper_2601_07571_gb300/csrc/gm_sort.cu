@@ -136,20 +136,12 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(const K* __restrict__ k
     }
 }
 
+// The passes proper, with caller-provided temporaries (n keys, n values, 256 * tiles counters).
 template <typename K>
-gm_status radix_sort(K* keys, uint32_t* vals, uint32_t n, int bits, cudaStream_t s, int* launches) {
-    if (n <= 1 || bits <= 0) return GM_OK;
+cudaError_t radix_passes(K* keys, uint32_t* vals, uint32_t n, int bits, K* k2, uint32_t* v2, uint32_t* hist,
+                         cudaStream_t s, int* launches) {
+    if (n <= 1 || bits <= 0) return cudaSuccess;
     const uint32_t nb = gm_div_up(n, RS_TILE);
-    K* k2 = nullptr;
-    uint32_t *v2 = nullptr, *hist = nullptr;
-    gm_status st = gm_alloc((void**)&k2, sizeof(K) * n, s);
-    if (st == GM_OK) st = gm_alloc((void**)&v2, sizeof(uint32_t) * n, s);
-    if (st == GM_OK) st = gm_alloc((void**)&hist, sizeof(uint32_t) * 256 * (size_t)nb, s);
-    if (st != GM_OK) {
-        if (k2) cudaFreeAsync(k2, s);
-        if (v2) cudaFreeAsync(v2, s);
-        return st;
-    }
     K *ka = keys, *kb = k2;
     uint32_t *va = vals, *vb = v2;
     int passes = 0;
@@ -166,6 +158,24 @@ gm_status radix_sort(K* keys, uint32_t* vals, uint32_t n, int bits, cudaStream_t
         e = cudaMemcpyAsync(keys, ka, sizeof(K) * n, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
     }
+    return e;
+}
+
+template <typename K>
+gm_status radix_sort(K* keys, uint32_t* vals, uint32_t n, int bits, cudaStream_t s, int* launches) {
+    if (n <= 1 || bits <= 0) return GM_OK;
+    const uint32_t nb = gm_div_up(n, RS_TILE);
+    K* k2 = nullptr;
+    uint32_t *v2 = nullptr, *hist = nullptr;
+    gm_status st = gm_alloc((void**)&k2, sizeof(K) * n, s);
+    if (st == GM_OK) st = gm_alloc((void**)&v2, sizeof(uint32_t) * n, s);
+    if (st == GM_OK) st = gm_alloc((void**)&hist, sizeof(uint32_t) * 256 * (size_t)nb, s);
+    if (st != GM_OK) {
+        if (k2) cudaFreeAsync(k2, s);
+        if (v2) cudaFreeAsync(v2, s);
+        return st;
+    }
+    cudaError_t e = radix_passes<K>(keys, vals, n, bits, k2, v2, hist, s, launches);
     cudaFreeAsync(k2, s);
     cudaFreeAsync(v2, s);
     cudaFreeAsync(hist, s);
@@ -245,6 +255,15 @@ gm_status gm_radix_sort_u64(uint64_t* keys, uint32_t* vals, uint32_t n, int bits
 
 gm_status gm_radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t n, int bits, cudaStream_t s, int* launches) {
     return radix_sort<uint32_t>(keys, vals, n, std::min(bits, 32), s, launches);
+}
+
+size_t gm_radix_sort_u32_hist_words(uint32_t n) { return 256 * (size_t)gm_div_up(n, RS_TILE); }
+
+gm_status gm_radix_sort_u32_prealloc(uint32_t* keys, uint32_t* vals, uint32_t n, int bits, uint32_t* tmp_keys,
+                                     uint32_t* tmp_vals, uint32_t* hist, cudaStream_t s, int* launches) {
+    cudaError_t e = radix_passes<uint32_t>(keys, vals, n, std::min(bits, 32), tmp_keys, tmp_vals, hist, s, launches);
+    if (e != cudaSuccess) return gm_cuda_error(e, "radix sort");
+    return GM_OK;
 }
 
 gm_status gm_inclusive_scan_i64(int64_t* data, uint32_t n, cudaStream_t s, int* launches) {
