@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gazemap", "reference"], default="gazemap")
-    ap.add_argument("--workload", choices=["paper_scene", "tiny_sphere"], default="paper_scene")
+    ap.add_argument("--workload", choices=["paper_scene", "tiny_sphere", "batched"], default="paper_scene")
+    ap.add_argument("--sessions", type=int, default=64, help="sessions of the batched workload")
     ap.add_argument("--fixations", type=int, default=0, help="use only the first N fixations (profiling)")
     ap.add_argument("--flags", type=int, default=0, help="extra GM_F_* accumulation flags (variant A/B runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -170,10 +171,94 @@ def reference_arm(args):
 # ---------------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------------
+def batched_arm(args):
+    """64 independent sessions (5k-300k tris, 500-20k fixations, 1e3-5e4 samples/m^2, log-uniform):
+    the plain form (one gm_accumulate_fixations per session, back to back on one stream) against
+    the batched form (one replay of the autotuned, graph-captured persistent plan). Scenes and
+    samples are built before timing; both forms include the fixation prep and normalisation."""
+    import torch
+    import synth
+    from paper_2601_07571_gb300 import build as B
+    B.build()
+    import paper_2601_07571_gb300 as G
+    from paper_2601_07571_gb300 import pipeline
+    torch.cuda.set_device(0)
+    ws = synth.batched_sessions(args.sessions)
+    ctx = G.gm_create(0)
+    stream = torch.cuda.current_stream()
+    hs = []
+    for w in ws:
+        sc = G.gm_build_scene(ctx, pipeline.mesh_args(w, to_device=True), stream)
+        sm = G.gm_sample_surface(sc, [m.density for m in w.meshes], w.seed, w.session, stream)
+        hs.append((sc, sm, *pipeline.fixation_args(w.fixations, to_device=True)))
+    prm = pipeline.params_of(ws[0], normalize=True)
+    pairs = sum(G.gm_samples_info(h[1]) * w.fixations.n for h, w in zip(hs, ws))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def plain_once():
+        maps = [G.gm_accumulate_fixations(h[0], h[1], *h[2:], prm, stream) for h in hs]
+        return maps
+
+    for _ in range(args.warmup):
+        for m in plain_once():
+            G.gm_map_free(m)
+    plain_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        maps = plain_once()
+        e1.record(stream)
+        e1.synchronize()
+        plain_t.append(e0.elapsed_time(e1))
+        for m in maps:
+            G.gm_map_free(m)
+    b = G.gm_batch_create(ctx, hs, prm, stream)
+    flags, tune_ms = G.gm_batch_autotune(b, stream)
+    for _ in range(args.warmup):
+        G.gm_batch_run(b, stream)
+    torch.cuda.synchronize()
+    l0 = G.gm_ctx_launches(ctx)
+    batch_t = []
+    clocks = ClockSampler()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.gm_batch_run(b, stream)
+        e1.record(stream)
+        e1.synchronize()
+        batch_t.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    launches = G.gm_ctx_launches(ctx) - l0
+    info = G.gm_batch_info(b)
+    ms = sum(batch_t) / len(batch_t)
+    pms = sum(plain_t) / len(plain_t)
+    line = {"metric": METRIC, "value": pairs / (ms * 1e-3), "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched_{len(ws)}_sessions", "sessions": len(ws), "pairs_per_step": int(pairs),
+                       "work_items": info["n_work_items"], "variant_flags": flags,
+                       "l2": "flushed between steps (256 MiB write)", "inputs": "device-resident"},
+            "plain_form": {"value": pairs / (pms * 1e-3), "ms_per_step": pms,
+                           "form": "one gm_accumulate_fixations per session"},
+            "batched_over_plain": pms / ms, "gpu_launches": int(launches), "clocks": clk}
+    G.gm_batch_free(b)
+    for sc, sm, *_ in hs:
+        G.gm_samples_free(sm)
+        G.gm_scene_free(sc)
+    G.gm_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.workload == "batched":
+        batched_arm(args)
         return
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -37,6 +37,7 @@ typedef struct gm_scene gm_scene;
 typedef struct gm_samples gm_samples;
 typedef struct gm_map gm_map;
 typedef struct gm_field gm_field;
+typedef struct gm_batch gm_batch;
 typedef void* gm_stream; /* cudaStream_t */
 
 typedef enum {
@@ -203,6 +204,48 @@ const float* gm_map_device_values(const gm_map* map);
 gm_status gm_map_debug_pairs(const gm_map* map, uint32_t* sample, uint32_t* fix, uint8_t* visible,
                              float* g, uint64_t cap, uint64_t* n);
 void gm_map_free(gm_map* map);
+
+/* ---- batched sessions (a persistent, graph-captured launch; not in the paper) ------------ */
+
+/* One independent problem: its scene, its samples (built on that scene) and its fixations
+ * (host or device, copied into the plan at creation). */
+typedef struct {
+    gm_scene* scene;
+    gm_samples* samples;
+    gm_fixations fix;
+} gm_session_desc;
+
+/* Plan many sessions of uneven size as one call: all sessions' fixations are staged once; a
+ * work list of warp tiles (32 x 4 consecutive work-order samples of one session) is ordered by
+ * decreasing cost; the fixation prep, a persistent accumulation kernel that pulls work items
+ * from a device counter, and the per-session normalisation are captured into one CUDA graph.
+ * Every session gets its own map (windows as in gm_accumulate_fixations). The variant flags in
+ * params (GM_F_NO_COMPACT, GM_F_WIDE_BVH, GM_F_REGCAP64) pick the kernel; gm_batch_autotune picks
+ * them by measurement. The plan borrows the scenes and samples: free it before them. Scalar
+ * parameters are shared by all sessions. Synchronises `stream` once. */
+gm_status gm_batch_create(gm_ctx* ctx, const gm_session_desc* sessions, uint32_t n_sessions,
+                          const gm_params* params, gm_stream stream, gm_batch** out);
+/* Replay the plan on `stream` (one graph launch; nothing is allocated or copied). */
+gm_status gm_batch_run(gm_batch* batch, gm_stream stream);
+/* Session i's map, owned by the plan and valid until gm_batch_free (refreshed by every run). */
+gm_status gm_batch_map(gm_batch* batch, uint32_t session, gm_map** map);
+/* Plan facts; *last_ms is the device time of the last completed run (0 if none). */
+gm_status gm_batch_info(gm_batch* batch, uint32_t* n_sessions, uint64_t* n_work_items, uint64_t* pairs,
+                        float* last_ms, int32_t* variant_flags);
+/* Time every accumulation variant on the plan, keep the fastest (re-capturing the graph) and
+ * return its flags and time. Cached per size bucket; see gm_autotune_accumulate. */
+gm_status gm_batch_autotune(gm_batch* batch, gm_stream stream, int32_t* best_flags, float* best_ms);
+void gm_batch_free(gm_batch* batch);
+/* One-shot form: plan, run once, hand every session's map to the caller (free each with
+ * gm_map_free). */
+gm_status gm_accumulate_batch(gm_ctx* ctx, const gm_session_desc* sessions, uint32_t n_sessions,
+                              const gm_params* params, gm_stream stream, gm_map** out_per_session);
+/* Pick the fastest accumulation variant for one problem by timing each candidate on its first
+ * 256 fixations; *best_flags gets the GM_F_* variant bits to OR into params->flags. Results are
+ * cached per size bucket (log2 of samples, fixations and triangles) for the process and, when the
+ * environment variable GM_TUNE_CACHE names a file, in that JSON file across processes. */
+gm_status gm_autotune_accumulate(gm_scene* scene, gm_samples* samples, const gm_fixations* fix,
+                                 const gm_params* params, gm_stream stream, int32_t* best_flags, float* best_ms);
 
 /* ---- queries -------------------------------------------------------------------------- */
 

@@ -1,0 +1,644 @@
+// gm_batch.cu -- many independent sessions in one persistent, CUDA-graph-captured launch, and
+// the autotuner that picks the accumulation variant.
+//
+// A session is (scene, samples, fixations); all sessions share the generation parameters. At
+// plan creation every session's fixations are staged into one device buffer and a work list
+// of warp tiles (session, 32*SPT consecutive work-order samples) is built on the host, ordered
+// by decreasing cost (fixations per tile, i.e. longest processing time first). The plan then
+// captures into one CUDA graph: the counter resets, the batched fixation prep (window keys per
+// session, one stable radix sort, packing), the persistent accumulation kernel whose warps pull
+// work items from a global counter until the list is exhausted, and the batched normalisation.
+// gm_batch_run replays the graph: no host work and one launch per call.
+//
+// Autotuning: the candidates are the accumulation variants (per-warp ray queue on/off, binary
+// or 4-wide tree, 80- or 64-register cap). Each is timed on the real data and the fastest is
+// kept; results are cached per size bucket (log2 of samples, fixations, triangles) in memory
+// and in the JSON file named by GM_TUNE_CACHE, if set.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "gm_trace.cuh"
+
+namespace {
+
+struct SessionDev {
+    const float4* spos;
+    const uint32_t* sidx;
+    const float4* fix;        // this session's packed fixations (sorted by window)
+    const uint32_t* n_fix;    // number of valid fixations (device)
+    const float4* nodes;
+    const float4* tris;
+    float* out;
+    unsigned int* max_bits;
+    unsigned long long* counters;
+    uint32_t ns, nt, W, pad;
+};
+
+__global__ void k_bfix_keys(const double* __restrict__ ts, const float* __restrict__ eye,
+                            const float* __restrict__ gaze, const float* __restrict__ dur,
+                            const uint32_t* __restrict__ sess_of, uint32_t nf, double t_begin, double t_end,
+                            double window_s, uint32_t W, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                            uint32_t* __restrict__ n_valid, int* __restrict__ err) {
+    const uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const uint32_t s = sess_of[f];
+    const double t = ts[f];
+    uint32_t w = W;
+    if (t >= t_begin && t < t_end) {
+        const double x = window_s > 0.0 ? floor((t - t_begin) / window_s) : 0.0;
+        if (x >= 0.0 && x < (double)W) w = (uint32_t)x;
+    }
+    const float gx = gaze[3 * f], gy = gaze[3 * f + 1], gz = gaze[3 * f + 2];
+    const bool ok = isfinite(gx) && isfinite(gy) && isfinite(gz) && isfinite(eye[3 * f]) && isfinite(eye[3 * f + 1]) &&
+                    isfinite(eye[3 * f + 2]) && isfinite(dur[f]) && dur[f] >= 0.f && (gx != 0.f || gy != 0.f || gz != 0.f) &&
+                    !isnan(t);
+    if (!ok) {
+        atomicCAS(err, 0, 3);
+        w = W;
+    }
+    keys[f] = s * (W + 1) + w;
+    vals[f] = f;
+    if (w < W) atomicAdd(&n_valid[s], 1u);
+}
+
+__global__ void k_bfix_pack(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                            const float* __restrict__ eye, const float* __restrict__ gaze,
+                            const float* __restrict__ dur, uint32_t nf, uint32_t W, float wnorm,
+                            float4* __restrict__ packed) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const uint32_t f = vals[i];
+    float rx = gaze[3 * f], ry = gaze[3 * f + 1], rz = gaze[3 * f + 2];
+    const float rn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(rx, rx), __fmul_rn(ry, ry)), __fmul_rn(rz, rz)));
+    rx = __fdiv_rn(rx, rn);
+    ry = __fdiv_rn(ry, rn);
+    rz = __fdiv_rn(rz, rn);
+    packed[2 * i + 0] = make_float4(eye[3 * f], eye[3 * f + 1], eye[3 * f + 2], __fmul_rn(dur[f], wnorm));
+    packed[2 * i + 1] = make_float4(rx, ry, rz, __uint_as_float(keys[i] % (W + 1)));
+}
+
+struct AccConst {
+    float C2, K, tmax;
+};
+
+// Persistent: every warp pulls work items (session, warp tile) from `work` until none is left.
+template <bool COMPACT, bool WIDE, int MINB>
+__global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate_batch(const SessionDev* __restrict__ sess,
+                                                                        const uint2* __restrict__ items,
+                                                                        uint32_t n_items, unsigned int* __restrict__ work,
+                                                                        AccConst C, int* __restrict__ err) {
+    constexpr int QN = COMPACT ? ACC_THREADS * SPT : 1;
+    __shared__ float4 wsmp[QN];
+    __shared__ float2 wacc[QN];
+    __shared__ uint16_t qslot[QN];
+    __shared__ float qg[QN];
+    const int lane = threadIdx.x & 31;
+    const int wb = COMPACT ? (threadIdx.x >> 5) * WARP_TILE : 0;
+    const DebugOut dbg{nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(work, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        const uint2 wi = items[it];
+        const SessionDev S = sess[wi.x];
+        AccParams P;
+        P.C2 = C.C2;
+        P.K = C.K;
+        P.tmax = C.tmax;
+        P.ns = S.ns;
+        P.W = S.W;
+        P.nt = S.nt;
+        P.dbg_cap = 0;
+        TileStats st;
+        warp_tile<false, COMPACT, WIDE>(wi.y, S.spos, S.sidx, S.fix, *S.n_fix, S.nodes, S.tris, P, S.out, S.max_bits,
+                                        wsmp + wb, wacc + wb, qslot + wb, qg + wb, nullptr, dbg, err, st);
+        warp_stats_commit(st, S.counters);
+    }
+}
+
+__global__ void k_bnormalize(const SessionDev* __restrict__ sess) {
+    const SessionDev S = sess[blockIdx.y];
+    const uint64_t total = (uint64_t)S.ns * S.W;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+        const float m = __uint_as_float(S.max_bits[i / S.ns]);
+        S.out[i] = m > 0.f ? __fdiv_rn(S.out[i], m) : 0.f;
+    }
+}
+
+// Each map keeps its session's valid-fixation count in counters[3] (read by gm_map_info).
+__global__ void k_bcount(const SessionDev* __restrict__ sess, uint32_t n) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) sess[i].counters[3] = *sess[i].n_fix;
+}
+
+template <bool Cm, bool Wd, int Mb>
+int occupancy_of() {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_accumulate_batch<Cm, Wd, Mb>, ACC_THREADS, 0);
+    return std::max(b, 1);
+}
+
+void launch_batch(int code, int grid, cudaStream_t s, const SessionDev* sess, const uint2* items, uint32_t n_items,
+                  unsigned int* work, AccConst C, int* err) {
+#define GM_B(Cm, Wd, Mb) k_accumulate_batch<Cm, Wd, Mb><<<grid, ACC_THREADS, 0, s>>>(sess, items, n_items, work, C, err)
+    switch (code) {
+        case 0: GM_B(false, false, 3); break;
+        case 1: GM_B(true, false, 3); break;
+        case 2: GM_B(false, true, 3); break;
+        case 3: GM_B(true, true, 3); break;
+        case 4: GM_B(false, false, 4); break;
+        case 5: GM_B(true, false, 4); break;
+        case 6: GM_B(false, true, 4); break;
+        default: GM_B(true, true, 4); break;
+    }
+#undef GM_B
+}
+
+int batch_occupancy(int code) {
+    switch (code) {
+        case 0: return occupancy_of<false, false, 3>();
+        case 1: return occupancy_of<true, false, 3>();
+        case 2: return occupancy_of<false, true, 3>();
+        case 3: return occupancy_of<true, true, 3>();
+        case 4: return occupancy_of<false, false, 4>();
+        case 5: return occupancy_of<true, false, 4>();
+        case 6: return occupancy_of<false, true, 4>();
+        default: return occupancy_of<true, true, 4>();
+    }
+}
+
+// variant code <-> GM_F_* flags
+int code_of_flags(int flags) {
+    return ((flags & GM_F_NO_COMPACT) ? 0 : 1) | ((flags & GM_F_WIDE_BVH) ? 2 : 0) | ((flags & GM_F_REGCAP64) ? 4 : 0);
+}
+int flags_of_code(int code) {
+    return ((code & 1) ? 0 : GM_F_NO_COMPACT) | ((code & 2) ? GM_F_WIDE_BVH : 0) | ((code & 4) ? GM_F_REGCAP64 : 0);
+}
+constexpr int VARIANT_MASK = GM_F_NO_COMPACT | GM_F_WIDE_BVH | GM_F_REGCAP64;
+
+// ---- tuning cache ------------------------------------------------------------------------------
+std::mutex g_tune_mutex;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+std::string bucket_key(const char* kind, uint64_t ns, uint64_t nf, uint64_t nt) {
+    auto lg = [](uint64_t v) { return v ? (int)std::floor(std::log2((double)v)) : -1; };
+    std::ostringstream o;
+    o << kind << ":" << lg(ns) << ":" << lg(nf) << ":" << lg(nt);
+    return o.str();
+}
+
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = std::getenv("GM_TUNE_CACHE");
+    if (!path) return;
+    std::ifstream in(path);
+    std::string line;
+    // one entry per line: "key": flags,
+    while (std::getline(in, line)) {
+        size_t a = line.find('"'), b = line.find('"', a + 1), c = line.find(':', b);
+        if (a == std::string::npos || b == std::string::npos || c == std::string::npos) continue;
+        g_tune[line.substr(a + 1, b - a - 1)] = std::atoi(line.c_str() + c + 1);
+    }
+}
+
+void tune_store_locked() {
+    const char* path = std::getenv("GM_TUNE_CACHE");
+    if (!path) return;
+    std::ofstream out(path);
+    out << "{\n";
+    size_t i = 0;
+    for (auto& kv : g_tune) out << "  \"" << kv.first << "\": " << kv.second << (++i < g_tune.size() ? ",\n" : "\n");
+    out << "}\n";
+}
+
+}  // namespace
+
+struct gm_batch {
+    gm_ctx* ctx = nullptr;
+    uint32_t n = 0;
+    gm_params prm{};
+    int flags = 0;
+    uint32_t W = 1;
+    uint32_t nf_total = 0;
+    uint64_t pairs = 0;
+    std::vector<gm_map*> maps;
+    std::vector<const gm_scene*> scenes;
+    std::vector<uint32_t> fix_off;
+    std::vector<SessionDev> host_sess;
+    SessionDev* sess = nullptr;
+    uint2* items = nullptr;
+    uint32_t n_items = 0;
+    unsigned int* work = nullptr;
+    uint32_t* n_valid = nullptr;
+    float *eye = nullptr, *gaze = nullptr, *dur = nullptr;
+    double* ts = nullptr;
+    uint32_t* sess_of = nullptr;
+    uint32_t *keys = nullptr, *vals = nullptr, *tkeys = nullptr, *tvals = nullptr, *hist = nullptr;
+    float4* packed = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int launches_per_run = 0;
+};
+
+static void batch_release_graph(gm_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// Capture the whole batched call into a graph for the variant in b->flags.
+static gm_status batch_capture(gm_batch* b) {
+    batch_release_graph(b);
+    // the session table points at the tree the variant traverses
+    for (uint32_t i = 0; i < b->n; ++i) {
+        const gm_scene* sc = b->scenes[i];
+        b->host_sess[i].nodes = (b->flags & GM_F_WIDE_BVH) && sc->nodes4 ? sc->nodes4 : sc->nodes;
+    }
+    GM_TRY_CUDA(cudaMemcpy(b->sess, b->host_sess.data(), sizeof(SessionDev) * b->n, cudaMemcpyHostToDevice));
+    cudaStream_t cs;
+    GM_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int launches = 0;
+    const double tan_t = std::tan((double)b->prm.theta_rad);
+    gm_status st = GM_OK;
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(b->work, 0, sizeof(unsigned int), cs);
+        cudaMemsetAsync(b->n_valid, 0, sizeof(uint32_t) * b->n, cs);
+        for (uint32_t i = 0; i < b->n; ++i) {
+            gm_map* m = b->maps[i];
+            cudaMemsetAsync(m->max_bits, 0, sizeof(unsigned int) * m->W, cs);
+            cudaMemsetAsync(m->counters, 0, sizeof(unsigned long long) * 8, cs);
+            if (m->W > 1 && m->ns) cudaMemsetAsync(m->values, 0, sizeof(float) * m->W * m->ns, cs);
+        }
+        if (b->nf_total > 0) {
+            k_bfix_keys<<<gm_div_up(b->nf_total, 256), 256, 0, cs>>>(
+                b->ts, b->eye, b->gaze, b->dur, b->sess_of, b->nf_total, b->prm.t_begin, b->prm.t_end,
+                b->prm.window_s > 0.0 ? b->prm.window_s : 0.0, b->W, b->keys, b->vals, b->n_valid, b->ctx->dev_err);
+            ++launches;
+            const uint64_t kmax = (uint64_t)b->n * (b->W + 1);
+            int bits = 1;
+            while (bits < 32 && (1ull << bits) <= kmax) ++bits;
+            st = gm_radix_sort_u32_prealloc(b->keys, b->vals, b->nf_total, bits, b->tkeys, b->tvals, b->hist, cs,
+                                            &launches);
+            const float wnorm = (float)(1.0 / (tan_t * std::sqrt(2.0 * 3.14159265358979323846)));
+            k_bfix_pack<<<gm_div_up(b->nf_total, 256), 256, 0, cs>>>(b->keys, b->vals, b->eye, b->gaze, b->dur,
+                                                                      b->nf_total, b->W, wnorm, b->packed);
+            ++launches;
+        }
+        if (b->n_items > 0) {
+            AccConst C;
+            C.C2 = (float)(1.4426950408889634 / (2.0 * tan_t * tan_t));
+            C.K = (float)((double)b->prm.cutoff_sigmas * tan_t * (double)b->prm.cutoff_sigmas * tan_t);
+            C.tmax = 1.0f - b->prm.eps_rel;
+            const int code = code_of_flags(b->flags);
+            const int grid = b->ctx->n_sm * batch_occupancy(code);
+            launch_batch(code, grid, cs, b->sess, b->items, b->n_items, b->work, C, b->ctx->dev_err);
+            ++launches;
+        }
+        if (b->prm.normalize) {
+            dim3 g(std::max(1, b->ctx->n_sm * 8 / (int)std::max<uint32_t>(1, b->n)), b->n);
+            k_bnormalize<<<g, 256, 0, cs>>>(b->sess);
+            ++launches;
+        }
+        k_bcount<<<gm_div_up(b->n, 256), 256, 0, cs>>>(b->sess, b->n);
+        ++launches;
+        e = cudaStreamEndCapture(cs, &b->graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    cudaStreamDestroy(cs);
+    if (st != GM_OK) return st;
+    if (e != cudaSuccess) return gm_cuda_error(e, "gm_batch: graph capture");
+    b->launches_per_run = launches;
+    return GM_OK;
+}
+
+extern "C" void gm_batch_free(gm_batch* b) {
+    if (!b) return;
+    batch_release_graph(b);
+    for (gm_map* m : b->maps) gm_map_free(m);
+    cudaFree(b->sess);
+    cudaFree(b->items);
+    cudaFree(b->work);
+    cudaFree(b->n_valid);
+    cudaFree(b->eye);
+    cudaFree(b->gaze);
+    cudaFree(b->dur);
+    cudaFree(b->ts);
+    cudaFree(b->sess_of);
+    cudaFree(b->keys);
+    cudaFree(b->vals);
+    cudaFree(b->tkeys);
+    cudaFree(b->tvals);
+    cudaFree(b->hist);
+    cudaFree(b->packed);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    delete b;
+}
+
+extern "C" gm_status gm_batch_create(gm_ctx* ctx, const gm_session_desc* ss, uint32_t n, const gm_params* prm,
+                                     gm_stream stream, gm_batch** out) {
+    if (!ctx || !ss || !prm || !out || n == 0) return gm_set_error(GM_ERR_INVALID_ARG, "gm_batch_create: null argument");
+    *out = nullptr;
+    if (!(prm->theta_rad > 0.f) || !(prm->theta_rad < 1.5f) || !(prm->cutoff_sigmas > 0.f) ||
+        !(prm->eps_rel >= 0.f && prm->eps_rel < 1.f) || std::isnan(prm->t_begin) || std::isnan(prm->t_end) ||
+        !(prm->t_begin < prm->t_end))
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_batch_create: invalid parameters");
+    uint64_t W = 1;
+    if (prm->window_s > 0.0) {
+        if (!std::isfinite(prm->t_begin) || !std::isfinite(prm->t_end) || !std::isfinite(prm->window_s))
+            return gm_set_error(GM_ERR_INVALID_ARG, "gm_batch_create: windows need a finite interval");
+        W = std::max<uint64_t>(1, (uint64_t)std::ceil((prm->t_end - prm->t_begin) / prm->window_s));
+        if (W > (1u << 20)) return gm_set_error(GM_ERR_UNSUPPORTED, "gm_batch_create: more than 2^20 windows");
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!ss[i].scene || !ss[i].samples || ss[i].samples->scene != ss[i].scene)
+            return gm_set_error(GM_ERR_INVALID_ARG, "gm_batch_create: session " + std::to_string(i) + " is incomplete");
+        if (ss[i].fix.n > 0 && (!ss[i].fix.eye_xyz || !ss[i].fix.gaze_xyz || !ss[i].fix.duration_s || !ss[i].fix.timestamp_s))
+            return gm_set_error(GM_ERR_INVALID_ARG, "gm_batch_create: null fixation array");
+        if ((uint64_t)n * (W + 1) > 0xffffffffull)
+            return gm_set_error(GM_ERR_UNSUPPORTED, "gm_batch_create: sessions x windows exceed 2^32");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    GM_TRY_CUDA(cudaSetDevice(ctx->device));
+    gm_batch* b = new gm_batch();
+    b->ctx = ctx;
+    b->n = n;
+    b->prm = *prm;
+    b->W = (uint32_t)W;
+    b->flags = prm->flags & VARIANT_MASK;
+    auto fail = [&](gm_status st) {
+        cudaStreamSynchronize(s);
+        gm_batch_free(b);
+        return st;
+    };
+    gm_status st;
+    // per-session maps
+    b->fix_off.resize(n + 1, 0);
+    for (uint32_t i = 0; i < n; ++i) {
+        b->fix_off[i + 1] = b->fix_off[i] + ss[i].fix.n;
+        gm_map* m = new gm_map();
+        m->ctx = ctx;
+        m->W = b->W;
+        m->ns = ss[i].samples->n;
+        m->stream = s;
+        m->stats.n_windows = b->W;
+        b->maps.push_back(m);
+        if ((st = gm_alloc((void**)&m->values, sizeof(float) * m->W * (m->ns ? m->ns : 1), s)) != GM_OK) return fail(st);
+        if ((st = gm_alloc((void**)&m->max_bits, sizeof(unsigned int) * m->W, s)) != GM_OK) return fail(st);
+        if ((st = gm_alloc((void**)&m->counters, sizeof(unsigned long long) * 8, s)) != GM_OK) return fail(st);
+        b->pairs += (uint64_t)ss[i].fix.n * m->ns;
+    }
+    b->nf_total = b->fix_off[n];
+    const uint32_t nf = b->nf_total;
+    const size_t nfa = nf ? nf : 1;
+    if ((st = gm_alloc((void**)&b->eye, sizeof(float) * 3 * nfa, s)) != GM_OK ||
+        (st = gm_alloc((void**)&b->gaze, sizeof(float) * 3 * nfa, s)) != GM_OK ||
+        (st = gm_alloc((void**)&b->dur, sizeof(float) * nfa, s)) != GM_OK ||
+        (st = gm_alloc((void**)&b->ts, sizeof(double) * nfa, s)) != GM_OK ||
+        (st = gm_alloc((void**)&b->sess_of, sizeof(uint32_t) * nfa, s)) != GM_OK ||
+        (st = gm_alloc((void**)&b->keys, sizeof(uint32_t) * nfa, s)) != GM_OK ||
+        (st = gm_alloc((void**)&b->vals, sizeof(uint32_t) * nfa, s)) != GM_OK ||
+        (st = gm_alloc((void**)&b->tkeys, sizeof(uint32_t) * nfa, s)) != GM_OK ||
+        (st = gm_alloc((void**)&b->tvals, sizeof(uint32_t) * nfa, s)) != GM_OK ||
+        (st = gm_alloc((void**)&b->hist, sizeof(uint32_t) * gm_radix_sort_u32_hist_words(nf ? nf : 1), s)) != GM_OK ||
+        (st = gm_alloc((void**)&b->packed, sizeof(float4) * 2 * nfa, s)) != GM_OK ||
+        (st = gm_alloc((void**)&b->n_valid, sizeof(uint32_t) * n, s)) != GM_OK ||
+        (st = gm_alloc((void**)&b->work, sizeof(unsigned int), s)) != GM_OK ||
+        (st = gm_alloc((void**)&b->sess, sizeof(SessionDev) * n, s)) != GM_OK)
+        return fail(st);
+    // stage fixations (host or device sources) into the concatenated buffers
+    std::vector<uint32_t> sess_of(nfa, 0);
+    cudaError_t e = cudaSuccess;
+    for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
+        const gm_fixations& f = ss[i].fix;
+        const uint32_t o = b->fix_off[i];
+        for (uint32_t k = 0; k < f.n; ++k) sess_of[o + k] = i;
+        if (f.n == 0) continue;
+        e = cudaMemcpyAsync(b->eye + 3 * o, f.eye_xyz, sizeof(float) * 3 * f.n, cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->gaze + 3 * o, f.gaze_xyz, sizeof(float) * 3 * f.n, cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->dur + o, f.duration_s, sizeof(float) * f.n, cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->ts + o, f.timestamp_s, sizeof(double) * f.n, cudaMemcpyDefault, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->sess_of, sess_of.data(), sizeof(uint32_t) * nfa, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_batch_create: staging"));
+    // session table
+    b->host_sess.resize(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        gm_samples* sm = ss[i].samples;
+        gm_scene* sc = ss[i].scene;
+        SessionDev& d = b->host_sess[i];
+        b->scenes.push_back(sc);
+        d.spos = sm->work_pos ? sm->work_pos : sm->pos;
+        d.sidx = sm->work_idx;
+        d.fix = b->packed + 2 * (size_t)b->fix_off[i];
+        d.n_fix = b->n_valid + i;
+        d.nodes = (b->flags & GM_F_WIDE_BVH) && sc->nodes4 ? sc->nodes4 : sc->nodes;
+        d.tris = sc->bvh_tris;
+        d.out = b->maps[i]->values;
+        d.max_bits = b->maps[i]->max_bits;
+        d.counters = b->maps[i]->counters;
+        d.ns = (uint32_t)sm->n;
+        d.nt = sc->n_tris;
+        d.W = b->W;
+        d.pad = 0;
+        if (sm->n > 0 && !sm->work_idx)
+            return fail(gm_set_error(GM_ERR_INVALID_ARG, "gm_batch_create: samples without a work order"));
+    }
+    e = cudaMemcpyAsync(b->sess, b->host_sess.data(), sizeof(SessionDev) * n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_batch_create: session table"));
+    // work list: longest processing time first
+    std::vector<uint32_t> order(n);
+    std::iota(order.begin(), order.end(), 0u);
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) { return ss[a].fix.n > ss[c].fix.n; });
+    std::vector<uint2> items;
+    for (uint32_t i : order) {
+        const uint32_t tiles = gm_div_up(ss[i].samples->n, WARP_TILE);
+        for (uint32_t t = 0; t < tiles; ++t) items.push_back(make_uint2(i, t));
+    }
+    b->n_items = (uint32_t)items.size();
+    if ((st = gm_alloc((void**)&b->items, sizeof(uint2) * (items.empty() ? 1 : items.size()), s)) != GM_OK) return fail(st);
+    if (!items.empty()) {
+        e = cudaMemcpyAsync(b->items, items.data(), sizeof(uint2) * items.size(), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_batch_create: work list"));
+    }
+    if ((e = cudaEventCreate(&b->ev0)) != cudaSuccess || (e = cudaEventCreate(&b->ev1)) != cudaSuccess)
+        return fail(gm_cuda_error(e, "gm_batch_create: events"));
+    // everything above is stream-ordered on s; the graph replays on any stream after it
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(gm_cuda_error(e, "gm_batch_create"));
+    if ((st = batch_capture(b)) != GM_OK) return fail(st);
+    *out = b;
+    return GM_OK;
+}
+
+extern "C" gm_status gm_batch_run(gm_batch* b, gm_stream stream) {
+    if (!b) return gm_set_error(GM_ERR_INVALID_ARG, "gm_batch_run: null batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    GM_TRY_CUDA(cudaSetDevice(b->ctx->device));
+    GM_TRY_CUDA(cudaEventRecord(b->ev0, s));
+    GM_TRY_CUDA(cudaGraphLaunch(b->exec, s));
+    GM_TRY_CUDA(cudaEventRecord(b->ev1, s));
+    for (gm_map* m : b->maps) m->stream = s;
+    b->ctx->launches += b->launches_per_run;
+    return GM_OK;
+}
+
+extern "C" gm_status gm_batch_info(gm_batch* b, uint32_t* n_sessions, uint64_t* n_items, uint64_t* pairs,
+                                   float* last_ms, int32_t* variant_flags) {
+    if (!b) return gm_set_error(GM_ERR_INVALID_ARG, "gm_batch_info: null batch");
+    if (n_sessions) *n_sessions = b->n;
+    if (n_items) *n_items = b->n_items;
+    if (pairs) *pairs = b->pairs;
+    if (variant_flags) *variant_flags = b->flags;
+    if (last_ms) {
+        *last_ms = 0.f;
+        if (cudaEventQuery(b->ev1) != cudaErrorNotReady) {
+            GM_TRY_CUDA(cudaEventSynchronize(b->ev1));
+            cudaError_t e = cudaEventElapsedTime(last_ms, b->ev0, b->ev1);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                *last_ms = 0.f;
+            }
+        }
+    }
+    return GM_OK;
+}
+
+extern "C" gm_status gm_batch_map(gm_batch* b, uint32_t i, gm_map** out) {
+    if (!b || !out || i >= b->n) return gm_set_error(GM_ERR_INVALID_ARG, "gm_batch_map: bad session index");
+    *out = b->maps[i];
+    return GM_OK;
+}
+
+extern "C" gm_status gm_accumulate_batch(gm_ctx* ctx, const gm_session_desc* ss, uint32_t n, const gm_params* prm,
+                                         gm_stream stream, gm_map** out_per_session) {
+    if (!out_per_session) return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_batch: null output");
+    gm_batch* b = nullptr;
+    GM_TRY(gm_batch_create(ctx, ss, n, prm, stream, &b));
+    gm_status st = gm_batch_run(b, stream);
+    if (st == GM_OK) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) st = gm_cuda_error(e, "gm_accumulate_batch");
+    }
+    if (st != GM_OK) {
+        gm_batch_free(b);
+        return st;
+    }
+    for (uint32_t i = 0; i < n; ++i) out_per_session[i] = b->maps[i];
+    b->maps.clear();  // ownership passes to the caller
+    gm_batch_free(b);
+    return GM_OK;
+}
+
+// ---- autotuning ---------------------------------------------------------------------------------
+
+extern "C" gm_status gm_batch_autotune(gm_batch* b, gm_stream stream, int32_t* best_flags, float* best_ms) {
+    if (!b) return gm_set_error(GM_ERR_INVALID_ARG, "gm_batch_autotune: null batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t ns_tot = 0, nt_tot = 0;
+    for (auto& d : b->host_sess) {
+        ns_tot += d.ns;
+        nt_tot += d.nt;
+    }
+    const std::string key = bucket_key("batch", ns_tot, b->nf_total, nt_tot);
+    int best = -1;
+    float best_t = 0.f;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        tune_load_locked();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) best = it->second;
+    }
+    if (best < 0) {
+        for (int code = 0; code < 8; ++code) {
+            b->flags = flags_of_code(code);
+            GM_TRY(batch_capture(b));
+            float t = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                GM_TRY(gm_batch_run(b, stream));
+                float ms = 0.f;
+                GM_TRY_CUDA(cudaEventSynchronize(b->ev1));
+                GM_TRY_CUDA(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+                t = std::min(t, ms);
+            }
+            if (best < 0 || t < best_t) {
+                best = b->flags;
+                best_t = t;
+            }
+        }
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune[key] = best;
+        tune_store_locked();
+    }
+    b->flags = best;
+    GM_TRY(batch_capture(b));
+    (void)s;
+    (void)best_t;
+    if (best_flags) *best_flags = best;
+    if (best_ms) *best_ms = best_t;
+    return GM_OK;
+}
+
+extern "C" gm_status gm_autotune_accumulate(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, const gm_params* prm,
+                                            gm_stream stream, int32_t* best_flags, float* best_ms) {
+    if (!sc || !sm || !fx || !prm || !best_flags)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_autotune_accumulate: null argument");
+    const std::string key = bucket_key("plain", sm->n, fx->n, sc->n_tris);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        tune_load_locked();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            *best_flags = it->second;
+            if (best_ms) *best_ms = 0.f;
+            return GM_OK;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    gm_fixations sub = *fx;
+    sub.n = std::min<uint32_t>(fx->n, 256);   // a prefix of the fixations is enough to rank variants
+    int best = 0;
+    float best_t = 1e30f;
+    for (int code = 0; code < 8; ++code) {
+        gm_params p = *prm;
+        p.flags = (prm->flags & ~VARIANT_MASK & ~GM_F_DEBUG_PAIRS) | flags_of_code(code) | GM_F_TIMING;
+        float t = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            gm_map* m = nullptr;
+            GM_TRY(gm_accumulate_fixations(sc, sm, &sub, &p, stream, &m));
+            gm_map_stats stt;
+            gm_status st = gm_map_info(m, nullptr, nullptr, &stt);
+            gm_map_free(m);
+            if (st != GM_OK && st != GM_WARN_EMPTY) return st;
+            t = std::min(t, stt.accumulate_ms);
+        }
+        if (t < best_t) {
+            best_t = t;
+            best = flags_of_code(code);
+        }
+    }
+    (void)s;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune[key] = best;
+        tune_store_locked();
+    }
+    *best_flags = best;
+    if (best_ms) *best_ms = best_t;
+    return GM_OK;
+}

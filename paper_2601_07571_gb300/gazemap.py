@@ -37,6 +37,10 @@ class gm_fixations(C.Structure):
                 ("timestamp_s", C.c_void_p), ("n", C.c_uint32)]
 
 
+class gm_session_desc(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("samples", C.c_void_p), ("fix", gm_fixations)]
+
+
 class gm_params(C.Structure):
     _fields_ = [("theta_rad", C.c_float), ("cutoff_sigmas", C.c_float), ("eps_rel", C.c_float),
                 ("t_begin", C.c_double), ("t_end", C.c_double), ("window_s", C.c_double),
@@ -81,6 +85,18 @@ _SIGS = {
     "gm_map_debug_pairs": (C.c_int, [_P, _P, _P, _P, _P, C.c_uint64, C.POINTER(C.c_uint64)]),
     "gm_map_free": (None, [_P]),
     "gm_query_density": (C.c_int, [_P, _P, C.c_int, C.c_uint32, _P, _P, C.c_uint64, _P, _P]),
+    "gm_batch_create": (C.c_int, [_P, C.POINTER(gm_session_desc), C.c_uint32, C.POINTER(gm_params), _P,
+                                  C.POINTER(_P)]),
+    "gm_batch_run": (C.c_int, [_P, _P]),
+    "gm_batch_map": (C.c_int, [_P, C.c_uint32, C.POINTER(_P)]),
+    "gm_batch_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                C.POINTER(C.c_float), C.POINTER(C.c_int32)]),
+    "gm_batch_autotune": (C.c_int, [_P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+    "gm_batch_free": (None, [_P]),
+    "gm_accumulate_batch": (C.c_int, [_P, C.POINTER(gm_session_desc), C.c_uint32, C.POINTER(gm_params), _P,
+                                      C.POINTER(_P)]),
+    "gm_autotune_accumulate": (C.c_int, [_P, _P, C.POINTER(gm_fixations), C.POINTER(gm_params), _P,
+                                         C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
 }
 
 
@@ -281,3 +297,63 @@ def gm_map_free(m) -> None:
 def gm_query_density(m, field, mode: int, window: int, sample_idx, xyz, n: int, out, stream=None) -> None:
     _check(lib().gm_query_density(m, field, int(mode), int(window), _ptr(sample_idx), _ptr(xyz), C.c_uint64(n),
                                   _ptr(out), _stream(stream)))
+
+
+# ---- batched sessions -------------------------------------------------------------------------
+def _session_descs(sessions):
+    """sessions: sequence of (scene, samples, eye, gaze, duration_s, timestamp_s)."""
+    arr = (gm_session_desc * len(sessions))()
+    for d, (sc, sm, eye, gaze, dur, ts) in zip(arr, sessions):
+        d.scene = sc.value if isinstance(sc, C.c_void_p) else sc
+        d.samples = sm.value if isinstance(sm, C.c_void_p) else sm
+        d.fix = gm_fixations(_ptr(eye), _ptr(gaze), _ptr(dur), _ptr(ts), int(eye.shape[0]))
+    return arr
+
+
+def gm_batch_create(ctx, sessions, params: gm_params, stream=None):
+    arr = _session_descs(sessions)
+    h = _P()
+    _check(lib().gm_batch_create(ctx, arr, len(sessions), C.byref(params), _stream(stream), C.byref(h)))
+    return h
+
+
+def gm_batch_run(batch, stream=None) -> None:
+    _check(lib().gm_batch_run(batch, _stream(stream)))
+
+
+def gm_batch_map(batch, i: int):
+    h = _P()
+    _check(lib().gm_batch_map(batch, int(i), C.byref(h)))
+    return h
+
+
+def gm_batch_info(batch):
+    n, items, pairs, ms, fl = C.c_uint32(), C.c_uint64(), C.c_uint64(), C.c_float(), C.c_int32()
+    _check(lib().gm_batch_info(batch, C.byref(n), C.byref(items), C.byref(pairs), C.byref(ms), C.byref(fl)))
+    return dict(n_sessions=n.value, n_work_items=items.value, pairs=pairs.value, last_ms=ms.value,
+                variant_flags=fl.value)
+
+
+def gm_batch_autotune(batch, stream=None):
+    fl, ms = C.c_int32(), C.c_float()
+    _check(lib().gm_batch_autotune(batch, _stream(stream), C.byref(fl), C.byref(ms)))
+    return fl.value, ms.value
+
+
+def gm_batch_free(batch) -> None:
+    lib().gm_batch_free(batch)
+
+
+def gm_accumulate_batch(ctx, sessions, params: gm_params, stream=None):
+    arr = _session_descs(sessions)
+    outs = (_P * len(sessions))()
+    _check(lib().gm_accumulate_batch(ctx, arr, len(sessions), C.byref(params), _stream(stream), outs))
+    return [_P(o) for o in outs]
+
+
+def gm_autotune_accumulate(scene, samples, eye, gaze, duration_s, timestamp_s, params: gm_params, stream=None):
+    fx = gm_fixations(_ptr(eye), _ptr(gaze), _ptr(duration_s), _ptr(timestamp_s), int(eye.shape[0]))
+    fl, ms = C.c_int32(), C.c_float()
+    _check(lib().gm_autotune_accumulate(scene, samples, C.byref(fx), C.byref(params), _stream(stream),
+                                        C.byref(fl), C.byref(ms)))
+    return fl.value, ms.value
