@@ -80,13 +80,16 @@ __global__ void k_fix_pack(const uint32_t* __restrict__ keys, const uint32_t* __
     orig[i] = f;
 }
 
-// One block = ACC_THREADS / 32 independent warp tiles (see warp_tile). MINB is the minimum number
-// of resident blocks per SM the register allocation must allow (3: up to 80 registers, 4: 64).
+// Persistent: every warp pulls warp tiles (WARP_TILE consecutive work-order samples, see
+// warp_tile) from a device counter until all n_tiles are done, so tiles that see many in-cone
+// rays (densely gazed patches) spread over the whole run instead of forming a tail. MINB is the
+// minimum number of resident blocks per SM the register allocation must allow (3: up to 80
+// registers, 4: up to 64).
 template <bool DEBUG, bool COMPACT, bool WIDE, int MINB>
 __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate(
     const float4* __restrict__ spos, const uint32_t* __restrict__ sidx, const float4* __restrict__ fix,
     const uint32_t* __restrict__ n_fix_dev, const float4* __restrict__ nodes, const float4* __restrict__ tris,
-    AccParams P, float* __restrict__ out, unsigned int* __restrict__ max_bits,
+    AccParams P, uint32_t n_tiles, float* __restrict__ out, unsigned int* __restrict__ max_bits,
     unsigned long long* __restrict__ counters, int* __restrict__ err, DebugOut dbg) {
     constexpr int QN = COMPACT ? ACC_THREADS * SPT : 1;
     __shared__ float4 wsmp[QN];     // per warp: its WARP_TILE samples (x, y, z, own triangle)
@@ -94,12 +97,27 @@ __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate(
     __shared__ uint16_t qslot[QN];  // per warp: queue of in-cone sample slots
     __shared__ float qg[QN];        // per warp: their weights
     const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int wb = COMPACT ? warp * WARP_TILE : 0;
+    const uint32_t nf = *n_fix_dev;
+    unsigned int* next = reinterpret_cast<unsigned int*>(&counters[6]);
     TileStats st;
-    warp_tile<DEBUG, COMPACT, WIDE>(blockIdx.x * (ACC_THREADS / 32) + warp, spos, sidx, fix, *n_fix_dev, nodes, tris,
-                                    P, out, max_bits, wsmp + wb, wacc + wb, qslot + wb, qg + wb, &counters[2], dbg,
-                                    err, st);
+    for (;;) {
+        uint32_t tile = 0;
+        if (lane == 0) tile = atomicAdd(next, 1u);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= n_tiles) break;
+        warp_tile<DEBUG, COMPACT, WIDE>(tile, spos, sidx, fix, nf, nodes, tris, P, out, max_bits, wsmp + wb, wacc + wb,
+                                        qslot + wb, qg + wb, &counters[2], dbg, err, st);
+    }
     warp_stats_commit(st, counters);
+}
+
+template <bool D, bool Cm, bool Wd, int Mb>
+int acc_occupancy() {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_accumulate<D, Cm, Wd, Mb>, ACC_THREADS, 0);
+    return b > 0 ? b : 1;
 }
 
 __global__ void k_normalize(float* __restrict__ v, uint64_t ns, uint32_t W, const unsigned int* __restrict__ max_bits) {
@@ -263,16 +281,21 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
             ++launches;
             sidx = ident;
         }
-        const uint32_t grid = gm_div_up(ns, (uint64_t)ACC_THREADS * SPT);
+        const uint32_t n_tiles = gm_div_up(ns, (uint64_t)WARP_TILE);
         const bool compact = !(prm->flags & GM_F_NO_COMPACT);
         const bool wide = (prm->flags & GM_F_WIDE_BVH) && sc->nodes4;
         const bool occ4 = (prm->flags & GM_F_REGCAP64) != 0;
         const float4* tree = wide ? sc->nodes4 : sc->nodes;
-#define GM_LAUNCH_ACC(D, Cm, Wd, Mb)                                                                          \
-    k_accumulate<D, Cm, Wd, Mb><<<grid, ACC_THREADS, 0, s>>>(spos, sidx, packed, n_valid, tree, sc->bvh_tris, \
-                                                            P, mp->values, mp->max_bits, mp->counters,        \
-                                                            ctx->dev_err, dbg)
         const int code = (compact ? 1 : 0) | (wide ? 2 : 0) | (occ4 ? 4 : 0);
+        // persistent grid: every resident block slot once, never more blocks than tiles need
+#define GM_LAUNCH_ACC(D, Cm, Wd, Mb)                                                                           \
+    do {                                                                                                       \
+        const uint32_t grid = std::min<uint32_t>((uint32_t)ctx->n_sm * acc_occupancy<D, Cm, Wd, Mb>(),         \
+                                                 gm_div_up(n_tiles, ACC_THREADS / 32));                        \
+        k_accumulate<D, Cm, Wd, Mb><<<grid, ACC_THREADS, 0, s>>>(spos, sidx, packed, n_valid, tree, sc->bvh_tris, \
+                                                                P, n_tiles, mp->values, mp->max_bits,           \
+                                                                mp->counters, ctx->dev_err, dbg);              \
+    } while (0)
         if (debug) {
             switch (code & 3) {
                 case 0: GM_LAUNCH_ACC(true, false, false, 3); break;

@@ -73,6 +73,7 @@ struct gm_map {
     unsigned int* max_bits = nullptr;  // W (bit pattern of a non-negative float)
     unsigned long long* counters = nullptr;  // [0] in_cone [1] visible [2] debug cursor [3] fixations used
                                              // [4] BVH nodes visited [5] triangles tested
+                                             // [6] next warp tile of the persistent kernel
     uint32_t* dbg_sample = nullptr;
     uint32_t* dbg_fix = nullptr;
     uint8_t* dbg_vis = nullptr;
