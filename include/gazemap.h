@@ -89,7 +89,9 @@ enum {
     GM_F_NO_REORDER = 4,    /* process samples in stored order (no spatial work order) */
     GM_F_NO_COMPACT = 8,    /* trace each lane's in-cone rays in place (no per-warp ray queue) */
     GM_F_WIDE_BVH = 16,     /* traverse the 4-wide collapse of the tree instead of the binary tree */
-    GM_F_REGCAP64 = 32      /* cap the accumulation kernel at 64 registers (4 blocks per SM) */
+    GM_F_REGCAP64 = 32,     /* cap the accumulation kernel at 64 registers (4 blocks per SM) */
+    GM_F_TILE_RUNS = 64,    /* warp tiles of four 32-sample runs spread over 1024 samples (else 128 consecutive) */
+    GM_F_STATIC_TILES = 128 /* one warp tile per warp of a full grid (else warps pull tiles from a counter) */
 };
 
 typedef struct {
@@ -246,6 +248,50 @@ gm_status gm_accumulate_batch(gm_ctx* ctx, const gm_session_desc* sessions, uint
  * environment variable GM_TUNE_CACHE names a file, in that JSON file across processes. */
 gm_status gm_autotune_accumulate(gm_scene* scene, gm_samples* samples, const gm_fixations* fix,
                                  const gm_params* params, gm_stream stream, int32_t* best_flags, float* best_ms);
+
+/* ---- neural density field (a learned stand-in for the map; not in the paper) ------------- */
+
+/* Parameters of the field, FP32, packed in this order: W1 (64 x 64, row = output unit), b1, W2,
+ * b2, W3, b3, W4, b4 (hidden layers), w5 (64), b5 (output). */
+#define GM_FIELD_N_PARAMS 16705
+
+typedef struct {
+    uint32_t steps;   /* Adam steps */
+    uint32_t batch;   /* points per step, drawn by Philox4x32-10(key = seed, counter = (step, i)) mod n */
+    float lr;         /* learning rate at step 0, cosine-decayed ... */
+    float lr_min;     /* ... to this at the last step */
+    uint64_t seed;
+} gm_field_cfg;
+
+/* The field f(x) = softplus(w5 . h4 + b5), h_l = bf16(relu(h_{l-1} bf16(W_l)^T + b_l)),
+ * h0 = bf16(features), features = [x~, sin(2^k pi x~), cos(2^k pi x~), k = 0..9, 0] of
+ * x~ = (x - centre) / (half the largest side of the box [box_lo, box_hi]). Hidden-layer products
+ * run on the tensor cores (BF16 in, FP32 accumulate). init_params: GM_FIELD_N_PARAMS FP32
+ * values (host or device), copied. Adam moments start at zero. */
+gm_status gm_field_create(gm_ctx* ctx, const float* box_lo, const float* box_hi, const float* init_params,
+                          gm_stream stream, gm_field** out);
+/* Train on a map: inputs are the samples' positions, targets the map values of `window` (use a
+ * map accumulated with normalize set, so targets lie in [0, 1]); mean squared error, Adam
+ * (beta 0.9, 0.999, eps 1e-8, bias-corrected). *final_loss (may be NULL) gets the last batch's
+ * mean squared error. Synchronises `stream` once at the end. */
+gm_status gm_field_train(gm_field* field, const gm_samples* samples, const gm_map* map, uint32_t window,
+                         const gm_field_cfg* cfg, gm_stream stream, float* final_loss);
+/* One Adam step on the points xyz[batch_idx[i]] (n x 3 FP32) with targets target[batch_idx[i]];
+ * all device memory; batch_idx NULL draws the batch with Philox as gm_field_train does. */
+gm_status gm_field_step(gm_field* field, const float* xyz, const float* target, uint64_t n,
+                        const uint32_t* batch_idx, uint32_t batch, float lr, gm_stream stream);
+/* Loss (mean squared error) and its gradient (GM_FIELD_N_PARAMS FP32, host or device) on one
+ * batch without updating the parameters; inputs in device memory. */
+gm_status gm_field_loss_grad(gm_field* field, const float* xyz, const float* target, uint64_t n,
+                             const uint32_t* batch_idx, uint32_t batch, float* grad_out, float* loss_out,
+                             gm_stream stream);
+/* Evaluate the field at n points (n x 3 FP32, host or device) into out (host or device). */
+gm_status gm_field_query(const gm_field* field, const float* xyz, uint64_t n, float* out, gm_stream stream);
+/* Copy the FP32 master parameters (GM_FIELD_N_PARAMS) to out (host or device). */
+gm_status gm_field_params(const gm_field* field, float* out, gm_stream stream);
+gm_status gm_field_info(const gm_field* field, uint32_t* n_params, uint32_t* steps_taken, float* last_loss,
+                        float* train_ms);
+void gm_field_free(gm_field* field);
 
 /* ---- queries -------------------------------------------------------------------------- */
 

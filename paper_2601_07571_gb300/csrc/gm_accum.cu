@@ -89,7 +89,7 @@ template <bool DEBUG, bool COMPACT, bool WIDE, int MINB>
 __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate(
     const float4* __restrict__ spos, const uint32_t* __restrict__ sidx, const float4* __restrict__ fix,
     const uint32_t* __restrict__ n_fix_dev, const float4* __restrict__ nodes, const float4* __restrict__ tris,
-    AccParams P, uint32_t n_tiles, float* __restrict__ out, unsigned int* __restrict__ max_bits,
+    AccParams P, uint32_t n_tiles, int persistent, float* __restrict__ out, unsigned int* __restrict__ max_bits,
     unsigned long long* __restrict__ counters, int* __restrict__ err, DebugOut dbg) {
     constexpr int QN = COMPACT ? ACC_THREADS * SPT : 1;
     __shared__ float4 wsmp[QN];     // per warp: its WARP_TILE samples (x, y, z, own triangle)
@@ -102,10 +102,15 @@ __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate(
     const uint32_t nf = *n_fix_dev;
     unsigned int* next = reinterpret_cast<unsigned int*>(&counters[6]);
     TileStats st;
-    for (;;) {
+    for (uint32_t round = 0;; ++round) {
         uint32_t tile = 0;
-        if (lane == 0) tile = atomicAdd(next, 1u);
-        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (persistent) {
+            if (lane == 0) tile = atomicAdd(next, 1u);
+            tile = __shfl_sync(0xffffffffu, tile, 0);
+        } else {
+            if (round > 0) break;
+            tile = blockIdx.x * (ACC_THREADS / 32) + warp;
+        }
         if (tile >= n_tiles) break;
         warp_tile<DEBUG, COMPACT, WIDE>(tile, spos, sidx, fix, nf, nodes, tris, P, out, max_bits, wsmp + wb, wacc + wb,
                                         qslot + wb, qg + wb, &counters[2], dbg, err, st);
@@ -281,7 +286,9 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
             ++launches;
             sidx = ident;
         }
-        const uint32_t n_tiles = gm_div_up(ns, (uint64_t)WARP_TILE);
+        P.group = (prm->flags & GM_F_TILE_RUNS) ? 8u : 1u;
+        const uint32_t n_tiles = gm_div_up(ns, (uint64_t)WARP_TILE * P.group) * P.group;
+        const int persistent = (prm->flags & GM_F_STATIC_TILES) ? 0 : 1;
         const bool compact = !(prm->flags & GM_F_NO_COMPACT);
         const bool wide = (prm->flags & GM_F_WIDE_BVH) && sc->nodes4;
         const bool occ4 = (prm->flags & GM_F_REGCAP64) != 0;
@@ -290,11 +297,13 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
         // persistent grid: every resident block slot once, never more blocks than tiles need
 #define GM_LAUNCH_ACC(D, Cm, Wd, Mb)                                                                           \
     do {                                                                                                       \
-        const uint32_t grid = std::min<uint32_t>((uint32_t)ctx->n_sm * acc_occupancy<D, Cm, Wd, Mb>(),         \
-                                                 gm_div_up(n_tiles, ACC_THREADS / 32));                        \
+        const uint32_t all = gm_div_up(n_tiles, ACC_THREADS / 32);                                            \
+        const uint32_t grid = persistent ? std::min<uint32_t>((uint32_t)ctx->n_sm * acc_occupancy<D, Cm, Wd, Mb>(), \
+                                                              all)                                             \
+                                         : all;                                                                \
         k_accumulate<D, Cm, Wd, Mb><<<grid, ACC_THREADS, 0, s>>>(spos, sidx, packed, n_valid, tree, sc->bvh_tris, \
-                                                                P, n_tiles, mp->values, mp->max_bits,           \
-                                                                mp->counters, ctx->dev_err, dbg);              \
+                                                                P, n_tiles, persistent, mp->values,            \
+                                                                mp->max_bits, mp->counters, ctx->dev_err, dbg); \
     } while (0)
         if (debug) {
             switch (code & 3) {
@@ -429,7 +438,6 @@ extern "C" void gm_map_free(gm_map* mp) {
 extern "C" gm_status gm_query_density(const gm_map* mp, const gm_field* field, gm_query_mode mode, uint32_t window,
                                       const uint32_t* sample_idx, const float* xyz, uint64_t n, float* out,
                                       gm_stream stream) {
-    (void)xyz;
     if (!out && n > 0) return gm_set_error(GM_ERR_INVALID_ARG, "gm_query_density: null output");
     cudaStream_t s = (cudaStream_t)stream;
     if (mode == GM_Q_SAMPLE) {
@@ -461,7 +469,7 @@ extern "C" gm_status gm_query_density(const gm_map* mp, const gm_field* field, g
                             "gm_accumulate_fixations");
     if (mode == GM_Q_FIELD) {
         if (!field) return gm_set_error(GM_ERR_INVALID_ARG, "gm_query_density: GM_Q_FIELD needs a field");
-        return gm_set_error(GM_ERR_UNSUPPORTED, "gm_query_density: neural field queries are not built in this library");
+        return gm_field_query(field, xyz, n, out, stream);
     }
     return gm_set_error(GM_ERR_INVALID_ARG, "gm_query_density: unknown mode");
 }

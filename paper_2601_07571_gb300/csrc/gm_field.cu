@@ -1,0 +1,677 @@
+// gm_field.cu -- the neural density field: a Fourier-feature MLP trained on the maps the plain
+// method produces, answering density queries at arbitrary surface points (not in the paper).
+//
+// Definition (64 features, 4 hidden layers of 64, softplus output):
+//   x~ = (x - c) / h  (c: centre, h: half the largest side of the scene box)
+//   f = [x~, sin(2^k pi x~), cos(2^k pi x~) for k = 0..9, 0]      (3 + 60 + 1 = 64 features)
+//   h0 = bf16(f); h_l = bf16(relu(h_{l-1} bf16(W_l)^T + b_l))  l = 1..4  (FP32 accumulation)
+//   out = softplus(h4 . w5 + b5)                                       (FP32)
+// Training minimises the mean squared error to the normalised map with Adam (FP32 master
+// weights and moments), one fused kernel per step for the forward and backward passes plus one
+// update kernel; every product of the hidden layers runs on the tensor cores as BF16
+// mma.sync.m16n8k16 with FP32 accumulation.
+//
+// Tensor-core data flow: a warp owns 16 points. Its activations stay in registers between
+// layers: the FP32 accumulator fragments of two adjacent n8 tiles, rounded to bf16, are exactly
+// the A fragment of the next k16 step. Weights live in shared memory as bf16 rows of 72 entries
+// (64 + 8 padding), which makes every B-fragment load bank-conflict free. In training, the
+// forward activations are also written transposed to shared memory so that the weight gradients
+// dW_l = dZ_l^T H_{l-1} of the block's 128 points are block-level tensor-core products.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "gm_internal.cuh"
+
+namespace {
+
+constexpr int FW = 64;               // width (features and hidden units)
+constexpr int FD = 4;                // hidden layers
+constexpr int FOCT = 10;             // octaves
+constexpr int WS = 72;               // bf16 row stride of weights in shared memory
+constexpr int TS = 136;              // bf16 row stride of transposed activations (128 points + 8)
+constexpr int NPAR = FD * (FW * FW + FW) + FW + 1;   // 16 705
+constexpr int TRAIN_PTS = 128;       // points per training block (8 warps x 16)
+
+__host__ __device__ constexpr int w_off(int l) { return l * (FW * FW + FW); }
+__host__ __device__ constexpr int b_off(int l) { return l * (FW * FW + FW) + FW * FW; }
+constexpr int W5_OFF = FD * (FW * FW + FW);
+constexpr int B5_OFF = W5_OFF + FW;
+
+struct FieldBox {
+    float cx, cy, cz, inv_h;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Feature `col` of a normalised position.
+__device__ __forceinline__ float feature(const float xt[3], int col) {
+    if (col < 3) return xt[col];
+    if (col >= 63) return 0.f;
+    const int c = col - 3, k = c / 6, r = c % 6;
+    const float y = ldexpf(xt[r % 3], k);   // 2^k x~, exact
+    return r < 3 ? sinpif(y) : cospif(y);
+}
+
+// A fragments (4 k16 chunks) of the 64 features of rows g and g + 8 of a 16-point group.
+__device__ __forceinline__ void encode_frags(const float xa[3], const float xb[3], int t, uint32_t a[4][4]) {
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const int c0 = 16 * kk + 2 * t, c1 = c0 + 8;
+        a[kk][0] = pack_bf16(feature(xa, c0), feature(xa, c0 + 1));
+        a[kk][1] = pack_bf16(feature(xb, c0), feature(xb, c0 + 1));
+        a[kk][2] = pack_bf16(feature(xa, c1), feature(xa, c1 + 1));
+        a[kk][3] = pack_bf16(feature(xb, c1), feature(xb, c1 + 1));
+    }
+}
+
+// acc[j] (n tile j: outputs 8j..8j+7) = bias + A x W^T, W rows in shared memory (stride WS).
+__device__ __forceinline__ void layer_mma(const uint32_t a[4][4], const __nv_bfloat16* __restrict__ W,
+                                          const float* __restrict__ bias, int g, int t, float acc[8][4]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float b0 = bias[8 * j + 2 * t], b1 = bias[8 * j + 2 * t + 1];
+        acc[j][0] = b0;
+        acc[j][1] = b1;
+        acc[j][2] = b0;
+        acc[j][3] = b1;
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const __nv_bfloat16* row = W + (8 * j + g) * WS + 16 * kk + 2 * t;
+            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(row);
+            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(row + 8);
+            mma16816(acc[j], a[kk], b0, b1);
+        }
+    }
+}
+
+// relu, round to bf16 and repack the accumulators as the next layer's A fragments.
+__device__ __forceinline__ void relu_to_frags(const float acc[8][4], uint32_t a[4][4]) {
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const float* p = acc[2 * kk];
+        const float* q = acc[2 * kk + 1];
+        a[kk][0] = pack_bf16(fmaxf(p[0], 0.f), fmaxf(p[1], 0.f));
+        a[kk][1] = pack_bf16(fmaxf(p[2], 0.f), fmaxf(p[3], 0.f));
+        a[kk][2] = pack_bf16(fmaxf(q[0], 0.f), fmaxf(q[1], 0.f));
+        a[kk][3] = pack_bf16(fmaxf(q[2], 0.f), fmaxf(q[3], 0.f));
+    }
+}
+
+__device__ __forceinline__ float frag_elem(const uint32_t a[4][4], int kk, int r, int hi) {
+    const uint32_t v = a[kk][r];
+    const unsigned short s = hi ? (unsigned short)(v >> 16) : (unsigned short)(v & 0xffffu);
+    return __bfloat162float(__ushort_as_bfloat16(s));
+}
+
+// Output layer: z5 of rows g (zr[0]) and g + 8 (zr[1]) from the h4 fragments, all four lanes of
+// a quad end with the full sums.
+__device__ __forceinline__ void output_dot(const uint32_t h[4][4], const float* __restrict__ w5, float b5, int t,
+                                           float zr[2]) {
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const int c0 = 16 * kk + 2 * t, c1 = c0 + 8;
+        s0 = fmaf(frag_elem(h, kk, 0, 0), w5[c0], s0);
+        s0 = fmaf(frag_elem(h, kk, 0, 1), w5[c0 + 1], s0);
+        s0 = fmaf(frag_elem(h, kk, 2, 0), w5[c1], s0);
+        s0 = fmaf(frag_elem(h, kk, 2, 1), w5[c1 + 1], s0);
+        s1 = fmaf(frag_elem(h, kk, 1, 0), w5[c0], s1);
+        s1 = fmaf(frag_elem(h, kk, 1, 1), w5[c0 + 1], s1);
+        s1 = fmaf(frag_elem(h, kk, 3, 0), w5[c1], s1);
+        s1 = fmaf(frag_elem(h, kk, 3, 1), w5[c1 + 1], s1);
+    }
+    s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+    s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+    zr[0] = s0 + b5;
+    zr[1] = s1 + b5;
+}
+
+__device__ __forceinline__ float softplusf(float z) { return z > 30.f ? z : log1pf(expf(z)); }
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.f / (1.f + expf(-z)); }
+
+__device__ __forceinline__ void load_xt(const float* __restrict__ xyz, uint64_t i, uint64_t n, FieldBox B, float xt[3]) {
+    if (i < n) {
+        xt[0] = (xyz[3 * i] - B.cx) * B.inv_h;
+        xt[1] = (xyz[3 * i + 1] - B.cy) * B.inv_h;
+        xt[2] = (xyz[3 * i + 2] - B.cz) * B.inv_h;
+    } else {
+        xt[0] = xt[1] = xt[2] = 0.f;
+    }
+}
+
+// ---- parameter maintenance --------------------------------------------------------------------
+// bf16 copies of the hidden-layer weights: W (row = output) and W^T (row = input), dense 64x64.
+__global__ void k_field_cast(const float* __restrict__ theta, __nv_bfloat16* __restrict__ wbf,
+                             __nv_bfloat16* __restrict__ wtbf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= FD * FW * FW) return;
+    const int l = i / (FW * FW), r = (i / FW) % FW, c = i % FW;
+    const __nv_bfloat16 v = __float2bfloat16_rn(theta[w_off(l) + r * FW + c]);
+    wbf[i] = v;
+    wtbf[l * FW * FW + c * FW + r] = v;
+}
+
+__global__ void k_field_adam(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
+                             float* __restrict__ grad, float lr, float bc1, float bc2,
+                             __nv_bfloat16* __restrict__ wbf, __nv_bfloat16* __restrict__ wtbf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NPAR) return;
+    const float g = grad[i];
+    const float mi = 0.9f * m[i] + 0.1f * g;
+    const float vi = 0.999f * v[i] + 0.001f * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float th = theta[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+    theta[i] = th;
+    grad[i] = 0.f;
+    // keep the bf16 copies of the hidden weights current
+    const int l = i / (FW * FW + FW), o = i % (FW * FW + FW);
+    if (l < FD && o < FW * FW) {
+        const int r = o / FW, c = o % FW;
+        const __nv_bfloat16 b = __float2bfloat16_rn(th);
+        wbf[l * FW * FW + r * FW + c] = b;
+        wtbf[l * FW * FW + c * FW + r] = b;
+    }
+}
+
+// Stage bf16 weights (dense 64 x 64 per layer) into shared memory rows of stride WS.
+__device__ __forceinline__ void stage_weights(const __nv_bfloat16* __restrict__ src, __nv_bfloat16* dst) {
+    for (int i = threadIdx.x; i < FD * FW * FW / 2; i += blockDim.x) {
+        const int e = 2 * i, l = e / (FW * FW), r = (e / FW) % FW, c = e % FW;
+        *reinterpret_cast<uint32_t*>(dst + l * FW * WS + r * WS + c) = reinterpret_cast<const uint32_t*>(src)[i];
+    }
+}
+
+// ---- inference --------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_field_query(const float* __restrict__ xyz, uint64_t n,
+                                                     const __nv_bfloat16* __restrict__ wbf,
+                                                     const float* __restrict__ theta, FieldBox B,
+                                                     float* __restrict__ out) {
+    __shared__ __align__(16) __nv_bfloat16 sW[FD * FW * WS];
+    __shared__ float sb[FD * FW];
+    __shared__ float sw5[FW + 1];
+    stage_weights(wbf, sW);
+    for (int i = threadIdx.x; i < FD * FW; i += blockDim.x) sb[i] = theta[b_off(i / FW) + i % FW];
+    for (int i = threadIdx.x; i <= FW; i += blockDim.x) sw5[i] = theta[W5_OFF + i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint64_t groups = (n + 15) / 16;
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t grp = warp0; grp < groups; grp += nwarps) {
+        const uint64_t ra = grp * 16 + g, rb = ra + 8;
+        float xa[3], xb[3];
+        load_xt(xyz, ra, n, B, xa);
+        load_xt(xyz, rb, n, B, xb);
+        uint32_t a[4][4];
+        encode_frags(xa, xb, t, a);
+        float acc[8][4];
+#pragma unroll 1
+        for (int l = 0; l < FD; ++l) {
+            layer_mma(a, sW + l * FW * WS, sb + l * FW, g, t, acc);
+            relu_to_frags(acc, a);
+        }
+        float z[2];
+        output_dot(a, sw5, sw5[FW], t, z);
+        if (t == 0) {
+            if (ra < n) out[ra] = softplusf(z[0]);
+            if (rb < n) out[rb] = softplusf(z[1]);
+        }
+    }
+}
+
+// ---- training: forward + backward of 128 points per block -------------------------------------
+struct TrainSmem {
+    __nv_bfloat16 W[FD * FW * WS];     // W_l rows (output) for the forward products
+    __nv_bfloat16 WT[FD * FW * WS];    // W_l^T rows (input) for dH = dZ W
+    __nv_bfloat16 HT[FD * FW * TS];    // H_0..H_3 transposed (feature rows, point columns)
+    __nv_bfloat16 DZT[FW * TS];        // dZ_l transposed (output rows, point columns)
+    float b[FD * FW];
+    float w5[FW + 1];
+    float gw5[FW];
+    float gb[FW];
+};
+
+__device__ __forceinline__ void store_frags_T(const uint32_t a[4][4], __nv_bfloat16* T, int p0, int g, int t) {
+    // fragment (rows = points p0 + g, p0 + g + 8; cols = features) -> T[feature][point]
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const int c0 = 16 * kk + 2 * t, c1 = c0 + 8;
+        const uint32_t* v = a[kk];
+        auto put = [&](int col, int row, uint32_t w) {
+            T[col * TS + row] = __ushort_as_bfloat16((unsigned short)(w & 0xffffu));
+            T[(col + 1) * TS + row] = __ushort_as_bfloat16((unsigned short)(w >> 16));
+        };
+        put(c0, p0 + g, v[0]);
+        put(c0, p0 + g + 8, v[1]);
+        put(c1, p0 + g, v[2]);
+        put(c1, p0 + g + 8, v[3]);
+    }
+}
+
+// dW (64 x 64, rows = outputs) += DZT x HT^T over the block's 128 points; each warp one m16 row
+// slab and four n8 tiles; results go to the global gradient with atomics.
+__device__ __forceinline__ void block_weight_grad(const __nv_bfloat16* DZT, const __nv_bfloat16* HTl,
+                                                  float* __restrict__ gW, int warp, int g, int t) {
+    const int m0 = 16 * (warp >> 1), n0 = 32 * (warp & 1);
+    float acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < TRAIN_PTS / 16; ++ks) {
+        const int k0 = 16 * ks + 2 * t;
+        uint32_t a[4];
+        a[0] = *reinterpret_cast<const uint32_t*>(DZT + (m0 + g) * TS + k0);
+        a[1] = *reinterpret_cast<const uint32_t*>(DZT + (m0 + g + 8) * TS + k0);
+        a[2] = *reinterpret_cast<const uint32_t*>(DZT + (m0 + g) * TS + k0 + 8);
+        a[3] = *reinterpret_cast<const uint32_t*>(DZT + (m0 + g + 8) * TS + k0 + 8);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const __nv_bfloat16* row = HTl + (n0 + 8 * j + g) * TS + k0;
+            mma16816(acc[j], a, *reinterpret_cast<const uint32_t*>(row), *reinterpret_cast<const uint32_t*>(row + 8));
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = n0 + 8 * j + 2 * t;
+        atomicAdd(&gW[(m0 + g) * FW + c], acc[j][0]);
+        atomicAdd(&gW[(m0 + g) * FW + c + 1], acc[j][1]);
+        atomicAdd(&gW[(m0 + g + 8) * FW + c], acc[j][2]);
+        atomicAdd(&gW[(m0 + g + 8) * FW + c + 1], acc[j][3]);
+    }
+}
+
+__device__ __forceinline__ uint32_t philox_x(uint32_t c0, uint32_t c1, uint32_t k0, uint32_t k1) {
+    uint32_t c2 = 0, c3 = 0;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c1 = lo1;
+        c3 = lo0;
+        c0 = n0;
+        c2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c0;
+}
+
+// One block: 128 batch points. `pts` are float4 (x, y, z, -) positions or, when stride is 3,
+// packed xyz; targets are FP32. Batch entries come from `idx` or, if null, from Philox
+// (key = seed, counter = (step, i)) modulo n.
+__global__ void __launch_bounds__(256, 1) k_field_train(const float* __restrict__ pts, int stride,
+                                                        const float* __restrict__ target, uint64_t n,
+                                                        const uint32_t* __restrict__ idx, uint32_t batch,
+                                                        uint32_t step, uint2 seed, FieldBox B,
+                                                        const __nv_bfloat16* __restrict__ wbf,
+                                                        const __nv_bfloat16* __restrict__ wtbf,
+                                                        const float* __restrict__ theta, float* __restrict__ grad,
+                                                        float* __restrict__ loss_sum) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    TrainSmem& S = *reinterpret_cast<TrainSmem*>(smraw);
+    stage_weights(wbf, S.W);
+    stage_weights(wtbf, S.WT);
+    for (int i = threadIdx.x; i < FD * FW; i += blockDim.x) S.b[i] = theta[b_off(i / FW) + i % FW];
+    for (int i = threadIdx.x; i <= FW; i += blockDim.x) S.w5[i] = theta[W5_OFF + i];
+    for (int i = threadIdx.x; i < FW; i += blockDim.x) {
+        S.gw5[i] = 0.f;
+        S.gb[i] = 0.f;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int p0 = 16 * warp;                               // this warp's first point in the block
+    const uint32_t e0 = blockIdx.x * TRAIN_PTS + p0 + g, e1 = e0 + 8;   // batch entries
+    auto draw = [&](uint32_t e) -> uint64_t {
+        if (e >= batch) return n;                           // padding row
+        if (idx) return idx[e];
+        return philox_x(step, e, seed.x, seed.y) % (uint32_t)n;
+    };
+    const uint64_t ia = draw(e0), ib = draw(e1);
+    float xa[3], xb[3];
+    auto load = [&](uint64_t i, float x[3]) {
+        if (i < n) {
+            x[0] = (pts[stride * i] - B.cx) * B.inv_h;
+            x[1] = (pts[stride * i + 1] - B.cy) * B.inv_h;
+            x[2] = (pts[stride * i + 2] - B.cz) * B.inv_h;
+        } else {
+            x[0] = x[1] = x[2] = 0.f;
+        }
+    };
+    load(ia, xa);
+    load(ib, xb);
+    // forward, keeping every layer's bf16 input fragments
+    uint32_t h[FD + 1][4][4];
+    encode_frags(xa, xb, t, h[0]);
+    float acc[8][4];
+#pragma unroll
+    for (int l = 0; l < FD; ++l) {
+        store_frags_T(h[l], S.HT + l * FW * TS, p0, g, t);
+        layer_mma(h[l], S.W + l * FW * WS, S.b + l * FW, g, t, acc);
+        relu_to_frags(acc, h[l + 1]);
+    }
+    float z[2];
+    output_dot(h[FD], S.w5, S.w5[FW], t, z);
+    const float inv_b = 1.f / (float)batch;
+    float dz5[2];
+    {
+        const float ya = ia < n ? target[ia] : 0.f, yb = ib < n ? target[ib] : 0.f;
+        const float fa = softplusf(z[0]), fb = softplusf(z[1]);
+        const float ra = e0 < batch ? fa - ya : 0.f, rb = e1 < batch ? fb - yb : 0.f;
+        dz5[0] = 2.f * ra * inv_b * sigmoidf_(z[0]);
+        dz5[1] = 2.f * rb * inv_b * sigmoidf_(z[1]);
+        float l2 = t == 0 ? ra * ra + rb * rb : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, o);
+        if (lane == 0) atomicAdd(loss_sum, l2);
+    }
+    // output layer gradients and dz4 = dz5 w5 (.) [h4 > 0]
+    uint32_t dz[4][4];
+    {
+        float gb5 = t == 0 ? dz5[0] + dz5[1] : 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int c0 = 16 * kk + 2 * t, c1 = c0 + 8;
+            const int cols[4] = {c0, c0 + 1, c1, c1 + 1};
+            float d0[4], d1[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r0 = q < 2 ? 0 : 2, hi = q & 1;
+                const float ha = frag_elem(h[FD], kk, r0, hi), hb = frag_elem(h[FD], kk, r0 + 1, hi);
+                float gsum = dz5[0] * ha + dz5[1] * hb;
+                gsum += __shfl_xor_sync(0xffffffffu, gsum, 4);
+                gsum += __shfl_xor_sync(0xffffffffu, gsum, 8);
+                gsum += __shfl_xor_sync(0xffffffffu, gsum, 16);
+                if (g == 0) atomicAdd(&S.gw5[cols[q]], gsum);
+                d0[q] = ha > 0.f ? dz5[0] * S.w5[cols[q]] : 0.f;
+                d1[q] = hb > 0.f ? dz5[1] * S.w5[cols[q]] : 0.f;
+            }
+            dz[kk][0] = pack_bf16(d0[0], d0[1]);
+            dz[kk][1] = pack_bf16(d1[0], d1[1]);
+            dz[kk][2] = pack_bf16(d0[2], d0[3]);
+            dz[kk][3] = pack_bf16(d1[2], d1[3]);
+        }
+        gb5 += __shfl_xor_sync(0xffffffffu, gb5, 4);
+        gb5 += __shfl_xor_sync(0xffffffffu, gb5, 8);
+        gb5 += __shfl_xor_sync(0xffffffffu, gb5, 16);
+        if (lane == 0) atomicAdd(&grad[B5_OFF], gb5);
+    }
+#pragma unroll
+    for (int l = FD - 1; l >= 0; --l) {
+        // bias gradient of layer l+1 (index l) and dZ_l^T into shared memory
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int c0 = 16 * kk + 2 * t, c1 = c0 + 8;
+            const int cols[4] = {c0, c0 + 1, c1, c1 + 1};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r0 = q < 2 ? 0 : 2, hi = q & 1;
+                float s = frag_elem(dz, kk, r0, hi) + frag_elem(dz, kk, r0 + 1, hi);
+                s += __shfl_xor_sync(0xffffffffu, s, 4);
+                s += __shfl_xor_sync(0xffffffffu, s, 8);
+                s += __shfl_xor_sync(0xffffffffu, s, 16);
+                if (g == 0) atomicAdd(&S.gb[cols[q]], s);
+            }
+        }
+        store_frags_T(dz, S.DZT, p0, g, t);
+        __syncthreads();
+        block_weight_grad(S.DZT, S.HT + l * FW * TS, grad + w_off(l), warp, g, t);
+        for (int i = threadIdx.x; i < FW; i += blockDim.x) {
+            atomicAdd(&grad[b_off(l) + i], S.gb[i]);
+            S.gb[i] = 0.f;
+        }
+        if (l > 0) {
+            // dH_{l-1} = dZ_l W_l, then the relu mask of h_l (the input of this layer)
+            float dh[8][4];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) dh[j][0] = dh[j][1] = dh[j][2] = dh[j][3] = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const __nv_bfloat16* row = S.WT + l * FW * WS + (8 * j + g) * WS + 16 * kk + 2 * t;
+                    mma16816(dh[j], dz[kk], *reinterpret_cast<const uint32_t*>(row),
+                             *reinterpret_cast<const uint32_t*>(row + 8));
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const float* p = dh[2 * kk];
+                const float* q = dh[2 * kk + 1];
+                const float m00 = frag_elem(h[l], kk, 0, 0) > 0.f, m01 = frag_elem(h[l], kk, 0, 1) > 0.f;
+                const float m10 = frag_elem(h[l], kk, 1, 0) > 0.f, m11 = frag_elem(h[l], kk, 1, 1) > 0.f;
+                const float m20 = frag_elem(h[l], kk, 2, 0) > 0.f, m21 = frag_elem(h[l], kk, 2, 1) > 0.f;
+                const float m30 = frag_elem(h[l], kk, 3, 0) > 0.f, m31 = frag_elem(h[l], kk, 3, 1) > 0.f;
+                dz[kk][0] = pack_bf16(p[0] * m00, p[1] * m01);
+                dz[kk][1] = pack_bf16(p[2] * m10, p[3] * m11);
+                dz[kk][2] = pack_bf16(q[0] * m20, q[1] * m21);
+                dz[kk][3] = pack_bf16(q[2] * m30, q[3] * m31);
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < FW; i += blockDim.x) atomicAdd(&grad[W5_OFF + i], S.gw5[i]);
+}
+
+}  // namespace
+
+struct gm_field {
+    gm_ctx* ctx = nullptr;
+    FieldBox box{};
+    float box_lo[3], box_hi[3];
+    float *theta = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *loss = nullptr;
+    __nv_bfloat16 *wbf = nullptr, *wtbf = nullptr;
+    uint32_t t = 0;   // Adam steps taken
+    float last_loss = 0.f;
+    float train_ms = 0.f;
+};
+
+static const size_t kTrainSmem = sizeof(TrainSmem);
+
+extern "C" gm_status gm_field_create(gm_ctx* ctx, const float* box_lo, const float* box_hi, const float* init_params,
+                                     gm_stream stream, gm_field** out) {
+    if (!ctx || !box_lo || !box_hi || !init_params || !out) return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_create: null argument");
+    *out = nullptr;
+    float ext = 0.f;
+    for (int k = 0; k < 3; ++k) {
+        if (!std::isfinite(box_lo[k]) || !std::isfinite(box_hi[k]) || box_hi[k] < box_lo[k])
+            return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_create: invalid box");
+        ext = std::max(ext, box_hi[k] - box_lo[k]);
+    }
+    if (!(ext > 0.f)) return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_create: empty box");
+    cudaStream_t s = (cudaStream_t)stream;
+    GM_TRY_CUDA(cudaSetDevice(ctx->device));
+    gm_field* f = new gm_field();
+    f->ctx = ctx;
+    for (int k = 0; k < 3; ++k) {
+        f->box_lo[k] = box_lo[k];
+        f->box_hi[k] = box_hi[k];
+    }
+    f->box = FieldBox{0.5f * (box_lo[0] + box_hi[0]), 0.5f * (box_lo[1] + box_hi[1]), 0.5f * (box_lo[2] + box_hi[2]),
+                      2.f / ext};
+    gm_status st;
+    auto fail = [&](gm_status e) {
+        gm_field_free(f);
+        return e;
+    };
+    if ((st = gm_alloc((void**)&f->theta, sizeof(float) * NPAR, s)) != GM_OK ||
+        (st = gm_alloc((void**)&f->m, sizeof(float) * NPAR, s)) != GM_OK ||
+        (st = gm_alloc((void**)&f->v, sizeof(float) * NPAR, s)) != GM_OK ||
+        (st = gm_alloc((void**)&f->grad, sizeof(float) * NPAR, s)) != GM_OK ||
+        (st = gm_alloc((void**)&f->loss, sizeof(float) * 4, s)) != GM_OK ||
+        (st = gm_alloc((void**)&f->wbf, sizeof(__nv_bfloat16) * FD * FW * FW, s)) != GM_OK ||
+        (st = gm_alloc((void**)&f->wtbf, sizeof(__nv_bfloat16) * FD * FW * FW, s)) != GM_OK)
+        return fail(st);
+    cudaError_t e = cudaMemcpyAsync(f->theta, init_params, sizeof(float) * NPAR, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->m, 0, sizeof(float) * NPAR, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->v, 0, sizeof(float) * NPAR, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->grad, 0, sizeof(float) * NPAR, s);
+    if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_field_create"));
+    k_field_cast<<<gm_div_up(FD * FW * FW, 256), 256, 0, s>>>(f->theta, f->wbf, f->wtbf);
+    ctx->launches += 1;
+    e = cudaFuncSetAttribute(k_field_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_field_create"));
+    *out = f;
+    return GM_OK;
+}
+
+static gm_status field_grad(gm_field* f, const float* pts, int stride, const float* target, uint64_t n,
+                            const uint32_t* idx, uint32_t batch, uint32_t step, uint64_t seed, cudaStream_t s) {
+    GM_TRY_CUDA(cudaMemsetAsync(f->loss, 0, sizeof(float), s));
+    k_field_train<<<gm_div_up(batch, TRAIN_PTS), 256, kTrainSmem, s>>>(
+        pts, stride, target, n, idx, batch, step, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), f->box, f->wbf,
+        f->wtbf, f->theta, f->grad, f->loss);
+    f->ctx->launches += 1;
+    GM_TRY_CUDA(cudaGetLastError());
+    return GM_OK;
+}
+
+static gm_status field_adam(gm_field* f, float lr, cudaStream_t s) {
+    f->t += 1;
+    const float bc1 = (float)(1.0 - std::pow(0.9, (double)f->t));
+    const float bc2 = (float)(1.0 - std::pow(0.999, (double)f->t));
+    k_field_adam<<<gm_div_up(NPAR, 256), 256, 0, s>>>(f->theta, f->m, f->v, f->grad, lr, bc1, bc2, f->wbf, f->wtbf);
+    f->ctx->launches += 1;
+    GM_TRY_CUDA(cudaGetLastError());
+    return GM_OK;
+}
+
+extern "C" gm_status gm_field_loss_grad(gm_field* f, const float* xyz, const float* target, uint64_t n,
+                                        const uint32_t* batch_idx, uint32_t batch, float* grad_out, float* loss_out,
+                                        gm_stream stream) {
+    if (!f || !xyz || !target || !batch_idx || batch == 0 || n == 0)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_loss_grad: null argument or empty batch");
+    if (!gm_is_device_ptr(xyz) || !gm_is_device_ptr(target) || !gm_is_device_ptr(batch_idx))
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_loss_grad: inputs must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    GM_TRY(field_grad(f, xyz, 3, target, n, batch_idx, batch, 0, 0, s));
+    if (grad_out) GM_TRY(gm_copy_out(grad_out, f->grad, sizeof(float) * NPAR, s));
+    if (loss_out) {
+        float l = 0.f;
+        GM_TRY(gm_copy_out(&l, f->loss, sizeof(float), s));
+        *loss_out = l / (float)batch;
+    }
+    GM_TRY_CUDA(cudaMemsetAsync(f->grad, 0, sizeof(float) * NPAR, s));
+    return GM_OK;
+}
+
+extern "C" gm_status gm_field_step(gm_field* f, const float* xyz, const float* target, uint64_t n,
+                                   const uint32_t* batch_idx, uint32_t batch, float lr, gm_stream stream) {
+    if (!f || !xyz || !target || batch == 0 || n == 0) return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_step: bad argument");
+    if (!gm_is_device_ptr(xyz) || !gm_is_device_ptr(target) || (batch_idx && !gm_is_device_ptr(batch_idx)))
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_step: inputs must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    GM_TRY(field_grad(f, xyz, 3, target, n, batch_idx, batch, f->t, 0, s));
+    return field_adam(f, lr, s);
+}
+
+extern "C" gm_status gm_field_train(gm_field* f, const gm_samples* sm, const gm_map* mp, uint32_t window,
+                                    const gm_field_cfg* cfg, gm_stream stream, float* final_loss) {
+    if (!f || !sm || !mp || !cfg) return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_train: null argument");
+    if (mp->ns != sm->n || window >= mp->W) return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_train: map does not match samples");
+    if (cfg->batch == 0 || cfg->steps == 0 || !(cfg->lr > 0.f) || !(cfg->lr_min >= 0.f) || sm->n == 0)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_train: empty configuration");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    GM_TRY_CUDA(cudaEventCreate(&e0));
+    GM_TRY_CUDA(cudaEventCreate(&e1));
+    cudaEventRecord(e0, s);
+    const float* targets = mp->values + (size_t)window * mp->ns;
+    gm_status st = GM_OK;
+    for (uint32_t k = 0; k < cfg->steps && st == GM_OK; ++k) {
+        const double lr = cfg->steps > 1 ? cfg->lr_min + 0.5 * (cfg->lr - cfg->lr_min) *
+                                                             (1.0 + std::cos(3.14159265358979323846 * k / (cfg->steps - 1)))
+                                         : cfg->lr;
+        st = field_grad(f, reinterpret_cast<const float*>(sm->pos), 4, targets, sm->n, nullptr, cfg->batch, f->t,
+                        cfg->seed, s);
+        if (st == GM_OK) st = field_adam(f, (float)lr, s);
+    }
+    cudaEventRecord(e1, s);
+    if (st == GM_OK) {
+        float l = 0.f;
+        st = gm_copy_out(&l, f->loss, sizeof(float), s);
+        f->last_loss = l / (float)cfg->batch;
+        cudaEventElapsedTime(&f->train_ms, e0, e1);
+        if (final_loss) *final_loss = f->last_loss;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+extern "C" gm_status gm_field_query(const gm_field* f, const float* xyz, uint64_t n, float* out, gm_stream stream) {
+    if (!f || (n > 0 && (!xyz || !out))) return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_query: null argument");
+    if (n == 0) return GM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    void* dx = nullptr;
+    bool ox = false;
+    GM_TRY(gm_stage_to_device(xyz, sizeof(float) * 3 * n, s, &dx, &ox));
+    const bool dev_out = gm_is_device_ptr(out);
+    float* dout = out;
+    gm_status st = GM_OK;
+    if (!dev_out) st = gm_alloc((void**)&dout, sizeof(float) * n, s);
+    if (st == GM_OK) {
+        const uint64_t groups = (n + 15) / 16;
+        const uint32_t grid = (uint32_t)std::min<uint64_t>((groups + 7) / 8, (uint64_t)f->ctx->n_sm * 8);
+        k_field_query<<<grid, 256, 0, s>>>((const float*)dx, n, f->wbf, f->theta, f->box, dout);
+        f->ctx->launches += 1;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) st = gm_cuda_error(e, "gm_field_query");
+        if (!dev_out) {
+            if (st == GM_OK) st = gm_copy_out(out, dout, sizeof(float) * n, s);
+            cudaFreeAsync(dout, s);
+        }
+    }
+    if (ox) cudaFreeAsync(dx, s);
+    return st;
+}
+
+extern "C" gm_status gm_field_params(const gm_field* f, float* out, gm_stream stream) {
+    if (!f || !out) return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_params: null argument");
+    return gm_copy_out(out, f->theta, sizeof(float) * NPAR, (cudaStream_t)stream);
+}
+
+extern "C" gm_status gm_field_info(const gm_field* f, uint32_t* n_params, uint32_t* steps_taken, float* last_loss,
+                                   float* train_ms) {
+    if (!f) return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_info: null field");
+    if (n_params) *n_params = NPAR;
+    if (steps_taken) *steps_taken = f->t;
+    if (last_loss) *last_loss = f->last_loss;
+    if (train_ms) *train_ms = f->train_ms;
+    return GM_OK;
+}
+
+extern "C" void gm_field_free(gm_field* f) {
+    if (!f) return;
+    cudaFree(f->theta);
+    cudaFree(f->m);
+    cudaFree(f->v);
+    cudaFree(f->grad);
+    cudaFree(f->loss);
+    cudaFree(f->wbf);
+    cudaFree(f->wtbf);
+    delete f;
+}

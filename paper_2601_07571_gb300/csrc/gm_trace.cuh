@@ -22,6 +22,10 @@ struct AccParams {
     uint32_t W;
     uint32_t nt;
     uint64_t dbg_cap;
+    // warp tile t covers samples base(t) + k * stride + lane (k < SPT) with group G:
+    // base = (t / G) * WARP_TILE * G + (t % G) * 32, stride = 32 * G. G = 1: 128 consecutive
+    // work-order samples; G = 8: four runs of 32, spread over 1024 samples shared by 8 tiles.
+    uint32_t group = 1;
 };
 
 struct DebugOut {
@@ -250,12 +254,15 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                                           unsigned long long* __restrict__ dbg_cursor, const DebugOut& dbg,
                                           int* __restrict__ err, TileStats& st) {
     const int lane = threadIdx.x & 31;
-    const uint32_t base = tile * (uint32_t)WARP_TILE + lane;
+    const uint32_t G = P.group;
+    const uint32_t stride = 32u * G;
+    const uint32_t base0 = (tile / G) * (uint32_t)WARP_TILE * G + (tile % G) * 32u;
+    const uint32_t base = base0 + lane;
     float sx[SPT], sy[SPT], sz[SPT], sum[SPT], cmp[SPT];
     uint32_t own[SPT];
 #pragma unroll
     for (int k = 0; k < SPT; ++k) {
-        const uint32_t j = base + k * 32;
+        const uint32_t j = base + k * stride;
         // padding lanes hold NaN positions: every cone test on them is false
         const float4 p = j < P.ns ? spos[j]
                                   : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, __uint_as_float(0xffffffffu));
@@ -282,7 +289,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                 sum[k] = wacc[k * 32 + lane].x;
                 wacc[k * 32 + lane] = make_float2(0.f, 0.f);
             }
-            const uint32_t j = base + k * 32;
+            const uint32_t j = base + k * stride;
             if (j < P.ns && (P.W == 1 || sum[k] != 0.f)) out[(size_t)w * P.ns + sidx[j]] = sum[k];
             m = fmaxf(m, sum[k]);
             sum[k] = 0.f;
@@ -353,7 +360,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                     if (DEBUG) {
                         const unsigned long long q = atomicAdd(dbg_cursor, 1ull);
                         if (q < P.dbg_cap) {
-                            dbg.sample[q] = sidx[tile * (uint32_t)WARP_TILE + slot];
+                            dbg.sample[q] = sidx[base0 + (slot >> 5) * stride + (slot & 31)];
                             dbg.fix[q] = dbg.fix_orig[i];
                             dbg.vis[q] = vis ? 1 : 0;
                             dbg.g[q] = g;
@@ -389,7 +396,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                     if (DEBUG) {
                         const unsigned long long q = atomicAdd(dbg_cursor, 1ull);
                         if (q < P.dbg_cap) {
-                            dbg.sample[q] = sidx[base + k * 32];
+                            dbg.sample[q] = sidx[base + k * stride];
                             dbg.fix[q] = dbg.fix_orig[i];
                             dbg.vis[q] = vis ? 1 : 0;
                             dbg.g[q] = g;

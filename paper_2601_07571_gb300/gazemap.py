@@ -17,7 +17,7 @@ from .build import LIB
 GM_OK, GM_ERR_INVALID_ARG, GM_ERR_CUDA, GM_ERR_OOM, GM_ERR_TIMEOUT = 0, 1, 2, 3, 4
 GM_ERR_UNSUPPORTED, GM_ERR_INTERNAL, GM_WARN_EMPTY = 5, 6, 100
 GM_F_TIMING, GM_F_DEBUG_PAIRS, GM_F_NO_REORDER, GM_F_NO_COMPACT, GM_F_WIDE_BVH = 1, 2, 4, 8, 16
-GM_F_REGCAP64 = 32
+GM_F_REGCAP64, GM_F_TILE_RUNS, GM_F_STATIC_TILES = 32, 64, 128
 GM_Q_SAMPLE, GM_Q_PLAIN, GM_Q_FIELD = 0, 1, 2
 
 
@@ -45,6 +45,14 @@ class gm_params(C.Structure):
     _fields_ = [("theta_rad", C.c_float), ("cutoff_sigmas", C.c_float), ("eps_rel", C.c_float),
                 ("t_begin", C.c_double), ("t_end", C.c_double), ("window_s", C.c_double),
                 ("normalize", C.c_int32), ("flags", C.c_int32), ("debug_pair_cap", C.c_uint64)]
+
+
+class gm_field_cfg(C.Structure):
+    _fields_ = [("steps", C.c_uint32), ("batch", C.c_uint32), ("lr", C.c_float), ("lr_min", C.c_float),
+                ("seed", C.c_uint64)]
+
+
+GM_FIELD_N_PARAMS = 16705
 
 
 class gm_map_stats(C.Structure):
@@ -97,6 +105,15 @@ _SIGS = {
                                       C.POINTER(_P)]),
     "gm_autotune_accumulate": (C.c_int, [_P, _P, C.POINTER(gm_fixations), C.POINTER(gm_params), _P,
                                          C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+    "gm_field_create": (C.c_int, [_P, _P, _P, _P, _P, C.POINTER(_P)]),
+    "gm_field_train": (C.c_int, [_P, _P, _P, C.c_uint32, C.POINTER(gm_field_cfg), _P, C.POINTER(C.c_float)]),
+    "gm_field_step": (C.c_int, [_P, _P, _P, C.c_uint64, _P, C.c_uint32, C.c_float, _P]),
+    "gm_field_loss_grad": (C.c_int, [_P, _P, _P, C.c_uint64, _P, C.c_uint32, _P, C.POINTER(C.c_float), _P]),
+    "gm_field_query": (C.c_int, [_P, _P, C.c_uint64, _P, _P]),
+    "gm_field_params": (C.c_int, [_P, _P, _P]),
+    "gm_field_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_float),
+                                C.POINTER(C.c_float)]),
+    "gm_field_free": (None, [_P]),
 }
 
 
@@ -357,3 +374,50 @@ def gm_autotune_accumulate(scene, samples, eye, gaze, duration_s, timestamp_s, p
     _check(lib().gm_autotune_accumulate(scene, samples, C.byref(fx), C.byref(params), _stream(stream),
                                         C.byref(fl), C.byref(ms)))
     return fl.value, ms.value
+
+
+# ---- neural density field ---------------------------------------------------------------------
+def gm_field_create(ctx, box_lo, box_hi, init_params, stream=None):
+    lo = np.ascontiguousarray(box_lo, np.float32)
+    hi = np.ascontiguousarray(box_hi, np.float32)
+    h = _P()
+    _check(lib().gm_field_create(ctx, _ptr(lo), _ptr(hi), _ptr(init_params), _stream(stream), C.byref(h)))
+    return h
+
+
+def gm_field_train(field, samples, m, window: int, steps: int, batch: int, lr: float, lr_min: float, seed: int,
+                   stream=None) -> float:
+    cfg = gm_field_cfg(int(steps), int(batch), float(lr), float(lr_min), int(seed))
+    loss = C.c_float()
+    _check(lib().gm_field_train(field, samples, m, int(window), C.byref(cfg), _stream(stream), C.byref(loss)))
+    return loss.value
+
+
+def gm_field_step(field, xyz, target, n: int, batch_idx, batch: int, lr: float, stream=None) -> None:
+    _check(lib().gm_field_step(field, _ptr(xyz), _ptr(target), C.c_uint64(n), _ptr(batch_idx), int(batch),
+                               float(lr), _stream(stream)))
+
+
+def gm_field_loss_grad(field, xyz, target, n: int, batch_idx, batch: int, grad_out, stream=None) -> float:
+    loss = C.c_float()
+    _check(lib().gm_field_loss_grad(field, _ptr(xyz), _ptr(target), C.c_uint64(n), _ptr(batch_idx), int(batch),
+                                    _ptr(grad_out), C.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def gm_field_query(field, xyz, n: int, out, stream=None) -> None:
+    _check(lib().gm_field_query(field, _ptr(xyz), C.c_uint64(n), _ptr(out), _stream(stream)))
+
+
+def gm_field_params(field, out, stream=None) -> None:
+    _check(lib().gm_field_params(field, _ptr(out), _stream(stream)))
+
+
+def gm_field_info(field):
+    n, t, loss, ms = C.c_uint32(), C.c_uint32(), C.c_float(), C.c_float()
+    _check(lib().gm_field_info(field, C.byref(n), C.byref(t), C.byref(loss), C.byref(ms)))
+    return dict(n_params=n.value, steps=t.value, last_loss=loss.value, train_ms=ms.value)
+
+
+def gm_field_free(field) -> None:
+    lib().gm_field_free(field)

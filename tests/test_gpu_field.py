@@ -1,0 +1,100 @@
+"""The neural density field on the GPU against the FP64 field oracle (which emulates the bf16
+rounding the definition fixes): queries, the loss gradient, one Adam step, and a short training
+run on the tiny sphere's map."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import field as F
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2601_07571_gb300 import build
+    build.build()
+    import paper_2601_07571_gb300 as G
+    ctx = G.gm_create(0)
+    yield G, torch, ctx
+    G.gm_destroy(ctx)
+
+
+BOX_LO, BOX_HI = np.array([-2.0, -1.0, -1.5], np.float32), np.array([2.0, 1.5, 1.0], np.float32)
+
+
+def _points(n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(BOX_LO, BOX_HI, size=(n, 3)).astype(np.float32)
+
+
+def test_field_query_matches_oracle(env):
+    G, torch, ctx = env
+    theta = synth.field_init(11)
+    theta[64 * 64:64 * 64 + 64] = np.random.default_rng(1).normal(0, 0.2, 64)   # some non-zero biases
+    f = G.gm_field_create(ctx, BOX_LO, BOX_HI, theta)
+    x = _points(5000, 2)
+    out = np.empty(len(x), np.float32)
+    G.gm_field_query(f, x, len(x), out)
+    feats = F.features(F.normalise(x.astype(np.float64), BOX_LO, BOX_HI))
+    ref, _ = F.forward(theta.astype(np.float64), feats, emulate_bf16=True)
+    err = np.abs(out - ref)
+    assert err.max() <= 1e-2 * np.abs(ref).max()
+    assert np.median(err / np.maximum(np.abs(ref), 1e-6)) < 2e-3
+    # the same through gm_query_density
+    out2 = np.empty(len(x), np.float32)
+    G.gm_query_density(None, f, G.GM_Q_FIELD, 0, None, x, len(x), out2)
+    assert np.array_equal(out, out2)
+    G.gm_field_free(f)
+
+
+def test_field_gradient_and_adam_step_match_oracle(env):
+    G, torch, ctx = env
+    theta = synth.field_init(12)
+    f = G.gm_field_create(ctx, BOX_LO, BOX_HI, theta)
+    n = 4000
+    x = _points(n, 3)
+    y = np.random.default_rng(4).uniform(0, 1, n).astype(np.float32)
+    idx = np.random.default_rng(5).choice(n, 300, replace=False).astype(np.uint32)
+    dx, dy, di = (torch.from_numpy(a).cuda() for a in (x, y, idx.view(np.int32)))
+    g = np.empty(G.GM_FIELD_N_PARAMS, np.float32)
+    loss = G.gm_field_loss_grad(f, dx, dy, n, di, len(idx), g)
+    feats = F.features(F.normalise(x[idx].astype(np.float64), BOX_LO, BOX_HI))
+    l_ref, g_ref = F.loss_and_grad(theta.astype(np.float64), feats, y[idx].astype(np.float64), emulate_bf16=True)
+    assert abs(loss - l_ref) <= 2e-3 * l_ref
+    assert F.relative_l2(g, g_ref) < 2e-2
+    # one Adam step: the first update is lr * g / (|g| + eps), i.e. +-lr wherever |g| is not tiny
+    lr = 1e-3
+    G.gm_field_step(f, dx, dy, n, di, len(idx), lr)
+    after = np.empty(G.GM_FIELD_N_PARAMS, np.float32)
+    G.gm_field_params(f, after)
+    th_ref, _, _ = F.adam_step(theta.astype(np.float64), 0.0, 0.0, g_ref, 1, lr)
+    sure = np.abs(g_ref) > 1e-3 * np.abs(g_ref).max()
+    assert sure.sum() > 1000
+    assert np.allclose(after[sure], th_ref[sure], rtol=0, atol=1e-6)
+    G.gm_field_free(f)
+
+
+def test_field_trains_on_the_tiny_sphere_map(env):
+    G, torch, ctx = env
+    from paper_2601_07571_gb300 import pipeline
+    w = synth.tiny_sphere()
+    h = pipeline.run(ctx, w, normalize=True)
+    xyz, tri, b2, obj = pipeline.samples_arrays(h)
+    target, _ = pipeline.map_array(h)
+    lo, hi = xyz.min(0), xyz.max(0)
+    f = G.gm_field_create(ctx, lo, hi, synth.field_init(3))
+    pred0 = np.empty(len(xyz), np.float32)
+    G.gm_field_query(f, xyz, len(xyz), pred0)
+    e0 = F.relative_l2(pred0, target)
+    loss = G.gm_field_train(f, h.samples, h.map, 0, steps=1500, batch=4096, lr=3e-3, lr_min=1e-4, seed=9)
+    pred = np.empty(len(xyz), np.float32)
+    G.gm_field_query(f, xyz, len(xyz), pred)
+    e1 = F.relative_l2(pred, target)
+    info = G.gm_field_info(f)
+    G.gm_field_free(f)
+    h.free()
+    assert info["steps"] == 1500 and np.isfinite(loss)
+    assert e1 < 0.5 * e0 and e1 < 0.6, (e0, e1)
