@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gazemap", "reference"], default="gazemap")
-    ap.add_argument("--workload", choices=["paper_scene", "tiny_sphere", "batched"], default="paper_scene")
+    ap.add_argument("--workload", choices=["paper_scene", "tiny_sphere", "batched", "field", "city"],
+                    default="paper_scene")
+    ap.add_argument("--field-steps", type=int, default=3000, help="Adam steps of the neural field")
+    ap.add_argument("--queries", type=int, default=10_000_000, help="query points of the field workload")
     ap.add_argument("--sessions", type=int, default=64, help="sessions of the batched workload")
     ap.add_argument("--fixations", type=int, default=0, help="use only the first N fixations (profiling)")
     ap.add_argument("--flags", type=int, default=0, help="extra GM_F_* accumulation flags (variant A/B runs)")
@@ -54,7 +57,7 @@ def parse():
 
 def make_workload(name, n_fix=0):
     import synth
-    w = synth.paper_scene() if name == "paper_scene" else synth.tiny_sphere()
+    w = {"paper_scene": synth.paper_scene, "tiny_sphere": synth.tiny_sphere, "city": synth.city_block}[name]()
     if n_fix:
         w.fixations = w.fixations.subset(slice(0, n_fix))
     return w
@@ -252,8 +255,92 @@ def batched_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def field_arm(args):
+    """Neural density field on the paper-shaped scene: train on the normalised map of its 2M
+    samples (MSE, Adam, batch 65 536, lr 1e-3 cosine to 1e-5, --field-steps steps), then answer
+    --queries fresh surface points (the sampler at 5x density, seed 33) with the field and with the
+    plain accumulation at the same points (the judge); report queries/s of both and the field's
+    relative L2 error against the plain values."""
+    import torch
+    import synth
+    from paper_2601_07571_gb300 import build as B
+    B.build()
+    import paper_2601_07571_gb300 as G
+    from paper_2601_07571_gb300 import pipeline
+    torch.cuda.set_device(0)
+    w = make_workload("paper_scene", args.fixations)
+    ctx = G.gm_create(0)
+    stream = torch.cuda.current_stream()
+    h = pipeline.run(ctx, w, stream=stream, normalize=True)
+    W, ns, st, _ = G.gm_map_info(h.map)
+    xyz = torch.empty((ns, 3), dtype=torch.float32, device="cuda")
+    G.gm_samples_copy(h.samples, xyz, None, None, None, stream)
+    lo, hi = xyz.min(0).values.cpu().numpy(), xyz.max(0).values.cpu().numpy()
+    # query points: the sampler again, another seed, density scaled to reach --queries
+    scale = args.queries / ns
+    qs = G.gm_sample_surface(h.scene, [m.density * scale for m in w.meshes], 33, 0, stream)
+    nq = G.gm_samples_info(qs)
+    qxyz = torch.empty((nq, 3), dtype=torch.float32, device="cuda")
+    G.gm_samples_copy(qs, qxyz, None, None, None, stream)
+    # the field: train, then query
+    f = G.gm_field_create(ctx, lo, hi, synth.field_init(3), stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = G.gm_field_train(f, h.samples, h.map, 0, steps=args.field_steps, batch=65536, lr=1e-3, lr_min=1e-5,
+                            seed=33, stream=stream)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    out = torch.empty(nq, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        G.gm_field_query(f, qxyz, nq, out, stream)
+    q_t = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.gm_field_query(f, qxyz, nq, out, stream)
+        e1.record(stream)
+        e1.synchronize()
+        q_t.append(e0.elapsed_time(e1))
+    field_ms = sum(q_t) / len(q_t)
+    # the judge: plain accumulation at the query points, normalised by the training map's maximum
+    # a normalised map keeps its raw maximum: gm_map_copy returns it
+    raw_max = G.gm_map_copy(h.map, 0, torch.empty(ns, dtype=torch.float32, device="cuda"), stream)
+    prm = pipeline.params_of(w, flags=G.GM_F_TIMING, normalize=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mq = G.gm_accumulate_fixations(h.scene, qs, *pipeline.fixation_args(w.fixations, True), prm, stream)
+    e1.record(stream)
+    _, _, qst, _ = G.gm_map_info(mq)
+    plain_ms = e0.elapsed_time(e1)
+    ref = torch.empty(nq, dtype=torch.float32, device="cuda")
+    G.gm_map_copy(mq, 0, ref, stream)
+    ref = ref / raw_max
+    err = float(torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref))
+    info = G.gm_field_info(f)
+    line = {"metric": "neural-field queries/s vs plain", "value": nq / (field_ms * 1e-3), "unit": "queries/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": field_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"field_on_{w.name}", "train_samples": int(ns), "queries": int(nq),
+                       "fixations": w.fixations.n, "field": "64 Fourier features, 4x64 ReLU, softplus",
+                       "train": {"steps": args.field_steps, "batch": 65536, "lr": "1e-3 cosine to 1e-5"}},
+            "field_rel_l2_vs_plain": err, "train_s": train_s, "train_ms_device": info["train_ms"],
+            "final_batch_mse": loss,
+            "plain_form": {"value": nq / (plain_ms * 1e-3), "ms": plain_ms, "pairs": int(qst["pairs"]),
+                           "form": "gm_accumulate_fixations at the query points"},
+            "field_over_plain": plain_ms / field_ms}
+    G.gm_field_free(f)
+    G.gm_map_free(mq)
+    G.gm_samples_free(qs)
+    h.free()
+    G.gm_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "field":
+        field_arm(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
         return

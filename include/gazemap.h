@@ -90,7 +90,7 @@ enum {
     GM_F_NO_COMPACT = 8,    /* trace each lane's in-cone rays in place (no per-warp ray queue) */
     GM_F_WIDE_BVH = 16,     /* traverse the 4-wide collapse of the tree instead of the binary tree */
     GM_F_REGCAP64 = 32,     /* cap the accumulation kernel at 64 registers (4 blocks per SM) */
-    GM_F_TILE_RUNS = 64,    /* warp tiles of four 32-sample runs spread over 1024 samples (else 128 consecutive) */
+    GM_F_TILE_CONSECUTIVE = 64, /* warp tiles of 128 consecutive samples (else four 32-sample runs over 1024) */
     GM_F_STATIC_TILES = 128 /* one warp tile per warp of a full grid (else warps pull tiles from a counter) */
 };
 

@@ -286,7 +286,7 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
             ++launches;
             sidx = ident;
         }
-        P.group = (prm->flags & GM_F_TILE_RUNS) ? 8u : 1u;
+        P.group = (prm->flags & GM_F_TILE_CONSECUTIVE) ? 1u : 8u;
         const uint32_t n_tiles = gm_div_up(ns, (uint64_t)WARP_TILE * P.group) * P.group;
         const int persistent = (prm->flags & GM_F_STATIC_TILES) ? 0 : 1;
         const bool compact = !(prm->flags & GM_F_NO_COMPACT);

@@ -91,6 +91,9 @@ struct AccConst {
     float C2, K, tmax;
 };
 
+// Warp tiles of the batch use the spread layout (four 32-sample runs over 1024 samples).
+constexpr uint32_t BATCH_GROUP = 8;
+
 // Persistent: every warp pulls work items (session, warp tile) from `work` until none is left.
 template <bool COMPACT, bool WIDE, int MINB>
 __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate_batch(const SessionDev* __restrict__ sess,
@@ -120,6 +123,7 @@ __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate_batch(const Se
         P.W = S.W;
         P.nt = S.nt;
         P.dbg_cap = 0;
+        P.group = BATCH_GROUP;
         TileStats st;
         warp_tile<false, COMPACT, WIDE>(wi.y, S.spos, S.sidx, S.fix, *S.n_fix, S.nodes, S.tris, P, S.out, S.max_bits,
                                         wsmp + wb, wacc + wb, qslot + wb, qg + wb, nullptr, dbg, err, st);
@@ -468,7 +472,7 @@ extern "C" gm_status gm_batch_create(gm_ctx* ctx, const gm_session_desc* ss, uin
     std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) { return ss[a].fix.n > ss[c].fix.n; });
     std::vector<uint2> items;
     for (uint32_t i : order) {
-        const uint32_t tiles = gm_div_up(ss[i].samples->n, WARP_TILE);
+        const uint32_t tiles = gm_div_up(ss[i].samples->n, (uint64_t)WARP_TILE * BATCH_GROUP) * BATCH_GROUP;
         for (uint32_t t = 0; t < tiles; ++t) items.push_back(make_uint2(i, t));
     }
     b->n_items = (uint32_t)items.size();

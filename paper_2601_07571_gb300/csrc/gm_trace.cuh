@@ -124,8 +124,12 @@ __device__ __forceinline__ bool leaf_hit(const Ray& R, const float4* __restrict_
 // between the eye and the sample is met sooner), leaves tested as soon as they are reached.
 __device__ bool occluded(const Ray& R, uint32_t own, const float4* __restrict__ nodes,
                          const float4* __restrict__ tris, uint32_t nt, int* __restrict__ err, uint32_t& n_node,
-                         uint32_t& n_tri) {
-    if (nt < 2) return nt == 1 ? leaf_hit(R, tris, 0, own, n_tri) : false;
+                         uint32_t& n_tri, int& hit_slot) {
+    if (nt < 2) {
+        const bool h = nt == 1 && leaf_hit(R, tris, 0, own, n_tri);
+        if (h) hit_slot = 0;
+        return h;
+    }
     int stack[STACK];
     int sp = 0;
     int node = 0;
@@ -139,11 +143,17 @@ __device__ bool occluded(const Ray& R, uint32_t own, const float4* __restrict__ 
         float tr = slab(R, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
         const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
         if (tl < INFINITY && cl < 0) {
-            if (leaf_hit(R, tris, ~cl, own, n_tri)) return true;
+            if (leaf_hit(R, tris, ~cl, own, n_tri)) {
+                hit_slot = ~cl;
+                return true;
+            }
             tl = INFINITY;
         }
         if (tr < INFINITY && cr < 0) {
-            if (leaf_hit(R, tris, ~cr, own, n_tri)) return true;
+            if (leaf_hit(R, tris, ~cr, own, n_tri)) {
+                hit_slot = ~cr;
+                return true;
+            }
             tr = INFINITY;
         }
         if (tl < INFINITY && tr < INFINITY) {
@@ -180,7 +190,7 @@ __device__ __forceinline__ void cswap(float& ta, int& la, float& tb, int& lb) {
 // sorting network on the entry distances), the others pushed far-to-near.
 __device__ bool occluded4(const Ray& R, uint32_t own, const float4* __restrict__ nodes4,
                           const float4* __restrict__ tris, int* __restrict__ err, uint32_t& n_node,
-                          uint32_t& n_tri) {
+                          uint32_t& n_tri, int& hit_slot) {
     int stack[STACK4];
     int sp = 0;
     int node = 0;
@@ -194,10 +204,10 @@ __device__ bool occluded4(const Ray& R, uint32_t own, const float4* __restrict__
         float t2 = slab(R, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z);
         float t3 = slab(R, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w);
         int c0 = __float_as_int(L.x), c1 = __float_as_int(L.y), c2 = __float_as_int(L.z), c3 = __float_as_int(L.w);
-        if (t0 < INFINITY && c0 < 0) { if (c0 != LINK_EMPTY && leaf_hit(R, tris, ~c0, own, n_tri)) return true; t0 = INFINITY; }
-        if (t1 < INFINITY && c1 < 0) { if (c1 != LINK_EMPTY && leaf_hit(R, tris, ~c1, own, n_tri)) return true; t1 = INFINITY; }
-        if (t2 < INFINITY && c2 < 0) { if (c2 != LINK_EMPTY && leaf_hit(R, tris, ~c2, own, n_tri)) return true; t2 = INFINITY; }
-        if (t3 < INFINITY && c3 < 0) { if (c3 != LINK_EMPTY && leaf_hit(R, tris, ~c3, own, n_tri)) return true; t3 = INFINITY; }
+        if (t0 < INFINITY && c0 < 0) { if (c0 != LINK_EMPTY && leaf_hit(R, tris, ~c0, own, n_tri)) { hit_slot = ~c0; return true; } t0 = INFINITY; }
+        if (t1 < INFINITY && c1 < 0) { if (c1 != LINK_EMPTY && leaf_hit(R, tris, ~c1, own, n_tri)) { hit_slot = ~c1; return true; } t1 = INFINITY; }
+        if (t2 < INFINITY && c2 < 0) { if (c2 != LINK_EMPTY && leaf_hit(R, tris, ~c2, own, n_tri)) { hit_slot = ~c2; return true; } t2 = INFINITY; }
+        if (t3 < INFINITY && c3 < 0) { if (c3 != LINK_EMPTY && leaf_hit(R, tris, ~c3, own, n_tri)) { hit_slot = ~c3; return true; } t3 = INFINITY; }
         cswap(t0, c0, t1, c1);
         cswap(t2, c2, t3, c3);
         cswap(t0, c0, t2, c2);
@@ -218,6 +228,22 @@ __device__ bool occluded4(const Ray& R, uint32_t own, const float4* __restrict__
         if (t1 < INFINITY) stack[sp++] = c1;
         node = c0;
     }
+}
+
+// Occlusion with a one-entry occluder cache per lane: the triangle that blocked this lane's
+// previous ray is tested first (neighbouring rays from one eye are usually blocked by the same
+// triangle). Any hitting triangle makes the segment occluded, so the answer is the traversal's.
+template <bool WIDE>
+__device__ __forceinline__ bool occluded_cached(const Ray& R, uint32_t own, const float4* __restrict__ nodes,
+                                                const float4* __restrict__ tris, uint32_t nt,
+                                                int* __restrict__ err, uint32_t& n_node, uint32_t& n_tri,
+                                                int& cache) {
+    if (cache >= 0 && leaf_hit(R, tris, cache, own, n_tri)) return true;
+    int slot = -1;
+    const bool occ = WIDE ? occluded4(R, own, nodes, tris, err, n_node, n_tri, slot)
+                          : occluded(R, own, nodes, tris, nt, err, n_node, n_tri, slot);
+    if (occ) cache = slot;
+    return occ;
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -279,6 +305,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
     }
     __syncwarp();
     uint32_t cur = 0xffffffffu;
+    int occ_cache = -1;   // leaf slot of the triangle that blocked this lane's previous ray
 
     auto flush = [&](uint32_t w) {
         float m = 0.f;
@@ -345,9 +372,8 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                     Ray R;
                     make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(sp.x - F0.x, sp.y - F0.y, sp.z - F0.z),
                              P.tmax);
-                    const bool vis = WIDE ? !occluded4(R, __float_as_uint(sp.w), nodes, tris, err, st.n_node, st.n_tri)
-                                          : !occluded(R, __float_as_uint(sp.w), nodes, tris, P.nt, err, st.n_node,
-                                                      st.n_tri);
+                    const bool vis = !occluded_cached<WIDE>(R, __float_as_uint(sp.w), nodes, tris, P.nt, err,
+                                                            st.n_node, st.n_tri, occ_cache);
                     if (vis) {
                         ++st.n_vis;
                         float2 a = wacc[slot];
@@ -383,8 +409,8 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                     ++st.n_in;
                     Ray R;
                     make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(px, py, pz), P.tmax);
-                    const bool vis = WIDE ? !occluded4(R, own[k], nodes, tris, err, st.n_node, st.n_tri)
-                                          : !occluded(R, own[k], nodes, tris, P.nt, err, st.n_node, st.n_tri);
+                    const bool vis = !occluded_cached<WIDE>(R, own[k], nodes, tris, P.nt, err, st.n_node, st.n_tri,
+                                                            occ_cache);
                     const float g = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
                     if (vis) {
                         ++st.n_vis;
