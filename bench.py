@@ -174,6 +174,16 @@ def reference_arm(args):
 # ---------------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------------
+def measured_bf16_peak():
+    """Dense BF16 peak (TFLOP/s) for a kernel timed alone: the driver's measured burst figure,
+    else the machine's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured burst cuBLAS bf16 (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback 1.9 PFLOP/s bf16"
+
+
 def batched_arm(args):
     """64 independent sessions (5k-300k tris, 500-20k fixations, 1e3-5e4 samples/m^2, log-uniform):
     the plain form (one gm_accumulate_fixations per session, back to back on one stream) against
@@ -317,6 +327,12 @@ def field_arm(args):
     ref = ref / raw_max
     err = float(torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref))
     info = G.gm_field_info(f)
+    flop_q = 2 * (4 * 64 * 64 + 64)            # hidden-layer MACs per query on the tensor cores (x2)
+    peak, basis = measured_bf16_peak()
+    ach = flop_q * nq / (field_ms * 1e-3) / 1e12
+    roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "kernel": "k_field_query", "peak_basis": basis,
+            "work_basis": f"{flop_q} FLOP per query (four 64x64 BF16 layers + output)"}
     line = {"metric": "neural-field queries/s vs plain", "value": nq / (field_ms * 1e-3), "unit": "queries/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": field_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
@@ -327,7 +343,7 @@ def field_arm(args):
             "final_batch_mse": loss,
             "plain_form": {"value": nq / (plain_ms * 1e-3), "ms": plain_ms, "pairs": int(qst["pairs"]),
                            "form": "gm_accumulate_fixations at the query points"},
-            "field_over_plain": plain_ms / field_ms}
+            "field_over_plain": plain_ms / field_ms, "roofline": roof}
     G.gm_field_free(f)
     G.gm_map_free(mq)
     G.gm_samples_free(qs)

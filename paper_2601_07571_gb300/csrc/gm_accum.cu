@@ -125,12 +125,30 @@ int acc_occupancy() {
     return b > 0 ? b : 1;
 }
 
-__global__ void k_normalize(float* __restrict__ v, uint64_t ns, uint32_t W, const unsigned int* __restrict__ max_bits) {
-    const uint64_t total = ns * W;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        float m = __uint_as_float(max_bits[i / ns]);
-        v[i] = m > 0.f ? __fdiv_rn(v[i], m) : 0.f;
+// v / max for every window: blockIdx.y = window - w0, float4 loads and stores over the window's
+// samples (a scalar tail when n_samples is not a multiple of 4); windows whose maximum is 0 stay 0.
+__global__ void k_normalize(float* __restrict__ v, uint64_t ns, const unsigned int* __restrict__ max_bits,
+                            uint32_t w0) {
+    const uint32_t win = w0 + blockIdx.y;
+    const float m = __uint_as_float(max_bits[win]);
+    if (!(m > 0.f)) return;
+    float* w = v + (size_t)win * ns;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if ((reinterpret_cast<uintptr_t>(w) & 15u) == 0) {
+        const uint64_t n4 = ns / 4;
+        float4* w4 = reinterpret_cast<float4*>(w);
+        for (uint64_t i = i0; i < n4; i += stride) {
+            float4 x = w4[i];
+            x.x = __fdiv_rn(x.x, m);
+            x.y = __fdiv_rn(x.y, m);
+            x.z = __fdiv_rn(x.z, m);
+            x.w = __fdiv_rn(x.w, m);
+            w4[i] = x;
+        }
+        for (uint64_t i = 4 * n4 + i0; i < ns; i += stride) w[i] = __fdiv_rn(w[i], m);
+    } else {
+        for (uint64_t i = i0; i < ns; i += stride) w[i] = __fdiv_rn(w[i], m);
     }
 }
 
@@ -329,9 +347,13 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
     }
     if (mp->timing) cudaEventRecord(mp->ev[2], s);
     if (prm->normalize && ns > 0) {
-        uint64_t total = ns * W;
-        uint32_t grid = (uint32_t)std::min<uint64_t>(gm_div_up(total, 256), (uint64_t)ctx->n_sm * 16);
-        k_normalize<<<grid, 256, 0, s>>>(mp->values, ns, (uint32_t)W, mp->max_bits);
+        // blocks per window: enough to cover the window with float4s, and ~8 waves overall
+        const uint64_t per_win = std::max<uint64_t>(1, std::min<uint64_t>(gm_div_up(ns, 1024),
+                                                                         (uint64_t)ctx->n_sm * 8 / std::max<uint64_t>(1, W) + 1));
+        for (uint64_t w0 = 0; w0 < W; w0 += 65535) {
+            dim3 grid((uint32_t)per_win, (uint32_t)std::min<uint64_t>(65535, W - w0));
+            k_normalize<<<grid, 256, 0, s>>>(mp->values, ns, mp->max_bits, (uint32_t)w0);
+        }
         ++launches;
     }
     if (mp->timing) cudaEventRecord(mp->ev[3], s);

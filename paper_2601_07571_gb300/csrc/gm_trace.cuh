@@ -230,22 +230,6 @@ __device__ bool occluded4(const Ray& R, uint32_t own, const float4* __restrict__
     }
 }
 
-// Occlusion with a one-entry occluder cache per lane: the triangle that blocked this lane's
-// previous ray is tested first (neighbouring rays from one eye are usually blocked by the same
-// triangle). Any hitting triangle makes the segment occluded, so the answer is the traversal's.
-template <bool WIDE>
-__device__ __forceinline__ bool occluded_cached(const Ray& R, uint32_t own, const float4* __restrict__ nodes,
-                                                const float4* __restrict__ tris, uint32_t nt,
-                                                int* __restrict__ err, uint32_t& n_node, uint32_t& n_tri,
-                                                int& cache) {
-    if (cache >= 0 && leaf_hit(R, tris, cache, own, n_tri)) return true;
-    int slot = -1;
-    const bool occ = WIDE ? occluded4(R, own, nodes, tris, err, n_node, n_tri, slot)
-                          : occluded(R, own, nodes, tris, nt, err, n_node, n_tri, slot);
-    if (occ) cache = slot;
-    return occ;
-}
-
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -305,7 +289,6 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
     }
     __syncwarp();
     uint32_t cur = 0xffffffffu;
-    int occ_cache = -1;   // leaf slot of the triangle that blocked this lane's previous ray
 
     auto flush = [&](uint32_t w) {
         float m = 0.f;
@@ -372,8 +355,11 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                     Ray R;
                     make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(sp.x - F0.x, sp.y - F0.y, sp.z - F0.z),
                              P.tmax);
-                    const bool vis = !occluded_cached<WIDE>(R, __float_as_uint(sp.w), nodes, tris, P.nt, err,
-                                                            st.n_node, st.n_tri, occ_cache);
+                    int hit = -1;
+                    const bool vis = WIDE ? !occluded4(R, __float_as_uint(sp.w), nodes, tris, err, st.n_node,
+                                                       st.n_tri, hit)
+                                          : !occluded(R, __float_as_uint(sp.w), nodes, tris, P.nt, err, st.n_node,
+                                                      st.n_tri, hit);
                     if (vis) {
                         ++st.n_vis;
                         float2 a = wacc[slot];
@@ -409,8 +395,9 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                     ++st.n_in;
                     Ray R;
                     make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(px, py, pz), P.tmax);
-                    const bool vis = !occluded_cached<WIDE>(R, own[k], nodes, tris, P.nt, err, st.n_node, st.n_tri,
-                                                            occ_cache);
+                    int hit = -1;
+                    const bool vis = WIDE ? !occluded4(R, own[k], nodes, tris, err, st.n_node, st.n_tri, hit)
+                                          : !occluded(R, own[k], nodes, tris, P.nt, err, st.n_node, st.n_tri, hit);
                     const float g = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
                     if (vis) {
                         ++st.n_vis;

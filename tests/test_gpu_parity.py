@@ -323,3 +323,38 @@ def test_accumulate_variants_agree_bit_for_bit(G, ctx, pipe, other):
         ka = np.sort(pa["sample"].astype(np.int64) * (1 << 32) + pa["fix"])
         kb = np.sort(pb["sample"].astype(np.int64) * (1 << 32) + pb["fix"])
         assert np.array_equal(ka, kb)
+
+
+def test_city_block_windows_sampled(G, ctx, pipe):
+    """A reduced city block (boxes + displaced spheres, 60 one-second windows): every window's
+    map at a seeded selection of samples against the oracle, one sample at a time."""
+    w = synth.city_block(n_fix=3000, n_samples=300_000, grid=4, boxes_per_block=5, n_spheres=3, sphere_lat=80,
+                         duration_s=60.0, window_s=1.0)
+    tri = oracle.world_triangles(w)
+    off = oracle.tri_offsets(oracle.areas(tri), oracle.tri_density(w))
+    s_all = oracle.samples(tri, off, w.seed, w.session)
+    rng = np.random.default_rng(7)
+    pick = set(rng.choice(len(s_all.tri), 30, replace=False).tolist())
+    fx = w.fixations
+    for f in rng.choice(fx.n, 30, replace=False):
+        p = s_all.xyz - fx.eye[f].astype(np.float64)
+        r = fx.gaze[f].astype(np.float64) / np.linalg.norm(fx.gaze[f])
+        d1 = p @ r
+        ang = np.linalg.norm(np.cross(p, r), axis=1) / np.maximum(d1, 1e-9)
+        ang[d1 <= 0] = np.inf
+        pick.update(np.argsort(ang)[:2].tolist())
+    which = np.array(sorted(pick), np.int64)
+    s = oracle.samples(tri, off, w.seed, w.session, which)
+    ora = oracle.accumulate(tri, s.xyz, s.tri, fx, w.params, delta_abs=3e-4, cone_band=1e-4)
+    h = pipe.run(ctx, w, normalize=False)
+    W, ns, stats, status = G.gm_map_info(h.map)
+    assert W == 60 and ns == off[-1]
+    dpos = 8 * ulp32(tri_max_coord(tri, s.tri))
+    nonzero = 0
+    for k in range(W):
+        v, _ = pipe.map_array(h, k)
+        d = ora["density"][k]
+        nonzero += int((d > 0).sum())
+        _check_density(v[which], d, ora["amb"][k], ora["sens"][k] * dpos)
+    h.free()
+    assert nonzero >= 30
