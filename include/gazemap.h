@@ -144,6 +144,16 @@ void gm_scene_free(gm_scene* scene);
  * once (to read the sample count). Fails with GM_ERR_UNSUPPORTED beyond 2^31 - 1 samples. */
 gm_status gm_sample_surface(gm_scene* scene, const double* density_per_mesh, uint64_t seed,
                             uint32_t session, gm_stream stream, gm_samples** out);
+/* The paper's own sampler (Section 3.1): triangle i gets the integer resolution r_i of the adaptive
+ * rule (D = 1 + 8 k_m A_i; r = 1 if D < 25, else rint((-3 + sqrt(D)) / 2)) and the
+ * (r+1)(r+2)/2 samples of its barycentric grid (Eq. 1), indexed in O(1) (Eq. 2): local sample idx
+ * sits at row = max m with m(m+1)/2 <= idx, col = idx - row(row+1)/2, with weights
+ * (col/r, 1 - row/r, (row - col)/r) on (v0, v1, v2) (Eq. 3; its printed third weight does not
+ * sum to one, 1 - w1 - w2 is used). Samples on shared edges and vertices are repeated per
+ * triangle, as in the paper. Same layout and calls as gm_sample_surface (bary2 = (w2, w3)).
+ * Synchronises `stream` once. Resolutions of 65535 or more return GM_ERR_UNSUPPORTED. */
+gm_status gm_sample_surface_grid(gm_scene* scene, const double* density_per_mesh, gm_stream stream,
+                                 gm_samples** out);
 /* Explicit query points (n x 3 FP32 world positions, each on triangle tri[i], which is
  * excluded from its occlusion test), host or device. Used for GM_Q_PLAIN queries. */
 gm_status gm_samples_from_points(gm_scene* scene, const float* xyz, const uint32_t* tri,

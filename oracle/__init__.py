@@ -62,6 +62,7 @@ def lib():
         _lib.ora_world_triangles.restype = C.c_int
         _lib.ora_pair_weight.restype = C.c_int
         _lib.ora_normalize.restype = C.c_double
+        _lib.ora_grid_samples.restype = C.c_int
     return _lib
 
 
@@ -232,6 +233,48 @@ def fixation_windows(ts, params) -> np.ndarray:
                                C.c_double(params.t_end), C.c_double(params.window_s),
                                C.c_int32(n_windows(params)), _p(out))
     return out
+
+
+def grid_resolution(area, density):
+    """Per-triangle integer resolution of the paper's grid sampler (and the real root)."""
+    area = np.ascontiguousarray(area, np.float64)
+    density = np.ascontiguousarray(np.broadcast_to(density, area.shape), np.float64)
+    r = np.empty(len(area), np.int64)
+    rr = np.empty(len(area), np.float64)
+    lib().ora_grid_resolution(_p(area), _p(density), C.c_int64(len(area)), _p(r), _p(rr))
+    return r, rr
+
+
+def grid_offsets(r):
+    r = np.ascontiguousarray(r, np.int64)
+    out = np.empty(len(r) + 1, np.int64)
+    lib().ora_grid_offsets(_p(r), C.c_int64(len(r)), _p(out))
+    return out
+
+
+def grid_index(idx):
+    row, col = C.c_int64(), C.c_int64()
+    lib().ora_grid_index(C.c_int64(int(idx)), C.byref(row), C.byref(col))
+    return row.value, col.value
+
+
+def grid_samples(tri, offsets, r, which=None):
+    tri = np.ascontiguousarray(tri, np.float32)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    r = np.ascontiguousarray(r, np.int64)
+    if which is None:
+        which = np.arange(int(offsets[-1]), dtype=np.int64)
+    which = np.ascontiguousarray(which, np.int64)
+    n = len(which)
+    t = np.empty(n, np.int64)
+    rc = np.empty((n, 2), np.int64)
+    b = np.empty((n, 3), np.float64)
+    x = np.empty((n, 3), np.float64)
+    st = lib().ora_grid_samples(_p(tri), _p(offsets), _p(r), C.c_int64(len(tri)), _p(which), C.c_int64(n),
+                                _p(t), _p(rc), _p(b), _p(x))
+    if st != 0:
+        raise ValueError("sample index out of range")
+    return dict(index=which, tri=t, rowcol=rc, bary=b, xyz=x)
 
 
 def run(workload, which=None, delta_abs=0.0, cone_band=0.0, record=False, nthreads=0):

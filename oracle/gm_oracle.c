@@ -483,3 +483,65 @@ void ora_philox_batch(const uint32_t* ctr, int64_t n, const uint32_t key[2], uin
 {
     for (int64_t i = 0; i < n; ++i) ora_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* The paper's own sampler (Section 3.1): every triangle is subdivided with an integer     */
+/* resolution r and holds #p = f(r) = (r+1)(r+2)/2 samples on its barycentric grid.       */
+/* Adaptive resolution (Section 3.1.2): with D = 1 + 8 k A, r = 1 when D < 25, else the    */
+/* positive root (-3 + sqrt(D)) / 2 of r^2 + 3r + 2 - 2kA = 0, rounded to the nearest      */
+/* integer (ties to even; the rounding is not stated).                                    */
+/* ------------------------------------------------------------------------------------ */
+void ora_grid_resolution(const double* area, const double* density, int64_t nt, int64_t* r_out, double* r_real)
+{
+    for (int64_t i = 0; i < nt; ++i) {
+        double D = 1.0 + 8.0 * density[i] * area[i];
+        double r = D < 25.0 ? 1.0 : (-3.0 + sqrt(D)) / 2.0;
+        if (r_real) r_real[i] = r;
+        int64_t ri = D < 25.0 ? 1 : (int64_t)nearbyint(r);
+        r_out[i] = ri < 1 ? 1 : ri;
+    }
+}
+
+/* Offsets of the grid samples: offsets[i+1] - offsets[i] = (r_i + 1)(r_i + 2) / 2. */
+void ora_grid_offsets(const int64_t* r, int64_t nt, int64_t* offsets)
+{
+    offsets[0] = 0;
+    for (int64_t i = 0; i < nt; ++i) offsets[i + 1] = offsets[i] + (r[i] + 1) * (r[i] + 2) / 2;
+}
+
+/* Sample idx of a triangle of resolution r: row = the largest m with m(m+1)/2 <= idx (the
+ * integer form of Eq. 2's ceil((-3 + sqrt(8 idx + 9)) / 2)), col = idx - row(row+1)/2;
+ * barycentrics (Eq. 3) w1 = col / r, w2 = 1 - row / r, w3 = 1 - w1 - w2 = (row - col) / r
+ * (the printed third coordinate does not sum to one); position w1 v0 + w2 v1 + w3 v2. */
+void ora_grid_index(int64_t idx, int64_t* row, int64_t* col)
+{
+    int64_t m = 0;
+    while ((m + 1) * (m + 2) / 2 <= idx) ++m;
+    *row = m;
+    *col = idx - m * (m + 1) / 2;
+}
+
+int ora_grid_samples(const float* tri, const int64_t* offsets, const int64_t* r, int64_t nt, const int64_t* which,
+                     int64_t n, int64_t* tri_out, int64_t* rowcol_out, double* bary_out, double* xyz_out)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t j = which[k];
+        if (j < 0 || j >= offsets[nt]) return -1;
+        int64_t lo = 0, hi = nt;
+        while (hi - lo > 1) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (offsets[mid] <= j) lo = mid; else hi = mid;
+        }
+        int64_t row, col;
+        ora_grid_index(j - offsets[lo], &row, &col);
+        double rr = (double)r[lo];
+        double w1 = col / rr, w2 = 1.0 - row / rr, w3 = (row - col) / rr;
+        const float* t = tri + 9 * lo;
+        tri_out[k] = lo;
+        if (rowcol_out) { rowcol_out[2 * k] = row; rowcol_out[2 * k + 1] = col; }
+        if (bary_out) { bary_out[3 * k] = w1; bary_out[3 * k + 1] = w2; bary_out[3 * k + 2] = w3; }
+        for (int c = 0; c < 3; ++c)
+            xyz_out[3 * k + c] = w1 * (double)t[c] + w2 * (double)t[3 + c] + w3 * (double)t[6 + c];
+    }
+    return 0;
+}

@@ -88,6 +88,74 @@ __global__ void k_expand(const int64_t* __restrict__ off, uint32_t nt, uint32_t 
     bary[j] = make_float2(b1, b2);
 }
 
+// ---- the paper's grid sampler (Section 3.1) ---------------------------------------------------
+// Resolution r_i (Section 3.1.2): D = 1 + 8 k A (FP64, same unfused order as the FP64 reference),
+// r = 1 when D < 25, else rint((-3 + sqrt(D)) / 2); count (r + 1)(r + 2) / 2 (Eq. 1).
+__global__ void k_grid_counts(const float4* __restrict__ tri, const uint32_t* __restrict__ tri_mesh,
+                              const double* __restrict__ dens, uint32_t nt, int64_t* __restrict__ cnt,
+                              uint32_t* __restrict__ res, int* __restrict__ err) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    float4 a = tri[3 * i], b = tri[3 * i + 1], c = tri[3 * i + 2];
+    double e1x = __dsub_rn(b.x, a.x), e1y = __dsub_rn(b.y, a.y), e1z = __dsub_rn(b.z, a.z);
+    double e2x = __dsub_rn(c.x, a.x), e2y = __dsub_rn(c.y, a.y), e2z = __dsub_rn(c.z, a.z);
+    double cx = __dsub_rn(__dmul_rn(e1y, e2z), __dmul_rn(e1z, e2y));
+    double cy = __dsub_rn(__dmul_rn(e1z, e2x), __dmul_rn(e1x, e2z));
+    double cz = __dsub_rn(__dmul_rn(e1x, e2y), __dmul_rn(e1y, e2x));
+    double n2 = __dadd_rn(__dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)), __dmul_rn(cz, cz));
+    double A = __dmul_rn(0.5, __dsqrt_rn(n2));
+    double D = __dadd_rn(1.0, __dmul_rn(__dmul_rn(8.0, dens[tri_mesh[i]]), A));
+    long long r = 1;
+    if (!(D < 25.0)) {
+        const double rr = __dmul_rn(__dadd_rn(-3.0, __dsqrt_rn(D)), 0.5);
+        if (!(rr < 65535.0)) {
+            atomicCAS(err, 0, GM_DEV_BAD_INDEX);
+            r = 1;
+        } else {
+            r = __double2ll_rn(rr);
+        }
+    }
+    if (r < 1) r = 1;
+    res[i] = (uint32_t)r;
+    cnt[i] = (int64_t)((r + 1) * (r + 2) / 2);
+}
+
+__global__ void k_excl_from_incl(const int64_t* __restrict__ S, uint32_t nt, int64_t* __restrict__ off) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) off[0] = 0;
+    if (i < nt) off[i + 1] = S[i];
+}
+
+// Sample j: triangle by binary search, local index idx -> row = max m with m(m+1)/2 <= idx,
+// col = idx - row(row+1)/2 (Eq. 2); weights (col/r, 1 - row/r, (row - col)/r) (Eq. 3, third
+// weight read as 1 - w1 - w2) of (v0, v1, v2).
+__global__ void k_grid_expand(const int64_t* __restrict__ off, const uint32_t* __restrict__ res, uint32_t nt,
+                              uint32_t n, const float4* __restrict__ tri, float4* __restrict__ pos,
+                              float2* __restrict__ bary) {
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    uint32_t lo = 0, hi = nt;
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= (int64_t)j) lo = mid; else hi = mid;
+    }
+    const long long idx = (long long)j - off[lo];
+    long long m = (long long)((sqrtf((float)(8 * idx + 1)) - 1.f) * 0.5f);
+    while (m > 0 && m * (m + 1) / 2 > idx) --m;
+    while ((m + 1) * (m + 2) / 2 <= idx) ++m;
+    const long long col = idx - m * (m + 1) / 2;
+    const float r = (float)res[lo];
+    const float w1 = __fdiv_rn((float)col, r);
+    const float w2 = __fsub_rn(1.0f, __fdiv_rn((float)m, r));
+    const float w3 = __fdiv_rn((float)(m - col), r);
+    const float4 a = tri[3 * lo], b = tri[3 * lo + 1], c = tri[3 * lo + 2];
+    const float x = fmaf(w3, c.x, fmaf(w2, b.x, w1 * a.x));
+    const float y = fmaf(w3, c.y, fmaf(w2, b.y, w1 * a.y));
+    const float z = fmaf(w3, c.z, fmaf(w2, b.z, w1 * a.z));
+    pos[j] = make_float4(x, y, z, __uint_as_float(lo));
+    bary[j] = make_float2(w2, w3);
+}
+
 // ---- spatial work order: 30-bit Morton code of each sample position in the scene box -------
 __device__ __forceinline__ uint32_t spread3_10(uint32_t v) {
     v &= 0x3ffu;
@@ -209,6 +277,73 @@ extern "C" gm_status gm_sample_surface(gm_scene* sc, const double* density_per_m
     sc->ctx->launches += launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_sample_surface launch"));
+    *out = sm;
+    return GM_OK;
+}
+
+extern "C" gm_status gm_sample_surface_grid(gm_scene* sc, const double* density_per_mesh, gm_stream stream,
+                                            gm_samples** out) {
+    if (!sc || !density_per_mesh || !out) return gm_set_error(GM_ERR_INVALID_ARG, "gm_sample_surface_grid: null argument");
+    *out = nullptr;
+    for (uint32_t m = 0; m < sc->n_meshes; ++m)
+        if (!(density_per_mesh[m] >= 0.0) || !std::isfinite(density_per_mesh[m]))
+            return gm_set_error(GM_ERR_INVALID_ARG, "gm_sample_surface_grid: density must be finite and >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    GM_TRY_CUDA(cudaSetDevice(sc->ctx->device));
+    const uint32_t nt = sc->n_tris;
+    gm_samples* sm = new gm_samples();
+    sm->scene = sc;
+    double* dens = nullptr;
+    int64_t* cnt = nullptr;
+    uint32_t* res = nullptr;
+    auto fail = [&](gm_status st) {
+        if (dens) cudaFreeAsync(dens, s);
+        if (cnt) cudaFreeAsync(cnt, s);
+        if (res) cudaFreeAsync(res, s);
+        gm_samples_free(sm);
+        return st;
+    };
+    gm_status st;
+    if ((st = gm_alloc((void**)&dens, sizeof(double) * sc->n_meshes, s)) != GM_OK) return fail(st);
+    if ((st = gm_alloc((void**)&cnt, sizeof(int64_t) * nt, s)) != GM_OK) return fail(st);
+    if ((st = gm_alloc((void**)&res, sizeof(uint32_t) * nt, s)) != GM_OK) return fail(st);
+    if ((st = gm_alloc((void**)&sm->tri_offset, sizeof(int64_t) * (nt + 1), s)) != GM_OK) return fail(st);
+    cudaError_t e = cudaMemcpyAsync(dens, density_per_mesh, sizeof(double) * sc->n_meshes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(gm_cuda_error(e, "density upload"));
+    int launches = 0;
+    k_grid_counts<<<gm_div_up(nt, 256), 256, 0, s>>>(sc->tri_canon, sc->tri_mesh, dens, nt, cnt, res, sc->ctx->dev_err);
+    if ((st = gm_inclusive_scan_i64(cnt, nt, s, &launches)) != GM_OK) return fail(st);
+    k_excl_from_incl<<<gm_div_up(nt, 256), 256, 0, s>>>(cnt, nt, sm->tri_offset);
+    launches += 2;
+    int64_t total = 0;
+    int herr = 0;
+    if ((e = cudaMemcpyAsync(&total, sm->tri_offset + nt, sizeof(int64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&herr, sc->ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return fail(gm_cuda_error(e, "gm_sample_surface_grid"));
+    if (herr) {
+        cudaMemsetAsync(sc->ctx->dev_err, 0, sizeof(int), s);
+        return fail(gm_set_error(GM_ERR_UNSUPPORTED, "gm_sample_surface_grid: a triangle needs a resolution of 65535 or more"));
+    }
+    if (total > 0x7fffffffLL) return fail(gm_set_error(GM_ERR_UNSUPPORTED, "gm_sample_surface_grid: more than 2^31-1 samples"));
+    sm->n = (uint64_t)total;
+    const uint32_t n = (uint32_t)total;
+    if ((st = gm_alloc((void**)&sm->pos, sizeof(float4) * n, s)) != GM_OK) return fail(st);
+    if ((st = gm_alloc((void**)&sm->bary, sizeof(float2) * n, s)) != GM_OK) return fail(st);
+    if (n > 0) {
+        k_grid_expand<<<gm_div_up(n, 256), 256, 0, s>>>(sm->tri_offset, res, nt, n, sc->tri_canon, sm->pos, sm->bary);
+        ++launches;
+    }
+    if ((st = build_work_order(sm, s, &launches)) != GM_OK) return fail(st);
+    sc->ctx->launches += launches;
+    cudaFreeAsync(dens, s);
+    cudaFreeAsync(cnt, s);
+    cudaFreeAsync(res, s);
+    dens = nullptr;
+    cnt = nullptr;
+    res = nullptr;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_sample_surface_grid launch"));
     *out = sm;
     return GM_OK;
 }

@@ -80,6 +80,7 @@ _SIGS = {
     "gm_scene_free": (None, [_P]),
     "gm_sample_surface": (C.c_int, [_P, _P, C.c_uint64, C.c_uint32, _P, C.POINTER(_P)]),
     "gm_samples_from_points": (C.c_int, [_P, _P, _P, C.c_uint64, _P, C.POINTER(_P)]),
+    "gm_sample_surface_grid": (C.c_int, [_P, _P, _P, C.POINTER(_P)]),
     "gm_samples_info": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
     "gm_samples_offsets": (C.c_int, [_P, _P, _P]),
     "gm_samples_copy": (C.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -232,6 +233,13 @@ def gm_sample_surface(scene, density_per_mesh, seed: int, session: int = 0, stre
     h = _P()
     _check(lib().gm_sample_surface(scene, _ptr(dens), C.c_uint64(seed), C.c_uint32(session), _stream(stream),
                                    C.byref(h)))
+    return h
+
+
+def gm_sample_surface_grid(scene, density_per_mesh, stream=None):
+    dens = np.ascontiguousarray(density_per_mesh, np.float64)
+    h = _P()
+    _check(lib().gm_sample_surface_grid(scene, _ptr(dens), _stream(stream), C.byref(h)))
     return h
 
 
