@@ -59,13 +59,17 @@ __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Feature `col` of a normalised position.
+// Feature `col` of a normalised position. y = 2^k x~ is exact; y - 2 rint(y / 2) is an exact
+// reduction to [-1, 1] (sin and cos of pi y have period 2 in y), after which the hardware sine
+// and cosine are accurate to ~1e-6 -- far below the bf16 rounding that follows.
 __device__ __forceinline__ float feature(const float xt[3], int col) {
     if (col < 3) return xt[col];
     if (col >= 63) return 0.f;
     const int c = col - 3, k = c / 6, r = c % 6;
-    const float y = ldexpf(xt[r % 3], k);   // 2^k x~, exact
-    return r < 3 ? sinpif(y) : cospif(y);
+    float y = ldexpf(xt[r % 3], k);
+    y = y - 2.f * rintf(0.5f * y);
+    const float a = 3.14159265358979f * y;
+    return r < 3 ? __sinf(a) : __cosf(a);
 }
 
 // A fragments (4 k16 chunks) of the 64 features of rows g and g + 8 of a 16-point group.
