@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--sessions", type=int, default=64, help="sessions of the batched workload")
     ap.add_argument("--fixations", type=int, default=0, help="use only the first N fixations (profiling)")
     ap.add_argument("--flags", type=int, default=0, help="extra GM_F_* accumulation flags (variant A/B runs)")
+    ap.add_argument("--builder", choices=["default", "lbvh", "ploc"], default="default", help="BVH builder")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     return ap.parse_args()
@@ -389,8 +390,10 @@ def main():
     prm = pipeline.params_of(w, flags=G.GM_F_TIMING | args.flags, normalize=True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
+    builder = {"default": None, "lbvh": G.GM_BUILD_LBVH, "ploc": G.GM_BUILD_PLOC}[args.builder]
+
     def step(meshes, fix):
-        sc = G.gm_build_scene(ctx, meshes, stream)
+        sc = G.gm_build_scene(ctx, meshes, stream, builder=builder)
         sm = G.gm_sample_surface(sc, dens, w.seed, w.session, stream)
         mp = G.gm_accumulate_fixations(sc, sm, *fix, prm, stream)
         return sc, sm, mp
@@ -491,7 +494,7 @@ def main():
                        "fixations": w.fixations.n, "pairs_per_step": int(pairs),
                        "l2": "flushed between steps (256 MiB write)", "inputs": "device-resident",
                        "parallelism": f"replicas{world}" if world > 1 else "single",
-                       "accumulate_flags": args.flags},
+                       "accumulate_flags": args.flags, "builder": args.builder},
             "stages_ms": {"accumulate": acc, "fixation_prep": sum(prep_ms) / len(prep_ms),
                           "normalize": sum(norm_ms) / len(norm_ms),
                           "build_and_sample": step_ms - acc - sum(prep_ms) / len(prep_ms) - sum(norm_ms) / len(norm_ms)},

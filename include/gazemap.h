@@ -128,6 +128,17 @@ gm_status gm_ctx_launches(const gm_ctx* ctx, uint64_t* kernel_launches);
  * order. Synchronises `stream` once (to check the tree depth). */
 gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes,
                          gm_stream stream, gm_scene** out);
+/* Builders of the hierarchy (same node layout and traversal either way):
+ *  GM_BUILD_LBVH: Karras' linear BVH from the Morton order (HPG 2012), fastest to build;
+ *  GM_BUILD_PLOC: parallel locally-ordered clustering (Meister & Bittner, TVCG 2018) from the same
+ *                 Morton order, merging mutual nearest neighbours by union-box surface area
+ *                 within +-16 positions; a tighter tree for a few more milliseconds of build. */
+enum { GM_BUILD_LBVH = 0, GM_BUILD_PLOC = 1, GM_BUILD_DEFAULT = GM_BUILD_LBVH };
+typedef struct {
+    int32_t builder;
+} gm_build_opts;
+gm_status gm_build_scene_opts(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes,
+                              const gm_build_opts* opts, gm_stream stream, gm_scene** out);
 gm_status gm_scene_info(const gm_scene* scene, uint32_t* n_tris, uint32_t* bvh_depth);
 /* Copy the world triangles (n_tris x 9 FP32, v0 v1 v2) to `dst` (host or device). */
 gm_status gm_scene_triangles(const gm_scene* scene, float* dst, gm_stream stream);

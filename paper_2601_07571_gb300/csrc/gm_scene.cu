@@ -294,10 +294,121 @@ __global__ void k_collapse4(const float4* __restrict__ nodes, int n_int, const i
     o[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// ---- PLOC: parallel locally-ordered clustering (Meister & Bittner, TVCG 2018) ----------------
+// Clusters start as the Morton-ordered leaves. Each round, every cluster finds the cluster within
+// +-R positions whose union box has the smallest surface area; mutual nearest neighbours merge
+// into a new node (the lower position keeps the merged cluster), and the array is compacted.
+// Node indices are handed out downwards from n - 2, so the last merge -- the root -- is node 0.
+
+struct Box6 {
+    float lo[3], hi[3];
+};
+
+__device__ __forceinline__ float union_area(const float4 al, const float4 ah, const float4 bl, const float4 bh) {
+    const float dx = fmaxf(ah.x, bh.x) - fminf(al.x, bl.x);
+    const float dy = fmaxf(ah.y, bh.y) - fminf(al.y, bl.y);
+    const float dz = fmaxf(ah.z, bh.z) - fminf(al.z, bl.z);
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void k_ploc_init(const float4* __restrict__ tri_canon, const uint32_t* __restrict__ order, int n,
+                            const unsigned int* __restrict__ bounds, int* __restrict__ cid, float4* __restrict__ blo,
+                            float4* __restrict__ bhi, float4* __restrict__ bvh_tris) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t t = order[i];
+    float4 a = tri_canon[3 * t], b = tri_canon[3 * t + 1], c = tri_canon[3 * t + 2];
+    bvh_tris[3 * i + 0] = make_float4(a.x, a.y, a.z, __uint_as_float(t));
+    bvh_tris[3 * i + 1] = b;
+    bvh_tris[3 * i + 2] = c;
+    float big = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) big = fmaxf(big, fmaxf(fabsf(ord2f(bounds[6 + k])), fabsf(ord2f(bounds[9 + k]))));
+    const float margin = big * (1.0f / 524288.0f) + 1e-30f;
+    blo[i] = make_float4(fminf(fminf(a.x, b.x), c.x) - margin, fminf(fminf(a.y, b.y), c.y) - margin,
+                         fminf(fminf(a.z, b.z), c.z) - margin, 0.f);
+    bhi[i] = make_float4(fmaxf(fmaxf(a.x, b.x), c.x) + margin, fmaxf(fmaxf(a.y, b.y), c.y) + margin,
+                         fmaxf(fmaxf(a.z, b.z), c.z) + margin, 0.f);
+    cid[i] = ~i;
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_ploc_nn(const float4* __restrict__ blo, const float4* __restrict__ bhi,
+                                                 int m, int* __restrict__ nn) {
+    __shared__ float4 sl[256 + 2 * R], sh[256 + 2 * R];
+    const int b0 = blockIdx.x * 256;
+    for (int k = threadIdx.x; k < 256 + 2 * R; k += 256) {
+        const int g = b0 - R + k;
+        if (g >= 0 && g < m) {
+            sl[k] = blo[g];
+            sh[k] = bhi[g];
+        }
+    }
+    __syncthreads();
+    const int i = b0 + threadIdx.x;
+    if (i >= m) return;
+    const float4 al = sl[threadIdx.x + R], ah = sh[threadIdx.x + R];
+    float best = INFINITY;
+    int bj = -1;
+    for (int d = -R; d <= R; ++d) {
+        const int j = i + d;
+        if (d == 0 || j < 0 || j >= m) continue;
+        const float a = union_area(al, ah, sl[threadIdx.x + R + d], sh[threadIdx.x + R + d]);
+        if (a < best || (a == best && j < bj)) {
+            best = a;
+            bj = j;
+        }
+    }
+    nn[i] = bj;
+}
+
+__global__ void k_ploc_merge(int m, const int* __restrict__ nn, int* __restrict__ cid, float4* __restrict__ blo,
+                             float4* __restrict__ bhi, int64_t* __restrict__ keep, int* __restrict__ counter,
+                             float4* __restrict__ nodes, int* __restrict__ parent_node, int* __restrict__ parent_leaf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int j = nn[i];
+    const bool mutual = j >= 0 && nn[j] == i;
+    if (!mutual) {
+        keep[i] = 1;
+        return;
+    }
+    if (i > j) {   // the lower position builds the node and keeps the merged cluster
+        keep[i] = 0;
+        return;
+    }
+    const int k = atomicSub(counter, 1) - 1;
+    const float4 al = blo[i], ah = bhi[i], bl = blo[j], bh = bhi[j];
+    const int ci = cid[i], cj = cid[j];
+    float* node = reinterpret_cast<float*>(nodes + 4 * k);
+    node[0] = al.x; node[1] = al.y; node[2] = al.z; node[3] = ah.x; node[4] = ah.y; node[5] = ah.z;
+    node[6] = bl.x; node[7] = bl.y; node[8] = bl.z; node[9] = bh.x; node[10] = bh.y; node[11] = bh.z;
+    nodes[4 * k + 3] = make_float4(__int_as_float(ci), __int_as_float(cj), 0.f, 0.f);
+    if (ci < 0) parent_leaf[~ci] = k; else parent_node[ci] = k;
+    if (cj < 0) parent_leaf[~cj] = k; else parent_node[cj] = k;
+    // position j is only read by its own thread (which returns above), so i may be rewritten here
+    cid[i] = k;
+    blo[i] = make_float4(fminf(al.x, bl.x), fminf(al.y, bl.y), fminf(al.z, bl.z), 0.f);
+    bhi[i] = make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), 0.f);
+    keep[i] = 1;
+}
+
+__global__ void k_ploc_compact(int m, const int64_t* __restrict__ incl, const int* __restrict__ cid,
+                               const float4* __restrict__ blo, const float4* __restrict__ bhi, int* __restrict__ cid2,
+                               float4* __restrict__ blo2, float4* __restrict__ bhi2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t before = i > 0 ? incl[i - 1] : 0;
+    if (incl[i] == before) return;
+    cid2[before] = cid[i];
+    blo2[before] = blo[i];
+    bhi2[before] = bhi[i];
+}
+
 }  // namespace
 
-extern "C" gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes,
-                                    gm_stream stream, gm_scene** out) {
+static gm_status build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes, int builder,
+                             gm_stream stream, gm_scene** out) {
     if (!ctx || !meshes || !out || n_meshes == 0)
         return gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene: null argument or no meshes");
     *out = nullptr;
@@ -389,11 +500,63 @@ extern "C" gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uin
     GM_TRY_CUDA(cudaMemsetAsync(depth, 0, sizeof(unsigned int), s));
     k_morton<<<gm_div_up(nt, 256), 256, 0, s>>>(sc->tri_canon, nt, bounds, keys, order);
     if ((st = gm_radix_sort_u64(keys, order, nt, 63, s, &launches)) != GM_OK) return fail(st);
-    if (nt > 1) k_hierarchy<<<gm_div_up(nt - 1, 256), 256, 0, s>>>(keys, (int)nt, sc->nodes, parent_node, parent_leaf);
-    k_refit<<<gm_div_up(nt, 256), 256, 0, s>>>(sc->tri_canon, order, (int)nt, sc->nodes, parent_node, parent_leaf,
-                                                flags, bounds, sc->bvh_tris);
+    if (builder == GM_BUILD_PLOC && nt > 1) {
+        int *cid = nullptr, *cid2 = nullptr, *nn = nullptr, *counter = nullptr;
+        float4 *blo = nullptr, *bhi = nullptr, *blo2 = nullptr, *bhi2 = nullptr;
+        int64_t* keep = nullptr;
+        TMP_ALLOC(cid, sizeof(int) * nt);
+        TMP_ALLOC(cid2, sizeof(int) * nt);
+        TMP_ALLOC(nn, sizeof(int) * nt);
+        TMP_ALLOC(counter, sizeof(int));
+        TMP_ALLOC(blo, sizeof(float4) * nt);
+        TMP_ALLOC(bhi, sizeof(float4) * nt);
+        TMP_ALLOC(blo2, sizeof(float4) * nt);
+        TMP_ALLOC(bhi2, sizeof(float4) * nt);
+        TMP_ALLOC(keep, sizeof(int64_t) * nt);
+        k_ploc_init<<<gm_div_up(nt, 256), 256, 0, s>>>(sc->tri_canon, order, (int)nt, bounds, cid, blo, bhi,
+                                                       sc->bvh_tris);
+        const int first = (int)nt - 1;
+        GM_TRY_CUDA(cudaMemcpyAsync(counter, &first, sizeof(int), cudaMemcpyHostToDevice, s));
+        launches += 1;
+        int m = (int)nt;
+        int64_t* m_host = nullptr;
+        GM_TRY_CUDA(cudaMallocHost(&m_host, sizeof(int64_t)));
+        int rounds = 0;
+        while (m > 1 && rounds < 4096) {
+            ++rounds;
+            k_ploc_nn<16><<<gm_div_up(m, 256), 256, 0, s>>>(blo, bhi, m, nn);
+            k_ploc_merge<<<gm_div_up(m, 256), 256, 0, s>>>(m, nn, cid, blo, bhi, keep, counter, sc->nodes, parent_node,
+                                                           parent_leaf);
+            if ((st = gm_inclusive_scan_i64(keep, (uint32_t)m, s, &launches)) != GM_OK) {
+                cudaFreeHost(m_host);
+                return fail(st);
+            }
+            k_ploc_compact<<<gm_div_up(m, 256), 256, 0, s>>>(m, keep, cid, blo, bhi, cid2, blo2, bhi2);
+            launches += 3;
+            std::swap(cid, cid2);
+            std::swap(blo, blo2);
+            std::swap(bhi, bhi2);
+            cudaError_t ce = cudaMemcpyAsync(m_host, keep + (m - 1), sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+            if (ce != cudaSuccess) {
+                cudaFreeHost(m_host);
+                return fail(gm_cuda_error(ce, "gm_build_scene (clustering)"));
+            }
+            if (*m_host >= m) {   // no mutual pair: cannot happen with consistent tie-breaking
+                cudaFreeHost(m_host);
+                return fail(gm_set_error(GM_ERR_INTERNAL, "gm_build_scene: clustering made no progress"));
+            }
+            m = (int)*m_host;
+        }
+        cudaFreeHost(m_host);
+    } else {
+        if (nt > 1) k_hierarchy<<<gm_div_up(nt - 1, 256), 256, 0, s>>>(keys, (int)nt, sc->nodes, parent_node, parent_leaf);
+        k_refit<<<gm_div_up(nt, 256), 256, 0, s>>>(sc->tri_canon, order, (int)nt, sc->nodes, parent_node, parent_leaf,
+                                                    flags, bounds, sc->bvh_tris);
+        launches += (nt > 1 ? 2 : 1);
+    }
     k_depth<<<gm_div_up(nt, 256), 256, 0, s>>>(parent_node, parent_leaf, (int)nt, depth);
-    launches += (nt > 1 ? 4 : 3);
+    launches += 2;
     ctx->launches += launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_build_scene launch"));
@@ -451,6 +614,19 @@ extern "C" gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uin
     return GM_OK;
 #undef SC_ALLOC
 #undef TMP_ALLOC
+}
+
+extern "C" gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes, gm_stream stream,
+                                    gm_scene** out) {
+    return build_scene(ctx, meshes, n_meshes, GM_BUILD_DEFAULT, stream, out);
+}
+
+extern "C" gm_status gm_build_scene_opts(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes,
+                                         const gm_build_opts* opts, gm_stream stream, gm_scene** out) {
+    const int b = opts ? opts->builder : GM_BUILD_DEFAULT;
+    if (b != GM_BUILD_LBVH && b != GM_BUILD_PLOC)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene_opts: unknown builder");
+    return build_scene(ctx, meshes, n_meshes, b, stream, out);
 }
 
 extern "C" gm_status gm_scene_info(const gm_scene* sc, uint32_t* n_tris, uint32_t* bvh_depth) {

@@ -75,6 +75,8 @@ _SIGS = {
     "gm_sync": (C.c_int, [_P, _P]),
     "gm_ctx_launches": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
     "gm_build_scene": (C.c_int, [_P, C.POINTER(gm_mesh_desc), C.c_uint32, _P, C.POINTER(_P)]),
+    "gm_build_scene_opts": (C.c_int, [_P, C.POINTER(gm_mesh_desc), C.c_uint32, C.POINTER(C.c_int32), _P,
+                                      C.POINTER(_P)]),
     "gm_scene_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "gm_scene_triangles": (C.c_int, [_P, _P, _P]),
     "gm_scene_free": (None, [_P]),
@@ -196,8 +198,12 @@ def gm_ctx_launches(ctx) -> int:
 
 
 # ---- scene -----------------------------------------------------------------------------------
-def gm_build_scene(ctx, meshes, stream=None):
-    """meshes: sequence of (vertices (nv,3) f32, indices (nt,3) u32, transform (4,4) f64, object_id)."""
+GM_BUILD_LBVH, GM_BUILD_PLOC = 0, 1
+
+
+def gm_build_scene(ctx, meshes, stream=None, builder=None):
+    """meshes: sequence of (vertices (nv,3) f32, indices (nt,3) u32, transform (4,4) f64, object_id).
+    builder: None (library default), GM_BUILD_LBVH or GM_BUILD_PLOC."""
     descs = (gm_mesh_desc * len(meshes))()
     keep = []
     for d, (v, f, xf, obj) in zip(descs, meshes):
@@ -209,7 +215,11 @@ def gm_build_scene(ctx, meshes, stream=None):
         d.transform = (C.c_double * 16)(*np.asarray(xf, np.float64).reshape(16).tolist())
         d.object_id = int(obj)
     h = _P()
-    _check(lib().gm_build_scene(ctx, descs, len(meshes), _stream(stream), C.byref(h)))
+    if builder is None:
+        _check(lib().gm_build_scene(ctx, descs, len(meshes), _stream(stream), C.byref(h)))
+    else:
+        opt = C.c_int32(int(builder))
+        _check(lib().gm_build_scene_opts(ctx, descs, len(meshes), C.byref(opt), _stream(stream), C.byref(h)))
     return h
 
 

@@ -61,9 +61,9 @@ def params_of(workload, flags: int = 0, normalize: Optional[bool] = None, debug_
 
 
 def run(ctx, workload, stream=None, flags: int = 0, normalize: Optional[bool] = None, debug_pair_cap: int = 0,
-        device_inputs: bool = False, points=None) -> Handles:
+        device_inputs: bool = False, points=None, builder=None) -> Handles:
     """Build, sample (or take explicit `points` = (xyz f32, tri u32)) and accumulate."""
-    scene = G.gm_build_scene(ctx, mesh_args(workload, device_inputs), stream)
+    scene = G.gm_build_scene(ctx, mesh_args(workload, device_inputs), stream, builder=builder)
     if points is None:
         samples = G.gm_sample_surface(scene, [m.density for m in workload.meshes], workload.seed, workload.session,
                                       stream)

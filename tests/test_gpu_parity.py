@@ -358,3 +358,24 @@ def test_city_block_windows_sampled(G, ctx, pipe):
         _check_density(v[which], d, ora["amb"][k], ora["sens"][k] * dpos)
     h.free()
     assert nonzero >= 30
+
+
+@pytest.mark.parametrize("which", ["tiny", "session"])
+def test_clustered_tree_gives_identical_maps(G, ctx, pipe, which):
+    """Both builders bound every triangle conservatively and the triangle test is the same, so
+    the any-hit answers -- and the maps -- cannot depend on the tree."""
+    w = synth.tiny_sphere() if which == "tiny" else synth.session(7)
+    if which == "session":
+        w.fixations = w.fixations.subset(slice(0, 300))
+    a = pipe.run(ctx, w, normalize=False, builder=G.GM_BUILD_LBVH, flags=G.GM_F_TIMING)
+    b = pipe.run(ctx, w, normalize=False, builder=G.GM_BUILD_PLOC, flags=G.GM_F_TIMING)
+    _, _, sa, _ = G.gm_map_info(a.map)
+    _, _, sb, _ = G.gm_map_info(b.map)
+    nta, da = G.gm_scene_info(a.scene)
+    ntb, db = G.gm_scene_info(b.scene)
+    va, vb = pipe.map_array(a)[0], pipe.map_array(b)[0]
+    a.free()
+    b.free()
+    assert nta == ntb and 0 < db <= 64
+    assert sa["in_cone"] == sb["in_cone"] and sa["visible"] == sb["visible"]
+    assert np.array_equal(va.view(np.uint32), vb.view(np.uint32))
