@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--workload", choices=["paper_scene", "tiny_sphere", "batched", "field", "city"],
                     default="paper_scene")
     ap.add_argument("--field-steps", type=int, default=30000, help="Adam steps of the neural field")
-    ap.add_argument("--field-lr", type=float, default=5e-3, help="initial learning rate of the field (cosine to 1%%)")
+    ap.add_argument("--field-lr", type=float, default=3e-3, help="initial learning rate of the field (cosine to 1%%)")
     ap.add_argument("--queries", type=int, default=10_000_000, help="query points of the field workload")
     ap.add_argument("--sessions", type=int, default=64, help="sessions of the batched workload")
     ap.add_argument("--fixations", type=int, default=0, help="use only the first N fixations (profiling)")
@@ -272,7 +272,7 @@ def field_arm(args):
     samples (MSE, Adam, batch 65 536, --field-lr cosine to 1 %, --field-steps steps), then answer
     --queries fresh surface points (the sampler at 5x density, seed 33) with the field and with the
     plain accumulation at the same points (the judge); report queries/s of both and the field's
-    relative L2 error against the plain values. (lr 5e-3 with 30 000 steps: larger rates diverge,
+    relative L2 error against the plain values. (lr 3e-3 with 30 000 steps: rates of 5e-3 and more become unstable or diverge,
     longer budgets plateau near 0.056 on fresh points.)"""
     import torch
     import synth

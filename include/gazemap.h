@@ -132,8 +132,9 @@ gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_mes
  *  GM_BUILD_LBVH: Karras' linear BVH from the Morton order (HPG 2012), fastest to build;
  *  GM_BUILD_PLOC: parallel locally-ordered clustering (Meister & Bittner, TVCG 2018) from the same
  *                 Morton order, merging mutual nearest neighbours by union-box surface area
- *                 within +-16 positions; a tighter tree for a few more milliseconds of build. */
-enum { GM_BUILD_LBVH = 0, GM_BUILD_PLOC = 1, GM_BUILD_DEFAULT = GM_BUILD_LBVH };
+ *                 within +-16 positions; a tighter tree for a few more milliseconds of build
+ *                 (the default used by gm_build_scene). */
+enum { GM_BUILD_LBVH = 0, GM_BUILD_PLOC = 1, GM_BUILD_DEFAULT = GM_BUILD_PLOC };
 typedef struct {
     int32_t builder;
 } gm_build_opts;
