@@ -78,15 +78,28 @@ __device__ __forceinline__ void make_ray(Ray& R, float3 o, float3 d, float tmax)
     R.Sz = 1.0f / dkz;
 }
 
-// Entry distance of the segment into the box, or +inf when it misses.
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Entry distance of the segment into the box, or +inf when it misses (three-input min/max).
 __device__ __forceinline__ float slab(const Ray& R, float lx, float ly, float lz, float hx, float hy, float hz) {
-    float t0x = fmaf(lx, R.idir.x, -R.oidir.x), t1x = fmaf(hx, R.idir.x, -R.oidir.x);
-    float t0y = fmaf(ly, R.idir.y, -R.oidir.y), t1y = fmaf(hy, R.idir.y, -R.oidir.y);
-    float t0z = fmaf(lz, R.idir.z, -R.oidir.z), t1z = fmaf(hz, R.idir.z, -R.oidir.z);
-    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.f));
-    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), R.tmax_box));
+    const float t0x = fmaf(lx, R.idir.x, -R.oidir.x), t1x = fmaf(hx, R.idir.x, -R.oidir.x);
+    const float t0y = fmaf(ly, R.idir.y, -R.oidir.y), t1y = fmaf(hy, R.idir.y, -R.oidir.y);
+    const float t0z = fmaf(lz, R.idir.z, -R.oidir.z), t1z = fmaf(hz, R.idir.z, -R.oidir.z);
+    const float tn = fmax3(fminf(t0x, t1x), fminf(t0y, t1y), fmaxf(fminf(t0z, t1z), 0.f));
+    const float tf = fmin3(fmaxf(t0x, t1x), fmaxf(t0y, t1y), fminf(fmaxf(t0z, t1z), R.tmax_box));
     return tn <= tf ? tn : INFINITY;
 }
+
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 // Woop, Benthin, Wald, "Watertight ray/triangle intersection", JCGT 2(1), 2013. Edge functions
 // are evaluated without fused multiply-add so that a shared edge gives exactly opposite values
@@ -135,13 +148,16 @@ __device__ bool occluded(const Ray& R, uint32_t own, const float4* __restrict__ 
     int node = 0;
     for (;;) {
         ++n_node;
+        const float4 n3 = __ldg(&nodes[4 * node + 3]);
         const float4 n0 = __ldg(&nodes[4 * node + 0]);
         const float4 n1 = __ldg(&nodes[4 * node + 1]);
         const float4 n2 = __ldg(&nodes[4 * node + 2]);
-        const float4 n3 = __ldg(&nodes[4 * node + 3]);
+        const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
+        // start fetching both children while the boxes are tested
+        prefetch_l1(cl >= 0 ? (const void*)(nodes + 4 * cl) : (const void*)(tris + 3 * ~cl));
+        prefetch_l1(cr >= 0 ? (const void*)(nodes + 4 * cr) : (const void*)(tris + 3 * ~cr));
         float tl = slab(R, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
         float tr = slab(R, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
-        const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
         if (tl < INFINITY && cl < 0) {
             if (leaf_hit(R, tris, ~cl, own, n_tri)) {
                 hit_slot = ~cl;
