@@ -99,8 +99,6 @@ __device__ __forceinline__ float slab(const Ray& R, float lx, float ly, float lz
     return tn <= tf ? tn : INFINITY;
 }
 
-__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
-
 // Woop, Benthin, Wald, "Watertight ray/triangle intersection", JCGT 2(1), 2013. Edge functions
 // are evaluated without fused multiply-add so that a shared edge gives exactly opposite values
 // in its two triangles (no ray slips between them).
@@ -153,9 +151,6 @@ __device__ bool occluded(const Ray& R, uint32_t own, const float4* __restrict__ 
         const float4 n1 = __ldg(&nodes[4 * node + 1]);
         const float4 n2 = __ldg(&nodes[4 * node + 2]);
         const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
-        // start fetching both children while the boxes are tested
-        prefetch_l1(cl >= 0 ? (const void*)(nodes + 4 * cl) : (const void*)(tris + 3 * ~cl));
-        prefetch_l1(cr >= 0 ? (const void*)(nodes + 4 * cr) : (const void*)(tris + 3 * ~cr));
         float tl = slab(R, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
         float tr = slab(R, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
         if (tl < INFINITY && cl < 0) {
