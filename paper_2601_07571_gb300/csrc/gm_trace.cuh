@@ -313,15 +313,16 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
         // padding lanes hold NaN positions: every cone test on them is false
         const float4 p = j < P.ns ? spos[j]
                                   : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, __uint_as_float(0xffffffffu));
-        sx[k] = p.x;
-        sy[k] = p.y;
-        sz[k] = p.z;
-        own[k] = __float_as_uint(p.w);
         sum[k] = 0.f;
         cmp[k] = 0.f;
         if (COMPACT) {
             wsmp[k * 32 + lane] = p;
             wacc[k * 32 + lane] = make_float2(0.f, 0.f);
+        } else {
+            sx[k] = p.x;
+            sy[k] = p.y;
+            sz[k] = p.z;
+            own[k] = __float_as_uint(p.w);
         }
     }
     __syncwarp();
@@ -364,7 +365,10 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
             int tot = 0;
 #pragma unroll
             for (int k = 0; k < SPT; ++k) {
-                const float px = sx[k] - F0.x, py = sy[k] - F0.y, pz = sz[k] - F0.z;
+                // the tile's samples are read from shared memory (they are there for the ray queue
+                // anyway), which keeps 4 x 4 registers free for occupancy
+                const float4 q = wsmp[k * 32 + lane];
+                const float px = q.x - F0.x, py = q.y - F0.y, pz = q.z - F0.z;
                 const float d1 = fmaf(px, F1.x, fmaf(py, F1.y, pz * F1.z));
                 const float cx = fmaf(py, F1.z, -pz * F1.y);
                 const float cy = fmaf(pz, F1.x, -px * F1.z);
