@@ -24,6 +24,9 @@
 
 namespace {
 
+// Store internal nodes in depth-first order (see k_dfs_index).
+constexpr bool kDfsLayout = true;
+
 struct Mat16 {
     double m[16];
 };
@@ -607,6 +610,24 @@ static gm_status build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n
         ctx->launches += launches;
         e = cudaGetLastError();
         if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_build_scene collapse"));
+    }
+    if (kDfsLayout && nt > 2) {
+        const int n_int = (int)nt - 1;
+        unsigned int* leaves = nullptr;
+        int* dfs = nullptr;
+        float4* reordered = nullptr;
+        TMP_ALLOC(leaves, sizeof(unsigned int) * n_int);
+        TMP_ALLOC(dfs, sizeof(int) * n_int);
+        GM_TRY_CUDA(cudaMemsetAsync(leaves, 0, sizeof(unsigned int) * n_int, s));
+        if ((st = gm_alloc((void**)&reordered, sizeof(float4) * 4 * (size_t)n_int, s)) != GM_OK) return fail(st);
+        k_leaf_counts<<<gm_div_up(nt, 256), 256, 0, s>>>(parent_leaf, parent_node_keep, (int)nt, leaves);
+        k_dfs_index<<<gm_div_up(n_int, 256), 256, 0, s>>>(sc->nodes, parent_node_keep, leaves, n_int, dfs);
+        k_dfs_remap<<<gm_div_up(n_int, 256), 256, 0, s>>>(sc->nodes, dfs, n_int, reordered);
+        ctx->launches += 3;
+        cudaFreeAsync(sc->nodes, s);
+        sc->nodes = reordered;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_build_scene layout"));
     }
     for (void* p : tmp) cudaFreeAsync(p, s);
     tmp.clear();
