@@ -408,6 +408,53 @@ __global__ void k_ploc_compact(int m, const int64_t* __restrict__ incl, const in
     bhi2[before] = bhi[i];
 }
 
+// ---- depth-first node layout ------------------------------------------------------------------
+// Renumber the internal nodes in depth-first order (a node, then its left subtree, then its right
+// subtree), so that a node's left child directly follows it in memory and often shares its
+// cache line. leaves[v] = number of leaves below v (bottom-up); the index of v is the sum, over
+// the path from the root, of 1 per step plus the left sibling's internal-node count when the
+// step goes right.
+__global__ void k_leaf_counts(const int* __restrict__ parent_leaf, const int* __restrict__ parent_node, int n,
+                              unsigned int* __restrict__ leaves) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int p = parent_leaf[i];
+    int guard = 0;
+    while (p >= 0 && guard++ < 4096) {
+        atomicAdd(&leaves[p], 1u);
+        p = p > 0 ? parent_node[p] : -1;
+    }
+}
+
+__global__ void k_dfs_index(const float4* __restrict__ nodes, const int* __restrict__ parent_node,
+                            const unsigned int* __restrict__ leaves, int n_int, int* __restrict__ dfs) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_int) return;
+    int idx = 0, u = v, guard = 0;
+    while (u > 0 && guard++ < 4096) {
+        const int p = parent_node[u];
+        const float4 l = nodes[4 * p + 3];
+        const int left = __float_as_int(l.x);
+        idx += 1;
+        if (left != u) idx += left >= 0 ? (int)leaves[left] - 1 : 0;   // internal nodes of the left subtree
+        u = p;
+    }
+    dfs[v] = idx;
+}
+
+__global__ void k_dfs_remap(const float4* __restrict__ nodes, const int* __restrict__ dfs, int n_int,
+                            float4* __restrict__ out) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_int) return;
+    const int d = dfs[v];
+    out[4 * d + 0] = nodes[4 * v + 0];
+    out[4 * d + 1] = nodes[4 * v + 1];
+    out[4 * d + 2] = nodes[4 * v + 2];
+    const float4 l = nodes[4 * v + 3];
+    const int a = __float_as_int(l.x), b = __float_as_int(l.y);
+    out[4 * d + 3] = make_float4(__int_as_float(a >= 0 ? dfs[a] : a), __int_as_float(b >= 0 ? dfs[b] : b), 0.f, 0.f);
+}
+
 }  // namespace
 
 static gm_status build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes, int builder,
