@@ -57,6 +57,21 @@ def parse():
     return ap.parse_args()
 
 
+def reduce_max(x: float, dist=None, device="cpu") -> float:
+    """Max of a per-rank value over all ranks (identity without torch.distributed)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, slowest_s: float) -> float:
+    """Units processed by all ranks divided by the slowest rank's time (weak scaling)."""
+    return world * units_per_rank / slowest_s
+
+
 def make_workload(name, n_fix=0):
     import synth
     w = {"paper_scene": synth.paper_scene, "tiny_sphere": synth.tiny_sphere, "city": synth.city_block}[name]()
@@ -439,13 +454,9 @@ def main():
         release(h)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    step_ms = sum(times) / len(times)
-    if dist:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = reduce_max(sum(times) / len(times), dist, "cuda")
     pairs = stats["pairs"]
-    value = world * pairs / (step_ms * 1e-3)
+    value = whole_job_rate(pairs, world, step_ms * 1e-3)
 
     # ---- end to end from pinned host buffers -------------------------------------------------
     host_meshes = [(torch.from_numpy(np.ascontiguousarray(v)).pin_memory(),
@@ -467,11 +478,7 @@ def main():
         if i >= min(args.warmup, 2):
             e2e_t.append(t1 - t0)
         release(h)
-    e2e_s = statistics.mean(e2e_t)
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max(statistics.mean(e2e_t), dist, "cuda")
 
     # ---- roofline of the dominant kernel (the fused accumulate) ------------------------------
     props = torch.cuda.get_device_properties(local)
@@ -503,7 +510,7 @@ def main():
             "nodes_per_ray": stats["nodes_visited"] / max(1, stats["in_cone"]),
             "tris_per_ray": stats["tris_tested"] / max(1, stats["in_cone"]),
             "roofline": roof,
-            "e2e": {"value": world * pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+            "e2e": {"value": whole_job_rate(pairs, world, e2e_s), "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(out.numel() * 4), "ms_per_step": e2e_s * 1e3},
             "gpu_launches": int(launches), "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
