@@ -180,6 +180,22 @@ gm_status gm_samples_copy(const gm_samples* s, float* xyz, uint32_t* tri, float*
                           uint32_t* obj, gm_stream stream);
 void gm_samples_free(gm_samples* s);
 
+/* The export record of Section 3.3.3, one entry per sample in stored order; any destination may
+ * be NULL, each host or device: value (FP32, the map's window `window`, normalised iff the map
+ * was), object id, triangle id (global), barycentrics (w0, w1, w2) FP32 x 3, mesh-local position
+ * FP32 x 3 (the world position mapped back by the inverse of the mesh transform, FP64),
+ * world position FP32 x 3. */
+typedef struct {
+    float* value;
+    uint32_t* object_id;
+    uint32_t* triangle;
+    float* bary3;
+    float* local_xyz;
+    float* world_xyz;
+} gm_export_dst;
+gm_status gm_samples_export(const gm_samples* s, const gm_map* map, uint32_t window, const gm_export_dst* dst,
+                            gm_stream stream);
+
 /* Allocation-free per-triangle sample offsets. The paper has no counterpart: this is a service
  * for callers that cannot allocate device memory when they need the offsets -- an engine
  * plugin whose host application owns all device memory through its own allocator, or a

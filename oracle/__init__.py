@@ -277,6 +277,24 @@ def grid_samples(tri, offsets, r, which=None):
     return dict(index=which, tri=t, rowcol=rc, bary=b, xyz=x)
 
 
+def export_record(workload, smp: Samples, values=None) -> dict:
+    """The per-sample export record of Section 3.3.3 for the oracle's samples: value, object id,
+    triangle id, barycentrics (w0, w1, w2), mesh-local position and world position. The local
+    position solves M x_local + t = x_world with the mesh's own FP64 transform (np.linalg.solve;
+    the inverse is not formed)."""
+    tri_mesh = np.repeat(np.arange(len(workload.meshes)), [m.n_tris for m in workload.meshes])
+    mesh = tri_mesh[smp.tri]
+    local = np.empty_like(smp.xyz)
+    for mi, m in enumerate(workload.meshes):
+        sel = mesh == mi
+        if sel.any():
+            T = np.asarray(m.transform, np.float64)
+            local[sel] = np.linalg.solve(T[:3, :3], (smp.xyz[sel] - T[:3, 3]).T).T
+    return dict(value=None if values is None else np.asarray(values, np.float64),
+                object_id=tri_object(workload)[smp.tri], triangle=smp.tri.copy(), bary3=smp.bary.copy(),
+                local_xyz=local, world_xyz=smp.xyz.copy())
+
+
 def run(workload, which=None, delta_abs=0.0, cone_band=0.0, record=False, nthreads=0):
     """Whole method for one workload: world triangles, counts, the chosen samples (all by
     default), their densities per window and the normalised maps."""

@@ -43,6 +43,8 @@ struct gm_scene {
     float4* tri_canon = nullptr;     // n_tris x 3 float4 (v0, v1, v2), stored (mesh) order
     uint32_t* tri_mesh = nullptr;    // n_tris mesh index
     uint32_t* mesh_object = nullptr; // n_meshes object id
+    double* mesh_inv = nullptr;      // n_meshes x 12: world -> local affine map (row-major 3x4)
+    bool mesh_inv_ok = true;         // every mesh transform was invertible
     float4* nodes = nullptr;         // (n_tris - 1) x 4 float4: child boxes + child links
     float4* bvh_tris = nullptr;      // n_tris x 3 float4 in leaf order, v0.w = global tri id
     uint32_t depth = 0;

@@ -453,6 +453,79 @@ extern "C" gm_status gm_samples_copy(const gm_samples* sm, float* xyz, uint32_t*
     return st;
 }
 
+namespace {
+__global__ void k_export_record(const float4* __restrict__ pos, const float2* __restrict__ bary,
+                                const uint32_t* __restrict__ tri_mesh, const uint32_t* __restrict__ mesh_obj,
+                                const double* __restrict__ inv, const float* __restrict__ values, uint32_t n,
+                                uint32_t nt, float* __restrict__ value, uint32_t* __restrict__ obj,
+                                uint32_t* __restrict__ tri, float* __restrict__ b3, float* __restrict__ local,
+                                float* __restrict__ world) {
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float4 p = pos[j];
+    const uint32_t t = __float_as_uint(p.w);
+    const uint32_t m = t < nt ? tri_mesh[t] : 0u;
+    if (value) value[j] = values[j];
+    if (obj) obj[j] = t < nt ? mesh_obj[m] : 0xffffffffu;
+    if (tri) tri[j] = t;
+    if (b3) {
+        const float2 b = bary ? bary[j] : make_float2(0.f, 0.f);
+        b3[3 * j] = 1.f - b.x - b.y;
+        b3[3 * j + 1] = b.x;
+        b3[3 * j + 2] = b.y;
+    }
+    if (world) {
+        world[3 * j] = p.x;
+        world[3 * j + 1] = p.y;
+        world[3 * j + 2] = p.z;
+    }
+    if (local) {
+        const double* A = inv + 12 * m;
+        for (int r = 0; r < 3; ++r)
+            local[3 * j + r] = (float)(A[4 * r] * p.x + A[4 * r + 1] * p.y + A[4 * r + 2] * p.z + A[4 * r + 3]);
+    }
+}
+}  // namespace
+
+extern "C" gm_status gm_samples_export(const gm_samples* sm, const gm_map* mp, uint32_t window,
+                                       const gm_export_dst* dst, gm_stream stream) {
+    if (!sm || !mp || !dst) return gm_set_error(GM_ERR_INVALID_ARG, "gm_samples_export: null argument");
+    if (mp->ns != sm->n || window >= mp->W)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_samples_export: map does not match samples or bad window");
+    if (dst->local_xyz && !sm->scene->mesh_inv_ok)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_samples_export: a mesh transform is singular (no local frame)");
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t n = (uint32_t)sm->n;
+    if (n == 0) return GM_OK;
+    void* outs[6] = {dst->value, dst->object_id, dst->triangle, dst->bary3, dst->local_xyz, dst->world_xyz};
+    const size_t sizes[6] = {4ull * n, 4ull * n, 4ull * n, 12ull * n, 12ull * n, 12ull * n};
+    void* dev[6] = {};
+    bool owned[6] = {};
+    gm_status st = GM_OK;
+    for (int k = 0; k < 6 && st == GM_OK; ++k) {
+        if (!outs[k]) continue;
+        if (gm_is_device_ptr(outs[k])) dev[k] = outs[k];
+        else if ((st = gm_alloc(&dev[k], sizes[k], s)) == GM_OK) owned[k] = true;
+    }
+    if (st == GM_OK) {
+        const gm_scene* sc = sm->scene;
+        k_export_record<<<gm_div_up(n, 256), 256, 0, s>>>(sm->pos, sm->bary, sc->tri_mesh, sc->mesh_object, sc->mesh_inv,
+                                                         mp->values + (size_t)window * mp->ns, n, sc->n_tris,
+                                                         (float*)dev[0], (uint32_t*)dev[1], (uint32_t*)dev[2],
+                                                         (float*)dev[3], (float*)dev[4], (float*)dev[5]);
+        sc->ctx->launches += 1;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) st = gm_cuda_error(e, "gm_samples_export launch");
+    }
+    for (int k = 0; k < 6; ++k) {
+        if (owned[k]) {
+            if (st == GM_OK) st = gm_copy_out(outs[k], dev[k], sizes[k], s);
+            cudaFreeAsync(dev[k], s);
+        }
+    }
+    return st;
+}
+
 extern "C" void gm_samples_free(gm_samples* sm) {
     if (!sm) return;
     cudaFree(sm->pos);

@@ -532,6 +532,29 @@ static gm_status build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n
         base += d.n_tris;
     }
     GM_TRY_CUDA(cudaMemcpyAsync(sc->mesh_object, objs.data(), sizeof(uint32_t) * n_meshes, cudaMemcpyHostToDevice, s));
+    // world -> mesh-local maps for the export format (affine inverse in FP64)
+    {
+        std::vector<double> inv(12 * (size_t)n_meshes, 0.0);
+        for (uint32_t m = 0; m < n_meshes; ++m) {
+            const double* M = meshes[m].transform;
+            const double a = M[0], b = M[1], c = M[2], d = M[4], e2 = M[5], f = M[6], g = M[8], h = M[9], k = M[10];
+            const double det = a * (e2 * k - f * h) - b * (d * k - f * g) + c * (d * h - e2 * g);
+            if (!(std::fabs(det) > 1e-300) || !std::isfinite(det)) {
+                sc->mesh_inv_ok = false;
+                continue;
+            }
+            const double r[9] = {(e2 * k - f * h) / det, (c * h - b * k) / det, (b * f - c * e2) / det,
+                                 (f * g - d * k) / det,  (a * k - c * g) / det,  (c * d - a * f) / det,
+                                 (d * h - e2 * g) / det, (b * g - a * h) / det,  (a * e2 - b * d) / det};
+            for (int i = 0; i < 3; ++i) {
+                for (int j = 0; j < 3; ++j) inv[12 * m + 4 * i + j] = r[3 * i + j];
+                inv[12 * m + 4 * i + 3] = -(r[3 * i] * M[3] + r[3 * i + 1] * M[7] + r[3 * i + 2] * M[11]);
+            }
+        }
+        SC_ALLOC(sc->mesh_inv, sizeof(double) * 12 * n_meshes);
+        GM_TRY_CUDA(cudaMemcpyAsync(sc->mesh_inv, inv.data(), sizeof(double) * 12 * n_meshes, cudaMemcpyHostToDevice, s));
+        GM_TRY_CUDA(cudaStreamSynchronize(s));   // inv is a host temporary
+    }
 
     uint64_t* keys = nullptr;
     uint32_t* order = nullptr;
@@ -741,6 +764,7 @@ extern "C" void gm_scene_free(gm_scene* sc) {
     cudaFree(sc->tri_canon);
     cudaFree(sc->tri_mesh);
     cudaFree(sc->mesh_object);
+    cudaFree(sc->mesh_inv);
     cudaFree(sc->nodes);
     cudaFree(sc->nodes4);
     cudaFree(sc->bvh_tris);

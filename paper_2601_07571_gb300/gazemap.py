@@ -55,6 +55,11 @@ class gm_field_cfg(C.Structure):
 GM_FIELD_N_PARAMS = 16705
 
 
+class gm_export_dst(C.Structure):
+    _fields_ = [("value", C.c_void_p), ("object_id", C.c_void_p), ("triangle", C.c_void_p), ("bary3", C.c_void_p),
+                ("local_xyz", C.c_void_p), ("world_xyz", C.c_void_p)]
+
+
 class gm_map_stats(C.Structure):
     _fields_ = [("pairs", C.c_uint64), ("in_cone", C.c_uint64), ("visible", C.c_uint64),
                 ("n_windows", C.c_uint32), ("n_fixations_used", C.c_uint32), ("prep_ms", C.c_float),
@@ -87,6 +92,7 @@ _SIGS = {
     "gm_samples_offsets": (C.c_int, [_P, _P, _P]),
     "gm_samples_copy": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "gm_samples_free": (None, [_P]),
+    "gm_samples_export": (C.c_int, [_P, _P, C.c_uint32, C.POINTER(gm_export_dst), _P]),
     "gm_tri_offsets_noalloc": (C.c_int, [_P, _P, _P, C.c_uint32, _P, _P]),
     "gm_accumulate_fixations": (C.c_int, [_P, _P, C.POINTER(gm_fixations), C.POINTER(gm_params), _P,
                                           C.POINTER(_P)]),
@@ -272,6 +278,12 @@ def gm_samples_offsets(samples, out, stream=None) -> None:
 
 def gm_samples_copy(samples, xyz=None, tri=None, bary2=None, obj=None, stream=None) -> None:
     _check(lib().gm_samples_copy(samples, _ptr(xyz), _ptr(tri), _ptr(bary2), _ptr(obj), _stream(stream)))
+
+
+def gm_samples_export(samples, m, window: int, value=None, object_id=None, triangle=None, bary3=None,
+                      local_xyz=None, world_xyz=None, stream=None) -> None:
+    dst = gm_export_dst(_ptr(value), _ptr(object_id), _ptr(triangle), _ptr(bary3), _ptr(local_xyz), _ptr(world_xyz))
+    _check(lib().gm_samples_export(samples, m, int(window), C.byref(dst), _stream(stream)))
 
 
 def gm_samples_free(samples) -> None:
