@@ -137,10 +137,23 @@ gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_mes
 enum { GM_BUILD_LBVH = 0, GM_BUILD_PLOC = 1, GM_BUILD_DEFAULT = GM_BUILD_PLOC };
 typedef struct {
     int32_t builder;
+    int32_t dynamic;   /* nonzero: keep the mesh-local triangles (48 B per triangle) so that
+                          gm_scene_pose can move the meshes later */
 } gm_build_opts;
 gm_status gm_build_scene_opts(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes,
                               const gm_build_opts* opts, gm_stream stream, gm_scene** out);
 gm_status gm_scene_info(const gm_scene* scene, uint32_t* n_tris, uint32_t* bvh_depth);
+/* Dynamic scenes. The surface-bound map ties densities to objects, not to world space (Section 2
+ * contrasts this with volumetric maps, which leave fixations behind when an object moves), so a
+ * mesh that moves carries its samples with it. gm_scene_pose gives every mesh a new row-major
+ * 4 x 4 transform (`transforms`: n_meshes x 16 FP64, host memory): the world triangles are
+ * recomputed from the kept mesh-local ones exactly as at build time (a pose equal to the build's
+ * transforms reproduces them bit for bit), the BVH boxes are refit bottom-up over the unchanged
+ * hierarchy (same depth, looser boxes as meshes move apart), the export's local frames follow,
+ * and the 4-wide collapse is dropped. Requires a scene built with gm_build_opts.dynamic;
+ * GM_ERR_INVALID_ARG otherwise or on a non-finite transform. Synchronises `stream` once. Sample
+ * sets of the scene keep stale positions until gm_samples_follow. */
+gm_status gm_scene_pose(gm_scene* scene, const double* transforms, gm_stream stream);
 /* Copy the world triangles (n_tris x 9 FP32, v0 v1 v2) to `dst` (host or device). */
 gm_status gm_scene_triangles(const gm_scene* scene, float* dst, gm_stream stream);
 void gm_scene_free(gm_scene* scene);
@@ -179,6 +192,10 @@ gm_status gm_samples_offsets(const gm_samples* s, int64_t* dst, gm_stream stream
 gm_status gm_samples_copy(const gm_samples* s, float* xyz, uint32_t* tri, float* bary2,
                           uint32_t* obj, gm_stream stream);
 void gm_samples_free(gm_samples* s);
+/* Re-place a Philox or grid sample set on its scene's current pose: same triangle, same
+ * barycentrics (same counts per triangle: the densities of the first pose stand), positions from
+ * the posed vertices by the sampler's own arithmetic. GM_ERR_INVALID_ARG for explicit points. */
+gm_status gm_samples_follow(gm_samples* s, gm_stream stream);
 
 /* The export record of Section 3.3.3, one entry per sample in stored order; any destination may
  * be NULL, each host or device: value (FP32, the map's window `window`, normalised iff the map
@@ -230,6 +247,17 @@ gm_status gm_tri_offsets_noalloc(gm_ctx* ctx, const float* tri_xyz, const double
  * the call returns GM_WARN_EMPTY at gm_map_info). */
 gm_status gm_accumulate_fixations(gm_scene* scene, gm_samples* samples, const gm_fixations* fix,
                                   const gm_params* params, gm_stream stream, gm_map** out);
+/* The same accumulation for a scene whose meshes move from window to window (params->window_s > 0
+ * gives the windows; one window otherwise). `window_transforms` holds n_windows x n_meshes x 16
+ * FP64 row-major transforms in host memory. For each window k in order: gm_scene_pose with the
+ * window's transforms, gm_samples_follow on `samples`, then the fixations of window k only
+ * (window k = floor((t - t_begin) / window_s), as above) are accumulated into window k of one
+ * map; every window is normalised at the end when params->normalize. The scene and the samples
+ * are left in the last window's pose. GM_F_TIMING is ignored (no stage times). Requires a scene
+ * built with gm_build_opts.dynamic and a Philox or grid sample set. */
+gm_status gm_accumulate_dynamic(gm_scene* scene, gm_samples* samples, const gm_fixations* fix,
+                                const gm_params* params, const double* window_transforms, gm_stream stream,
+                                gm_map** out);
 /* Number of windows, samples and statistics; waits for the map's work to finish. */
 gm_status gm_map_info(gm_map* map, uint32_t* n_windows, uint64_t* n_samples, gm_map_stats* stats);
 /* Copy window `window` (n_samples FP32 values in stored sample order) to `dst` (host or

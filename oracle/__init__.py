@@ -295,6 +295,36 @@ def export_record(workload, smp: Samples, values=None) -> dict:
                 local_xyz=local, world_xyz=smp.xyz.copy())
 
 
+def run_dynamic(workload, window_transforms, which=None, delta_abs=0.0, cone_band=0.0, nthreads=0):
+    """Densities of a scene whose meshes move from window to window. Surface-bound values belong
+    to the objects, not to world space (Section 2 holds this against volumetric maps, whose cells
+    stay behind when an object moves), so every sample keeps its triangle and barycentrics: the
+    counts are those of the workload's own (rest) transforms, and in window k the samples sit on
+    the triangles posed by window_transforms[k] (n_meshes x 4 x 4 each). Window k accumulates the
+    fixations of window k only (the windows of Section 3.2's time interval), against the scene in
+    that pose. Returns density/amb/sens of shape (n_windows, n_samples) and the normalised maps."""
+    import copy
+    p = workload.params
+    W = n_windows(p)
+    wins = fixation_windows(workload.fixations.timestamp_s, p)
+    off = tri_offsets(areas(world_triangles(workload)), tri_density(workload))
+    n = int(off[-1]) if which is None else len(which)
+    dens, amb, sens = (np.zeros((W, n)) for _ in range(3))
+    for k in range(W):
+        wk = copy.copy(workload)
+        wk.meshes = [copy.copy(m) for m in workload.meshes]
+        for m, T in zip(wk.meshes, window_transforms[k]):
+            m.transform = np.asarray(T, np.float64)
+        tri = world_triangles(wk)
+        smp = samples(tri, off, workload.seed, workload.session, which)
+        sel = np.nonzero(wins == k)[0]
+        acc = accumulate(tri, smp.xyz, smp.tri, workload.fixations.subset(sel), p, delta_abs, cone_band,
+                         nthreads=nthreads)
+        dens[k], amb[k], sens[k] = acc["density"][k], acc["amb"][k], acc["sens"][k]
+    norm = np.stack([normalize(d)[0] for d in dens])
+    return dict(offsets=off, density=dens, amb=amb, sens=sens, normalized=norm)
+
+
 def run(workload, which=None, delta_abs=0.0, cone_band=0.0, record=False, nthreads=0):
     """Whole method for one workload: world triangles, counts, the chosen samples (all by
     default), their densities per window and the normalised maps."""

@@ -37,7 +37,7 @@ namespace {
 // ------------------------------------------------------------------------------------------
 __global__ void k_fix_keys(const double* __restrict__ ts, const float* __restrict__ eye,
                            const float* __restrict__ gaze, const float* __restrict__ dur, uint32_t nf,
-                           double t_begin, double t_end, double window_s, uint32_t W,
+                           double t_begin, double t_end, double window_s, uint32_t W, uint32_t only,
                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                            uint32_t* __restrict__ n_valid, int* __restrict__ err) {
     uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -48,6 +48,7 @@ __global__ void k_fix_keys(const double* __restrict__ ts, const float* __restric
         // the window bucket of a FP64 timestamp (one division per fixation)
         double w = window_s > 0.0 ? floor((t - t_begin) / window_s) : 0.0;
         if (w >= 0.0 && w < (double)W) key = (uint32_t)w;
+        if (only != 0xffffffffu && key != only) key = W;   // one window of a dynamic scene at a time
     }
     float gx = gaze[3 * f], gy = gaze[3 * f + 1], gz = gaze[3 * f + 2];
     float ex = eye[3 * f], ey = eye[3 * f + 1], ez = eye[3 * f + 2];
@@ -85,18 +86,18 @@ __global__ void k_fix_pack(const uint32_t* __restrict__ keys, const uint32_t* __
 // rays (densely gazed patches) spread over the whole run instead of forming a tail. MINB is the
 // minimum number of resident blocks per SM the register allocation must allow (3: up to 80
 // registers, 4: up to 64).
-template <bool DEBUG, bool COMPACT, bool WIDE, int MINB>
-__global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate(
+template <bool DEBUG, bool COMPACT, bool WIDE, int MINB, int NT = ACC_THREADS>
+__global__ void __launch_bounds__(NT, MINB) k_accumulate(
     const float4* __restrict__ spos, const uint32_t* __restrict__ sidx, const float4* __restrict__ fix,
     const uint32_t* __restrict__ n_fix_dev, const float4* __restrict__ nodes, const float4* __restrict__ tris,
     AccParams P, uint32_t n_tiles, int persistent, float* __restrict__ out, unsigned int* __restrict__ max_bits,
     unsigned long long* __restrict__ counters, int* __restrict__ err, DebugOut dbg) {
-    constexpr int QN = COMPACT ? ACC_THREADS * SPT : 1;
+    constexpr int QN = COMPACT ? NT * SPT : 1;
     __shared__ float4 wsmp[QN];     // per warp: its WARP_TILE samples (x, y, z, own triangle)
     __shared__ float2 wacc[QN];     // per warp: (sum, compensation) of each sample
     __shared__ uint16_t qslot[QN];  // per warp: queue of in-cone sample slots
     __shared__ float qg[QN];        // per warp: their weights
-    __shared__ int qhead[ACC_THREADS / 32];   // per warp: next queue entry to hand out
+    __shared__ int qhead[NT / 32];  // per warp: next queue entry to hand out
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int wb = COMPACT ? warp * WARP_TILE : 0;
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate(
             tile = __shfl_sync(0xffffffffu, tile, 0);
         } else {
             if (round > 0) break;
-            tile = blockIdx.x * (ACC_THREADS / 32) + warp;
+            tile = blockIdx.x * (NT / 32) + warp;
         }
         if (tile >= n_tiles) break;
         warp_tile<DEBUG, COMPACT, WIDE>(tile, spos, sidx, fix, nf, nodes, tris, P, out, max_bits, wsmp + wb, wacc + wb,
@@ -121,10 +122,10 @@ __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate(
 
 // (The driver's default shared-memory carveout is kept: preferring the largest L1 leaves room for
 // fewer blocks per SM and measured 316 vs 253 ms at the paper scene.)
-template <bool D, bool Cm, bool Wd, int Mb>
+template <bool D, bool Cm, bool Wd, int Mb, int NT = ACC_THREADS>
 int acc_occupancy() {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_accumulate<D, Cm, Wd, Mb>, ACC_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_accumulate<D, Cm, Wd, Mb, NT>, NT, 0);
     return b > 0 ? b : 1;
 }
 
@@ -173,12 +174,47 @@ __global__ void k_gather_values(const float* __restrict__ v, uint64_t ns, uint32
     out[i] = v[(size_t)w * ns + j];
 }
 
-}  // namespace
+__global__ void k_add_valid(unsigned long long* __restrict__ c, const uint32_t* __restrict__ n_valid) {
+    c[0] += *n_valid;
+}
 
-extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const gm_fixations* fx,
-                                             const gm_params* prm, gm_stream stream, gm_map** out) {
-    if (!sc || !sm || !fx || !prm || !out) return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: null argument");
-    *out = nullptr;
+// v / max for every window of a map (windows whose maximum is 0 stay 0); returns launches.
+int launch_normalize(gm_map* mp, int n_sm, cudaStream_t s) {
+    const uint64_t ns = mp->ns, W = mp->W;
+    if (ns == 0) return 0;
+    // blocks per window: enough to cover the window with float4s, and ~8 waves overall
+    const uint64_t per_win = std::max<uint64_t>(1, std::min<uint64_t>(gm_div_up(ns, 1024),
+                                                                     (uint64_t)n_sm * 8 / std::max<uint64_t>(1, W) + 1));
+    int launches = 0;
+    for (uint64_t w0 = 0; w0 < W; w0 += 65535) {
+        dim3 grid((uint32_t)per_win, (uint32_t)std::min<uint64_t>(65535, W - w0));
+        k_normalize<<<grid, 256, 0, s>>>(mp->values, ns, mp->max_bits, (uint32_t)w0);
+        ++launches;
+    }
+    return launches;
+}
+
+gm_status n_windows_of(const gm_params* prm, uint64_t* W_out) {
+    uint64_t W = 1;
+    if (prm->window_s > 0.0) {
+        if (!std::isfinite(prm->t_begin) || !std::isfinite(prm->t_end) || !std::isfinite(prm->window_s))
+            return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: windows need a finite interval");
+        W = (uint64_t)std::ceil((prm->t_end - prm->t_begin) / prm->window_s);
+        if (W == 0) W = 1;
+        if (W > (1u << 24)) return gm_set_error(GM_ERR_UNSUPPORTED, "gm_accumulate_fixations: more than 2^24 windows");
+    }
+    *W_out = W;
+    return GM_OK;
+}
+
+// The accumulation of one fixation set. into == nullptr: a new map (returned in *out) over all
+// windows. into != nullptr: adds the fixations of window `only_window` to that existing map
+// (no normalisation, no stage timing), for dynamic scenes posed window by window.
+gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, const gm_params* prm,
+                          gm_stream stream, gm_map* into, int64_t only_window, gm_map** out) {
+    if (!sc || !sm || !fx || !prm || (!out && !into))
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: null argument");
+    if (out) *out = nullptr;
     if (sm->scene != sc) return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: samples belong to another scene");
     if (!(prm->theta_rad > 0.f) || !(prm->theta_rad < 1.5f))
         return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: theta must be in (0, 1.5) rad");
@@ -191,31 +227,30 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
     if (fx->n > 0 && (!fx->eye_xyz || !fx->gaze_xyz || !fx->duration_s || !fx->timestamp_s))
         return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: null fixation array");
     uint64_t W = 1;
-    if (prm->window_s > 0.0) {
-        if (!std::isfinite(prm->t_begin) || !std::isfinite(prm->t_end) || !std::isfinite(prm->window_s))
-            return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: windows need a finite interval");
-        W = (uint64_t)std::ceil((prm->t_end - prm->t_begin) / prm->window_s);
-        if (W == 0) W = 1;
-        if (W > (1u << 24)) return gm_set_error(GM_ERR_UNSUPPORTED, "gm_accumulate_fixations: more than 2^24 windows");
-    }
-    const bool debug = (prm->flags & GM_F_DEBUG_PAIRS) && prm->debug_pair_cap > 0;
+    GM_TRY(n_windows_of(prm, &W));
+    if (into && (into->W != W || into->ns != sm->n))
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: map does not match windows or samples");
+    const bool debug = into ? ((prm->flags & GM_F_DEBUG_PAIRS) && into->dbg_cap > 0)
+                            : ((prm->flags & GM_F_DEBUG_PAIRS) && prm->debug_pair_cap > 0);
     cudaStream_t s = (cudaStream_t)stream;
     gm_ctx* ctx = sc->ctx;
     GM_TRY_CUDA(cudaSetDevice(ctx->device));
     const uint64_t ns = sm->n;
     const uint32_t nf = fx->n;
 
-    gm_map* mp = new gm_map();
-    mp->ctx = ctx;
-    mp->W = (uint32_t)W;
-    mp->ns = ns;
-    mp->stream = s;
-    mp->timing = (prm->flags & GM_F_TIMING) != 0;
-    mp->stats.n_windows = (uint32_t)W;
+    gm_map* mp = into ? into : new gm_map();
+    if (!into) {
+        mp->ctx = ctx;
+        mp->W = (uint32_t)W;
+        mp->ns = ns;
+        mp->stream = s;
+        mp->timing = (prm->flags & GM_F_TIMING) != 0;
+        mp->stats.n_windows = (uint32_t)W;
+    }
     std::vector<void*> tmp;
     auto fail = [&](gm_status st) {
         for (void* p : tmp) cudaFreeAsync(p, s);
-        gm_map_free(mp);
+        if (!into) gm_map_free(mp);
         return st;
     };
     gm_status st;
@@ -227,20 +262,26 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
 #define MAP_ALLOC(ptr, bytes) \
     if ((st = gm_alloc((void**)&(ptr), (bytes), s)) != GM_OK) return fail(st)
 
-    if (mp->timing) {
+    const bool timing = mp->timing && !into;
+    if (timing) {
         for (int i = 0; i < 4; ++i) {
             cudaError_t e = cudaEventCreate(&mp->ev[i]);
             if (e != cudaSuccess) return fail(gm_cuda_error(e, "cudaEventCreate"));
         }
         cudaEventRecord(mp->ev[0], s);
     }
-    MAP_ALLOC(mp->values, sizeof(float) * W * ns);
-    MAP_ALLOC(mp->max_bits, sizeof(unsigned int) * W);
-    MAP_ALLOC(mp->counters, sizeof(unsigned long long) * 8);
-    GM_TRY_CUDA(cudaMemsetAsync(mp->max_bits, 0, sizeof(unsigned int) * W, s));
-    GM_TRY_CUDA(cudaMemsetAsync(mp->counters, 0, sizeof(unsigned long long) * 8, s));
-    if (W > 1) GM_TRY_CUDA(cudaMemsetAsync(mp->values, 0, sizeof(float) * W * ns, s));
-    if (debug) {
+    if (into) {
+        // the persistent kernel's tile counter starts from 0 on every launch
+        GM_TRY_CUDA(cudaMemsetAsync(&mp->counters[6], 0, sizeof(unsigned long long), s));
+    } else {
+        MAP_ALLOC(mp->values, sizeof(float) * W * ns);
+        MAP_ALLOC(mp->max_bits, sizeof(unsigned int) * W);
+        MAP_ALLOC(mp->counters, sizeof(unsigned long long) * 8);
+        GM_TRY_CUDA(cudaMemsetAsync(mp->max_bits, 0, sizeof(unsigned int) * W, s));
+        GM_TRY_CUDA(cudaMemsetAsync(mp->counters, 0, sizeof(unsigned long long) * 8, s));
+        if (W > 1) GM_TRY_CUDA(cudaMemsetAsync(mp->values, 0, sizeof(float) * W * ns, s));
+    }
+    if (debug && !into) {
         mp->dbg_cap = prm->debug_pair_cap;
         MAP_ALLOC(mp->dbg_sample, sizeof(uint32_t) * mp->dbg_cap);
         MAP_ALLOC(mp->dbg_fix, sizeof(uint32_t) * mp->dbg_cap);
@@ -274,8 +315,9 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
     if (nf > 0) {
         k_fix_keys<<<gm_div_up(nf, 256), 256, 0, s>>>((const double*)d_ts, (const float*)d_eye, (const float*)d_gaze,
                                                       (const float*)d_dur, nf, prm->t_begin, prm->t_end,
-                                                      prm->window_s > 0.0 ? prm->window_s : 0.0, (uint32_t)W, keys, vals,
-                                                      n_valid, ctx->dev_err);
+                                                      prm->window_s > 0.0 ? prm->window_s : 0.0, (uint32_t)W,
+                                                      only_window >= 0 ? (uint32_t)only_window : 0xffffffffu, keys,
+                                                      vals, n_valid, ctx->dev_err);
         ++launches;
         int bits = 1;
         while (bits < 32 && (1ull << bits) <= W) ++bits;
@@ -284,7 +326,7 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
                                                       (const float*)d_dur, nf, wnorm, packed, orig);
         ++launches;
     }
-    if (mp->timing) cudaEventRecord(mp->ev[1], s);
+    if (timing) cudaEventRecord(mp->ev[1], s);
 
     // ---- accumulate -----------------------------------------------------------------------
     AccParams P;
@@ -316,16 +358,16 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
         const float4* tree = wide ? sc->nodes4 : sc->nodes;
         const int code = (compact ? 1 : 0) | (wide ? 2 : 0) | (occ4 ? 4 : 0);
         // persistent grid: every resident block slot once, never more blocks than tiles need
-#define GM_LAUNCH_ACC(D, Cm, Wd, Mb)                                                                           \
+#define GM_LAUNCH_ACC_NT(D, Cm, Wd, Mb, NT)                                                                    \
     do {                                                                                                       \
-        const uint32_t all = gm_div_up(n_tiles, ACC_THREADS / 32);                                            \
-        const uint32_t grid = persistent ? std::min<uint32_t>((uint32_t)ctx->n_sm * acc_occupancy<D, Cm, Wd, Mb>(), \
-                                                              all)                                             \
-                                         : all;                                                                \
-        k_accumulate<D, Cm, Wd, Mb><<<grid, ACC_THREADS, 0, s>>>(spos, sidx, packed, n_valid, tree, sc->bvh_tris, \
+        const uint32_t all = gm_div_up(n_tiles, NT / 32);                                                      \
+        const uint32_t grid =                                                                                  \
+            persistent ? std::min<uint32_t>((uint32_t)ctx->n_sm * acc_occupancy<D, Cm, Wd, Mb, NT>(), all) : all; \
+        k_accumulate<D, Cm, Wd, Mb, NT><<<grid, NT, 0, s>>>(spos, sidx, packed, n_valid, tree, sc->bvh_tris,    \
                                                                 P, n_tiles, persistent, mp->values,            \
                                                                 mp->max_bits, mp->counters, ctx->dev_err, dbg); \
     } while (0)
+#define GM_LAUNCH_ACC(D, Cm, Wd, Mb) GM_LAUNCH_ACC_NT(D, Cm, Wd, Mb, ACC_THREADS)
         if (debug) {
             switch (code & 3) {
                 case 0: GM_LAUNCH_ACC(true, false, false, 3); break;
@@ -346,31 +388,75 @@ extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const
             }
         }
 #undef GM_LAUNCH_ACC
+#undef GM_LAUNCH_ACC_NT
         ++launches;
     }
-    if (mp->timing) cudaEventRecord(mp->ev[2], s);
-    if (prm->normalize && ns > 0) {
-        // blocks per window: enough to cover the window with float4s, and ~8 waves overall
-        const uint64_t per_win = std::max<uint64_t>(1, std::min<uint64_t>(gm_div_up(ns, 1024),
-                                                                         (uint64_t)ctx->n_sm * 8 / std::max<uint64_t>(1, W) + 1));
-        for (uint64_t w0 = 0; w0 < W; w0 += 65535) {
-            dim3 grid((uint32_t)per_win, (uint32_t)std::min<uint64_t>(65535, W - w0));
-            k_normalize<<<grid, 256, 0, s>>>(mp->values, ns, mp->max_bits, (uint32_t)w0);
-        }
-        ++launches;
-    }
-    if (mp->timing) cudaEventRecord(mp->ev[3], s);
+    if (timing) cudaEventRecord(mp->ev[2], s);
+    if (prm->normalize && !into) launches += launch_normalize(mp, ctx->n_sm, s) > 0 ? 1 : 0;
+    if (timing) cudaEventRecord(mp->ev[3], s);
     // keep the valid-fixation count with the map for gm_map_info
-    GM_TRY_CUDA(cudaMemcpyAsync(&mp->counters[3], n_valid, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    if (into) {
+        k_add_valid<<<1, 1, 0, s>>>(&mp->counters[3], n_valid);
+        ++launches;
+    } else {
+        GM_TRY_CUDA(cudaMemcpyAsync(&mp->counters[3], n_valid, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_accumulate_fixations launch"));
     for (void* p : tmp) cudaFreeAsync(p, s);
-    mp->stats.launches = (uint32_t)launches;
+    mp->stats.launches = (into ? mp->stats.launches : 0) + (uint32_t)launches;
     ctx->launches += launches;
-    *out = mp;
+    if (out) *out = mp;
     return GM_OK;
 #undef TMP_ALLOC
 #undef MAP_ALLOC
+}
+
+}  // namespace
+
+extern "C" gm_status gm_accumulate_fixations(gm_scene* sc, gm_samples* sm, const gm_fixations* fx,
+                                             const gm_params* prm, gm_stream stream, gm_map** out) {
+    if (!out) return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_fixations: null argument");
+    return accumulate_impl(sc, sm, fx, prm, stream, nullptr, -1, out);
+}
+
+extern "C" gm_status gm_accumulate_dynamic(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, const gm_params* prm,
+                                           const double* window_transforms, gm_stream stream, gm_map** out) {
+    if (!sc || !sm || !fx || !prm || !window_transforms || !out)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_dynamic: null argument");
+    *out = nullptr;
+    if (sm->scene != sc) return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_dynamic: samples belong to another scene");
+    if (!sc->tri_local)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_dynamic: the scene was not built with gm_build_opts.dynamic");
+    if (sm->kind == GM_SAMPLES_POINTS)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_accumulate_dynamic: explicit points do not follow the meshes");
+    uint64_t W = 1;
+    GM_TRY(n_windows_of(prm, &W));
+    gm_params p = *prm;
+    p.normalize = 0;
+    p.flags &= ~(int32_t)GM_F_TIMING;
+    gm_map* mp = nullptr;
+    for (uint64_t k = 0; k < W; ++k) {
+        gm_status st = gm_scene_pose(sc, window_transforms + 16 * (size_t)sc->n_meshes * k, stream);
+        if (st == GM_OK) st = gm_samples_follow(sm, stream);
+        if (st == GM_OK) st = accumulate_impl(sc, sm, fx, &p, stream, mp, (int64_t)k, k == 0 ? &mp : nullptr);
+        if (st != GM_OK) {
+            gm_map_free(mp);
+            return st;
+        }
+    }
+    if (prm->normalize) {
+        const int l = launch_normalize(mp, sc->ctx->n_sm, (cudaStream_t)stream);
+        sc->ctx->launches += l;
+        mp->stats.launches += (uint32_t)l;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            gm_map_free(mp);
+            return gm_cuda_error(e, "gm_accumulate_dynamic normalise");
+        }
+    }
+    *out = mp;
+    return GM_OK;
 }
 
 extern "C" gm_status gm_map_info(gm_map* mp, uint32_t* n_windows, uint64_t* n_samples, gm_map_stats* stats) {

@@ -45,6 +45,7 @@ struct gm_scene {
     uint32_t* mesh_object = nullptr; // n_meshes object id
     double* mesh_inv = nullptr;      // n_meshes x 12: world -> local affine map (row-major 3x4)
     bool mesh_inv_ok = true;         // every mesh transform was invertible
+    float4* tri_local = nullptr;     // n_tris x 3 float4 mesh-local vertices (scenes built dynamic only)
     float4* nodes = nullptr;         // (n_tris - 1) x 4 float4: child boxes + child links
     float4* bvh_tris = nullptr;      // n_tris x 3 float4 in leaf order, v0.w = global tri id
     uint32_t depth = 0;
@@ -56,12 +57,18 @@ struct gm_scene {
     float box_lo[3], box_hi[3];      // world bounds of all vertices
 };
 
+enum { GM_SAMPLES_PHILOX = 0, GM_SAMPLES_GRID = 1, GM_SAMPLES_POINTS = 2 };
+
 struct gm_samples {
     gm_scene* scene = nullptr;
     uint64_t n = 0;
     float4* pos = nullptr;           // n: (x, y, z, global tri id as bits), stored order
     float2* bary = nullptr;          // n: (b1, b2); null for explicit points
     int64_t* tri_offset = nullptr;   // n_tris + 1; null for explicit points
+    int kind = 0;                    // GM_SAMPLES_PHILOX, GM_SAMPLES_GRID or GM_SAMPLES_POINTS
+    uint2 key{0u, 0u};               // Philox key (seed) of a Philox sample set
+    uint32_t session = 0;            // Philox counter word of a Philox sample set
+    uint32_t* res = nullptr;         // n_tris grid resolutions of a grid sample set
     // spatial work order for the accumulation (Morton order of the sample positions)
     float4* work_pos = nullptr;      // n, work order
     uint32_t* work_idx = nullptr;    // n, stored index of each work-order sample

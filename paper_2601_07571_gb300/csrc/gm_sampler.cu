@@ -268,10 +268,12 @@ extern "C" gm_status gm_sample_surface(gm_scene* sc, const double* density_per_m
     const uint32_t n = (uint32_t)total;
     if ((st = gm_alloc((void**)&sm->pos, sizeof(float4) * n, s)) != GM_OK) return fail(st);
     if ((st = gm_alloc((void**)&sm->bary, sizeof(float2) * n, s)) != GM_OK) return fail(st);
+    sm->kind = GM_SAMPLES_PHILOX;
+    sm->key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    sm->session = session;
     if (n > 0)
-        k_expand<<<gm_div_up(n, 256), 256, 0, s>>>(sm->tri_offset, nt, n, sc->tri_canon,
-                                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), session,
-                                                  sm->pos, sm->bary);
+        k_expand<<<gm_div_up(n, 256), 256, 0, s>>>(sm->tri_offset, nt, n, sc->tri_canon, sm->key, session, sm->pos,
+                                                  sm->bary);
     if (n > 0) ++launches;
     if ((st = build_work_order(sm, s, &launches)) != GM_OK) return fail(st);
     sc->ctx->launches += launches;
@@ -338,7 +340,8 @@ extern "C" gm_status gm_sample_surface_grid(gm_scene* sc, const double* density_
     sc->ctx->launches += launches;
     cudaFreeAsync(dens, s);
     cudaFreeAsync(cnt, s);
-    cudaFreeAsync(res, s);
+    sm->kind = GM_SAMPLES_GRID;
+    sm->res = res;   // kept: a dynamic scene re-places the grid samples on every pose
     dens = nullptr;
     cnt = nullptr;
     res = nullptr;
@@ -359,6 +362,7 @@ extern "C" gm_status gm_samples_from_points(gm_scene* sc, const float* xyz, cons
     gm_samples* sm = new gm_samples();
     sm->scene = sc;
     sm->n = n;
+    sm->kind = GM_SAMPLES_POINTS;
     void *dx = nullptr, *dt = nullptr;
     bool ox = false, ot = false;
     auto fail = [&](gm_status st) {
@@ -526,10 +530,35 @@ extern "C" gm_status gm_samples_export(const gm_samples* sm, const gm_map* mp, u
     return st;
 }
 
+extern "C" gm_status gm_samples_follow(gm_samples* sm, gm_stream stream) {
+    if (!sm) return gm_set_error(GM_ERR_INVALID_ARG, "gm_samples_follow: null samples");
+    if (sm->kind == GM_SAMPLES_POINTS)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_samples_follow: explicit points are not attached to a triangle frame");
+    const gm_scene* sc = sm->scene;
+    cudaStream_t s = (cudaStream_t)stream;
+    GM_TRY_CUDA(cudaSetDevice(sc->ctx->device));
+    const uint32_t n = (uint32_t)sm->n;
+    if (n == 0) return GM_OK;
+    // the same expansion as at sampling time, on the posed triangles: same counts, same
+    // barycentrics, new positions
+    if (sm->kind == GM_SAMPLES_PHILOX)
+        k_expand<<<gm_div_up(n, 256), 256, 0, s>>>(sm->tri_offset, sc->n_tris, n, sc->tri_canon, sm->key, sm->session,
+                                                  sm->pos, sm->bary);
+    else
+        k_grid_expand<<<gm_div_up(n, 256), 256, 0, s>>>(sm->tri_offset, sm->res, sc->n_tris, n, sc->tri_canon, sm->pos,
+                                                       sm->bary);
+    // the work order of the first pose is kept (it only groups samples into warp tiles)
+    k_gather_work<<<gm_div_up(n, 256), 256, 0, s>>>(sm->pos, sm->work_idx, n, sm->work_pos);
+    sc->ctx->launches += 2;
+    GM_TRY_CUDA(cudaGetLastError());
+    return GM_OK;
+}
+
 extern "C" void gm_samples_free(gm_samples* sm) {
     if (!sm) return;
     cudaFree(sm->pos);
     cudaFree(sm->bary);
+    cudaFree(sm->res);
     cudaFree(sm->tri_offset);
     cudaFree(sm->work_pos);
     cudaFree(sm->work_idx);

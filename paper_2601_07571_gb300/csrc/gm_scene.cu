@@ -457,8 +457,120 @@ __global__ void k_dfs_remap(const float4* __restrict__ nodes, const int* __restr
 
 }  // namespace
 
+// ---- dynamic scenes: re-pose every mesh, refit the boxes over the unchanged topology ----------
+// Mesh-local triangle vertices in stored (mesh) order, kept for re-posing.
+__global__ void k_gather_local(const float* __restrict__ v, const uint32_t* __restrict__ idx, uint32_t nt,
+                               uint32_t nv, uint32_t tri_base, float4* __restrict__ tri_local) {
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        uint32_t vi = idx[3 * t + k];
+        if (vi >= nv) vi = 0;   // the world gather of the same mesh reports the bad index
+        tri_local[3 * (tri_base + t) + k] = make_float4(v[3 * vi], v[3 * vi + 1], v[3 * vi + 2], 0.f);
+    }
+}
+
+// World triangles of a new pose: the transform of k_transform (same FP64 operation order, so a
+// pose equal to the build's transforms reproduces the built triangles bit for bit), one thread
+// per triangle; scene bounds as in k_gather (centroid box in [0, 6), vertex box in [6, 12)).
+__global__ void k_pose(const float4* __restrict__ tri_local, const uint32_t* __restrict__ tri_mesh,
+                       const double* __restrict__ xf, uint32_t nt, float4* __restrict__ tri_canon,
+                       unsigned int* __restrict__ bounds) {
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    float lo[6], hi[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) { lo[c] = INFINITY; hi[c] = -INFINITY; }
+    if (t < nt) {
+        const double* M = xf + 12 * tri_mesh[t];
+        float w[9];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 p = tri_local[3 * t + k];
+            const double x = p.x, y = p.y, z = p.z;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                double a = __dadd_rn(__dmul_rn(M[4 * r + 0], x), __dmul_rn(M[4 * r + 1], y));
+                a = __dadd_rn(a, __dmul_rn(M[4 * r + 2], z));
+                a = __dadd_rn(a, M[4 * r + 3]);
+                w[3 * k + r] = __double2float_rn(a);
+            }
+            tri_canon[3 * t + k] = make_float4(w[3 * k], w[3 * k + 1], w[3 * k + 2], 0.f);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = hi[a] = (w[a] + w[3 + a] + w[6 + a]) * (1.f / 3.f);
+            lo[3 + a] = fminf(fminf(w[a], w[3 + a]), w[6 + a]);
+            hi[3 + a] = fmaxf(fmaxf(w[a], w[3 + a]), w[6 + a]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0 && blockIdx.x * blockDim.x + (threadIdx.x & ~31u) < nt) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&bounds[a], f2ord(lo[a]));
+            atomicMax(&bounds[3 + a], f2ord(hi[a]));
+            atomicMin(&bounds[6 + a], f2ord(lo[3 + a]));
+            atomicMax(&bounds[9 + a], f2ord(hi[3 + a]));
+        }
+    }
+}
+
+// Triangle id of every leaf slot (v0.w of the leaf-order copy).
+__global__ void k_leaf_order(const float4* __restrict__ bvh_tris, uint32_t n, uint32_t* __restrict__ order) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) order[i] = __float_as_uint(bvh_tris[3 * i].w);
+}
+
+// Parents in the final node layout, from the child links (root: -1 from the memset).
+__global__ void k_final_parents(const float4* __restrict__ nodes, int n_int, int n_leaves,
+                                int* __restrict__ parent_node, int* __restrict__ parent_leaf) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_int) return;
+    const float4 l = nodes[4 * p + 3];
+    const int c[2] = {__float_as_int(l.x), __float_as_int(l.y)};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (c[k] >= 0) {
+            if (c[k] < n_int) parent_node[c[k]] = p;
+        } else if (~c[k] < n_leaves) {
+            parent_leaf[~c[k]] = p;
+        }
+    }
+}
+
+// Inverse affine maps (world -> mesh-local, row-major 3 x 4) of row-major 4 x 4 transforms, by the
+// adjugate in FP64; false if any transform is singular (its rows are left zero).
+static bool mesh_inverses(const double* xf, uint32_t n_meshes, std::vector<double>& inv) {
+    inv.assign(12 * (size_t)n_meshes, 0.0);
+    bool ok = true;
+    for (uint32_t m = 0; m < n_meshes; ++m) {
+        const double* M = xf + 16 * m;
+        const double a = M[0], b = M[1], c = M[2], d = M[4], e2 = M[5], f = M[6], g = M[8], h = M[9], k = M[10];
+        const double det = a * (e2 * k - f * h) - b * (d * k - f * g) + c * (d * h - e2 * g);
+        if (!(std::fabs(det) > 1e-300) || !std::isfinite(det)) {
+            ok = false;
+            continue;
+        }
+        const double r[9] = {(e2 * k - f * h) / det, (c * h - b * k) / det, (b * f - c * e2) / det,
+                             (f * g - d * k) / det,  (a * k - c * g) / det,  (c * d - a * f) / det,
+                             (d * h - e2 * g) / det, (b * g - a * h) / det,  (a * e2 - b * d) / det};
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) inv[12 * m + 4 * i + j] = r[3 * i + j];
+            inv[12 * m + 4 * i + 3] = -(r[3 * i] * M[3] + r[3 * i + 1] * M[7] + r[3 * i + 2] * M[11]);
+        }
+    }
+    return ok;
+}
+
 static gm_status build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes, int builder,
-                             gm_stream stream, gm_scene** out) {
+                             bool dynamic, gm_stream stream, gm_scene** out) {
     if (!ctx || !meshes || !out || n_meshes == 0)
         return gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene: null argument or no meshes");
     *out = nullptr;
@@ -501,6 +613,7 @@ static gm_status build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n
     SC_ALLOC(sc->tri_mesh, sizeof(uint32_t) * (size_t)nt);
     SC_ALLOC(sc->mesh_object, sizeof(uint32_t) * n_meshes);
     SC_ALLOC(sc->bvh_tris, sizeof(float4) * 3 * (size_t)nt);
+    if (dynamic) SC_ALLOC(sc->tri_local, sizeof(float4) * 3 * (size_t)nt);
     if (nt > 1) SC_ALLOC(sc->nodes, sizeof(float4) * 4 * (size_t)(nt - 1));
     unsigned int* bounds = nullptr;
     int* err = nullptr;
@@ -529,28 +642,20 @@ static gm_status build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n
         k_gather<<<gm_div_up(d.n_tris, 256), 256, 0, s>>>(wv, (const uint32_t*)di, d.n_tris, d.n_verts, base, m,
                                                           sc->tri_canon, sc->tri_mesh, bounds, err);
         launches += 2;
+        if (dynamic) {
+            k_gather_local<<<gm_div_up(d.n_tris, 256), 256, 0, s>>>((const float*)dv, (const uint32_t*)di, d.n_tris,
+                                                                    d.n_verts, base, sc->tri_local);
+            ++launches;
+        }
         base += d.n_tris;
     }
     GM_TRY_CUDA(cudaMemcpyAsync(sc->mesh_object, objs.data(), sizeof(uint32_t) * n_meshes, cudaMemcpyHostToDevice, s));
     // world -> mesh-local maps for the export format (affine inverse in FP64)
     {
-        std::vector<double> inv(12 * (size_t)n_meshes, 0.0);
-        for (uint32_t m = 0; m < n_meshes; ++m) {
-            const double* M = meshes[m].transform;
-            const double a = M[0], b = M[1], c = M[2], d = M[4], e2 = M[5], f = M[6], g = M[8], h = M[9], k = M[10];
-            const double det = a * (e2 * k - f * h) - b * (d * k - f * g) + c * (d * h - e2 * g);
-            if (!(std::fabs(det) > 1e-300) || !std::isfinite(det)) {
-                sc->mesh_inv_ok = false;
-                continue;
-            }
-            const double r[9] = {(e2 * k - f * h) / det, (c * h - b * k) / det, (b * f - c * e2) / det,
-                                 (f * g - d * k) / det,  (a * k - c * g) / det,  (c * d - a * f) / det,
-                                 (d * h - e2 * g) / det, (b * g - a * h) / det,  (a * e2 - b * d) / det};
-            for (int i = 0; i < 3; ++i) {
-                for (int j = 0; j < 3; ++j) inv[12 * m + 4 * i + j] = r[3 * i + j];
-                inv[12 * m + 4 * i + 3] = -(r[3 * i] * M[3] + r[3 * i + 1] * M[7] + r[3 * i + 2] * M[11]);
-            }
-        }
+        std::vector<double> xf(16 * (size_t)n_meshes);
+        for (uint32_t m = 0; m < n_meshes; ++m) memcpy(&xf[16 * m], meshes[m].transform, sizeof(double) * 16);
+        std::vector<double> inv;
+        sc->mesh_inv_ok = mesh_inverses(xf.data(), n_meshes, inv);
         SC_ALLOC(sc->mesh_inv, sizeof(double) * 12 * n_meshes);
         GM_TRY_CUDA(cudaMemcpyAsync(sc->mesh_inv, inv.data(), sizeof(double) * 12 * n_meshes, cudaMemcpyHostToDevice, s));
         GM_TRY_CUDA(cudaStreamSynchronize(s));   // inv is a host temporary
@@ -709,7 +814,7 @@ static gm_status build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n
 
 extern "C" gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes, gm_stream stream,
                                     gm_scene** out) {
-    return build_scene(ctx, meshes, n_meshes, GM_BUILD_DEFAULT, stream, out);
+    return build_scene(ctx, meshes, n_meshes, GM_BUILD_DEFAULT, false, stream, out);
 }
 
 extern "C" gm_status gm_build_scene_opts(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes,
@@ -717,7 +822,95 @@ extern "C" gm_status gm_build_scene_opts(gm_ctx* ctx, const gm_mesh_desc* meshes
     const int b = opts ? opts->builder : GM_BUILD_DEFAULT;
     if (b != GM_BUILD_LBVH && b != GM_BUILD_PLOC)
         return gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene_opts: unknown builder");
-    return build_scene(ctx, meshes, n_meshes, b, stream, out);
+    return build_scene(ctx, meshes, n_meshes, b, opts && opts->dynamic != 0, stream, out);
+}
+
+extern "C" gm_status gm_scene_pose(gm_scene* sc, const double* transforms, gm_stream stream) {
+    if (!sc || !transforms) return gm_set_error(GM_ERR_INVALID_ARG, "gm_scene_pose: null argument");
+    if (!sc->tri_local)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_scene_pose: the scene was not built with gm_build_opts.dynamic");
+    const uint32_t nm = sc->n_meshes, nt = sc->n_tris;
+    for (size_t k = 0; k < 16 * (size_t)nm; ++k)
+        if (!std::isfinite(transforms[k])) return gm_set_error(GM_ERR_INVALID_ARG, "gm_scene_pose: non-finite transform");
+    cudaStream_t s = (cudaStream_t)stream;
+    gm_ctx* ctx = sc->ctx;
+    GM_TRY_CUDA(cudaSetDevice(ctx->device));
+    std::vector<double> xf12(12 * (size_t)nm);
+    for (uint32_t m = 0; m < nm; ++m) memcpy(&xf12[12 * m], transforms + 16 * m, sizeof(double) * 12);
+    std::vector<double> inv;
+    const bool inv_ok = mesh_inverses(transforms, nm, inv);
+    std::vector<void*> tmp;
+    auto done = [&](gm_status st) {
+        for (void* p : tmp) cudaFreeAsync(p, s);
+        return st;
+    };
+    gm_status st;
+#define POSE_TMP(ptr, bytes)                                                          \
+    do {                                                                              \
+        if ((st = gm_alloc((void**)&(ptr), (bytes), s)) != GM_OK) return done(st);    \
+        tmp.push_back((void*)(ptr));                                                  \
+    } while (0)
+    double* d_xf = nullptr;
+    unsigned int* bounds = nullptr;
+    uint32_t* order = nullptr;
+    int *parent_node = nullptr, *parent_leaf = nullptr;
+    unsigned int* flags = nullptr;
+    const uint32_t n_int = nt > 1 ? nt - 1 : 1;
+    POSE_TMP(d_xf, sizeof(double) * 12 * nm);
+    POSE_TMP(bounds, sizeof(unsigned int) * 16);
+    POSE_TMP(order, sizeof(uint32_t) * nt);
+    POSE_TMP(parent_node, sizeof(int) * n_int);
+    POSE_TMP(parent_leaf, sizeof(int) * nt);
+    POSE_TMP(flags, sizeof(unsigned int) * n_int);
+#undef POSE_TMP
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_xf, xf12.data(), sizeof(double) * 12 * nm, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(sc->mesh_inv, inv.data(), sizeof(double) * 12 * nm, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(parent_node, 0xff, sizeof(int) * n_int, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(parent_leaf, 0xff, sizeof(int) * nt, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(flags, 0, sizeof(unsigned int) * n_int, s)) != cudaSuccess)
+        return done(gm_cuda_error(e, "gm_scene_pose"));
+    k_bounds_init<<<1, 32, 0, s>>>(bounds);
+    k_pose<<<gm_div_up(nt, 256), 256, 0, s>>>(sc->tri_local, sc->tri_mesh, d_xf, nt, sc->tri_canon, bounds);
+    k_leaf_order<<<gm_div_up(nt, 256), 256, 0, s>>>(sc->bvh_tris, nt, order);
+    int launches = 3;
+    if (nt > 1) {
+        k_final_parents<<<gm_div_up(nt - 1, 256), 256, 0, s>>>(sc->nodes, (int)(nt - 1), (int)nt, parent_node,
+                                                               parent_leaf);
+        ++launches;
+    }
+    // leaf-order triangles rewritten from the posed ones, then the boxes bottom-up (the
+    // hierarchy and its depth are unchanged)
+    k_refit<<<gm_div_up(nt, 256), 256, 0, s>>>(sc->tri_canon, order, (int)nt, sc->nodes, parent_node, parent_leaf,
+                                                flags, bounds, sc->bvh_tris);
+    ++launches;
+    unsigned int hb[12] = {0};
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(hb, bounds, sizeof(hb), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return done(gm_cuda_error(e, "gm_scene_pose"));
+    ctx->launches += launches;
+    auto dec = [](unsigned int o) {
+        unsigned int b = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+        float f;
+        memcpy(&f, &b, 4);
+        return f;
+    };
+    for (int k = 0; k < 3; ++k) {
+        sc->box_lo[k] = dec(hb[6 + k]);
+        sc->box_hi[k] = dec(hb[9 + k]);
+    }
+    sc->mesh_inv_ok = inv_ok;
+    // the 4-wide collapse holds the old boxes: drop it (the binary tree serves every variant)
+    if (sc->nodes4) {
+        cudaFreeAsync(sc->nodes4, s);
+        sc->nodes4 = nullptr;
+        sc->n4 = 0;
+    }
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(sc->box_lo[k]) || !std::isfinite(sc->box_hi[k]))
+            return done(gm_set_error(GM_ERR_INVALID_ARG, "gm_scene_pose: non-finite vertex"));
+    return done(GM_OK);
 }
 
 extern "C" gm_status gm_scene_info(const gm_scene* sc, uint32_t* n_tris, uint32_t* bvh_depth) {
@@ -768,5 +961,6 @@ extern "C" void gm_scene_free(gm_scene* sc) {
     cudaFree(sc->nodes);
     cudaFree(sc->nodes4);
     cudaFree(sc->bvh_tris);
+    cudaFree(sc->tri_local);
     delete sc;
 }

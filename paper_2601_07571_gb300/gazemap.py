@@ -55,6 +55,10 @@ class gm_field_cfg(C.Structure):
 GM_FIELD_N_PARAMS = 16705
 
 
+class gm_build_opts(C.Structure):
+    _fields_ = [("builder", C.c_int32), ("dynamic", C.c_int32)]
+
+
 class gm_export_dst(C.Structure):
     _fields_ = [("value", C.c_void_p), ("object_id", C.c_void_p), ("triangle", C.c_void_p), ("bary3", C.c_void_p),
                 ("local_xyz", C.c_void_p), ("world_xyz", C.c_void_p)]
@@ -80,8 +84,12 @@ _SIGS = {
     "gm_sync": (C.c_int, [_P, _P]),
     "gm_ctx_launches": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
     "gm_build_scene": (C.c_int, [_P, C.POINTER(gm_mesh_desc), C.c_uint32, _P, C.POINTER(_P)]),
-    "gm_build_scene_opts": (C.c_int, [_P, C.POINTER(gm_mesh_desc), C.c_uint32, C.POINTER(C.c_int32), _P,
+    "gm_build_scene_opts": (C.c_int, [_P, C.POINTER(gm_mesh_desc), C.c_uint32, C.POINTER(gm_build_opts), _P,
                                       C.POINTER(_P)]),
+    "gm_scene_pose": (C.c_int, [_P, C.POINTER(C.c_double), _P]),
+    "gm_samples_follow": (C.c_int, [_P, _P]),
+    "gm_accumulate_dynamic": (C.c_int, [_P, _P, C.POINTER(gm_fixations), C.POINTER(gm_params), C.POINTER(C.c_double),
+                                        _P, C.POINTER(_P)]),
     "gm_scene_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "gm_scene_triangles": (C.c_int, [_P, _P, _P]),
     "gm_scene_free": (None, [_P]),
@@ -207,9 +215,10 @@ def gm_ctx_launches(ctx) -> int:
 GM_BUILD_LBVH, GM_BUILD_PLOC = 0, 1
 
 
-def gm_build_scene(ctx, meshes, stream=None, builder=None):
+def gm_build_scene(ctx, meshes, stream=None, builder=None, dynamic=False):
     """meshes: sequence of (vertices (nv,3) f32, indices (nt,3) u32, transform (4,4) f64, object_id).
-    builder: None (library default), GM_BUILD_LBVH or GM_BUILD_PLOC."""
+    builder: None (library default), GM_BUILD_LBVH or GM_BUILD_PLOC. dynamic: keep the mesh-local
+    triangles for gm_scene_pose."""
     descs = (gm_mesh_desc * len(meshes))()
     keep = []
     for d, (v, f, xf, obj) in zip(descs, meshes):
@@ -221,12 +230,27 @@ def gm_build_scene(ctx, meshes, stream=None, builder=None):
         d.transform = (C.c_double * 16)(*np.asarray(xf, np.float64).reshape(16).tolist())
         d.object_id = int(obj)
     h = _P()
-    if builder is None:
+    if builder is None and not dynamic:
         _check(lib().gm_build_scene(ctx, descs, len(meshes), _stream(stream), C.byref(h)))
     else:
-        opt = C.c_int32(int(builder))
+        opt = gm_build_opts(GM_BUILD_PLOC if builder is None else int(builder), 1 if dynamic else 0)
         _check(lib().gm_build_scene_opts(ctx, descs, len(meshes), C.byref(opt), _stream(stream), C.byref(h)))
     return h
+
+
+def _f64(a):
+    a = np.ascontiguousarray(np.asarray(a, np.float64))
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def gm_scene_pose(scene, transforms, stream=None) -> None:
+    """transforms: (n_meshes, 4, 4) FP64 row-major."""
+    a, p = _f64(transforms)
+    _check(lib().gm_scene_pose(scene, p, _stream(stream)))
+
+
+def gm_samples_follow(samples, stream=None) -> None:
+    _check(lib().gm_samples_follow(samples, _stream(stream)))
 
 
 def gm_scene_info(scene):
@@ -307,6 +331,16 @@ def gm_accumulate_fixations(scene, samples, eye, gaze, duration_s, timestamp_s, 
     fx = gm_fixations(_ptr(eye), _ptr(gaze), _ptr(duration_s), _ptr(timestamp_s), int(eye.shape[0]))
     h = _P()
     _check(lib().gm_accumulate_fixations(scene, samples, C.byref(fx), C.byref(params), _stream(stream), C.byref(h)))
+    return h
+
+
+def gm_accumulate_dynamic(scene, samples, eye, gaze, duration_s, timestamp_s, params: gm_params, window_transforms,
+                          stream=None):
+    """window_transforms: (n_windows, n_meshes, 4, 4) FP64 row-major."""
+    fx = gm_fixations(_ptr(eye), _ptr(gaze), _ptr(duration_s), _ptr(timestamp_s), int(eye.shape[0]))
+    a, p = _f64(window_transforms)
+    h = _P()
+    _check(lib().gm_accumulate_dynamic(scene, samples, C.byref(fx), C.byref(params), p, _stream(stream), C.byref(h)))
     return h
 
 

@@ -98,7 +98,7 @@ def test_batch_session_against_oracle(env):
     v = np.empty(int(off[-1]), np.float32)
     G.gm_map_copy(maps[2], 0, v)
     d = ora["density"][0]
-    tol = 1e-4 * d + ora["amb"][0] + ora["sens"][0] * 8 * ulp32(tri_max_coord(r_tri, s.tri)) + 1e-30
+    tol = 1e-4 * (d + ora["amb"][0]) + ora["amb"][0] + ora["sens"][0] * 8 * ulp32(tri_max_coord(r_tri, s.tri)) + 1e-30
     assert np.all(np.abs(v[which].astype(np.float64) - d) <= tol)
     for m in maps:
         G.gm_map_free(m)

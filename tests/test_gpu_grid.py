@@ -68,5 +68,5 @@ def test_grid_densities_against_oracle(env):
     G.gm_scene_free(sc)
     d = ora["density"][0]
     assert (d > 0).sum() > 100
-    tol = 1e-4 * d + ora["amb"][0] + ora["sens"][0] * 8 * ulp32(tri_max_coord(tri, s["tri"])) + 1e-30
+    tol = 1e-4 * (d + ora["amb"][0]) + ora["amb"][0] + ora["sens"][0] * 8 * ulp32(tri_max_coord(tri, s["tri"])) + 1e-30
     assert np.all(np.abs(v.astype(np.float64) - d) <= tol)

@@ -5,7 +5,7 @@ Bars (see the oracle for the readings of the paper):
   - barycentrics within 2^-21, positions within 8 ulp of the triangle's largest coordinate;
   - in-cone pairs identical except at the cone edge; visibility identical except where the
     oracle marks the pair ambiguous (grazing within delta metres);
-  - densities: |gpu - oracle| <= 1e-4 * oracle + amb (+ sens * position error when the GPU
+  - densities: |gpu - oracle| <= 1e-4 * (oracle + amb) + amb (+ sens * position error when the GPU
     places its own samples), with amb and sens from the oracle.
 """
 import math
@@ -64,7 +64,7 @@ def _run_shared(G, ctx, pipe, w, delta, band=1e-5, record=True):
 
 
 def _check_density(gpu, ora, amb, extra=0.0):
-    tol = REL * ora + amb + extra + 1e-30
+    tol = REL * (ora + amb) + amb + extra + 1e-30
     err = np.abs(gpu.astype(np.float64) - ora)
     bad = err > tol
     assert not bad.any(), (f"{bad.sum()} samples off; worst rel "
@@ -180,7 +180,7 @@ def test_end_to_end_tiny_with_normalisation(G, ctx, pipe):
     assert mxn == mx
     on, omax = oracle.normalize(ora)
     assert abs(mx - omax) <= REL * omax
-    tol = (REL * ora + r["amb"][0] + r["sens"][0] * dpos) / omax + 2 * REL
+    tol = (REL * (ora + r["amb"][0]) + r["amb"][0] + r["sens"][0] * dpos) / omax + 2 * REL
     assert np.all(np.abs(gn - on) <= tol)
 
 
