@@ -51,6 +51,22 @@ class _Stats(C.Structure):
                 ("visible", C.c_int64), ("ambiguous", C.c_int64), ("cone_edge", C.c_int64)]
 
 
+class _Frustum(C.Structure):
+    _fields_ = [("e", C.c_double * 3), ("right", C.c_double * 3), ("up", C.c_double * 3), ("fwd", C.c_double * 3),
+                ("n", C.c_double), ("f", C.c_double), ("l", C.c_double), ("r", C.c_double), ("b", C.c_double),
+                ("t", C.c_double), ("ok", C.c_int32)]
+
+
+class _ZbParams(C.Structure):
+    _fields_ = [("res", C.c_int32), ("n", C.c_double), ("f", C.c_double), ("eps", C.c_double),
+                ("delta_px", C.c_double), ("delta_w_rel", C.c_double)]
+
+
+class _ZbStats(C.Structure):
+    _fields_ = [("in_cone", C.c_int64), ("visible", C.c_int64), ("ambiguous", C.c_int64),
+                ("skipped_fixations", C.c_int64)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -63,6 +79,9 @@ def lib():
         _lib.ora_pair_weight.restype = C.c_int
         _lib.ora_normalize.restype = C.c_double
         _lib.ora_grid_samples.restype = C.c_int
+        for fn in ("ora_camera_basis", "ora_crop_paper", "ora_crop_exact", "ora_zb_frustum", "ora_zb_render",
+                   "ora_zb_accumulate"):
+            getattr(_lib, fn).restype = C.c_int
     return _lib
 
 
@@ -335,3 +354,118 @@ def run(workload, which=None, delta_abs=0.0, cone_band=0.0, record=False, nthrea
     acc = accumulate(tri, smp.xyz, smp.tri, workload.fixations, workload.params, delta_abs,
                      cone_band, record, nthreads)
     return dict(tri=tri, area=A, offsets=off, samples=smp, **acc)
+
+
+# ---- the paper's z-buffer occlusion path (Sections 3.2.2, 3.3.2, Appendix A) ----------------
+@dataclass
+class ZBuffer:
+    """Parameters of the z-buffer form: resolution (pixels per side of the crop window), clip
+    planes and the +-eps depth tolerance (metres)."""
+    res: int = 256
+    near: float = 0.05
+    far: float = 100.0
+    eps: float = 0.005
+
+
+def _d3(a):
+    return np.ascontiguousarray(np.asarray(a, np.float64).reshape(3))
+
+
+def camera_basis(fwd, up):
+    r, u, f = (np.empty(3) for _ in range(3))
+    rc = lib().ora_camera_basis(_p(_d3(fwd)), _p(_d3(up)), _p(r), _p(u), _p(f))
+    if rc != 0:
+        raise ValueError("zero forward vector")
+    return r, u, f
+
+
+def crop_paper(rc, phi, n):
+    """Appendix A's crop window for the unit camera-space gaze rc: dict l, r, b, t, E, a, b_, alpha."""
+    out = np.empty(9)
+    if lib().ora_crop_paper(_p(_d3(rc)), C.c_double(phi), C.c_double(n), _p(out)) != 0:
+        return None
+    return dict(l=out[0], r=out[1], b=out[2], t=out[3], E=out[4:6].copy(), a=out[6], b_=out[7], alpha=out[8])
+
+
+def crop_exact(rc, phi, n):
+    out = np.empty(4)
+    if lib().ora_crop_exact(_p(_d3(rc)), C.c_double(phi), C.c_double(n), _p(out)) != 0:
+        return None
+    return out
+
+
+def _frustum_dict(F):
+    return dict(e=np.array(F.e), right=np.array(F.right), up=np.array(F.up), fwd=np.array(F.fwd), n=F.n, f=F.f,
+                l=F.l, r=F.r, b=F.b, t=F.t, ok=bool(F.ok))
+
+
+def zb_frustum(eye, gaze, cam_fwd, cam_up, theta, cutoff, near, far):
+    F = _Frustum()
+    f32 = lambda a: np.ascontiguousarray(np.asarray(a, np.float32).reshape(3))
+    rc = lib().ora_zb_frustum(_p(f32(eye)), _p(f32(gaze)), _p(f32(cam_fwd)), _p(f32(cam_up)), C.c_double(theta),
+                              C.c_double(cutoff), C.c_double(near), C.c_double(far), C.byref(F))
+    return _frustum_dict(F) if rc == 0 else None
+
+
+def zb_render(tri, frustum, res, delta_px=1e-3):
+    F = _Frustum()
+    for k in ("e", "right", "up", "fwd"):
+        getattr(F, k)[:] = list(np.asarray(frustum[k], np.float64))
+    for k in ("n", "f", "l", "r", "b", "t"):
+        setattr(F, k, float(frustum[k]))
+    F.ok = 1
+    tri = np.ascontiguousarray(tri, np.float32)
+    z = np.empty((res, res))
+    a = np.empty((res, res), np.uint8)
+    if lib().ora_zb_render(_p(tri), C.c_int64(len(tri)), C.byref(F), C.c_int32(res), C.c_double(delta_px), _p(z),
+                           _p(a)) != 0:
+        raise ValueError("bad frustum")
+    return z, a.astype(bool)
+
+
+def zb_accumulate(tri, sxyz, fixations, cam_fwd, cam_up, params, zb: ZBuffer, delta_px=1e-3, delta_w_rel=1e-5,
+                  cone_band=0.0, record=False, keep_buffers=False, nthreads=0, rec_cap=10_000_000):
+    """Densities of the z-buffer form for the given samples (FP64). Returns density/amb/sens
+    (n_windows, n_samples), stats, the frusta and (keep_buffers) every fixation's z-buffer."""
+    tri = np.ascontiguousarray(tri, np.float32)
+    sxyz = np.ascontiguousarray(sxyz, np.float64).reshape(-1, 3)
+    fx = fixations
+    eye = np.ascontiguousarray(fx.eye, np.float32)
+    gaze = np.ascontiguousarray(fx.gaze, np.float32)
+    dur = np.ascontiguousarray(fx.duration_s, np.float32)
+    ts = np.ascontiguousarray(fx.timestamp_s, np.float64)
+    cf = np.ascontiguousarray(cam_fwd, np.float32).reshape(-1, 3)
+    cu = np.ascontiguousarray(cam_up, np.float32).reshape(-1, 3)
+    W = n_windows(params)
+    P = _Params(params.theta_rad, params.cutoff_sigmas, params.eps_rel, params.t_begin, params.t_end,
+                params.window_s, 0.0, cone_band, W, nthreads)
+    Z = _ZbParams(int(zb.res), zb.near, zb.far, zb.eps, delta_px, delta_w_rel)
+    ns, nf = len(sxyz), fx.n
+    dens, amb, sens = (np.empty((W, ns)) for _ in range(3))
+    st = _ZbStats()
+    cap = rec_cap if record else -1
+    m = max(cap, 0)
+    rs, rf = np.empty(m, np.int64), np.empty(m, np.int32)
+    rfl, rg = np.empty(m, np.uint8), np.empty(m, np.float64)
+    nrec = C.c_int64(0)
+    frusta = (_Frustum * max(nf, 1))()
+    zbuf = np.empty((nf, zb.res, zb.res)) if keep_buffers else None
+    zamb = np.empty((nf, zb.res, zb.res), np.uint8) if keep_buffers else None
+    rc = lib().ora_zb_accumulate(_p(tri), C.c_int64(len(tri)), _p(sxyz), C.c_int64(ns), _p(eye), _p(gaze), _p(dur),
+                                 _p(ts), _p(cf), _p(cu), C.c_int64(nf), C.byref(P), C.byref(Z), _p(dens), _p(amb),
+                                 _p(sens), C.byref(st), C.c_int64(cap), _p(rs), _p(rf), _p(rfl), _p(rg),
+                                 C.byref(nrec), frusta, _p(zbuf) if keep_buffers else None,
+                                 _p(zamb) if keep_buffers else None)
+    if rc != 0:
+        raise RuntimeError(f"ora_zb_accumulate failed ({rc})")
+    out = dict(density=dens, amb=amb, sens=sens, frusta=[_frustum_dict(frusta[i]) for i in range(nf)],
+               stats=dict(in_cone=st.in_cone, visible=st.visible, ambiguous=st.ambiguous,
+                          skipped_fixations=st.skipped_fixations))
+    if keep_buffers:
+        out["zbuf"], out["zamb"] = zbuf, zamb.astype(bool)
+    if record:
+        k = min(nrec.value, m)
+        if nrec.value > m:
+            raise RuntimeError("pair record capacity exceeded")
+        out["pairs"] = dict(sample=rs[:k], fix=rf[:k], flag=rfl[:k], g=rg[:k])
+    return out

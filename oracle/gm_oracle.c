@@ -545,3 +545,484 @@ int ora_grid_samples(const float* tri, const int64_t* offsets, const int64_t* r,
     }
     return 0;
 }
+
+/* ==================================================================================== */
+/* The paper's own occlusion path (Sections 3.2.2 and 3.3.2, Appendix A): per fixation a  */
+/* camera at the eye, the near-plane crop window of the 4 sigma cone, a z-buffer of that  */
+/* window and the +-eps depth comparison. Readings (the paper leaves these open):         */
+/*  - camera: x right, y up, looking down -z; forward and up hints per fixation (the head */
+/*    pose); the gaze r is a direction in that frame;                                     */
+/*  - the z-buffer stores linear view depth w = (p - e).forward (metres), the +-eps test  */
+/*    compares it with the sample's w; a pixel holds the nearest surface that covers its  */
+/*    centre (point sampling), with geometry clipped to n <= w <= f; triangles two-sided; */
+/*  - the crop window used for filtering is the exact bounding box of the cone's section */
+/*    (tangent planes through the eye); the printed construction (E-centred ellipse with */
+/*    quaternion-rotated rays) is kept below as ora_crop_paper for comparison, since the */
+/*    centre of an oblique conic section is not the gaze point E;                        */
+/*  - samples keep the exact 4 sigma cone test of the ray path; the crop is a filter.    */
+/* ==================================================================================== */
+
+static void v3_cross(const double a[3], const double b[3], double o[3])
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double v3_dot(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static int v3_unit(double a[3])
+{
+    double l = sqrt(v3_dot(a, a));
+    if (!(l > 0.0) || !isfinite(l)) return -1;
+    a[0] /= l; a[1] /= l; a[2] /= l;
+    return 0;
+}
+
+/* Camera basis from a forward and an up hint: fwd = unit(forward), right = unit(fwd x up),
+ * up = right x fwd. An up hint within 1e-6 of parallel to forward is replaced by world z.
+ * Returns 0, or -1 for a zero forward. */
+int ora_camera_basis(const double fwd_in[3], const double up_in[3], double right[3], double up[3], double fwd[3])
+{
+    double f[3] = {fwd_in[0], fwd_in[1], fwd_in[2]}, u[3] = {up_in[0], up_in[1], up_in[2]};
+    if (v3_unit(f)) return -1;
+    double r[3];
+    v3_cross(f, u, r);
+    double lu = sqrt(v3_dot(u, u));
+    if (!(sqrt(v3_dot(r, r)) > 1e-6 * lu)) {
+        double z[3] = {0.0, 0.0, 1.0};
+        v3_cross(f, z, r);
+        if (!(sqrt(v3_dot(r, r)) > 1e-6)) { double x[3] = {1.0, 0.0, 0.0}; v3_cross(f, x, r); }
+    }
+    v3_unit(r);
+    v3_cross(r, f, u);
+    for (int k = 0; k < 3; ++k) { right[k] = r[k]; up[k] = u[k]; fwd[k] = f[k]; }
+    return 0;
+}
+
+/* Hamilton product helpers for the rotation q v q^-1 of Appendix A. */
+static void quat_rotate(const double axis[3], double ang, const double v[3], double out[3])
+{
+    double c = cos(0.5 * ang), s = sin(0.5 * ang);
+    double q[4] = {c, s * axis[0], s * axis[1], s * axis[2]};        /* w, x, y, z */
+    double qi[4] = {c, -q[1], -q[2], -q[3]};
+    double p[4] = {0.0, v[0], v[1], v[2]};
+    double t[4], r[4];
+    /* t = q p */
+    t[0] = q[0] * p[0] - q[1] * p[1] - q[2] * p[2] - q[3] * p[3];
+    t[1] = q[0] * p[1] + q[1] * p[0] + q[2] * p[3] - q[3] * p[2];
+    t[2] = q[0] * p[2] - q[1] * p[3] + q[2] * p[0] + q[3] * p[1];
+    t[3] = q[0] * p[3] + q[1] * p[2] - q[2] * p[1] + q[3] * p[0];
+    /* r = t qi */
+    r[0] = t[0] * qi[0] - t[1] * qi[1] - t[2] * qi[2] - t[3] * qi[3];
+    r[1] = t[0] * qi[1] + t[1] * qi[0] + t[2] * qi[3] - t[3] * qi[2];
+    r[2] = t[0] * qi[2] - t[1] * qi[3] + t[2] * qi[0] + t[3] * qi[1];
+    r[3] = t[0] * qi[3] + t[1] * qi[2] - t[2] * qi[1] + t[3] * qi[0];
+    out[0] = r[1]; out[1] = r[2]; out[2] = r[3];
+}
+
+/* The crop window as Appendix A constructs it, for a unit gaze direction rc in camera space
+ * (x right, y up, z back) and the cone half-angle phi = atan(cutoff tan theta): rays rotated
+ * by -+phi about u1 = rc x i and u2 = rc x u1 (i = the forward axis (0, 0, -1); both axes
+ * normalised) meet the near plane z = -n at A0, A1, B0, B1; a = |A1 - A0| / 2, b = |B1 - B0| / 2,
+ * E = the gaze ray's point on the plane, alpha = acos(j . unit(E - M)) with j = (1, 0, 0) and
+ * M = (0, 0, -n); bounds E -+ sqrt(a^2 cos^2 alpha + b^2 sin^2 alpha) in x and
+ * E -+ sqrt(a^2 sin^2 alpha + b^2 cos^2 alpha) in y. When rc is along the forward axis u1 is
+ * undefined: the section is a circle, a = b = n tan phi, alpha = 0.
+ * out: l, r, b, t, E_x, E_y, a, b, alpha. Returns -1 if a rotated ray does not reach the plane. */
+int ora_crop_paper(const double rc_in[3], double phi, double n, double* out)
+{
+    double rc[3] = {rc_in[0], rc_in[1], rc_in[2]};
+    if (v3_unit(rc)) return -1;
+    if (!(rc[2] < 0.0)) return -1;
+    double Ex = -n / rc[2] * rc[0], Ey = -n / rc[2] * rc[1];
+    double i_ax[3] = {0.0, 0.0, -1.0};
+    double u1[3], u2[3];
+    v3_cross(rc, i_ax, u1);
+    double a, b, alpha;
+    if (sqrt(v3_dot(u1, u1)) < 1e-12) {
+        a = b = n * tan(phi);
+        alpha = 0.0;
+    } else {
+        v3_unit(u1);
+        v3_cross(rc, u1, u2);
+        v3_unit(u2);
+        double a0[3], a1[3], b0[3], b1[3];
+        quat_rotate(u1, -phi, rc, a0);
+        quat_rotate(u1, phi, rc, a1);
+        quat_rotate(u2, -phi, rc, b0);
+        quat_rotate(u2, phi, rc, b1);
+        if (!(a0[2] < 0.0 && a1[2] < 0.0 && b0[2] < 0.0 && b1[2] < 0.0)) return -1;
+        a = 0.5 * n * sqrt(pow(a0[0] / a0[2] - a1[0] / a1[2], 2) + pow(a0[1] / a0[2] - a1[1] / a1[2], 2));
+        b = 0.5 * n * sqrt(pow(b0[0] / b0[2] - b1[0] / b1[2], 2) + pow(b0[1] / b0[2] - b1[1] / b1[2], 2));
+        double me[3] = {Ex, Ey, 0.0};
+        v3_unit(me);
+        double c = me[0];
+        if (c > 1.0) c = 1.0;
+        if (c < -1.0) c = -1.0;
+        alpha = acos(c);
+    }
+    double hx = sqrt(a * a * cos(alpha) * cos(alpha) + b * b * sin(alpha) * sin(alpha));
+    double hy = sqrt(a * a * sin(alpha) * sin(alpha) + b * b * cos(alpha) * cos(alpha));
+    out[0] = Ex - hx; out[1] = Ex + hx; out[2] = Ey - hy; out[3] = Ey + hy;
+    out[4] = Ex; out[5] = Ey; out[6] = a; out[7] = b; out[8] = alpha;
+    return 0;
+}
+
+/* The exact crop window: the cone of half-angle phi about the unit direction rc (camera
+ * space) meets the near plane z = -n in a conic whose x-extent is bounded by the two planes
+ * through the eye, x + c z = 0, tangent to the cone: |(1, 0, c) . rc| = sin(phi) sqrt(1 + c^2),
+ * i.e. (rc_z^2 - s^2) c^2 + 2 rc_x rc_z c + (rc_x^2 - s^2) = 0 with s = sin(phi); the plane
+ * meets z = -n at x = c n. The same with y. Needs the whole cone in front of the camera
+ * (rc_z < 0 and rc_z^2 > s^2); returns -1 otherwise. out: l, r, b, t. */
+int ora_crop_exact(const double rc_in[3], double phi, double n, double* out)
+{
+    double rc[3] = {rc_in[0], rc_in[1], rc_in[2]};
+    if (v3_unit(rc)) return -1;
+    double s = sin(phi);
+    double A = rc[2] * rc[2] - s * s;
+    if (!(rc[2] < 0.0) || !(A > 0.0)) return -1;
+    for (int k = 0; k < 2; ++k) {
+        double q = rc[k];
+        double disc = s * sqrt(q * q + rc[2] * rc[2] - s * s);
+        double c1 = (-q * rc[2] - disc) / A, c2 = (-q * rc[2] + disc) / A;
+        out[2 * k] = n * (c1 < c2 ? c1 : c2);
+        out[2 * k + 1] = n * (c1 < c2 ? c2 : c1);
+    }
+    return 0;
+}
+
+/* Ray o + t d (t > 0) against one triangle, FP64 Moller-Trumbore. Returns 1 on a hit and its
+ * t; *near is set when the point is within delta (metres, in the triangle's plane) of an edge,
+ * on either side (a coverage decision an FP32 rasteriser may take the other way). */
+static int ray_tri_t(const double o[3], const double d[3], const float* T, double delta, double* t_out, int* near,
+                     double* t_plane)
+{
+    double v0[3] = {T[0], T[1], T[2]}, v1[3] = {T[3], T[4], T[5]}, v2[3] = {T[6], T[7], T[8]};
+    double e1[3] = {v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2]};
+    double e2[3] = {v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2]};
+    double nrm[3];
+    v3_cross(e1, e2, nrm);
+    double area2 = sqrt(v3_dot(nrm, nrm));
+    *near = 0;
+    *t_plane = INFINITY;
+    if (area2 == 0.0) return 0;
+    double P[3];
+    v3_cross(d, e2, P);
+    double det = v3_dot(e1, P);
+    double dl = sqrt(v3_dot(d, d));
+    double cosinc = fabs(v3_dot(nrm, d)) / (area2 * dl);
+    if (det == 0.0 || cosinc < 1e-9) return 0;
+    double Tv[3] = {o[0] - v0[0], o[1] - v0[1], o[2] - v0[2]};
+    double u = v3_dot(Tv, P) / det;
+    double Q[3];
+    v3_cross(Tv, e1, Q);
+    double v = v3_dot(d, Q) / det;
+    double t = v3_dot(e2, Q) / det;
+    *t_plane = t;
+    double b[3] = {1.0 - u - v, u, v};
+    double l12 = sqrt(pow(v2[0] - v1[0], 2) + pow(v2[1] - v1[1], 2) + pow(v2[2] - v1[2], 2));
+    double l02 = sqrt(v3_dot(e2, e2)), l01 = sqrt(v3_dot(e1, e1));
+    double md = b[0] * (area2 / l12), m1 = b[1] * (area2 / l02), m2 = b[2] * (area2 / l01);
+    if (m1 < md) md = m1;
+    if (m2 < md) md = m2;
+    double de = delta / cosinc;
+    *near = t > 0.0 && fabs(md) <= de;
+    if (b[0] >= 0.0 && b[1] >= 0.0 && b[2] >= 0.0 && t > 0.0) {
+        *t_out = t;
+        return 1;
+    }
+    return 0;
+}
+
+typedef struct {
+    double e[3], right[3], up[3], fwd[3];
+    double n, f, l, r, b, t;
+    int32_t ok;
+} ora_frustum;
+
+/* Frustum of one fixation: camera basis, gaze in camera space, exact crop window. */
+int ora_zb_frustum(const float* eye, const float* gaze, const float* cam_fwd, const float* cam_up, double theta,
+                   double cutoff, double n, double f, ora_frustum* F)
+{
+    double fw[3] = {cam_fwd[0], cam_fwd[1], cam_fwd[2]}, uh[3] = {cam_up[0], cam_up[1], cam_up[2]};
+    memset(F, 0, sizeof(*F));
+    for (int k = 0; k < 3; ++k) F->e[k] = eye[k];
+    F->n = n; F->f = f;
+    if (ora_camera_basis(fw, uh, F->right, F->up, F->fwd)) return -1;
+    double g[3] = {gaze[0], gaze[1], gaze[2]};
+    if (v3_unit(g)) return -1;
+    double rc[3] = {v3_dot(g, F->right), v3_dot(g, F->up), -v3_dot(g, F->fwd)};
+    double phi = atan(cutoff * tan(theta));
+    double bnd[4];
+    if (ora_crop_exact(rc, phi, n, bnd)) return -1;
+    F->l = bnd[0]; F->r = bnd[1]; F->b = bnd[2]; F->t = bnd[3];
+    F->ok = 1;
+    return 0;
+}
+
+/* Z-buffer of one frustum: res x res pixels over the crop window; pixel (px, py) has its centre
+ * at x = l + (px + 1/2)(r - l)/res, y = b + (py + 1/2)(t - b)/res on the near plane; its depth
+ * is the smallest w = t n over triangles that the ray e + t (x right + y up + n fwd) meets with
+ * n <= w <= f (+inf when none). amb[p] is set when a triangle whose edge passes within delta_px
+ * pixels of the centre (at its own depth) lies no deeper than the pixel's depth (plus 1e-6
+ * relative), or a hit lies within 1e-9 relative of a clip plane. zbuf and amb: res * res. */
+int ora_zb_render(const float* tri, int64_t nt, const ora_frustum* F, int32_t res, double delta_px, double* zbuf,
+                  uint8_t* amb)
+{
+    if (!F->ok || res <= 0) return -1;
+    double pxw = (F->r - F->l) / res, pxh = (F->t - F->b) / res;
+    for (int32_t py = 0; py < res; ++py) {
+        for (int32_t px = 0; px < res; ++px) {
+            double x = F->l + (px + 0.5) * pxw, y = F->b + (py + 0.5) * pxh;
+            double d[3];
+            for (int k = 0; k < 3; ++k) d[k] = x * F->right[k] + y * F->up[k] + F->n * F->fwd[k];
+            double best = INFINITY, near_best = INFINITY;
+            int clip_amb = 0;
+            for (int64_t j = 0; j < nt; ++j) {
+                double t, tp;
+                int nr;
+                /* delta in metres at this depth: delta_px pixels of width (r - l)/res at the near plane */
+                double dw = delta_px * pxw / F->n;
+                int hit = ray_tri_t(F->e, d, tri + 9 * j, 0.0, &t, &nr, &tp);
+                double w = hit ? t * F->n : INFINITY;
+                double wp = tp * F->n;
+                /* edge proximity measured at the plane hit depth */
+                int nr2;
+                double tt, tp2;
+                ray_tri_t(F->e, d, tri + 9 * j, dw * (wp > 0.0 ? wp : 0.0), &tt, &nr2, &tp2);
+                if (hit) {
+                    if (fabs(w - F->n) <= 1e-9 * F->n || fabs(w - F->f) <= 1e-9 * F->f) clip_amb = 1;
+                    if (w >= F->n && w <= F->f && w < best) best = w;
+                }
+                if (nr2 && wp >= F->n * (1.0 - 1e-9) && wp <= F->f * (1.0 + 1e-9) && wp < near_best) near_best = wp;
+            }
+            zbuf[(size_t)py * res + px] = best;
+            amb[(size_t)py * res + px] = (uint8_t)(clip_amb || near_best <= best * (1.0 + 1e-6));
+        }
+    }
+    return 0;
+}
+
+typedef struct {
+    int32_t res;
+    double n, f;              /* clip planes (metres) */
+    double eps;               /* +-eps depth tolerance (metres) */
+    double delta_px;          /* pixel-position margin of the ambiguity bookkeeping (pixels) */
+    double delta_w_rel;       /* depth margin of the ambiguity bookkeeping (relative) */
+} ora_zb_params;
+
+typedef struct {
+    int64_t in_cone, visible, ambiguous, skipped_fixations;
+} ora_zb_stats;
+
+typedef struct {
+    const float* tri; int64_t nt;
+    const ora_frustum* F; const double* Z; const uint8_t* A; int32_t res;
+    int64_t f0, f1;
+    const ora_zb_params* zp;
+    int err;
+} ora_render_job;
+
+static void* render_range(void* arg)
+{
+    ora_render_job* J = (ora_render_job*)arg;
+    size_t px = (size_t)J->res * (size_t)J->res;
+    for (int64_t f = J->f0; f < J->f1; ++f) {
+        if (!J->F[f].ok) continue;
+        if (ora_zb_render(J->tri, J->nt, &J->F[f], J->res, J->zp->delta_px, (double*)J->Z + px * f,
+                          (uint8_t*)J->A + px * f))
+            J->err = -1;
+    }
+    return NULL;
+}
+
+/* z-buffer visibility of a point of camera-space depth w and near-plane coordinates (xn, yn)
+ * in pixel (px, py): |w - Z| <= eps. */
+static int zb_pixel_visible(const double* Z, int32_t res, int32_t px, int32_t py, double w, double eps)
+{
+    double z = Z[(size_t)py * res + px];
+    return isfinite(z) && fabs(w - z) <= eps;
+}
+
+typedef struct {
+    const float* tri; int64_t nt;
+    const double* sxyz; int64_t s0, s1, ns;
+    const float *eye, *gaze, *dur; const int32_t* win; int64_t nf;
+    const ora_frustum* F; const double* Z; const uint8_t* A;
+    const ora_params* prm; const ora_zb_params* zp;
+    double *density, *amb, *sens;
+    ora_zb_stats st;
+    int record;
+    int64_t *ps; int32_t* pf; uint8_t* pflag; double* pg; int64_t np, cap;
+    int err;
+} ora_zb_job;
+
+static void* zb_accumulate_range(void* arg)
+{
+    ora_zb_job* J = (ora_zb_job*)arg;
+    const ora_params* P = J->prm;
+    const ora_zb_params* zp = J->zp;
+    const int32_t res = zp->res;
+    const size_t npx = (size_t)res * (size_t)res;
+    double tan_t = tan(P->theta);
+    for (int64_t s = J->s0; s < J->s1; ++s) {
+        const double* sp = J->sxyz + 3 * s;
+        for (int64_t f = 0; f < J->nf; ++f) {
+            int32_t wi = J->win[f];
+            if (wi < 0 || !J->F[f].ok) continue;
+            double e[3] = {J->eye[3 * f], J->eye[3 * f + 1], J->eye[3 * f + 2]};
+            double r[3] = {J->gaze[3 * f], J->gaze[3 * f + 1], J->gaze[3 * f + 2]};
+            pair_eval pe;
+            int in = gaussian_pair(sp, e, r, (double)J->dur[f], P->theta, P->cutoff, P->cone_band, &pe);
+            if (!in && !pe.edge) continue;
+            const ora_frustum* F = &J->F[f];
+            const double* Z = J->Z + npx * f;
+            const uint8_t* A = J->A + npx * f;
+            double v[3] = {sp[0] - F->e[0], sp[1] - F->e[1], sp[2] - F->e[2]};
+            double x = v3_dot(v, F->right), y = v3_dot(v, F->up), w = v3_dot(v, F->fwd);
+            int vis = 0, amb_vis = 0;
+            if (fabs(w - F->n) <= 1e-6 * F->n || fabs(w - F->f) <= 1e-6 * F->f) amb_vis = 1;
+            if (w >= F->n && w <= F->f) {
+                double u = (F->n * x / w - F->l) / (F->r - F->l) * res;
+                double q = (F->n * y / w - F->b) / (F->t - F->b) * res;
+                double dp = zp->delta_px;
+                if (u < dp || u > res - dp || q < dp || q > res - dp) {
+                    /* on the crop border: inside or filtered out depending on rounding */
+                    if (u < -dp || u > res + dp || q < -dp || q > res + dp) { /* clearly outside */ }
+                    else amb_vis = 1;
+                }
+                if (u >= 0.0 && u <= res && q >= 0.0 && q <= res) {
+                    int32_t cx[2], cy[2];
+                    cx[0] = (int32_t)floor(u - dp); cx[1] = (int32_t)floor(u + dp);
+                    cy[0] = (int32_t)floor(q - dp); cy[1] = (int32_t)floor(q + dp);
+                    for (int k = 0; k < 2; ++k) {
+                        if (cx[k] < 0) cx[k] = 0;
+                        if (cx[k] > res - 1) cx[k] = res - 1;
+                        if (cy[k] < 0) cy[k] = 0;
+                        if (cy[k] > res - 1) cy[k] = res - 1;
+                    }
+                    int32_t px = (int32_t)floor(u), py = (int32_t)floor(q);
+                    if (px > res - 1) px = res - 1;
+                    if (py > res - 1) py = res - 1;
+                    vis = zb_pixel_visible(Z, res, px, py, w, zp->eps);
+                    double dw = zp->delta_w_rel * w;
+                    for (int a = 0; a < 2; ++a) {
+                        for (int b = 0; b < 2; ++b) {
+                            size_t p = (size_t)cy[b] * res + cx[a];
+                            if (A[p]) amb_vis = 1;
+                            if (zb_pixel_visible(Z, res, cx[a], cy[b], w, zp->eps) != vis) amb_vis = 1;
+                            double z = Z[p];
+                            if (isfinite(z) && fabs(fabs(w - z) - zp->eps) <= dw) amb_vis = 1;
+                        }
+                    }
+                }
+            }
+            size_t o = (size_t)wi * (size_t)J->ns + (size_t)s;
+            uint8_t flag = (uint8_t)((in ? PF_IN_CONE : 0) | (vis ? PF_VISIBLE : 0) | (amb_vis ? PF_VIS_AMBIG : 0)
+                                     | (pe.edge ? PF_CONE_EDGE : 0));
+            if (in) {
+                J->st.in_cone++;
+                if (vis) {
+                    J->st.visible++;
+                    J->density[o] += pe.g;
+                    if (J->sens)
+                        J->sens[o] += pe.g * (pe.d2 / (pe.d1 * pe.d1)) * (1.0 + pe.d2 / pe.d1) / (tan_t * tan_t);
+                }
+            }
+            if (amb_vis || pe.edge) {
+                if (J->amb) J->amb[o] += pe.g;
+                J->st.ambiguous += amb_vis;
+            }
+            if (J->record) {
+                ora_job tmp;
+                memset(&tmp, 0, sizeof(tmp));
+                tmp.ps = J->ps; tmp.pf = J->pf; tmp.pflag = J->pflag; tmp.pg = J->pg; tmp.np = J->np; tmp.cap = J->cap;
+                push_pair(&tmp, s, (int32_t)f, flag, pe.g);
+                J->ps = tmp.ps; J->pf = tmp.pf; J->pflag = tmp.pflag; J->pg = tmp.pg; J->np = tmp.np; J->cap = tmp.cap;
+                if (tmp.err) J->err = tmp.err;
+            }
+        }
+    }
+    return NULL;
+}
+
+/* The z-buffer form of the accumulation (Sections 3.2.2 and 3.3.2): for every fixation its
+ * frustum and z-buffer, then for every sample x fixation pair the exact 4 sigma cone test, the
+ * crop-window filter and the +-eps depth comparison in the sample's pixel; visible in-cone
+ * pairs add the same Gaussian as the ray form. Fixations whose cone is not entirely in front
+ * of their camera are skipped (counted). frusta_out (nf) and zbuf_out / amb_out (nf * res^2)
+ * may be NULL. Arguments otherwise as ora_accumulate. */
+int ora_zb_accumulate(const float* tri, int64_t nt, const double* sxyz, int64_t ns, const float* eye,
+                      const float* gaze, const float* dur, const double* ts, const float* cam_fwd,
+                      const float* cam_up, int64_t nf, const ora_params* prm, const ora_zb_params* zp,
+                      double* density, double* amb, double* sens, ora_zb_stats* st, int64_t rec_cap,
+                      int64_t* rec_s, int32_t* rec_f, uint8_t* rec_flag, double* rec_g, int64_t* n_rec,
+                      ora_frustum* frusta_out, double* zbuf_out, uint8_t* amb_out)
+{
+    size_t npx = (size_t)zp->res * (size_t)zp->res;
+    int32_t* win = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nf > 0 ? nf : 1));
+    ora_frustum* F = (ora_frustum*)calloc((size_t)(nf > 0 ? nf : 1), sizeof(ora_frustum));
+    double* Z = zbuf_out ? zbuf_out : (double*)malloc(sizeof(double) * npx * (size_t)(nf > 0 ? nf : 1));
+    uint8_t* A = amb_out ? amb_out : (uint8_t*)malloc(npx * (size_t)(nf > 0 ? nf : 1));
+    if (!win || !F || !Z || !A) return -2;
+    ora_fixation_windows(ts, nf, prm->t_begin, prm->t_end, prm->window_s, prm->n_windows, win);
+    ora_zb_stats tot = {0, 0, 0, 0};
+    for (int64_t f = 0; f < nf; ++f) {
+        if (ora_zb_frustum(eye + 3 * f, gaze + 3 * f, cam_fwd + 3 * f, cam_up + 3 * f, prm->theta, prm->cutoff, zp->n,
+                           zp->f, &F[f]))
+            F[f].ok = 0;
+        if (!F[f].ok && win[f] >= 0) tot.skipped_fixations++;
+    }
+    int nth = prm->nthreads > 0 ? prm->nthreads : (int)sysconf(_SC_NPROCESSORS_ONLN);
+    if (nth < 1) nth = 1;
+    int err = 0;
+    {
+        int nr = nth < nf ? nth : (nf > 0 ? (int)nf : 1);
+        ora_render_job* rj = (ora_render_job*)calloc((size_t)nr, sizeof(ora_render_job));
+        pthread_t* th = (pthread_t*)calloc((size_t)nr, sizeof(pthread_t));
+        for (int i = 0; i < nr; ++i) {
+            rj[i].tri = tri; rj[i].nt = nt; rj[i].F = F; rj[i].Z = Z; rj[i].A = A; rj[i].res = zp->res;
+            rj[i].f0 = nf * i / nr; rj[i].f1 = nf * (i + 1) / nr; rj[i].zp = zp;
+        }
+        for (int i = 1; i < nr; ++i) pthread_create(&th[i], NULL, render_range, &rj[i]);
+        render_range(&rj[0]);
+        for (int i = 1; i < nr; ++i) pthread_join(th[i], NULL);
+        for (int i = 0; i < nr; ++i) if (rj[i].err) err = rj[i].err;
+        free(rj); free(th);
+    }
+    size_t nout = (size_t)prm->n_windows * (size_t)ns;
+    memset(density, 0, sizeof(double) * nout);
+    if (amb) memset(amb, 0, sizeof(double) * nout);
+    if (sens) memset(sens, 0, sizeof(double) * nout);
+    if (nth > ns) nth = ns > 0 ? (int)ns : 1;
+    ora_zb_job* jobs = (ora_zb_job*)calloc((size_t)nth, sizeof(ora_zb_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)nth, sizeof(pthread_t));
+    for (int i = 0; i < nth; ++i) {
+        ora_zb_job* J = &jobs[i];
+        J->tri = tri; J->nt = nt; J->sxyz = sxyz; J->ns = ns; J->s0 = ns * i / nth; J->s1 = ns * (i + 1) / nth;
+        J->eye = eye; J->gaze = gaze; J->dur = dur; J->win = win; J->nf = nf;
+        J->F = F; J->Z = Z; J->A = A; J->prm = prm; J->zp = zp;
+        J->density = density; J->amb = amb; J->sens = sens; J->record = rec_cap >= 0;
+    }
+    for (int i = 1; i < nth; ++i) pthread_create(&th[i], NULL, zb_accumulate_range, &jobs[i]);
+    zb_accumulate_range(&jobs[0]);
+    for (int i = 1; i < nth; ++i) pthread_join(th[i], NULL);
+    int64_t nrec = 0;
+    for (int i = 0; i < nth; ++i) {
+        ora_zb_job* J = &jobs[i];
+        if (J->err) err = J->err;
+        tot.in_cone += J->st.in_cone; tot.visible += J->st.visible; tot.ambiguous += J->st.ambiguous;
+        for (int64_t k = 0; k < J->np; ++k, ++nrec) {
+            if (nrec < rec_cap) {
+                rec_s[nrec] = J->ps[k]; rec_f[nrec] = J->pf[k]; rec_flag[nrec] = J->pflag[k]; rec_g[nrec] = J->pg[k];
+            }
+        }
+        free(J->ps); free(J->pf); free(J->pflag); free(J->pg);
+    }
+    if (st) *st = tot;
+    if (n_rec) *n_rec = nrec;
+    if (frusta_out) memcpy(frusta_out, F, sizeof(ora_frustum) * (size_t)nf);
+    free(jobs); free(th); free(win); free(F);
+    if (!zbuf_out) free(Z);
+    if (!amb_out) free(A);
+    return err;
+}
