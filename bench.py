@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gazemap", "reference"], default="gazemap")
-    ap.add_argument("--workload", choices=["paper_scene", "tiny_sphere", "batched", "field", "city"],
+    ap.add_argument("--workload", choices=["paper_scene", "tiny_sphere", "batched", "field", "city", "zbuffer"],
                     default="paper_scene")
     ap.add_argument("--field-steps", type=int, default=30000, help="Adam steps of the neural field")
     ap.add_argument("--field-lr", type=float, default=3e-3, help="initial learning rate of the field (cosine to 1%%)")
@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--fixations", type=int, default=0, help="use only the first N fixations (profiling)")
     ap.add_argument("--flags", type=int, default=0, help="extra GM_F_* accumulation flags (variant A/B runs)")
     ap.add_argument("--builder", choices=["default", "lbvh", "ploc"], default="default", help="BVH builder")
+    ap.add_argument("--zb-res", type=int, default=256, help="z-buffer pixels per side (zbuffer workload)")
+    ap.add_argument("--zb-eps", type=float, default=0.005, help="z-buffer depth tolerance, metres (zbuffer workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     return ap.parse_args()
@@ -306,6 +308,81 @@ def batched_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def zbuffer_arm(args):
+    """The paper's own occlusion form (Sections 3.2.2 and 3.3.2: per-fixation crop frustum, z-buffer,
+    +-eps depth test) beside the exact ray form, on the paper-shaped scene with head poses within
+    15 degrees of the gaze. Scene and samples are built before timing; both forms include the
+    fixation prep and the normalisation. One untimed run with the ray test beside the z-buffer
+    counts the in-cone pairs on which the two disagree."""
+    import torch
+    import synth
+    from paper_2601_07571_gb300 import build as B
+    B.build()
+    import paper_2601_07571_gb300 as G
+    from paper_2601_07571_gb300 import pipeline
+    torch.cuda.set_device(0)
+    w = make_workload("paper_scene", args.fixations)
+    fwd, up = synth.head_frames(w.fixations)
+    ctx = G.gm_create(0)
+    stream = torch.cuda.current_stream()
+    sc = G.gm_build_scene(ctx, pipeline.mesh_args(w, to_device=True), stream)
+    sm = G.gm_sample_surface(sc, [m.density for m in w.meshes], w.seed, w.session, stream)
+    fix = pipeline.fixation_args(w.fixations, to_device=True)
+    d_fwd, d_up = torch.from_numpy(fwd).cuda(), torch.from_numpy(up).cuda()
+    prm = pipeline.params_of(w, normalize=True)
+    zbp = G.zbuffer_params(args.zb_res, 0.05, 100.0, args.zb_eps)
+    ns = G.gm_samples_info(sm)
+    pairs = ns * w.fixations.n
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            G.gm_map_free(fn())
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            G.gm_map_free(m)
+        return sum(ts) / len(ts)
+
+    clocks = ClockSampler()
+    clocks.start()
+    l0 = G.gm_ctx_launches(ctx)
+    zb_ms = timed(lambda: G.gm_accumulate_zbuffer(sc, sm, *fix, prm, zbp, d_fwd, d_up, stream))
+    launches = (G.gm_ctx_launches(ctx) - l0) // max(1, args.steps + args.warmup)
+    clk = clocks.stop()
+    ray_ms = timed(lambda: G.gm_accumulate_fixations(sc, sm, *fix, prm, stream))
+    cmp = G.zbuffer_params(args.zb_res, 0.05, 100.0, args.zb_eps, compare=True)
+    m = G.gm_accumulate_zbuffer(sc, sm, *fix, prm, cmp, d_fwd, d_up, stream)
+    _, _, st, _ = G.gm_map_info(m)
+    zs = G.gm_zbuffer_stats(m)
+    G.gm_map_free(m)
+    line = {"metric": METRIC, "value": pairs / (zb_ms * 1e-3), "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": zb_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name + "_zbuffer", "form": "z-buffer (Sections 3.2.2, 3.3.2)",
+                       "zbuffer_res": args.zb_res, "eps_m": args.zb_eps, "near_m": 0.05, "far_m": 100.0,
+                       "head_pose": "forward within 15 deg of the gaze, up +y", "samples": int(ns),
+                       "fixations": w.fixations.n, "pairs_per_step": int(pairs),
+                       "l2": "flushed between steps (256 MiB write)", "inputs": "device-resident"},
+            "ray_form": {"value": pairs / (ray_ms * 1e-3), "ms_per_step": ray_ms},
+            "zbuffer_over_ray_speed": ray_ms / zb_ms,
+            "flips": {"in_cone_pairs": st["in_cone"], "zbuffer_visible_ray_hidden": zs["flips_to_visible"],
+                      "zbuffer_hidden_ray_visible": zs["flips_to_hidden"],
+                      "rate": (zs["flips_to_visible"] + zs["flips_to_hidden"]) / max(1, st["in_cone"])},
+            "raster_pairs": zs["raster_pairs"], "gpu_launches": int(launches), "clocks": clk}
+    G.gm_samples_free(sm)
+    G.gm_scene_free(sc)
+    G.gm_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def field_arm(args):
     """Neural density field on the paper-shaped scene: train on the normalised map of its 2M
     samples (MSE, Adam, batch 65 536, --field-lr cosine to 1 %, --field-steps steps), then answer
@@ -405,6 +482,9 @@ def main():
         return
     if args.workload == "batched":
         batched_arm(args)
+        return
+    if args.workload == "zbuffer":
+        zbuffer_arm(args)
         return
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

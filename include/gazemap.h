@@ -258,6 +258,44 @@ gm_status gm_accumulate_fixations(gm_scene* scene, gm_samples* samples, const gm
 gm_status gm_accumulate_dynamic(gm_scene* scene, gm_samples* samples, const gm_fixations* fix,
                                 const gm_params* params, const double* window_transforms, gm_stream stream,
                                 gm_map** out);
+/* ---- the paper's z-buffer occlusion path (Sections 3.2.2, 3.3.2, Appendix A) -------------
+ * The same accumulation with the paper's visibility test in place of the exact ray: for every
+ * fixation a camera at the eye (forward and up hints per fixation: the head pose; NULL forward =
+ * the gaze, NULL up = +y), the crop window of the cutoff cone on the near plane, a z-buffer of
+ * res x res pixels over that window holding the linear view depth w of the nearest surface at
+ * each pixel centre (geometry clipped to near <= w <= far, triangles two-sided), and a pair
+ * counts as visible when the sample lies in the crop frustum (the NDC filter of Section 3.3.2)
+ * and |w_sample - w_zbuffer| <= eps (Section 3.2.2). The crop window is the exact bounding box of
+ * the cone's section (Appendix A centres its box on the gaze point E, which is not the centre of
+ * an oblique conic section, so the printed box can cut the cone). The cone test, the Gaussian,
+ * windows, compensated sums and normalisation are those of gm_accumulate_fixations. Fixations
+ * whose cone reaches behind their camera have no crop window and are skipped (counted). With
+ * `compare` the exact ray test also runs on every in-cone pair and the disagreements are counted
+ * (gm_zbuffer_stats). Z-buffers are built for chunks of fixations of at most `zbuffer_bytes`
+ * (0: 2 GiB). Synchronises `stream` a few times per chunk. */
+typedef struct {
+    uint32_t res;            /* z-buffer pixels per side (a generation parameter, Section 3.3.4) */
+    float near_m, far_m;     /* clip planes, metres, 0 < near < far */
+    float eps_m;             /* the +-eps of the depth comparison, metres */
+    uint32_t compare;        /* nonzero: count disagreements with the exact ray test */
+    uint64_t zbuffer_bytes;  /* device memory for one chunk of z-buffers (0: 2 GiB) */
+} gm_zbuffer_params;
+gm_status gm_accumulate_zbuffer(gm_scene* scene, gm_samples* samples, const gm_fixations* fix,
+                                const float* cam_forward, const float* cam_up, const gm_params* params,
+                                const gm_zbuffer_params* zb, gm_stream stream, gm_map** out);
+/* Statistics of a z-buffer map: fixations skipped (no crop window), in-cone pairs the z-buffer
+ * calls visible but the ray test hides, pairs it hides but the ray test sees (both 0 unless
+ * `compare`), and (fixation, triangle) pairs sent to the rasteriser. */
+gm_status gm_zbuffer_stats(const gm_map* map, uint64_t* skipped_fixations, uint64_t* flips_to_visible,
+                           uint64_t* flips_to_hidden, uint64_t* raster_pairs);
+/* The z-buffers themselves, for n fixations in input order (no windows, no accumulation):
+ * zbuf (host or device) receives n x res x res FP32 depths (row = pixel y from the window's
+ * bottom, +inf where no surface), crop (host, may be NULL) n x 4 FP64 (l, r, b, t on the near
+ * plane; NaN for a fixation without a crop window). Synchronises `stream`. */
+gm_status gm_zbuffer_render(gm_scene* scene, const float* eye, const float* gaze, const float* cam_forward,
+                            const float* cam_up, uint32_t n, float theta_rad, float cutoff_sigmas,
+                            const gm_zbuffer_params* zb, float* zbuf, double* crop, gm_stream stream);
+
 /* Number of windows, samples and statistics; waits for the map's work to finish. */
 gm_status gm_map_info(gm_map* map, uint32_t* n_windows, uint64_t* n_samples, gm_map_stats* stats);
 /* Copy window `window` (n_samples FP32 values in stored sample order) to `dst` (host or

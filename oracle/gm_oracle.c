@@ -764,7 +764,8 @@ int ora_zb_frustum(const float* eye, const float* gaze, const float* cam_fwd, co
  * is the smallest w = t n over triangles that the ray e + t (x right + y up + n fwd) meets with
  * n <= w <= f (+inf when none). amb[p] is set when a triangle whose edge passes within delta_px
  * pixels of the centre (at its own depth) lies no deeper than the pixel's depth (plus 1e-6
- * relative), or a hit lies within 1e-9 relative of a clip plane. zbuf and amb: res * res. */
+ * relative), or a hit lies within 1e-5 relative of a clip plane (an FP32 clipper may move the
+ * clip edge by that much). zbuf and amb: res * res. */
 int ora_zb_render(const float* tri, int64_t nt, const ora_frustum* F, int32_t res, double delta_px, double* zbuf,
                   uint8_t* amb)
 {
@@ -790,13 +791,13 @@ int ora_zb_render(const float* tri, int64_t nt, const ora_frustum* F, int32_t re
                 double tt, tp2;
                 ray_tri_t(F->e, d, tri + 9 * j, dw * (wp > 0.0 ? wp : 0.0), &tt, &nr2, &tp2);
                 if (hit) {
-                    if (fabs(w - F->n) <= 1e-9 * F->n || fabs(w - F->f) <= 1e-9 * F->f) clip_amb = 1;
+                    if (fabs(w - F->n) <= 1e-5 * F->n || fabs(w - F->f) <= 1e-5 * F->f) clip_amb = 1;
                     if (w >= F->n && w <= F->f && w < best) best = w;
                 }
                 if (nr2 && wp >= F->n * (1.0 - 1e-9) && wp <= F->f * (1.0 + 1e-9) && wp < near_best) near_best = wp;
             }
             zbuf[(size_t)py * res + px] = best;
-            amb[(size_t)py * res + px] = (uint8_t)(clip_amb || near_best <= best * (1.0 + 1e-6));
+            amb[(size_t)py * res + px] = (uint8_t)(clip_amb || (isfinite(near_best) && near_best <= best * (1.0 + 1e-6)));
         }
     }
     return 0;

@@ -90,6 +90,7 @@ struct gm_map {
     uint64_t dbg_cap = 0;
     gm_map_stats stats{};
     bool timing = false;
+    bool zbuffer = false;                    // made by gm_accumulate_zbuffer: 16 counters, [8..11] its own
     cudaEvent_t ev[6] = {};
     cudaStream_t stream = nullptr;
 };

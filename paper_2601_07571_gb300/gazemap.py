@@ -59,6 +59,11 @@ class gm_build_opts(C.Structure):
     _fields_ = [("builder", C.c_int32), ("dynamic", C.c_int32)]
 
 
+class gm_zbuffer_params(C.Structure):
+    _fields_ = [("res", C.c_uint32), ("near_m", C.c_float), ("far_m", C.c_float), ("eps_m", C.c_float),
+                ("compare", C.c_uint32), ("zbuffer_bytes", C.c_uint64)]
+
+
 class gm_export_dst(C.Structure):
     _fields_ = [("value", C.c_void_p), ("object_id", C.c_void_p), ("triangle", C.c_void_p), ("bary3", C.c_void_p),
                 ("local_xyz", C.c_void_p), ("world_xyz", C.c_void_p)]
@@ -104,6 +109,11 @@ _SIGS = {
     "gm_tri_offsets_noalloc": (C.c_int, [_P, _P, _P, C.c_uint32, _P, _P]),
     "gm_accumulate_fixations": (C.c_int, [_P, _P, C.POINTER(gm_fixations), C.POINTER(gm_params), _P,
                                           C.POINTER(_P)]),
+    "gm_accumulate_zbuffer": (C.c_int, [_P, _P, C.POINTER(gm_fixations), _P, _P, C.POINTER(gm_params),
+                                        C.POINTER(gm_zbuffer_params), _P, C.POINTER(_P)]),
+    "gm_zbuffer_stats": (C.c_int, [_P] + [C.POINTER(C.c_uint64)] * 4),
+    "gm_zbuffer_render": (C.c_int, [_P, _P, _P, _P, _P, C.c_uint32, C.c_float, C.c_float,
+                                    C.POINTER(gm_zbuffer_params), _P, _P, _P]),
     "gm_map_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(gm_map_stats)]),
     "gm_map_copy": (C.c_int, [_P, C.c_uint32, _P, C.POINTER(C.c_float), _P]),
     "gm_map_device_values": (_P, [_P]),
@@ -342,6 +352,37 @@ def gm_accumulate_dynamic(scene, samples, eye, gaze, duration_s, timestamp_s, pa
     h = _P()
     _check(lib().gm_accumulate_dynamic(scene, samples, C.byref(fx), C.byref(params), p, _stream(stream), C.byref(h)))
     return h
+
+
+def zbuffer_params(res=256, near=0.05, far=100.0, eps=0.005, compare=False, zbuffer_bytes=0):
+    return gm_zbuffer_params(int(res), float(near), float(far), float(eps), 1 if compare else 0, int(zbuffer_bytes))
+
+
+def gm_accumulate_zbuffer(scene, samples, eye, gaze, duration_s, timestamp_s, params: gm_params,
+                          zb: gm_zbuffer_params, cam_forward=None, cam_up=None, stream=None):
+    fx = gm_fixations(_ptr(eye), _ptr(gaze), _ptr(duration_s), _ptr(timestamp_s), int(eye.shape[0]))
+    h = _P()
+    _check(lib().gm_accumulate_zbuffer(scene, samples, C.byref(fx), _ptr(cam_forward), _ptr(cam_up), C.byref(params),
+                                       C.byref(zb), _stream(stream), C.byref(h)))
+    return h
+
+
+def gm_zbuffer_stats(m) -> dict:
+    v = [C.c_uint64() for _ in range(4)]
+    _check(lib().gm_zbuffer_stats(m, *[C.byref(x) for x in v]))
+    return dict(skipped_fixations=v[0].value, flips_to_visible=v[1].value, flips_to_hidden=v[2].value,
+                raster_pairs=v[3].value)
+
+
+def gm_zbuffer_render(scene, eye, gaze, theta_rad, cutoff_sigmas, zb: gm_zbuffer_params, cam_forward=None,
+                      cam_up=None, stream=None):
+    """Returns (zbuf (n, res, res) float32, crop (n, 4) float64)."""
+    n = int(np.asarray(eye).shape[0])
+    z = np.empty((n, zb.res, zb.res), np.float32)
+    crop = np.empty((n, 4), np.float64)
+    _check(lib().gm_zbuffer_render(scene, _ptr(eye), _ptr(gaze), _ptr(cam_forward), _ptr(cam_up), n, float(theta_rad),
+                                   float(cutoff_sigmas), C.byref(zb), _ptr(z), _ptr(crop), _stream(stream)))
+    return z, crop
 
 
 def gm_map_info(m):

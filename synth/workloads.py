@@ -317,3 +317,19 @@ def flatten(w: Workload):
     nv = np.array([len(m.vertices) for m in w.meshes], dtype=np.int64)
     dens = np.array([m.density for m in w.meshes], dtype=np.float64)
     return verts, idx, xf, nt, nv, dens
+
+
+def head_frames(fixations: Fixations, seed: int = 9, max_dev_deg: float = 15.0):
+    """Head pose per fixation for the z-buffer form: the head's forward vector is the gaze turned
+    by a uniform angle in [0, max_dev_deg] about a random axis perpendicular to it (the eyes look
+    up to that far from straight ahead), its up hint is +y. Returns (forward, up), (n, 3) float32."""
+    rng = np.random.default_rng(seed)
+    g = fixations.gaze.astype(np.float64)
+    g = g / np.linalg.norm(g, axis=1, keepdims=True)
+    a = rng.normal(size=g.shape)
+    a -= (a * g).sum(1, keepdims=True) * g
+    a /= np.linalg.norm(a, axis=1, keepdims=True)
+    ang = np.radians(rng.uniform(0.0, max_dev_deg, size=len(g)))[:, None]
+    fwd = g * np.cos(ang) + np.cross(a, g) * np.sin(ang)
+    up = np.tile(np.array([0.0, 1.0, 0.0]), (len(g), 1))
+    return fwd.astype(np.float32), up.astype(np.float32)

@@ -1,0 +1,164 @@
+"""The paper's z-buffer path on the GPU (gm_zbuffer_render, gm_accumulate_zbuffer) against the
+oracle: crop windows, z-buffer depths outside the oracle's ambiguous pixels, per-pair visibility
+outside its ambiguous pairs, densities within the accumulation tolerance; chunking and windows
+leave the map unchanged; the disagreement counters agree with the two paths' own pair records."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.parity_utils import tri_max_coord, ulp32
+
+pytestmark = pytest.mark.gpu
+
+DPX = 5e-3      # pixel-position margin covering FP32 sample positions and the FP32 pixel mapping
+
+
+def f32(x):
+    """The C ABI takes clip planes and eps as FP32: the oracle gets the same values."""
+    return float(np.float32(x))
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2601_07571_gb300 import build
+    build.build()
+    import paper_2601_07571_gb300 as G
+    from paper_2601_07571_gb300 import pipeline
+    ctx = G.gm_create(0)
+    yield G, pipeline, ctx
+    G.gm_destroy(ctx)
+
+
+def _workload(n_fix=100, theta_deg=1.0):
+    w = synth.tiny_sphere(n_fix=n_fix)
+    # theta exactly representable in FP32 (the C ABI takes it as a float)
+    w.params = synth.Params(theta_rad=float(np.float32(math.radians(theta_deg))))
+    fwd, up = synth.head_frames(w.fixations)
+    return w, fwd, up
+
+
+def test_crop_windows_and_zbuffers_against_oracle(env):
+    G, pipe, ctx = env
+    w, fwd, up = _workload(n_fix=8, theta_deg=3.0)
+    zb = oracle.ZBuffer(res=64, near=f32(0.05), far=100.0)
+    sc = G.gm_build_scene(ctx, pipe.mesh_args(w))
+    fx = w.fixations
+    z, crop = G.gm_zbuffer_render(sc, fx.eye, fx.gaze, w.params.theta_rad, w.params.cutoff_sigmas,
+                                  G.zbuffer_params(zb.res, zb.near, zb.far), fwd, up)
+    G.gm_scene_free(sc)
+    tri = oracle.world_triangles(w)
+    checked = covered = 0
+    for i in range(fx.n):
+        F = oracle.zb_frustum(fx.eye[i], fx.gaze[i], fwd[i], up[i], w.params.theta_rad, w.params.cutoff_sigmas,
+                              zb.near, zb.far)
+        assert F is not None
+        ref = np.array([F["l"], F["r"], F["b"], F["t"]])
+        # FP64 on both sides; the GPU contracts multiply-adds, so compare against the window's width
+        assert np.all(np.abs(crop[i] - ref) <= 1e-12 * (ref[1] - ref[0]))
+        zo, amb = oracle.zb_render(tri, F, zb.res, delta_px=DPX)
+        zg = z[i].astype(np.float64)
+        sure = ~amb
+        assert np.array_equal(np.isinf(zg[sure]), np.isinf(zo[sure]))
+        fin = sure & np.isfinite(zo)
+        assert np.all(np.abs(zg[fin] - zo[fin]) <= 1e-4 * zo[fin])
+        checked += int(sure.sum())
+        covered += int(fin.sum())
+    assert checked > 0.95 * fx.n * zb.res ** 2 and covered > 2000
+
+
+def _gpu_zb_map(G, pipe, ctx, w, fwd, up, zbp, cap=2_000_000, normalize=False):
+    sc = G.gm_build_scene(ctx, pipe.mesh_args(w))
+    sm = G.gm_sample_surface(sc, [m.density for m in w.meshes], w.seed, w.session)
+    eye, gaze, dur, ts = pipe.fixation_args(w.fixations)
+    prm = pipe.params_of(w, normalize=normalize, flags=G.GM_F_DEBUG_PAIRS, debug_pair_cap=cap)
+    m = G.gm_accumulate_zbuffer(sc, sm, eye, gaze, dur, ts, prm, zbp, fwd, up)
+    W, ns, stats, _ = G.gm_map_info(m)
+    vals = []
+    for k in range(W):
+        v = np.empty(ns, np.float32)
+        G.gm_map_copy(m, k, v)
+        vals.append(v)
+    pairs = G.gm_map_debug_pairs(m, cap)
+    zs = G.gm_zbuffer_stats(m)
+    G.gm_map_free(m)
+    G.gm_samples_free(sm)
+    G.gm_scene_free(sc)
+    return np.array(vals), pairs, stats, zs
+
+
+def test_zbuffer_accumulation_against_oracle(env):
+    G, pipe, ctx = env
+    w, fwd, up = _workload(n_fix=100, theta_deg=2.0)
+    zb = oracle.ZBuffer(res=128, near=f32(0.05), far=100.0, eps=f32(0.005))
+    tri = oracle.world_triangles(w)
+    off = oracle.tri_offsets(oracle.areas(tri), oracle.tri_density(w))
+    smp = oracle.samples(tri, off, w.seed, w.session)
+    ora = oracle.zb_accumulate(tri, smp.xyz, w.fixations, fwd, up, w.params, zb, delta_px=DPX, cone_band=1e-4,
+                               record=True)
+    vals, pairs, stats, zs = _gpu_zb_map(G, pipe, ctx, w, fwd, up, G.zbuffer_params(zb.res, zb.near, zb.far, zb.eps))
+    assert zs["skipped_fixations"] == ora["stats"]["skipped_fixations"] == 0
+    d = ora["density"][0]
+    M = tri_max_coord(tri, smp.tri)
+    tol = 1e-4 * (d + ora["amb"][0]) + ora["amb"][0] + ora["sens"][0] * 8 * ulp32(M) + 1e-30
+    assert (d > 0).sum() > 300
+    assert np.all(np.abs(vals[0].astype(np.float64) - d) <= tol)
+    # pair by pair: visibility equal wherever the oracle's decision is not ambiguous
+    P = ora["pairs"]
+    inc = (P["flag"] & oracle.PF_IN_CONE) > 0
+    key_o = P["sample"][inc] * (1 << 20) + P["fix"][inc]
+    vis_o = (P["flag"][inc] & oracle.PF_VISIBLE) > 0
+    amb_o = (P["flag"][inc] & oracle.PF_VIS_AMBIG) > 0
+    key_g = pairs["sample"].astype(np.int64) * (1 << 20) + pairs["fix"]
+    og, gg = np.argsort(key_o), np.argsort(key_g)
+    edge = (P["flag"][inc] & oracle.PF_CONE_EDGE) > 0
+    common, io, ig = np.intersect1d(key_o[og], key_g[gg], return_indices=True)
+    assert len(common) >= len(key_o) - edge.sum() and len(common) >= len(key_g) - edge.sum()
+    vo, ao, vg = vis_o[og][io], amb_o[og][io], pairs["visible"][gg][ig].astype(bool)
+    assert np.array_equal(vo[~ao], vg[~ao])
+    assert stats["visible"] == int(pairs["visible"].sum())
+
+
+def test_chunks_and_windows_leave_the_map_unchanged(env):
+    G, pipe, ctx = env
+    w, fwd, up = _workload(n_fix=100, theta_deg=2.0)
+    w.params = synth.Params(theta_rad=w.params.theta_rad, t_begin=0.0, t_end=40.0, window_s=10.0)
+    one, _, _, _ = _gpu_zb_map(G, pipe, ctx, w, fwd, up, G.zbuffer_params(96, 0.05, 100.0, 0.005), cap=0)
+    # 7 fixations per chunk: chunk boundaries fall inside windows
+    many, _, _, zs = _gpu_zb_map(G, pipe, ctx, w, fwd, up,
+                                 G.zbuffer_params(96, 0.05, 100.0, 0.005, zbuffer_bytes=7 * 96 * 96 * 4), cap=0)
+    assert one.shape == many.shape == (4, one.shape[1])
+    assert np.array_equal(one.view(np.uint32), many.view(np.uint32))
+    assert (one > 0).sum(1).min() > 50
+
+
+def test_disagreement_counters_match_the_pair_records(env):
+    G, pipe, ctx = env
+    w, fwd, up = _workload(n_fix=100, theta_deg=2.0)
+    zbp = G.zbuffer_params(128, 0.05, 100.0, 0.002, compare=True)
+    _, zp, _, zs = _gpu_zb_map(G, pipe, ctx, w, fwd, up, zbp)
+    h = pipe.run(ctx, w, normalize=False, flags=G.GM_F_DEBUG_PAIRS, debug_pair_cap=2_000_000)
+    rp = G.gm_map_debug_pairs(h.map, 2_000_000)
+    h.free()
+    kz = zp["sample"].astype(np.int64) * (1 << 20) + zp["fix"]
+    kr = rp["sample"].astype(np.int64) * (1 << 20) + rp["fix"]
+    oz, orr = np.argsort(kz), np.argsort(kr)
+    assert np.array_equal(kz[oz], kr[orr])          # the same in-cone pairs on both paths
+    vz, vr = zp["visible"][oz].astype(bool), rp["visible"][orr].astype(bool)
+    assert zs["flips_to_visible"] == int((vz & ~vr).sum())
+    assert zs["flips_to_hidden"] == int((~vz & vr).sum())
+    assert zs["flips_to_visible"] + zs["flips_to_hidden"] > 0
+
+
+def test_cone_behind_the_camera_is_skipped(env):
+    G, pipe, ctx = env
+    w, fwd, up = _workload(n_fix=10, theta_deg=1.0)
+    fwd = fwd.copy()
+    fwd[3] = -w.fixations.gaze[3]       # the head faces away from where the eyes look
+    vals, pairs, stats, zs = _gpu_zb_map(G, pipe, ctx, w, fwd, up, G.zbuffer_params(64, 0.05, 100.0, 0.005))
+    assert zs["skipped_fixations"] == 1
+    assert not np.any(pairs["fix"] == 3)
