@@ -46,6 +46,7 @@ struct gm_scene {
     double* mesh_inv = nullptr;      // n_meshes x 12: world -> local affine map (row-major 3x4)
     bool mesh_inv_ok = true;         // every mesh transform was invertible
     float4* tri_local = nullptr;     // n_tris x 3 float4 mesh-local vertices (scenes built dynamic only)
+    uint64_t zb_pairs_per_fix = 0;   // z-buffer path: raster pairs per fixation seen last (capacity hint)
     float4* nodes = nullptr;         // (n_tris - 1) x 4 float4: child boxes + child links
     float4* bvh_tris = nullptr;      // n_tris x 3 float4 in leaf order, v0.w = global tri id
     uint32_t depth = 0;

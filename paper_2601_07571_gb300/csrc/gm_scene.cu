@@ -414,14 +414,24 @@ __global__ void k_ploc_compact(int m, const int64_t* __restrict__ incl, const in
 // cache line. leaves[v] = number of leaves below v (bottom-up); the index of v is the sum, over
 // the path from the root, of 1 per step plus the left sibling's internal-node count when the
 // step goes right.
-__global__ void k_leaf_counts(const int* __restrict__ parent_leaf, const int* __restrict__ parent_node, int n,
-                              unsigned int* __restrict__ leaves) {
+// Leaves under every internal node, bottom-up: the second of a node's two children to arrive
+// sums the children's counts and climbs on (one atomic per node, as in the box refit).
+__global__ void k_leaf_counts(const int* __restrict__ parent_leaf, const int* __restrict__ parent_node,
+                              const float4* __restrict__ nodes, int n, unsigned int* __restrict__ leaves,
+                              unsigned int* __restrict__ flags) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int p = parent_leaf[i];
     int guard = 0;
     while (p >= 0 && guard++ < 4096) {
-        atomicAdd(&leaves[p], 1u);
+        __threadfence();
+        if (atomicAdd(&flags[p], 1u) == 0u) return;   // the sibling finishes this node
+        __threadfence();
+        const float4 l = nodes[4 * p + 3];
+        const int a = __float_as_int(l.x), b = __float_as_int(l.y);
+        const unsigned int ca = a >= 0 ? __ldcg(&leaves[a]) : 1u;
+        const unsigned int cb = b >= 0 ? __ldcg(&leaves[b]) : 1u;
+        leaves[p] = ca + cb;
         p = p > 0 ? parent_node[p] : -1;
     }
 }
@@ -454,8 +464,6 @@ __global__ void k_dfs_remap(const float4* __restrict__ nodes, const int* __restr
     const int a = __float_as_int(l.x), b = __float_as_int(l.y);
     out[4 * d + 3] = make_float4(__int_as_float(a >= 0 ? dfs[a] : a), __int_as_float(b >= 0 ? dfs[b] : b), 0.f, 0.f);
 }
-
-}  // namespace
 
 // ---- dynamic scenes: re-pose every mesh, refit the boxes over the unchanged topology ----------
 // Mesh-local triangle vertices in stored (mesh) order, kept for re-posing.
@@ -544,6 +552,8 @@ __global__ void k_final_parents(const float4* __restrict__ nodes, int n_int, int
         }
     }
 }
+
+}  // namespace
 
 // Inverse affine maps (world -> mesh-local, row-major 3 x 4) of row-major 4 x 4 transforms, by the
 // adjugate in FP64; false if any transform is singular (its rows are left zero).
@@ -790,12 +800,16 @@ static gm_status build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n
         const int n_int = (int)nt - 1;
         unsigned int* leaves = nullptr;
         int* dfs = nullptr;
+        unsigned int* arrived = nullptr;
         float4* reordered = nullptr;
         TMP_ALLOC(leaves, sizeof(unsigned int) * n_int);
         TMP_ALLOC(dfs, sizeof(int) * n_int);
+        TMP_ALLOC(arrived, sizeof(unsigned int) * n_int);
         GM_TRY_CUDA(cudaMemsetAsync(leaves, 0, sizeof(unsigned int) * n_int, s));
+        GM_TRY_CUDA(cudaMemsetAsync(arrived, 0, sizeof(unsigned int) * n_int, s));
         if ((st = gm_alloc((void**)&reordered, sizeof(float4) * 4 * (size_t)n_int, s)) != GM_OK) return fail(st);
-        k_leaf_counts<<<gm_div_up(nt, 256), 256, 0, s>>>(parent_leaf, parent_node_keep, (int)nt, leaves);
+        k_leaf_counts<<<gm_div_up(nt, 256), 256, 0, s>>>(parent_leaf, parent_node_keep, sc->nodes, (int)nt, leaves,
+                                                         arrived);
         k_dfs_index<<<gm_div_up(n_int, 256), 256, 0, s>>>(sc->nodes, parent_node_keep, leaves, n_int, dfs);
         k_dfs_remap<<<gm_div_up(n_int, 256), 256, 0, s>>>(sc->nodes, dfs, n_int, reordered);
         ctx->launches += 3;

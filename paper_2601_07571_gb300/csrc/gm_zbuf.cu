@@ -516,7 +516,7 @@ struct RasterBuffers {
     unsigned long long* counts = nullptr;   // [0] pairs [1] big
 };
 
-gm_status render_zbuffers(gm_ctx* ctx, const gm_scene* sc, const ZbFrustum* frusta, uint32_t nfix, uint32_t res,
+gm_status render_zbuffers(gm_ctx* ctx, gm_scene* sc, const ZbFrustum* frusta, uint32_t nfix, uint32_t res,
                           uint32_t* zbuf, RasterBuffers& rb, cudaStream_t s, int* launches,
                           unsigned long long* raster_pairs) {
     const size_t npx = (size_t)res * res;
@@ -540,6 +540,8 @@ gm_status render_zbuffers(gm_ctx* ctx, const gm_scene* sc, const ZbFrustum* frus
             continue;
         }
         if (raster_pairs) *raster_pairs += np;
+        // the next call on this scene starts with room for this density of pairs
+        sc->zb_pairs_per_fix = std::max<uint64_t>(sc->zb_pairs_per_fix, np / nfix + 1);
         if (np > 0) {
             if (np > 0xffffffffull) return gm_set_error(GM_ERR_UNSUPPORTED, "z-buffer: more than 2^32 raster pairs");
             k_zb_raster<<<(uint32_t)((np + ZB_THREADS - 1) / ZB_THREADS), ZB_THREADS, 0, s>>>(
@@ -617,7 +619,7 @@ extern "C" gm_status gm_zbuffer_render(gm_scene* sc, const float* eye, const flo
     uint32_t* zb = nullptr;
     float* zf = nullptr;
     RasterBuffers rb;
-    rb.cap = std::max<uint64_t>(1u << 16, (uint64_t)n * 4096);
+    rb.cap = std::max<uint64_t>(1u << 16, (uint64_t)n * std::max<uint64_t>(4096, sc->zb_pairs_per_fix * 5 / 4));
 #define ZB_TMP(ptr, bytes)                                                          \
     do {                                                                            \
         if ((st = gm_alloc((void**)&(ptr), (bytes), s)) != GM_OK) return done(st);  \
@@ -803,7 +805,7 @@ extern "C" gm_status gm_accumulate_zbuffer(gm_scene* sc, gm_samples* sm, const g
     float2* state = nullptr;
     TMP_ALLOC(zbuf, sizeof(uint32_t) * npx * chunk);
     if (chunk < nv) TMP_ALLOC(state, sizeof(float2) * (ns ? ns : 1));
-    rb.cap = std::max<uint64_t>(1u << 20, (uint64_t)chunk * 2048);
+    rb.cap = std::max<uint64_t>(1u << 20, (uint64_t)chunk * std::max<uint64_t>(2048, sc->zb_pairs_per_fix * 5 / 4));
     TMP_ALLOC(rb.counts, sizeof(unsigned long long) * 2);
     if ((st = gm_alloc((void**)&rb.pairs, sizeof(PairFT) * rb.cap, s)) != GM_OK) return fail(st);
     if ((st = gm_alloc((void**)&rb.big, sizeof(uint32_t) * rb.cap, s)) != GM_OK) return fail(st);
