@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--fixations", type=int, default=0, help="use only the first N fixations (profiling)")
     ap.add_argument("--flags", type=int, default=0, help="extra GM_F_* accumulation flags (variant A/B runs)")
     ap.add_argument("--builder", choices=["default", "lbvh", "ploc"], default="default", help="BVH builder")
+    ap.add_argument("--eps-rel", type=float, default=None,
+                    help="occlusion segment end (1 - eps_rel of the way to the sample); default the workload's 1e-5")
     ap.add_argument("--zb-res", type=int, default=256, help="z-buffer pixels per side (zbuffer workload)")
     ap.add_argument("--zb-eps", type=float, default=0.005, help="z-buffer depth tolerance, metres (zbuffer workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -501,6 +503,8 @@ def main():
     from paper_2601_07571_gb300 import pipeline
 
     w = make_workload(args.workload, args.fixations)
+    if args.eps_rel is not None:
+        w.params.eps_rel = args.eps_rel
     ctx = G.gm_create(local)
     stream = torch.cuda.current_stream()
     dev_meshes = pipeline.mesh_args(w, to_device=True)
@@ -605,7 +609,7 @@ def main():
                        "fixations": w.fixations.n, "pairs_per_step": int(pairs),
                        "l2": "flushed between steps (256 MiB write)", "inputs": "device-resident",
                        "parallelism": f"replicas{world}" if world > 1 else "single",
-                       "accumulate_flags": args.flags, "builder": args.builder},
+                       "accumulate_flags": args.flags, "builder": args.builder, "eps_rel": w.params.eps_rel},
             "stages_ms": {"accumulate": acc, "fixation_prep": sum(prep_ms) / len(prep_ms),
                           "normalize": sum(norm_ms) / len(norm_ms),
                           "build_and_sample": step_ms - acc - sum(prep_ms) / len(prep_ms) - sum(norm_ms) / len(norm_ms)},
