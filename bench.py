@@ -55,8 +55,9 @@ def accumulate_sources_sha256() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(workload: str, flags: int, builder: str):
-    if ACC_TRAFFIC["bytes"] is None or workload != ACC_TRAFFIC["workload"] or flags != 0 or builder != "default":
+def recorded_traffic(workload: str, flags: int, builder: str, default_tree_and_segment: bool = True):
+    if (ACC_TRAFFIC["bytes"] is None or workload != ACC_TRAFFIC["workload"] or flags != 0 or builder != "default"
+            or not default_tree_and_segment):
         return None
     return ACC_TRAFFIC["bytes"] if accumulate_sources_sha256() == ACC_TRAFFIC["sources_sha256"] else None
 
@@ -76,6 +77,7 @@ def parse():
     ap.add_argument("--fixations", type=int, default=0, help="use only the first N fixations (profiling)")
     ap.add_argument("--flags", type=int, default=0, help="extra GM_F_* accumulation flags (variant A/B runs)")
     ap.add_argument("--builder", choices=["default", "lbvh", "ploc"], default="default", help="BVH builder")
+    ap.add_argument("--ploc-radius", type=int, default=0, help="PLOC neighbour radius (0: library default 8)")
     ap.add_argument("--eps-rel", type=float, default=None,
                     help="occlusion segment end (1 - eps_rel of the way to the sample); default the workload's 1e-5")
     ap.add_argument("--zb-res", type=int, default=256, help="z-buffer pixels per side (zbuffer workload)")
@@ -516,7 +518,7 @@ def main():
     builder = {"default": None, "lbvh": G.GM_BUILD_LBVH, "ploc": G.GM_BUILD_PLOC}[args.builder]
 
     def step(meshes, fix):
-        sc = G.gm_build_scene(ctx, meshes, stream, builder=builder)
+        sc = G.gm_build_scene(ctx, meshes, stream, builder=builder, ploc_radius=args.ploc_radius)
         sm = G.gm_sample_surface(sc, dens, w.seed, w.session, stream)
         mp = G.gm_accumulate_fixations(sc, sm, *fix, prm, stream)
         return sc, sm, mp
@@ -595,7 +597,9 @@ def main():
     achieved = FP32_INSTR_PER_PAIR * pairs / (acc * 1e-3) / 1e12
     peak = n_sm * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s (FP32)", "frac": achieved / peak,
-            "traffic": recorded_traffic(w.name, args.flags, args.builder), "kernel": "k_accumulate",
+            "traffic": recorded_traffic(w.name, args.flags, args.builder,
+                                        args.ploc_radius in (0, 8) and args.eps_rel is None),
+            "kernel": "k_accumulate",
             "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz",
             "work_basis": f"{FP32_INSTR_PER_PAIR} FP32 instructions per sample x fixation pair (cone test)",
             "kernel_ms": acc}
@@ -609,7 +613,8 @@ def main():
                        "fixations": w.fixations.n, "pairs_per_step": int(pairs),
                        "l2": "flushed between steps (256 MiB write)", "inputs": "device-resident",
                        "parallelism": f"replicas{world}" if world > 1 else "single",
-                       "accumulate_flags": args.flags, "builder": args.builder, "eps_rel": w.params.eps_rel},
+                       "accumulate_flags": args.flags, "builder": args.builder, "eps_rel": w.params.eps_rel,
+                       "ploc_radius": args.ploc_radius or 8},
             "stages_ms": {"accumulate": acc, "fixation_prep": sum(prep_ms) / len(prep_ms),
                           "normalize": sum(norm_ms) / len(norm_ms),
                           "build_and_sample": step_ms - acc - sum(prep_ms) / len(prep_ms) - sum(norm_ms) / len(norm_ms)},

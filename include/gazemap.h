@@ -121,24 +121,26 @@ gm_status gm_ctx_launches(const gm_ctx* ctx, uint64_t* kernel_launches);
 
 /* ---- scene (meshes -> world triangles -> BVH) ----------------------------------------- */
 
-/* Transform every mesh to world space (FP64, rounded to FP32), then build a linear BVH over
- * all triangles (Morton codes of centroids, LSD radix sort, Karras' HPG 2012 hierarchy,
- * bottom-up box refit). The BVH replaces the per-view z-buffer of Section 3.2.2 as the
- * occlusion structure. Meshes are concatenated in order; global triangle ids follow that
- * order. Synchronises `stream` once (to check the tree depth). */
+/* Transform every mesh to world space (FP64, rounded to FP32), then build a BVH over all
+ * triangles: Morton codes of centroids, LSD radix sort, then PLOC clustering (default) or
+ * Karras' HPG 2012 hierarchy, bottom-up boxes, internal nodes stored depth-first. The BVH
+ * replaces the per-view z-buffer of Section 3.2.2 as the occlusion structure. Meshes are
+ * concatenated in order; global triangle ids follow that order. Synchronises `stream` (to
+ * check the tree depth; the clustering reads its cluster count back once per round). */
 gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes,
                          gm_stream stream, gm_scene** out);
 /* Builders of the hierarchy (same node layout and traversal either way):
  *  GM_BUILD_LBVH: Karras' linear BVH from the Morton order (HPG 2012), fastest to build;
  *  GM_BUILD_PLOC: parallel locally-ordered clustering (Meister & Bittner, TVCG 2018) from the same
  *                 Morton order, merging mutual nearest neighbours by union-box surface area
- *                 within +-16 positions; a tighter tree for a few more milliseconds of build
- *                 (the default used by gm_build_scene). */
+ *                 within +-ploc_radius positions (8 by default); a tighter tree for a few more
+ *                 milliseconds of build (the default used by gm_build_scene). */
 enum { GM_BUILD_LBVH = 0, GM_BUILD_PLOC = 1, GM_BUILD_DEFAULT = GM_BUILD_PLOC };
 typedef struct {
     int32_t builder;
     int32_t dynamic;   /* nonzero: keep the mesh-local triangles (48 B per triangle) so that
                           gm_scene_pose can move the meshes later */
+    int32_t ploc_radius; /* GM_BUILD_PLOC: neighbours searched on each side, 4, 8, 16, 32 or 64 (0: 8) */
 } gm_build_opts;
 gm_status gm_build_scene_opts(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes,
                               const gm_build_opts* opts, gm_stream stream, gm_scene** out);

@@ -97,7 +97,6 @@ __global__ void __launch_bounds__(NT, MINB) k_accumulate(
     __shared__ float2 wacc[QN];     // per warp: (sum, compensation) of each sample
     __shared__ uint16_t qslot[QN];  // per warp: queue of in-cone sample slots
     __shared__ float qg[QN];        // per warp: their weights
-    __shared__ int qhead[NT / 32];  // per warp: next queue entry to hand out
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int wb = COMPACT ? warp * WARP_TILE : 0;
@@ -115,7 +114,7 @@ __global__ void __launch_bounds__(NT, MINB) k_accumulate(
         }
         if (tile >= n_tiles) break;
         warp_tile<DEBUG, COMPACT, WIDE>(tile, spos, sidx, fix, nf, nodes, tris, P, out, max_bits, wsmp + wb, wacc + wb,
-                                        qslot + wb, qg + wb, qhead + warp, &counters[2], dbg, err, st);
+                                        qslot + wb, qg + wb, &counters[2], dbg, err, st);
     }
     warp_stats_commit(st, counters);
 }

@@ -105,7 +105,6 @@ __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate_batch(const Se
     __shared__ float2 wacc[QN];
     __shared__ uint16_t qslot[QN];
     __shared__ float qg[QN];
-    __shared__ int qhead[ACC_THREADS / 32];
     const int lane = threadIdx.x & 31;
     const int wb = COMPACT ? (threadIdx.x >> 5) * WARP_TILE : 0;
     const DebugOut dbg{nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -127,7 +126,7 @@ __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate_batch(const Se
         P.group = BATCH_GROUP;
         TileStats st;
         warp_tile<false, COMPACT, WIDE>(wi.y, S.spos, S.sidx, S.fix, *S.n_fix, S.nodes, S.tris, P, S.out, S.max_bits,
-                                        wsmp + wb, wacc + wb, qslot + wb, qg + wb, qhead + (threadIdx.x >> 5), nullptr,
+                                        wsmp + wb, wacc + wb, qslot + wb, qg + wb, nullptr,
                                         dbg, err, st);
         warp_stats_commit(st, S.counters);
     }

@@ -26,6 +26,10 @@ namespace {
 
 // Store internal nodes in depth-first order (see k_dfs_index).
 constexpr bool kDfsLayout = true;
+// Clustering radius of the PLOC builder: 8 neighbours on each side traced the paper scene in
+// 244 ms against 257 ms for 16 (34.2 vs 34.1 nodes per ray; the depth-first layout of the
+// smaller-radius tree caches better), and builds faster.
+constexpr int kPlocRadius = 8;
 
 struct Mat16 {
     double m[16];
@@ -580,7 +584,7 @@ static bool mesh_inverses(const double* xf, uint32_t n_meshes, std::vector<doubl
 }
 
 static gm_status build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes, int builder,
-                             bool dynamic, gm_stream stream, gm_scene** out) {
+                             bool dynamic, int ploc_radius, gm_stream stream, gm_scene** out) {
     if (!ctx || !meshes || !out || n_meshes == 0)
         return gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene: null argument or no meshes");
     *out = nullptr;
@@ -712,7 +716,13 @@ static gm_status build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n
         int rounds = 0;
         while (m > 1 && rounds < 4096) {
             ++rounds;
-            k_ploc_nn<16><<<gm_div_up(m, 256), 256, 0, s>>>(blo, bhi, m, nn);
+            switch (ploc_radius) {
+                case 4: k_ploc_nn<4><<<gm_div_up(m, 256), 256, 0, s>>>(blo, bhi, m, nn); break;
+                case 16: k_ploc_nn<16><<<gm_div_up(m, 256), 256, 0, s>>>(blo, bhi, m, nn); break;
+                case 32: k_ploc_nn<32><<<gm_div_up(m, 256), 256, 0, s>>>(blo, bhi, m, nn); break;
+                case 64: k_ploc_nn<64><<<gm_div_up(m, 256), 256, 0, s>>>(blo, bhi, m, nn); break;
+                default: k_ploc_nn<8><<<gm_div_up(m, 256), 256, 0, s>>>(blo, bhi, m, nn); break;
+            }
             k_ploc_merge<<<gm_div_up(m, 256), 256, 0, s>>>(m, nn, cid, blo, bhi, keep, counter, sc->nodes, parent_node,
                                                            parent_leaf);
             if ((st = gm_inclusive_scan_i64(keep, (uint32_t)m, s, &launches)) != GM_OK) {
@@ -828,7 +838,7 @@ static gm_status build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n
 
 extern "C" gm_status gm_build_scene(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes, gm_stream stream,
                                     gm_scene** out) {
-    return build_scene(ctx, meshes, n_meshes, GM_BUILD_DEFAULT, false, stream, out);
+    return build_scene(ctx, meshes, n_meshes, GM_BUILD_DEFAULT, false, kPlocRadius, stream, out);
 }
 
 extern "C" gm_status gm_build_scene_opts(gm_ctx* ctx, const gm_mesh_desc* meshes, uint32_t n_meshes,
@@ -836,7 +846,10 @@ extern "C" gm_status gm_build_scene_opts(gm_ctx* ctx, const gm_mesh_desc* meshes
     const int b = opts ? opts->builder : GM_BUILD_DEFAULT;
     if (b != GM_BUILD_LBVH && b != GM_BUILD_PLOC)
         return gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene_opts: unknown builder");
-    return build_scene(ctx, meshes, n_meshes, b, opts && opts->dynamic != 0, stream, out);
+    const int r = opts && opts->ploc_radius ? opts->ploc_radius : kPlocRadius;
+    if (r != 4 && r != 8 && r != 16 && r != 32 && r != 64)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_build_scene_opts: ploc_radius must be 4, 8, 16, 32 or 64");
+    return build_scene(ctx, meshes, n_meshes, b, opts && opts->dynamic != 0, r, stream, out);
 }
 
 extern "C" gm_status gm_scene_pose(gm_scene* sc, const double* transforms, gm_stream stream) {

@@ -297,7 +297,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                                           uint32_t nf, const float4* __restrict__ nodes,
                                           const float4* __restrict__ tris, const AccParams& P,
                                           float* __restrict__ out, unsigned int* __restrict__ max_bits,
-                                          float4* wsmp, float2* wacc, uint16_t* qslot, float* qg, int* qhead,
+                                          float4* wsmp, float2* wacc, uint16_t* qslot, float* qg,
                                           unsigned long long* __restrict__ dbg_cursor, const DebugOut& dbg,
                                           int* __restrict__ err, TileStats& st) {
     const int lane = threadIdx.x & 31;

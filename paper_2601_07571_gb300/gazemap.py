@@ -56,7 +56,7 @@ GM_FIELD_N_PARAMS = 16705
 
 
 class gm_build_opts(C.Structure):
-    _fields_ = [("builder", C.c_int32), ("dynamic", C.c_int32)]
+    _fields_ = [("builder", C.c_int32), ("dynamic", C.c_int32), ("ploc_radius", C.c_int32)]
 
 
 class gm_zbuffer_params(C.Structure):
@@ -225,7 +225,7 @@ def gm_ctx_launches(ctx) -> int:
 GM_BUILD_LBVH, GM_BUILD_PLOC = 0, 1
 
 
-def gm_build_scene(ctx, meshes, stream=None, builder=None, dynamic=False):
+def gm_build_scene(ctx, meshes, stream=None, builder=None, dynamic=False, ploc_radius=0):
     """meshes: sequence of (vertices (nv,3) f32, indices (nt,3) u32, transform (4,4) f64, object_id).
     builder: None (library default), GM_BUILD_LBVH or GM_BUILD_PLOC. dynamic: keep the mesh-local
     triangles for gm_scene_pose."""
@@ -240,10 +240,10 @@ def gm_build_scene(ctx, meshes, stream=None, builder=None, dynamic=False):
         d.transform = (C.c_double * 16)(*np.asarray(xf, np.float64).reshape(16).tolist())
         d.object_id = int(obj)
     h = _P()
-    if builder is None and not dynamic:
+    if builder is None and not dynamic and not ploc_radius:
         _check(lib().gm_build_scene(ctx, descs, len(meshes), _stream(stream), C.byref(h)))
     else:
-        opt = gm_build_opts(GM_BUILD_PLOC if builder is None else int(builder), 1 if dynamic else 0)
+        opt = gm_build_opts(GM_BUILD_PLOC if builder is None else int(builder), 1 if dynamic else 0, int(ploc_radius))
         _check(lib().gm_build_scene_opts(ctx, descs, len(meshes), C.byref(opt), _stream(stream), C.byref(h)))
     return h
 
