@@ -349,7 +349,9 @@ void gm_batch_free(gm_batch* batch);
 gm_status gm_accumulate_batch(gm_ctx* ctx, const gm_session_desc* sessions, uint32_t n_sessions,
                               const gm_params* params, gm_stream stream, gm_map** out_per_session);
 /* Pick the fastest accumulation variant for one problem by timing each candidate on its first
- * 256 fixations; *best_flags gets the GM_F_* variant bits to OR into params->flags. Results are
+ * 256 fixations: ray queue on/off, binary or 4-wide tree, 80- or 64-register cap, spread or
+ * consecutive warp tiles, persistent or static scheduling (32 candidates); *best_flags gets the
+ * GM_F_* variant bits to OR into params->flags. Results are
  * cached per size bucket (log2 of samples, fixations and triangles) for the process and, when the
  * environment variable GM_TUNE_CACHE names a file, in that JSON file across processes. */
 gm_status gm_autotune_accumulate(gm_scene* scene, gm_samples* samples, const gm_fixations* fix,

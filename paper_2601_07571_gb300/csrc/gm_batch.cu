@@ -619,9 +619,14 @@ extern "C" gm_status gm_autotune_accumulate(gm_scene* sc, gm_samples* sm, const 
     sub.n = std::min<uint32_t>(fx->n, 256);   // a prefix of the fixations is enough to rank variants
     int best = 0;
     float best_t = 1e30f;
-    for (int code = 0; code < 8; ++code) {
+    // the three kernel variants of the batched search, times the warp-tile shape (four spread
+    // 32-sample runs or 128 consecutive samples) and the scheduling (persistent or one tile per warp)
+    constexpr int kTileFlags = GM_F_TILE_CONSECUTIVE | GM_F_STATIC_TILES;
+    for (int code = 0; code < 32; ++code) {
         gm_params p = *prm;
-        p.flags = (prm->flags & ~VARIANT_MASK & ~GM_F_DEBUG_PAIRS) | flags_of_code(code) | GM_F_TIMING;
+        const int f = flags_of_code(code & 7) | ((code & 8) ? GM_F_TILE_CONSECUTIVE : 0) |
+                      ((code & 16) ? GM_F_STATIC_TILES : 0);
+        p.flags = (prm->flags & ~VARIANT_MASK & ~kTileFlags & ~GM_F_DEBUG_PAIRS) | f | GM_F_TIMING;
         float t = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
             gm_map* m = nullptr;
@@ -634,7 +639,7 @@ extern "C" gm_status gm_autotune_accumulate(gm_scene* sc, gm_samples* sm, const 
         }
         if (t < best_t) {
             best_t = t;
-            best = flags_of_code(code);
+            best = f;
         }
     }
     (void)s;

@@ -129,7 +129,19 @@ def test_autotune_picks_a_variant_and_keeps_results(env, tmp_path, monkeypatch):
         assert np.array_equal(a.view(np.uint32), before[i].view(np.uint32))
     G.gm_batch_free(b)
     fl2, _ = G.gm_autotune_accumulate(hs[0][0], hs[0][1], *hs[0][2:], prm)
-    assert fl2 & ~(G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64) == 0
+    assert fl2 & ~(G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64 | G.GM_F_TILE_CONSECUTIVE
+                   | G.GM_F_STATIC_TILES) == 0
+    # the tuned variant gives the same map as the default one
+    ref = G.gm_accumulate_fixations(hs[0][0], hs[0][1], *hs[0][2:], prm)
+    p2 = pipe.params_of(ws[0], normalize=False, flags=fl2)
+    tuned = G.gm_accumulate_fixations(hs[0][0], hs[0][1], *hs[0][2:], p2)
+    a0 = np.empty(G.gm_samples_info(hs[0][1]), np.float32)
+    a1 = np.empty_like(a0)
+    G.gm_map_copy(ref, 0, a0)
+    G.gm_map_copy(tuned, 0, a1)
+    G.gm_map_free(ref)
+    G.gm_map_free(tuned)
+    assert np.array_equal(a0.view(np.uint32), a1.view(np.uint32))
     for sc, sm, *_ in hs:
         G.gm_samples_free(sm)
         G.gm_scene_free(sc)
