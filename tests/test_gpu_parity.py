@@ -267,6 +267,29 @@ def test_edge_cases(G, ctx, pipe):
         G.gm_build_scene(ctx, pipe.mesh_args(bad))
 
 
+@pytest.mark.parametrize("radius", [4, 8, 16, 32, 64])
+def test_clustering_radius_leaves_maps_unchanged(G, ctx, pipe, radius):
+    """Any tree gives the same maps (boxes are conservative, sums run in fixation order); radii
+    outside the supported set are rejected."""
+    w = synth.tiny_sphere()
+    ref = pipe.run(ctx, w, normalize=False)
+    va = pipe.map_array(ref)[0]
+    ref.free()
+    sc = G.gm_build_scene(ctx, pipe.mesh_args(w), ploc_radius=radius)
+    sm = G.gm_sample_surface(sc, [m.density for m in w.meshes], w.seed, w.session)
+    eye, gaze, dur, ts = pipe.fixation_args(w.fixations)
+    m = G.gm_accumulate_fixations(sc, sm, eye, gaze, dur, ts, pipe.params_of(w, normalize=False))
+    vb = np.empty(G.gm_samples_info(sm), np.float32)
+    G.gm_map_copy(m, 0, vb)
+    G.gm_map_free(m)
+    G.gm_samples_free(sm)
+    G.gm_scene_free(sc)
+    assert np.array_equal(va.view(np.uint32), vb.view(np.uint32))
+    if radius == 64:
+        with pytest.raises(G.GazeMapError, match="ploc_radius"):
+            G.gm_build_scene(ctx, pipe.mesh_args(w), ploc_radius=12)
+
+
 def test_paper_scene_full_size_sampled(G, ctx, pipe):
     """The paper-shaped scene at full size (800k tris, ~2M samples, 6000 fixations), in the
     launch configuration the benchmark times; the oracle recomputes a seeded selection of

@@ -162,3 +162,22 @@ def test_cone_behind_the_camera_is_skipped(env):
     vals, pairs, stats, zs = _gpu_zb_map(G, pipe, ctx, w, fwd, up, G.zbuffer_params(64, 0.05, 100.0, 0.005))
     assert zs["skipped_fixations"] == 1
     assert not np.any(pairs["fix"] == 3)
+
+
+def test_invalid_zbuffer_parameters_are_rejected(env):
+    G, pipe, ctx = env
+    w, fwd, up = _workload(n_fix=4)
+    sc = G.gm_build_scene(ctx, pipe.mesh_args(w))
+    sm = G.gm_sample_surface(sc, [m.density for m in w.meshes], w.seed, w.session)
+    eye, gaze, dur, ts = pipe.fixation_args(w.fixations)
+    prm = pipe.params_of(w)
+    for zbp in (G.zbuffer_params(0), G.zbuffer_params(64, near=0.0), G.zbuffer_params(64, near=1.0, far=0.5),
+                G.zbuffer_params(64, eps=-1.0), G.zbuffer_params(64, far=float("inf"))):
+        with pytest.raises(G.GazeMapError):
+            G.gm_accumulate_zbuffer(sc, sm, eye, gaze, dur, ts, prm, zbp, fwd, up)
+    h = G.gm_accumulate_fixations(sc, sm, eye, gaze, dur, ts, prm)
+    with pytest.raises(G.GazeMapError, match="gm_accumulate_zbuffer"):
+        G.gm_zbuffer_stats(h)          # a ray-form map has no z-buffer statistics
+    G.gm_map_free(h)
+    G.gm_samples_free(sm)
+    G.gm_scene_free(sc)
