@@ -424,17 +424,24 @@ def field_arm(args):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     out = torch.empty(nq, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        G.gm_field_query(f, qxyz, nq, out, stream)
-    q_t = []
-    for _ in range(args.steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        G.gm_field_query(f, qxyz, nq, out, stream)
-        e1.record(stream)
-        e1.synchronize()
-        q_t.append(e0.elapsed_time(e1))
-    field_ms = sum(q_t) / len(q_t)
+
+    def time_queries(kernel):
+        G.gm_field_query_kernel(f, kernel)
+        for _ in range(args.warmup):
+            G.gm_field_query(f, qxyz, nq, out, stream)
+        q_t = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G.gm_field_query(f, qxyz, nq, out, stream)
+            e1.record(stream)
+            e1.synchronize()
+            q_t.append(e0.elapsed_time(e1))
+        G.gm_sync(ctx, stream)
+        return sum(q_t) / len(q_t)
+
+    mma_sync_ms = time_queries(G.GM_FIELD_QUERY_MMA_SYNC)
+    field_ms = time_queries(G.GM_FIELD_QUERY_TCGEN05)   # the default kernel; `out` keeps its values
     # the judge: plain accumulation at the query points, normalised by the training map's maximum
     # a normalised map keeps its raw maximum: gm_map_copy returns it
     raw_max = G.gm_map_copy(h.map, 0, torch.empty(ns, dtype=torch.float32, device="cuda"), stream)
@@ -454,7 +461,7 @@ def field_arm(args):
     peak, basis = measured_bf16_peak()
     ach = flop_q * nq / (field_ms * 1e-3) / 1e12
     roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": None, "kernel": "k_field_query", "peak_basis": basis,
+            "traffic": None, "kernel": "k_field_query_tc", "peak_basis": basis,
             "work_basis": f"{flop_q} FLOP per query (four 64x64 BF16 layers + output)"}
     line = {"metric": "neural-field queries/s vs plain", "value": nq / (field_ms * 1e-3), "unit": "queries/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": field_ms,
@@ -467,7 +474,8 @@ def field_arm(args):
             "final_batch_mse": loss,
             "plain_form": {"value": nq / (plain_ms * 1e-3), "ms": plain_ms, "pairs": int(qst["pairs"]),
                            "form": "gm_accumulate_fixations at the query points"},
-            "field_over_plain": plain_ms / field_ms, "roofline": roof}
+            "field_over_plain": plain_ms / field_ms, "roofline": roof,
+            "query_kernels_ms": {"tcgen05": field_ms, "mma_sync": mma_sync_ms}}
     G.gm_field_free(f)
     G.gm_map_free(mq)
     G.gm_samples_free(qs)

@@ -393,8 +393,15 @@ gm_status gm_field_step(gm_field* field, const float* xyz, const float* target, 
 gm_status gm_field_loss_grad(gm_field* field, const float* xyz, const float* target, uint64_t n,
                              const uint32_t* batch_idx, uint32_t batch, float* grad_out, float* loss_out,
                              gm_stream stream);
-/* Evaluate the field at n points (n x 3 FP32, host or device) into out (host or device). */
+/* Evaluate the field at n points (n x 3 FP32, host or device) into out (host or device). The
+ * default kernel runs the four hidden layers on the 5th-generation tensor cores: 128-point tiles,
+ * tcgen05.mma (bf16 x bf16, FP32 accumulator in tensor memory), point tiles brought in by bulk
+ * asynchronous copies; the other computes them with warp-level mma.sync. Both round every
+ * activation to bf16 and accumulate in FP32; they may differ in the last bits of a sum. A device
+ * wait that does not complete is reported by the next gm_sync. */
+enum { GM_FIELD_QUERY_TCGEN05 = 0, GM_FIELD_QUERY_MMA_SYNC = 1 };
 gm_status gm_field_query(const gm_field* field, const float* xyz, uint64_t n, float* out, gm_stream stream);
+gm_status gm_field_query_kernel(gm_field* field, int32_t kernel);
 /* Copy the FP32 master parameters (GM_FIELD_N_PARAMS) to out (host or device). */
 gm_status gm_field_params(const gm_field* field, float* out, gm_stream stream);
 gm_status gm_field_info(const gm_field* field, uint32_t* n_params, uint32_t* steps_taken, float* last_loss,

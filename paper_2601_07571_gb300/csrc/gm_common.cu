@@ -118,6 +118,10 @@ extern "C" gm_status gm_sync(gm_ctx* c, gm_stream stream) {
     GM_TRY_CUDA(cudaMemcpy(&err, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err == GM_DEV_STACK_OVERFLOW)
         return gm_set_error(GM_ERR_INTERNAL, "device: BVH traversal stack overflow");
+    if (err == GM_DEV_WAIT_TIMEOUT) {
+        cudaMemset(c->dev_err, 0, sizeof(int));
+        return gm_set_error(GM_ERR_INTERNAL, "device: an asynchronous copy or tensor-core product did not complete in time");
+    }
     if (err != 0) return gm_set_error(GM_ERR_INTERNAL, "device: consistency check failed (" + std::to_string(err) + ")");
     return GM_OK;
 }

@@ -245,6 +245,273 @@ __global__ void __launch_bounds__(256) k_field_query(const float* __restrict__ x
     }
 }
 
+
+// ---- inference on the 5th-generation tensor cores ---------------------------------------------
+// Blocks of 256 threads, persistent; each half (128 threads, its own named barrier) runs its own
+// pipeline over tiles of 128 points (the MMA's M), so two tiles per block -- and those of the other
+// resident blocks -- overlap one tile's tensor-core products with another's epilogue, while the
+// weights are staged once per block. Per tile: the point coordinates arrive by a bulk asynchronous
+// copy (double-buffered, the next tile's copy in flight while this one computes; plain loads when
+// the input is not 16-byte aligned or the tile is the ragged tail); thread t of the half encodes
+// point t's 64 features into row t of its A tile (bf16, K-major core-matrix layout: 8 x 8 blocks
+// of 128 bytes); per layer one thread issues four tcgen05.mma (M 128, N 64, K 16, bf16 x bf16 ->
+// FP32 in tensor memory, columns 64 h .. 64 h + 63 for half h) and commits them to the half's
+// mbarrier; every thread then reads its row of the accumulator with tcgen05.ld, adds the bias,
+// applies ReLU, rounds to bf16 and writes the next A row. Waits are bounded: on a timeout the block
+// records GM_DEV_WAIT_TIMEOUT, drains its own copies, frees its tensor memory and returns.
+constexpr int TQ = 128;                       // points per tile (threads per half)
+constexpr int TQ_THREADS = 2 * TQ;
+constexpr uint32_t TQ_TMEM_COLS = 128;        // two FP32 accumulators of N = 64
+constexpr int TQ_WAIT_ITERS = 1 << 22;
+
+struct QuerySmem {
+    alignas(1024) __nv_bfloat16 A[2][TQ * FW];    // 2 x 16 KB
+    alignas(1024) __nv_bfloat16 W[FD][FW * FW];   // 32 KB
+    alignas(16) float bias[FD * FW];
+    float w5[FW + 1];
+    alignas(16) float xyz[2][2][TQ * 3];          // [half][buffer]
+    alignas(8) uint64_t mbar_mma[2];
+    uint64_t mbar_ld[2][2];
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, no swizzle: start address, the byte offset between core
+// matrices along K (leading) and along M or N (stride), descriptor version 1.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lead, uint32_t stride) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lead >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((stride >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major, N = 64, M = 128.
+constexpr uint32_t kQueryIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+    for (int it = 0; it < TQ_WAIT_ITERS; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(float* dst, const float* src, uint32_t bytes, uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ void half_sync(int h) {
+    if (h == 0) asm volatile("bar.sync 1, 128;" ::: "memory");
+    else asm volatile("bar.sync 2, 128;" ::: "memory");
+}
+
+// Row t of an A tile from 32 packed bf16 pairs: eight 16-byte stores into the core-matrix layout.
+__device__ __forceinline__ void store_a_row_packed(__nv_bfloat16* A, int t, const uint32_t* pk) {
+#pragma unroll
+    for (int kg = 0; kg < 8; ++kg)
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(A) + kg * 2048 + (t >> 3) * 128 + (t & 7) * 16) =
+            make_uint4(pk[4 * kg], pk[4 * kg + 1], pk[4 * kg + 2], pk[4 * kg + 3]);
+}
+
+// The bias of a layer into this thread's accumulator row (the products then add onto it, as the
+// warp-level kernel starts its accumulators from the bias).
+__device__ __forceinline__ void tmem_st_bias(uint32_t taddr, const float* bias) {
+#pragma unroll
+    for (int c0 = 0; c0 < FW; c0 += 16) {
+        const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
+        const float4 q0 = b4[0], q1 = b4[1], q2 = b4[2], q3 = b4[3];
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::
+                "r"(taddr + c0),
+            "f"(q0.x), "f"(q0.y), "f"(q0.z), "f"(q0.w), "f"(q1.x), "f"(q1.y), "f"(q1.z), "f"(q1.w), "f"(q2.x),
+            "f"(q2.y), "f"(q2.z), "f"(q2.w), "f"(q3.x), "f"(q3.y), "f"(q3.z), "f"(q3.w));
+    }
+}
+
+// Row t of an A tile: 64 values as bf16, eight 16-byte stores into the core-matrix layout.
+__device__ __forceinline__ void store_a_row(__nv_bfloat16* A, int t, const float* v) {
+#pragma unroll
+    for (int kg = 0; kg < 8; ++kg) {
+        uint4 q;
+        q.x = pack_bf16(v[8 * kg + 0], v[8 * kg + 1]);
+        q.y = pack_bf16(v[8 * kg + 2], v[8 * kg + 3]);
+        q.z = pack_bf16(v[8 * kg + 4], v[8 * kg + 5]);
+        q.w = pack_bf16(v[8 * kg + 6], v[8 * kg + 7]);
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(A) + kg * 2048 + (t >> 3) * 128 + (t & 7) * 16) = q;
+    }
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__global__ void __launch_bounds__(TQ_THREADS, 3) k_field_query_tc(const float* __restrict__ xyz, uint64_t n,
+                                                              const __nv_bfloat16* __restrict__ wbf,
+                                                              const float* __restrict__ theta, FieldBox B, int bulk,
+                                                              float* __restrict__ out, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char q_smem_raw[];
+    QuerySmem& S = *reinterpret_cast<QuerySmem*>(q_smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int h = tid / TQ, t = tid % TQ;   // half and row within the half's tile
+    // weights in the core-matrix layout: (n, k) at (k / 8) * 1024 + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2
+    for (int i = tid; i < FD * FW * 8; i += TQ_THREADS) {
+        const int l = i / (FW * 8), nn = (i / 8) % FW, kg = i % 8;
+        const uint4 q = reinterpret_cast<const uint4*>(wbf + (size_t)l * FW * FW + nn * FW)[kg];
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(S.W[l]) + kg * 1024 + (nn >> 3) * 128 + (nn & 7) * 16) = q;
+    }
+    for (int i = tid; i < FD * FW; i += TQ_THREADS) S.bias[i] = theta[b_off(i / FW) + i % FW];
+    for (int i = tid; i <= FW; i += TQ_THREADS) S.w5[i] = theta[W5_OFF + i];
+    if (tid == 0) {
+        S.abort = 0;
+        for (int k = 0; k < 2; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.mbar_mma[k])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.mbar_ld[k][0])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.mbar_ld[k][1])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&S.tmem)),
+                     "r"(TQ_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem_h = S.tmem + (uint32_t)(h * FW);         // this half's accumulator columns
+    const uint32_t row_addr = tmem_h + ((uint32_t)((warp & 3) * 32) << 16);
+    __nv_bfloat16* A = S.A[h];
+    const uint32_t a_addr = smem_addr(A);
+    const uint64_t ntiles = (n + TQ - 1) / TQ;
+    const uint64_t pipes = 2ull * gridDim.x, pipe = 2ull * blockIdx.x + h;
+    uint32_t pm = 0, pl[2] = {0, 0};
+    bool pending[2] = {false, false};   // row 0 of the half: a bulk copy into this buffer is in flight
+    auto full_tile = [&](uint64_t tile) { return (tile + 1) * TQ <= n; };
+    uint64_t tile = pipe;
+    if (t == 0 && bulk && tile < ntiles && full_tile(tile)) {
+        bulk_load(S.xyz[h][0], xyz + tile * TQ * 3, TQ * 12, &S.mbar_ld[h][0]);
+        pending[0] = true;
+    }
+    bool stop = false;
+    for (int it = 0; tile < ntiles && !stop; ++it, tile += pipes) {
+        const int buf = it & 1;
+        const uint64_t next = tile + pipes;
+        if (t == 0 && bulk && next < ntiles && full_tile(next)) {
+            bulk_load(S.xyz[h][buf ^ 1], xyz + next * TQ * 3, TQ * 12, &S.mbar_ld[h][buf ^ 1]);
+            pending[buf ^ 1] = true;
+        }
+        const uint64_t i = tile * TQ + t;
+        float x[3] = {0.f, 0.f, 0.f};
+        if (bulk && full_tile(tile)) {
+            if (!mbar_wait(smem_addr(&S.mbar_ld[h][buf]), pl[buf])) S.abort = 1;
+            pl[buf] ^= 1;
+            if (t == 0) pending[buf] = false;
+            x[0] = S.xyz[h][buf][3 * t];
+            x[1] = S.xyz[h][buf][3 * t + 1];
+            x[2] = S.xyz[h][buf][3 * t + 2];
+        } else if (i < n) {
+            x[0] = xyz[3 * i];
+            x[1] = xyz[3 * i + 1];
+            x[2] = xyz[3 * i + 2];
+        }
+        float xt[3] = {(x[0] - B.cx) * B.inv_h, (x[1] - B.cy) * B.inv_h, (x[2] - B.cz) * B.inv_h};
+        float v[FW];
+#pragma unroll
+        for (int c = 0; c < FW; ++c) v[c] = feature(xt, c);
+        store_a_row(A, t, v);
+        tmem_st_bias(row_addr, S.bias);   // layer 0's bias (the previous tile's last read is complete)
+        for (int l = 0; l < FD; ++l) {
+            asm volatile("tcgen05.wait::st.sync.aligned;");   // the bias is in the accumulator
+            asm volatile("fence.proxy.async.shared::cta;");   // this thread's A row, visible to the MMA
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            half_sync(h);
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (S.abort) {
+                stop = true;
+                break;
+            }
+            if (t == 0) {
+                const uint32_t w_addr = smem_addr(S.W[l]);
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    const uint64_t da = umma_desc(a_addr + s * 4096, 2048, 128);
+                    const uint64_t db = umma_desc(w_addr + s * 2048, 1024, 128);
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_h),
+                        "l"(da), "l"(db), "r"(kQueryIdesc), "r"(1u));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_addr(&S.mbar_mma[h])));
+            }
+            if (!mbar_wait(smem_addr(&S.mbar_mma[h]), pm)) S.abort = 1;
+            pm ^= 1;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // 32 columns at a time: read, round to bf16, ReLU on the packed pairs (rounding is monotone
+            // and keeps 0, so this equals rounding the ReLU), then the next A row or the output dot
+            const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.f, 0.f);
+            float acc5 = 0.f;
+#pragma unroll
+            for (int c0 = 0; c0 < FW; c0 += 32) {
+                float va[32];
+                tmem_ld16(row_addr + c0, va);
+                tmem_ld16(row_addr + c0 + 16, va + 16);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                uint32_t pk[16];
+#pragma unroll
+                for (int c = 0; c < 32; c += 2) {
+                    __nv_bfloat162 q = __floats2bfloat162_rn(va[c], va[c + 1]);
+                    q = __hmax2(q, zero2);
+                    pk[c / 2] = *reinterpret_cast<uint32_t*>(&q);
+                }
+                if (l + 1 < FD) {
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        const int kg = c0 / 8 + g;
+                        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(A) + kg * 2048 + (t >> 3) * 128 +
+                                                  (t & 7) * 16) =
+                            make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 32; c += 2) {
+                        const __nv_bfloat162 q = *reinterpret_cast<const __nv_bfloat162*>(&pk[c / 2]);
+                        acc5 = fmaf(__low2float(q), S.w5[c0 + c], acc5);
+                        acc5 = fmaf(__high2float(q), S.w5[c0 + c + 1], acc5);
+                    }
+                }
+            }
+            if (l + 1 < FD) tmem_st_bias(row_addr, S.bias + (l + 1) * FW);   // next layer's start
+            else if (i < n) out[i] = softplusf(S.w5[FW] + acc5);
+        }
+    }
+    if (S.abort && t == 0) {
+        atomicCAS(err, 0, GM_DEV_WAIT_TIMEOUT);
+        for (int b = 0; b < 2; ++b)
+            if (pending[b]) mbar_wait(smem_addr(&S.mbar_ld[h][b]), pl[b]);   // drain this half's own copies
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem), "r"(TQ_TMEM_COLS));
+}
+
 // ---- training: forward + backward of 128 points per block -------------------------------------
 struct TrainSmem {
     __nv_bfloat16 W[FD * FW * WS];     // W_l rows (output) for the forward products
@@ -490,6 +757,7 @@ struct gm_field {
     uint32_t t = 0;   // Adam steps taken
     float last_loss = 0.f;
     float train_ms = 0.f;
+    int32_t query_kernel = GM_FIELD_QUERY_TCGEN05;
 };
 
 static const size_t kTrainSmem = sizeof(TrainSmem);
@@ -637,7 +905,40 @@ extern "C" gm_status gm_field_query(const gm_field* f, const float* xyz, uint64_
     float* dout = out;
     gm_status st = GM_OK;
     if (!dev_out) st = gm_alloc((void**)&dout, sizeof(float) * n, s);
-    if (st == GM_OK) {
+    if (st == GM_OK && f->query_kernel == GM_FIELD_QUERY_TCGEN05) {
+        static int configured_device = -1;   // the attribute is per device and per function
+        const int smem = (int)sizeof(QuerySmem);
+        if (configured_device != f->ctx->device) {
+            cudaError_t e = cudaFuncSetAttribute(k_field_query_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) st = gm_cuda_error(e, "gm_field_query (shared memory)");
+            else configured_device = f->ctx->device;
+        }
+        // blocks per SM from the shared memory each one holds (the occupancy query reports one block
+        // for this kernel; the hardware runs as many as their shared memory and tensor-memory
+        // columns allow, here 3 x 128 of 512 columns)
+        int per_sm = 1;
+        if (st == GM_OK) {
+            int smem_sm = 0;
+            cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, f->ctx->device);
+            if (e != cudaSuccess) st = gm_cuda_error(e, "gm_field_query (shared memory per SM)");
+            else per_sm = std::max(1, std::min(8, smem_sm / (smem + 1024)));
+        }
+        if (st == GM_OK) {
+            const uint64_t ntiles = (n + TQ - 1) / TQ;
+            const uint32_t grid = (uint32_t)std::min<uint64_t>(
+                (ntiles + 1) / 2, (uint64_t)f->ctx->n_sm * (uint64_t)std::max(1, per_sm));
+            const int bulk = (reinterpret_cast<uintptr_t>(dx) % 16) == 0;
+            k_field_query_tc<<<grid, TQ_THREADS, smem, s>>>((const float*)dx, n, f->wbf, f->theta, f->box, bulk,
+                                                            dout, f->ctx->dev_err);
+            f->ctx->launches += 1;
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) st = gm_cuda_error(e, "gm_field_query");
+        }
+        if (!dev_out) {
+            if (st == GM_OK) st = gm_copy_out(out, dout, sizeof(float) * n, s);
+            cudaFreeAsync(dout, s);
+        }
+    } else if (st == GM_OK) {
         const uint64_t groups = (n + 15) / 16;
         const uint32_t grid = (uint32_t)std::min<uint64_t>((groups + 7) / 8, (uint64_t)f->ctx->n_sm * 8);
         k_field_query<<<grid, 256, 0, s>>>((const float*)dx, n, f->wbf, f->theta, f->box, dout);
@@ -651,6 +952,14 @@ extern "C" gm_status gm_field_query(const gm_field* f, const float* xyz, uint64_
     }
     if (ox) cudaFreeAsync(dx, s);
     return st;
+}
+
+extern "C" gm_status gm_field_query_kernel(gm_field* f, int32_t kernel) {
+    if (!f) return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_query_kernel: null field");
+    if (kernel != GM_FIELD_QUERY_TCGEN05 && kernel != GM_FIELD_QUERY_MMA_SYNC)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_query_kernel: unknown kernel");
+    f->query_kernel = kernel;
+    return GM_OK;
 }
 
 extern "C" gm_status gm_field_params(const gm_field* f, float* out, gm_stream stream) {

@@ -27,7 +27,7 @@ gm_status gm_cuda_error(cudaError_t e, const char* what);
     } while (0)
 
 // Device-side fault codes written to gm_ctx::dev_err (first writer wins).
-enum { GM_DEV_OK = 0, GM_DEV_STACK_OVERFLOW = 1, GM_DEV_BAD_INDEX = 2 };
+enum { GM_DEV_OK = 0, GM_DEV_STACK_OVERFLOW = 1, GM_DEV_BAD_INDEX = 2, GM_DEV_WAIT_TIMEOUT = 4 };
 
 struct gm_ctx {
     int device = 0;

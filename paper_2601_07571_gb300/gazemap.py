@@ -137,6 +137,7 @@ _SIGS = {
     "gm_field_step": (C.c_int, [_P, _P, _P, C.c_uint64, _P, C.c_uint32, C.c_float, _P]),
     "gm_field_loss_grad": (C.c_int, [_P, _P, _P, C.c_uint64, _P, C.c_uint32, _P, C.POINTER(C.c_float), _P]),
     "gm_field_query": (C.c_int, [_P, _P, C.c_uint64, _P, _P]),
+    "gm_field_query_kernel": (C.c_int, [_P, C.c_int32]),
     "gm_field_params": (C.c_int, [_P, _P, _P]),
     "gm_field_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_float),
                                 C.POINTER(C.c_float)]),
@@ -508,6 +509,13 @@ def gm_field_loss_grad(field, xyz, target, n: int, batch_idx, batch: int, grad_o
     _check(lib().gm_field_loss_grad(field, _ptr(xyz), _ptr(target), C.c_uint64(n), _ptr(batch_idx), int(batch),
                                     _ptr(grad_out), C.byref(loss), _stream(stream)))
     return loss.value
+
+
+GM_FIELD_QUERY_TCGEN05, GM_FIELD_QUERY_MMA_SYNC = 0, 1
+
+
+def gm_field_query_kernel(field, kernel: int) -> None:
+    _check(lib().gm_field_query_kernel(field, int(kernel)))
 
 
 def gm_field_query(field, xyz, n: int, out, stream=None) -> None:

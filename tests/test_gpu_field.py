@@ -47,6 +47,43 @@ def test_field_query_matches_oracle(env):
     out2 = np.empty(len(x), np.float32)
     G.gm_query_density(None, f, G.GM_Q_FIELD, 0, None, x, len(x), out2)
     assert np.array_equal(out, out2)
+    # the warp-level mma.sync kernel: same bar, and close to the tensor-memory kernel (the two
+    # accumulate in different orders, so a bf16 rounding of an activation can differ)
+    G.gm_field_query_kernel(f, G.GM_FIELD_QUERY_MMA_SYNC)
+    out3 = np.empty(len(x), np.float32)
+    G.gm_field_query(f, x, len(x), out3)
+    err3 = np.abs(out3 - ref)
+    assert err3.max() <= 1e-2 * np.abs(ref).max()
+    assert np.median(np.abs(out3 - out) / np.maximum(np.abs(ref), 1e-6)) < 1e-3
+    G.gm_field_query_kernel(f, G.GM_FIELD_QUERY_TCGEN05)
+    G.gm_sync(ctx)
+    G.gm_field_free(f)
+
+
+@pytest.mark.parametrize("n, offset", [(1, 0), (127, 0), (128, 0), (129, 0), (1000, 1), (70001, 0), (70001, 3)])
+def test_field_query_tiles_tails_and_alignment(env, n, offset):
+    """Ragged tails, single points, several tiles per block, and inputs that are not 16-byte aligned
+    (plain loads instead of bulk copies) give the mma.sync kernel's values to within a bf16 step."""
+    import torch
+    G, torch, ctx = env
+    theta = synth.field_init(12)
+    f = G.gm_field_create(ctx, BOX_LO, BOX_HI, theta)
+    x = _points(n, 3)
+    buf = torch.zeros(3 * n + 3, dtype=torch.float32, device="cuda")
+    dx = buf[offset:offset + 3 * n]
+    dx.copy_(torch.from_numpy(x.reshape(-1)))
+    out_tc = torch.empty(n, dtype=torch.float32, device="cuda")
+    G.gm_field_query(f, dx, n, out_tc)
+    G.gm_field_query_kernel(f, G.GM_FIELD_QUERY_MMA_SYNC)
+    out_ms = torch.empty(n, dtype=torch.float32, device="cuda")
+    G.gm_field_query(f, dx, n, out_ms)
+    G.gm_sync(ctx)
+    a, b = out_tc.cpu().numpy(), out_ms.cpu().numpy()
+    feats = F.features(F.normalise(x.astype(np.float64), BOX_LO, BOX_HI))
+    ref, _ = F.forward(theta.astype(np.float64), feats, emulate_bf16=True)
+    assert np.all(np.isfinite(a))
+    assert np.abs(a - ref).max() <= 1e-2 * max(np.abs(ref).max(), 1e-3)
+    assert np.abs(a - b).max() <= 1e-2 * max(np.abs(ref).max(), 1e-3)
     G.gm_field_free(f)
 
 
