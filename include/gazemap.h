@@ -91,7 +91,8 @@ enum {
     GM_F_WIDE_BVH = 16,     /* traverse the 4-wide collapse of the tree instead of the binary tree */
     GM_F_REGCAP64 = 32,     /* cap the accumulation kernel at 64 registers (4 blocks per SM) */
     GM_F_TILE_CONSECUTIVE = 64, /* warp tiles of 128 consecutive samples (else four 32-sample runs over 1024) */
-    GM_F_STATIC_TILES = 128 /* one warp tile per warp of a full grid (else warps pull tiles from a counter) */
+    GM_F_STATIC_TILES = 128, /* one warp tile per warp of a full grid (else warps pull tiles from a counter) */
+    GM_F_NO_TILE_CULL = 256  /* test every sample against every fixation (no warp-tile sphere test) */
 };
 
 typedef struct {

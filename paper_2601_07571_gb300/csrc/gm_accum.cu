@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(NT, MINB) k_accumulate(
     constexpr int QN = COMPACT ? NT * SPT : 1;
     __shared__ float4 wsmp[QN];     // per warp: its WARP_TILE samples (x, y, z, own triangle)
     __shared__ float2 wacc[QN];     // per warp: (sum, compensation) of each sample
+    __shared__ float4 wbox[NT / 32];   // per warp: its tile's bounding sphere
     __shared__ uint16_t qslot[QN];  // per warp: queue of in-cone sample slots
     __shared__ float qg[QN];        // per warp: their weights
     const int warp = threadIdx.x >> 5;
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(NT, MINB) k_accumulate(
         }
         if (tile >= n_tiles) break;
         warp_tile<DEBUG, COMPACT, WIDE>(tile, spos, sidx, fix, nf, nodes, tris, P, out, max_bits, wsmp + wb, wacc + wb,
-                                        qslot + wb, qg + wb, &counters[2], dbg, err, st);
+                                        qslot + wb, qg + wb, wbox + warp, &counters[2], dbg, err, st);
     }
     warp_stats_commit(st, counters);
 }
@@ -349,6 +350,8 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
             sidx = ident;
         }
         P.group = (prm->flags & GM_F_TILE_CONSECUTIVE) ? 1u : 8u;
+        P.tile_cull = (prm->flags & GM_F_NO_TILE_CULL) ? 0u : 1u;
+        P.tanphi = (float)(std::sqrt((double)P.K) * 1.00001);
         const uint32_t n_tiles = gm_div_up(ns, (uint64_t)WARP_TILE * P.group) * P.group;
         const int persistent = (prm->flags & GM_F_STATIC_TILES) ? 0 : 1;
         const bool compact = !(prm->flags & GM_F_NO_COMPACT);

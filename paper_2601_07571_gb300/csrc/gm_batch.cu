@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate_batch(const Se
     constexpr int QN = COMPACT ? ACC_THREADS * SPT : 1;
     __shared__ float4 wsmp[QN];
     __shared__ float2 wacc[QN];
+    __shared__ float4 wbox[ACC_THREADS / 32];
     __shared__ uint16_t qslot[QN];
     __shared__ float qg[QN];
     const int lane = threadIdx.x & 31;
@@ -124,9 +125,10 @@ __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate_batch(const Se
         P.nt = S.nt;
         P.dbg_cap = 0;
         P.group = BATCH_GROUP;
+        P.tanphi = sqrtf(C.K) * 1.00001f;
         TileStats st;
         warp_tile<false, COMPACT, WIDE>(wi.y, S.spos, S.sidx, S.fix, *S.n_fix, S.nodes, S.tris, P, S.out, S.max_bits,
-                                        wsmp + wb, wacc + wb, qslot + wb, qg + wb, nullptr,
+                                        wsmp + wb, wacc + wb, qslot + wb, qg + wb, wbox + (threadIdx.x >> 5), nullptr,
                                         dbg, err, st);
         warp_stats_commit(st, S.counters);
     }

@@ -26,6 +26,8 @@ struct AccParams {
     // base = (t / G) * WARP_TILE * G + (t % G) * 32, stride = 32 * G. G = 1: 128 consecutive
     // work-order samples; G = 8: four runs of 32, spread over 1024 samples shared by 8 tiles.
     uint32_t group = 1;
+    uint32_t tile_cull = 1;   // skip fixations whose cone misses the warp tile's bounding sphere
+    float tanphi = 0.f;       // cutoff tan theta, slightly enlarged (the sphere test's cone)
 };
 
 struct DebugOut {
@@ -297,7 +299,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                                           uint32_t nf, const float4* __restrict__ nodes,
                                           const float4* __restrict__ tris, const AccParams& P,
                                           float* __restrict__ out, unsigned int* __restrict__ max_bits,
-                                          float4* wsmp, float2* wacc, uint16_t* qslot, float* qg,
+                                          float4* wsmp, float2* wacc, uint16_t* qslot, float* qg, float4* wbox,
                                           unsigned long long* __restrict__ dbg_cursor, const DebugOut& dbg,
                                           int* __restrict__ err, TileStats& st) {
     const int lane = threadIdx.x & 31;
@@ -307,12 +309,21 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
     const uint32_t base = base0 + lane;
     float sx[SPT], sy[SPT], sz[SPT], sum[SPT], cmp[SPT];
     uint32_t own[SPT];
+    float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
 #pragma unroll
     for (int k = 0; k < SPT; ++k) {
         const uint32_t j = base + k * stride;
         // padding lanes hold NaN positions: every cone test on them is false
         const float4 p = j < P.ns ? spos[j]
                                   : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, __uint_as_float(0xffffffffu));
+        if (j < P.ns) {
+            blo[0] = fminf(blo[0], p.x);
+            blo[1] = fminf(blo[1], p.y);
+            blo[2] = fminf(blo[2], p.z);
+            bhi[0] = fmaxf(bhi[0], p.x);
+            bhi[1] = fmaxf(bhi[1], p.y);
+            bhi[2] = fmaxf(bhi[2], p.z);
+        }
         sum[k] = 0.f;
         cmp[k] = 0.f;
         if (COMPACT) {
@@ -325,6 +336,25 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
             own[k] = __float_as_uint(p.w);
         }
     }
+    __syncwarp();
+    // the tile's bounding sphere (centre of its box, half the box diagonal): a fixation whose cone
+    // cannot reach the sphere is skipped without per-sample tests, which leaves every in-cone pair
+    // and every sum as it is
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        for (int o = 16; o > 0; o >>= 1) {
+            blo[c] = fminf(blo[c], __shfl_xor_sync(0xffffffffu, blo[c], o));
+            bhi[c] = fmaxf(bhi[c], __shfl_xor_sync(0xffffffffu, bhi[c], o));
+        }
+    }
+    // the sphere stays in the warp's shared-memory slot (registers are the traversal's)
+    const bool tile_box = P.tile_cull && blo[0] <= bhi[0];
+    if (lane == 0)
+        *wbox = make_float4(0.5f * (blo[0] + bhi[0]), 0.5f * (blo[1] + bhi[1]), 0.5f * (blo[2] + bhi[2]),
+                            tile_box ? 0.5f * sqrtf((bhi[0] - blo[0]) * (bhi[0] - blo[0]) +
+                                                    (bhi[1] - blo[1]) * (bhi[1] - blo[1]) +
+                                                    (bhi[2] - blo[2]) * (bhi[2] - blo[2])) * 1.0001f
+                                     : -1.f);
     __syncwarp();
     uint32_t cur = 0xffffffffu;
 
@@ -360,6 +390,22 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
         if (win != cur) {
             if (cur != 0xffffffffu) flush(cur);
             cur = win;
+        }
+        const float4 bs = *wbox;
+        if (bs.w >= 0.f) {
+            // a point p = q + u with |u| <= R has d1 <= d1c + R and |p x r^| >= |q x r^| - R; it is
+            // in the cone only if |p x r^| <= tan(phi) d1. Compared squared (both sides are
+            // non-negative); the margin, from the L1 norm of q, covers FP32 rounding on both sides.
+            const float bR = bs.w;
+            const float qx = bs.x - F0.x, qy = bs.y - F0.y, qz = bs.z - F0.z;
+            const float d1c = fmaf(qx, F1.x, fmaf(qy, F1.y, qz * F1.z));
+            const float ux = fmaf(qy, F1.z, -qz * F1.y);
+            const float uy = fmaf(qz, F1.x, -qx * F1.z);
+            const float uz = fmaf(qx, F1.y, -qy * F1.x);
+            const float margin = 1e-4f * (fabsf(qx) + fabsf(qy) + fabsf(qz) + bR);
+            const float reach = d1c + bR;
+            const float lim = bR + fmaf(P.tanphi, fmaxf(reach, 0.f), margin);
+            if (reach <= -margin || fmaf(ux, ux, fmaf(uy, uy, uz * uz)) > lim * lim) continue;
         }
         if (COMPACT) {
             int tot = 0;
