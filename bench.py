@@ -41,7 +41,7 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # The figure stands only while the sources that shape the kernel and its inputs are the ones it
 # was taken on: their SHA-256 is stored beside it and `traffic` is null on any mismatch.
 ACC_TRAFFIC = {"workload": "paper_scene_800ktri_2Msample_6000fix", "bytes": 262.98e6,
-               "sources_sha256": "e333ad4496879aa63bf49cdc3b9caddff6c0ad8005a9d730fdf071b7f17683a4"}
+               "sources_sha256": "124fe0f009697d4cb53a9b638e7bc0871780a28b68ccde7eb87f0edb2d8696f1"}
 ACC_TRAFFIC_SOURCES = ("paper_2601_07571_gb300/csrc/gm_trace.cuh", "paper_2601_07571_gb300/csrc/gm_accum.cu",
                        "paper_2601_07571_gb300/csrc/gm_scene.cu", "paper_2601_07571_gb300/csrc/gm_sampler.cu")
 

@@ -1,20 +1,28 @@
-// gm_scene.cu -- gm_build_scene: meshes -> world triangles -> linear BVH.
+// gm_scene.cu -- gm_build_scene: meshes -> world triangles -> BVH; gm_scene_pose: re-posed meshes.
 //
 // The paper tests occlusion with a z-buffer rendered per point of view (Section 3.2.2); here
-// occlusion is an exact segment test against every triangle, accelerated by a binary BVH
-// built on the GPU in five data-parallel steps (Karras, "Maximizing parallelism in the
-// construction of BVHs, octrees, and k-d trees", HPG 2012):
+// occlusion is an exact segment test against every triangle, accelerated by a binary BVH built
+// on the GPU in data-parallel steps:
 //   1. world vertices: FP64 transform per vertex, rounded to FP32 (same operation order as
 //      the FP64 reference: ((m0 x + m1 y) + m2 z) + m3, no fused multiply-add);
 //   2. 63-bit Morton code of each triangle centroid in the centroid bounds;
 //   3. stable radix sort of the codes (leaf order);
-//   4. one thread per internal node finds its key range and split (longest common prefix,
-//      ties between equal codes broken by leaf index);
-//   5. bottom-up refit: the second child to arrive at a node writes the node's union box.
+//   4. the hierarchy, by one of two builders:
+//      PLOC (default; Meister & Bittner, "Parallel locally-ordered clustering for bounding volume
+//      hierarchy construction", TVCG 2018): rounds of nearest-neighbour search by union-box
+//      surface area within +-8 positions of the Morton order, merging of mutual pairs and
+//      compaction, until one cluster is left;
+//      LBVH (Karras, "Maximizing parallelism in the construction of BVHs, octrees, and k-d
+//      trees", HPG 2012): one thread per internal node finds its key range and split, then a
+//      bottom-up refit in which the second child to arrive writes the node's union box;
+//   5. internal nodes renumbered in depth-first order (a parent's nearer child is often in the
+//      next 64 bytes).
 // Node layout (64 B): the boxes of both children plus the two child links, so one node fetch
 // decides both children. A child link >= 0 is an internal node, < 0 is leaf ~link (one
 // triangle). Boxes are widened by 2^-19 of the scene's largest coordinate so that the FP32
 // slab test never rejects a triangle the watertight triangle test would hit.
+// Dynamic scenes keep the mesh-local triangles; gm_scene_pose recomputes the world triangles for
+// new transforms and refits every box bottom-up over the unchanged hierarchy.
 #include <cmath>
 #include <cstring>
 #include <string>
