@@ -14,8 +14,9 @@
 //                  centres with edge functions evaluated in a canonical vertex order (a shared
 //                  edge gives exactly opposite values, no cracks), perspective-correct 1/w, and
 //                  atomicMin of the linear depth w (positive floats order as their bits); pairs
-//                  covering more than RASTER_THREAD_PIXELS pixels go to k_zb_raster_big, one block
-//                  each
+//                  covering more than RASTER_THREAD_PIXELS pixels go to k_zb_raster_warp (one warp
+//                  each, lanes over pixels), more than RASTER_WARP_PIXELS to k_zb_raster_big (one
+//                  block each): lanes of a warp no longer wait for one lane's large triangle
 //   k_zb_accumulate one thread per work-order sample over the chunk's fixations: the exact cone
 //                  test and Gaussian of the ray path, visibility |w - zbuf| <= eps, compensated
 //                  sums carried across chunks, per-window writes and maxima; optionally the exact
@@ -30,7 +31,8 @@ namespace {
 
 constexpr int ZB_THREADS = 256;
 constexpr int ZB_SMEM_FRUSTA = 64;            // frusta staged per pass of the cull kernel
-constexpr int RASTER_THREAD_PIXELS = 256;     // larger pixel boxes go to the block rasteriser
+constexpr int RASTER_THREAD_PIXELS = 64;      // larger pixel boxes go to the warp rasteriser,
+constexpr int RASTER_WARP_PIXELS = 1024;      // and larger ones still to the block rasteriser
 constexpr uint32_t ZB_EMPTY = 0xffffffffu;    // cleared z-buffer word (above every finite depth)
 constexpr uint32_t NO_WINDOW = 0xffffffffu;
 
@@ -206,7 +208,10 @@ __global__ void __launch_bounds__(ZB_THREADS) k_zb_cull(const float4* __restrict
     }
     const int lane = threadIdx.x & 31;
     const float R = (float)res;
-    for (uint32_t f0 = 0; f0 < nfix; f0 += ZB_SMEM_FRUSTA) {
+    // blockIdx.y picks a group of fixations (one shared-memory load of their frusta); the blocks of
+    // one group run together, so the pairs they emit -- and the raster's atomics -- stay on a few
+    // z-buffers that fit in L2
+    for (uint32_t f0 = blockIdx.y * ZB_SMEM_FRUSTA; f0 < nfix; f0 += gridDim.y * ZB_SMEM_FRUSTA) {
         const uint32_t m = min((uint32_t)ZB_SMEM_FRUSTA, nfix - f0);
         __syncthreads();
         for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) sF[k] = frusta[f0 + k];
@@ -306,11 +311,13 @@ __device__ __forceinline__ void poly_bbox(const ClipPoly& P, int res, int& x0, i
         vmin = fminf(vmin, P.v[k]);
         vmax = fmaxf(vmax, P.v[k]);
     }
-    // pixel centres px + 1/2 within [umin, umax], with one pixel of slack for rounding
-    x0 = max(0, (int)floorf(fmaxf(umin, -2.f)) - 1);
-    x1 = min(res - 1, (int)floorf(fminf(umax, (float)res + 2.f)) + 1);
-    y0 = max(0, (int)floorf(fmaxf(vmin, -2.f)) - 1);
-    y1 = min(res - 1, (int)floorf(fminf(vmax, (float)res + 2.f)) + 1);
+    // pixel centres px + 1/2 within [umin, umax], widened by 1/100 pixel for the rounding of the
+    // edge functions (an FP32 error of a few 1e-4 pixels at these coordinates)
+    constexpr float e = 0.01f;
+    x0 = max(0, (int)ceilf(fmaxf(umin, -2.f) - 0.5f - e));
+    x1 = min(res - 1, (int)floorf(fminf(umax, (float)res + 2.f) - 0.5f + e));
+    y0 = max(0, (int)ceilf(fmaxf(vmin, -2.f) - 0.5f - e));
+    y1 = min(res - 1, (int)floorf(fminf(vmax, (float)res + 2.f) - 0.5f + e));
 }
 
 // Depth test of one pixel against the fan triangles of the polygon.
@@ -331,29 +338,70 @@ __device__ __forceinline__ void shade_pixel(const ClipPoly& P, int px, int py, f
     }
 }
 
+// Append `value` to a list for every lane that wants to, with one atomic per warp. All 32 lanes call it.
+__device__ __forceinline__ void warp_push(bool want, uint32_t value, uint32_t* __restrict__ list, uint64_t cap,
+                                          unsigned long long* __restrict__ counter) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (want) {
+        const unsigned long long q = base + __popc(m & gm_lanemask_lt());
+        if (q < cap) list[q] = value;
+    }
+}
+
 __global__ void __launch_bounds__(ZB_THREADS) k_zb_raster(const PairFT* __restrict__ pairs, uint64_t n_pairs,
                                                           const ZbFrustum* __restrict__ frusta,
                                                           const float4* __restrict__ tris, uint32_t res,
                                                           uint32_t* __restrict__ zbuf, uint32_t* __restrict__ big,
-                                                          uint64_t big_cap, unsigned long long* __restrict__ n_big) {
+                                                          uint32_t* __restrict__ mid, uint64_t list_cap,
+                                                          unsigned long long* __restrict__ n_lists) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_pairs) return;
-    const PairFT pr = pairs[i];
-    const ZbFrustum F = frusta[pr.fix];
+    PairFT pr{0u, 0u};
+    ZbFrustum F;
     ClipPoly P;
-    clip_project(F, tris[3 * pr.tri], tris[3 * pr.tri + 1], tris[3 * pr.tri + 2], P);
-    if (P.n < 3) return;
-    int x0, x1, y0, y1;
-    poly_bbox(P, (int)res, x0, x1, y0, y1);
-    if (x1 < x0 || y1 < y0) return;
-    if ((x1 - x0 + 1) * (y1 - y0 + 1) > RASTER_THREAD_PIXELS) {
-        const unsigned long long q = atomicAdd(n_big, 1ull);
-        if (q < big_cap) big[q] = (uint32_t)i;
-        return;
+    P.n = 0;
+    int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
+    if (i < n_pairs) {
+        pr = pairs[i];
+        F = frusta[pr.fix];
+        clip_project(F, tris[3 * pr.tri], tris[3 * pr.tri + 1], tris[3 * pr.tri + 2], P);
+        if (P.n >= 3) poly_bbox(P, (int)res, x0, x1, y0, y1);
     }
+    const int npx = (P.n >= 3 && x1 >= x0 && y1 >= y0) ? (x1 - x0 + 1) * (y1 - y0 + 1) : 0;
+    const bool to_big = npx > RASTER_WARP_PIXELS, to_mid = npx > RASTER_THREAD_PIXELS && !to_big;
+    warp_push(to_big, (uint32_t)i, big, list_cap, &n_lists[0]);
+    warp_push(to_mid, (uint32_t)i, mid, list_cap, &n_lists[1]);
+    if (npx == 0 || to_big || to_mid) return;
     uint32_t* zb = zbuf + (size_t)pr.fix * res * res;
     for (int py = y0; py <= y1; ++py)
         for (int px = x0; px <= x1; ++px) shade_pixel(P, px, py, F.n, F.f, zb, (int)res);
+}
+
+__global__ void __launch_bounds__(ZB_THREADS) k_zb_raster_warp(const uint32_t* __restrict__ mid, uint64_t n_mid,
+                                                               const PairFT* __restrict__ pairs,
+                                                               const ZbFrustum* __restrict__ frusta,
+                                                               const float4* __restrict__ tris, uint32_t res,
+                                                               uint32_t* __restrict__ zbuf) {
+    const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (uint64_t q = warp0; q < n_mid; q += nwarps) {
+        const PairFT pr = pairs[mid[q]];
+        const ZbFrustum F = frusta[pr.fix];
+        ClipPoly P;
+        clip_project(F, tris[3 * pr.tri], tris[3 * pr.tri + 1], tris[3 * pr.tri + 2], P);
+        if (P.n < 3) continue;
+        int x0, x1, y0, y1;
+        poly_bbox(P, (int)res, x0, x1, y0, y1);
+        if (x1 < x0 || y1 < y0) continue;
+        const int wdt = x1 - x0 + 1, cnt = wdt * (y1 - y0 + 1);
+        uint32_t* zb = zbuf + (size_t)pr.fix * res * res;
+        for (int k = lane; k < cnt; k += 32) shade_pixel(P, x0 + k % wdt, y0 + k / wdt, F.n, F.f, zb, (int)res);
+    }
 }
 
 __global__ void __launch_bounds__(ZB_THREADS) k_zb_raster_big(const uint32_t* __restrict__ big,
@@ -512,9 +560,26 @@ __global__ void k_zb_set_valid(unsigned long long* __restrict__ c, const uint32_
 struct RasterBuffers {
     PairFT* pairs = nullptr;
     uint32_t* big = nullptr;
+    uint32_t* mid = nullptr;
     uint64_t cap = 0;
-    unsigned long long* counts = nullptr;   // [0] pairs [1] big
+    unsigned long long* counts = nullptr;   // [0] pairs [1] big [2] mid
 };
+
+gm_status rb_alloc(RasterBuffers& rb, uint64_t cap, cudaStream_t s) {
+    rb.cap = cap;
+    GM_TRY(gm_alloc((void**)&rb.pairs, sizeof(PairFT) * cap, s));
+    GM_TRY(gm_alloc((void**)&rb.big, sizeof(uint32_t) * cap, s));
+    GM_TRY(gm_alloc((void**)&rb.mid, sizeof(uint32_t) * cap, s));
+    return GM_OK;
+}
+
+void rb_free(RasterBuffers& rb, cudaStream_t s) {
+    if (rb.pairs) cudaFreeAsync(rb.pairs, s);
+    if (rb.big) cudaFreeAsync(rb.big, s);
+    if (rb.mid) cudaFreeAsync(rb.mid, s);
+    rb.pairs = nullptr;
+    rb.big = rb.mid = nullptr;
+}
 
 gm_status render_zbuffers(gm_ctx* ctx, gm_scene* sc, const ZbFrustum* frusta, uint32_t nfix, uint32_t res,
                           uint32_t* zbuf, RasterBuffers& rb, cudaStream_t s, int* launches,
@@ -522,21 +587,17 @@ gm_status render_zbuffers(gm_ctx* ctx, gm_scene* sc, const ZbFrustum* frusta, ui
     const size_t npx = (size_t)res * res;
     for (int attempt = 0; attempt < 3; ++attempt) {
         GM_TRY_CUDA(cudaMemsetAsync(zbuf, 0xff, sizeof(uint32_t) * npx * nfix, s));
-        GM_TRY_CUDA(cudaMemsetAsync(rb.counts, 0, sizeof(unsigned long long) * 2, s));
-        k_zb_cull<<<gm_div_up(sc->n_tris, ZB_THREADS), ZB_THREADS, 0, s>>>(sc->tri_canon, sc->n_tris, frusta, nfix,
+        GM_TRY_CUDA(cudaMemsetAsync(rb.counts, 0, sizeof(unsigned long long) * 3, s));
+        const dim3 cgrid(gm_div_up(sc->n_tris, ZB_THREADS), std::min<uint32_t>(gm_div_up(nfix, ZB_SMEM_FRUSTA), 65535));
+        k_zb_cull<<<cgrid, ZB_THREADS, 0, s>>>(sc->tri_canon, sc->n_tris, frusta, nfix,
                                                                           res, rb.pairs, rb.cap, &rb.counts[0]);
         ++*launches;
         unsigned long long np = 0;
         GM_TRY_CUDA(cudaMemcpyAsync(&np, &rb.counts[0], sizeof(np), cudaMemcpyDeviceToHost, s));
         GM_TRY_CUDA(cudaStreamSynchronize(s));
         if (np > rb.cap) {
-            cudaFreeAsync(rb.pairs, s);
-            cudaFreeAsync(rb.big, s);
-            rb.pairs = nullptr;
-            rb.big = nullptr;
-            rb.cap = np + np / 4;
-            GM_TRY(gm_alloc((void**)&rb.pairs, sizeof(PairFT) * rb.cap, s));
-            GM_TRY(gm_alloc((void**)&rb.big, sizeof(uint32_t) * rb.cap, s));
+            rb_free(rb, s);
+            GM_TRY(rb_alloc(rb, np + np / 4, s));
             continue;
         }
         if (raster_pairs) *raster_pairs += np;
@@ -545,12 +606,18 @@ gm_status render_zbuffers(gm_ctx* ctx, gm_scene* sc, const ZbFrustum* frusta, ui
         if (np > 0) {
             if (np > 0xffffffffull) return gm_set_error(GM_ERR_UNSUPPORTED, "z-buffer: more than 2^32 raster pairs");
             k_zb_raster<<<(uint32_t)((np + ZB_THREADS - 1) / ZB_THREADS), ZB_THREADS, 0, s>>>(
-                rb.pairs, np, frusta, sc->tri_canon, res, zbuf, rb.big, rb.cap, &rb.counts[1]);
+                rb.pairs, np, frusta, sc->tri_canon, res, zbuf, rb.big, rb.mid, rb.cap, &rb.counts[1]);
             ++*launches;
-            unsigned long long nb = 0;
-            GM_TRY_CUDA(cudaMemcpyAsync(&nb, &rb.counts[1], sizeof(nb), cudaMemcpyDeviceToHost, s));
+            unsigned long long nl[2] = {0, 0};
+            GM_TRY_CUDA(cudaMemcpyAsync(nl, &rb.counts[1], sizeof(nl), cudaMemcpyDeviceToHost, s));
             GM_TRY_CUDA(cudaStreamSynchronize(s));
-            nb = std::min<unsigned long long>(nb, rb.cap);
+            const unsigned long long nb = std::min<unsigned long long>(nl[0], rb.cap);
+            const unsigned long long nm = std::min<unsigned long long>(nl[1], rb.cap);
+            if (nm > 0) {
+                const uint32_t wblocks = (uint32_t)std::min<unsigned long long>((nm + 7) / 8, (uint64_t)ctx->n_sm * 16);
+                k_zb_raster_warp<<<wblocks, ZB_THREADS, 0, s>>>(rb.mid, nm, rb.pairs, frusta, sc->tri_canon, res, zbuf);
+                ++*launches;
+            }
             for (unsigned long long b0 = 0; b0 < nb; b0 += 1u << 30) {
                 const uint32_t nblk = (uint32_t)std::min<unsigned long long>(nb - b0, 1u << 30);
                 k_zb_raster_big<<<nblk, ZB_THREADS, 0, s>>>(rb.big + b0, rb.pairs, frusta, sc->tri_canon, res, zbuf);
@@ -628,10 +695,9 @@ extern "C" gm_status gm_zbuffer_render(gm_scene* sc, const float* eye, const flo
     ZB_TMP(fr, sizeof(ZbFrustum) * n);
     ZB_TMP(crop, sizeof(double) * 4 * n);
     ZB_TMP(zb, sizeof(uint32_t) * npx * n);
-    ZB_TMP(rb.counts, sizeof(unsigned long long) * 2);
-    if ((st = gm_alloc((void**)&rb.pairs, sizeof(PairFT) * rb.cap, s)) != GM_OK) return done(st);
-    if ((st = gm_alloc((void**)&rb.big, sizeof(uint32_t) * rb.cap, s)) != GM_OK) {
-        cudaFreeAsync(rb.pairs, s);
+    ZB_TMP(rb.counts, sizeof(unsigned long long) * 3);
+    if ((st = rb_alloc(rb, rb.cap, s)) != GM_OK) {
+        rb_free(rb, s);
         return done(st);
     }
     int launches = 0;
@@ -652,8 +718,7 @@ extern "C" gm_status gm_zbuffer_render(gm_scene* sc, const float* eye, const flo
         }
     }
     if (st == GM_OK && crop_out) st = gm_copy_out(crop_out, crop, sizeof(double) * 4 * n, s);
-    cudaFreeAsync(rb.pairs, s);
-    cudaFreeAsync(rb.big, s);
+    rb_free(rb, s);
     ctx->launches += launches;
     if (st == GM_OK) {
         cudaError_t e = cudaGetLastError();
@@ -713,8 +778,7 @@ extern "C" gm_status gm_accumulate_zbuffer(gm_scene* sc, gm_samples* sm, const g
     RasterBuffers rb;
     auto fail = [&](gm_status st) {
         for (void* p : tmp) cudaFreeAsync(p, s);
-        if (rb.pairs) cudaFreeAsync(rb.pairs, s);
-        if (rb.big) cudaFreeAsync(rb.big, s);
+        rb_free(rb, s);
         gm_map_free(mp);
         return st;
     };
@@ -806,9 +870,8 @@ extern "C" gm_status gm_accumulate_zbuffer(gm_scene* sc, gm_samples* sm, const g
     TMP_ALLOC(zbuf, sizeof(uint32_t) * npx * chunk);
     if (chunk < nv) TMP_ALLOC(state, sizeof(float2) * (ns ? ns : 1));
     rb.cap = std::max<uint64_t>(1u << 20, (uint64_t)chunk * std::max<uint64_t>(2048, sc->zb_pairs_per_fix * 5 / 4));
-    TMP_ALLOC(rb.counts, sizeof(unsigned long long) * 2);
-    if ((st = gm_alloc((void**)&rb.pairs, sizeof(PairFT) * rb.cap, s)) != GM_OK) return fail(st);
-    if ((st = gm_alloc((void**)&rb.big, sizeof(uint32_t) * rb.cap, s)) != GM_OK) return fail(st);
+    TMP_ALLOC(rb.counts, sizeof(unsigned long long) * 3);
+    if ((st = rb_alloc(rb, rb.cap, s)) != GM_OK) return fail(st);
 
     ZbAccParams P;
     P.C2 = (float)(1.4426950408889634 / (2.0 * tan_t * tan_t));
@@ -881,8 +944,7 @@ extern "C" gm_status gm_accumulate_zbuffer(gm_scene* sc, gm_samples* sm, const g
     if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_accumulate_zbuffer launch"));
     GM_TRY_CUDA(cudaStreamSynchronize(s));   // raster_pairs and the host vectors above are host temporaries
     for (void* p : tmp) cudaFreeAsync(p, s);
-    cudaFreeAsync(rb.pairs, s);
-    cudaFreeAsync(rb.big, s);
+    rb_free(rb, s);
     mp->stats.launches = (uint32_t)launches;
     ctx->launches += launches;
     *out = mp;
