@@ -201,13 +201,37 @@ __global__ void __launch_bounds__(ZB_THREADS) k_zb_cull(const float4* __restrict
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = t < nt;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
-    if (valid) {
+    if (valid) {   // leaf order: a warp's 32 triangles are neighbours in space; v0.w = triangle id
         a = tris[3 * t];
         b = tris[3 * t + 1];
         c = tris[3 * t + 2];
     }
+    const uint32_t id = __float_as_uint(a.w);
     const int lane = threadIdx.x & 31;
     const float R = (float)res;
+    // the warp's triangles in one sphere (box centre, half diagonal), tested against each frustum
+    // before the per-triangle tests
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (valid) {
+        lo[0] = fminf(fminf(a.x, b.x), c.x);
+        lo[1] = fminf(fminf(a.y, b.y), c.y);
+        lo[2] = fminf(fminf(a.z, b.z), c.z);
+        hi[0] = fmaxf(fmaxf(a.x, b.x), c.x);
+        hi[1] = fmaxf(fmaxf(a.y, b.y), c.y);
+        hi[2] = fmaxf(fmaxf(a.z, b.z), c.z);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[q] = fminf(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
+            hi[q] = fmaxf(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
+        }
+    }
+    const bool wbox = lo[0] <= hi[0];
+    const float wx = 0.5f * (lo[0] + hi[0]), wy = 0.5f * (lo[1] + hi[1]), wz = 0.5f * (lo[2] + hi[2]);
+    const float wR = wbox ? 0.5f * sqrtf((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                                         (hi[2] - lo[2]) * (hi[2] - lo[2])) * 1.0001f
+                          : 0.f;
     // blockIdx.y picks a group of fixations (one shared-memory load of their frusta); the blocks of
     // one group run together, so the pairs they emit -- and the raster's atomics -- stay on a few
     // z-buffers that fit in L2
@@ -218,8 +242,23 @@ __global__ void __launch_bounds__(ZB_THREADS) k_zb_cull(const float4* __restrict
         __syncthreads();
         for (uint32_t k = 0; k < m; ++k) {
             const ZbFrustum& F = sF[k];
+            if (!F.ok || !wbox) continue;
+            {
+                // the sphere against the six planes (the side planes pass through the eye; their
+                // unit normals in camera coordinates from the pixel mapping with one pixel of slack)
+                float xc, yc, wc;
+                to_camera(F, wx, wy, wz, xc, yc, wc);
+                const float slack = wR + 1e-4f * (fabsf(xc) + fabsf(yc) + fabsf(wc) + wR);
+                const float l0 = F.ox + 1.f, l1 = R + 1.f - F.ox, b0 = F.oy + 1.f, b1 = R + 1.f - F.oy;
+                const bool out = wc < F.n - slack || wc > F.f + slack ||
+                                 fmaf(F.sx, xc, l0 * wc) < -slack * sqrtf(fmaf(F.sx, F.sx, l0 * l0)) ||
+                                 fmaf(-F.sx, xc, l1 * wc) < -slack * sqrtf(fmaf(F.sx, F.sx, l1 * l1)) ||
+                                 fmaf(F.sy, yc, b0 * wc) < -slack * sqrtf(fmaf(F.sy, F.sy, b0 * b0)) ||
+                                 fmaf(-F.sy, yc, b1 * wc) < -slack * sqrtf(fmaf(F.sy, F.sy, b1 * b1));
+                if (out) continue;
+            }
             bool keep = false;
-            if (valid && F.ok) {
+            if (valid) {
                 float x[3], y[3], w[3];
                 to_camera(F, a.x, a.y, a.z, x[0], y[0], w[0]);
                 to_camera(F, b.x, b.y, b.z, x[1], y[1], w[1]);
@@ -244,7 +283,7 @@ __global__ void __launch_bounds__(ZB_THREADS) k_zb_cull(const float4* __restrict
                 base = __shfl_sync(0xffffffffu, base, __ffs(msk) - 1);
                 if (keep) {
                     const unsigned long long q = base + __popc(msk & gm_lanemask_lt());
-                    if (q < cap) pairs[q] = PairFT{f0 + k, t};
+                    if (q < cap) pairs[q] = PairFT{f0 + k, id};
                 }
             }
         }
@@ -589,7 +628,7 @@ gm_status render_zbuffers(gm_ctx* ctx, gm_scene* sc, const ZbFrustum* frusta, ui
         GM_TRY_CUDA(cudaMemsetAsync(zbuf, 0xff, sizeof(uint32_t) * npx * nfix, s));
         GM_TRY_CUDA(cudaMemsetAsync(rb.counts, 0, sizeof(unsigned long long) * 3, s));
         const dim3 cgrid(gm_div_up(sc->n_tris, ZB_THREADS), std::min<uint32_t>(gm_div_up(nfix, ZB_SMEM_FRUSTA), 65535));
-        k_zb_cull<<<cgrid, ZB_THREADS, 0, s>>>(sc->tri_canon, sc->n_tris, frusta, nfix,
+        k_zb_cull<<<cgrid, ZB_THREADS, 0, s>>>(sc->bvh_tris, sc->n_tris, frusta, nfix,
                                                                           res, rb.pairs, rb.cap, &rb.counts[0]);
         ++*launches;
         unsigned long long np = 0;
