@@ -70,7 +70,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gazemap", "reference"], default="gazemap")
-    ap.add_argument("--workload", choices=["paper_scene", "tiny_sphere", "batched", "field", "city", "zbuffer"],
+    ap.add_argument("--workload", choices=["paper_scene", "tiny_sphere", "batched", "field", "city", "zbuffer",
+                                           "dynamic"],
                     default="paper_scene")
     ap.add_argument("--field-steps", type=int, default=30000, help="Adam steps of the neural field")
     ap.add_argument("--field-lr", type=float, default=3e-3, help="initial learning rate of the field (cosine to 1%%)")
@@ -389,6 +390,93 @@ def zbuffer_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def dynamic_arm(args):
+    """Dynamic scene: the paper-shaped scene over ten windows of 600 fixations each, one mesh (the
+    torus knot) turning 3 degrees per window about the vertical axis. The timed call is
+    gm_accumulate_dynamic (per window: pose + refit, samples follow, accumulation of the window's
+    fixations; normalisation at the end) against gm_accumulate_fixations on the static scene with
+    the same windows; the pose and follow cost is also timed on its own."""
+    import torch
+    import synth
+    from paper_2601_07571_gb300 import build as B
+    B.build()
+    import paper_2601_07571_gb300 as G
+    from paper_2601_07571_gb300 import pipeline
+    torch.cuda.set_device(0)
+    w = make_workload("paper_scene", args.fixations)
+    n_win = 10
+    t_end = float(w.fixations.timestamp_s.max()) + 1e-3
+    w.params = synth.Params(t_begin=0.0, t_end=t_end, window_s=t_end / n_win)
+    rest = np.stack([m.transform for m in w.meshes])
+    xf = []
+    for k in range(n_win):
+        a = math.radians(3.0 * k)
+        R = np.eye(4)
+        R[0, 0], R[0, 2], R[2, 0], R[2, 2] = math.cos(a), math.sin(a), -math.sin(a), math.cos(a)
+        wk = rest.copy()
+        wk[1] = R @ rest[1]
+        xf.append(wk)
+    xf = np.stack(xf)
+    ctx = G.gm_create(0)
+    stream = torch.cuda.current_stream()
+    sc = G.gm_build_scene(ctx, pipeline.mesh_args(w, to_device=True), stream, dynamic=True)
+    sm = G.gm_sample_surface(sc, [m.density for m in w.meshes], w.seed, w.session, stream)
+    fix = pipeline.fixation_args(w.fixations, to_device=True)
+    prm = pipeline.params_of(w, normalize=True)
+    ns = G.gm_samples_info(sm)
+    pairs = ns * w.fixations.n
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(fn, free=True):
+        for _ in range(args.warmup):
+            r = fn()
+            if free and r is not None:
+                G.gm_map_free(r)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            if free and r is not None:
+                G.gm_map_free(r)
+        return sum(ts) / len(ts)
+
+    clocks = ClockSampler()
+    clocks.start()
+    l0 = G.gm_ctx_launches(ctx)
+    dyn_ms = timed(lambda: G.gm_accumulate_dynamic(sc, sm, *fix, prm, xf, stream))
+    launches = (G.gm_ctx_launches(ctx) - l0) // max(1, args.steps + args.warmup)
+    clk = clocks.stop()
+
+    def pose_all():
+        for k in range(n_win):
+            G.gm_scene_pose(sc, xf[k], stream)
+            G.gm_samples_follow(sm, stream)
+        return None
+
+    pose_ms = timed(pose_all, free=False)
+    G.gm_scene_pose(sc, rest, stream)
+    G.gm_samples_follow(sm, stream)
+    static_ms = timed(lambda: G.gm_accumulate_fixations(sc, sm, *fix, prm, stream))
+    line = {"metric": METRIC, "value": pairs / (dyn_ms * 1e-3), "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dyn_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name + "_dynamic_10win", "windows": n_win, "moving_mesh": "torus knot, 3 deg per window",
+                       "samples": int(ns), "fixations": w.fixations.n, "pairs_per_step": int(pairs),
+                       "l2": "flushed between steps (256 MiB write)", "inputs": "device-resident"},
+            "static_same_windows_ms": static_ms, "pose_and_follow_10_windows_ms": pose_ms,
+            "dynamic_over_static": dyn_ms / static_ms, "gpu_launches": int(launches), "clocks": clk}
+    G.gm_samples_free(sm)
+    G.gm_scene_free(sc)
+    G.gm_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def field_arm(args):
     """Neural density field on the paper-shaped scene: train on the normalised map of its 2M
     samples (MSE, Adam, batch 65 536, --field-lr cosine to 1 %, --field-steps steps), then answer
@@ -499,6 +587,9 @@ def main():
         return
     if args.workload == "zbuffer":
         zbuffer_arm(args)
+        return
+    if args.workload == "dynamic":
+        dynamic_arm(args)
         return
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
