@@ -80,7 +80,7 @@ def lib():
         _lib.ora_normalize.restype = C.c_double
         _lib.ora_grid_samples.restype = C.c_int
         for fn in ("ora_camera_basis", "ora_crop_paper", "ora_crop_exact", "ora_zb_frustum", "ora_zb_render",
-                   "ora_zb_accumulate"):
+                   "ora_zb_accumulate", "ora_zb_pairs"):
             getattr(_lib, fn).restype = C.c_int
     return _lib
 
@@ -469,3 +469,23 @@ def zb_accumulate(tri, sxyz, fixations, cam_fwd, cam_up, params, zb: ZBuffer, de
             raise RuntimeError("pair record capacity exceeded")
         out["pairs"] = dict(sample=rs[:k], fix=rf[:k], flag=rfl[:k], g=rg[:k])
     return out
+
+
+def zb_pairs(tri, sxyz, eye, gaze, cam_fwd, cam_up, theta, cutoff, zb: ZBuffer, delta_px=1e-3, delta_w_rel=1e-5,
+             nthreads=0):
+    """z-buffer visibility of individual (sample, fixation) pairs (one row per pair in every array),
+    casting only the pixels each decision reads: the full-size form of zb_accumulate's test.
+    Returns (vis, amb, frustum_ok) as bool arrays."""
+    tri = np.ascontiguousarray(tri, np.float32)
+    sxyz = np.ascontiguousarray(sxyz, np.float64).reshape(-1, 3)
+    n = len(sxyz)
+    f32 = lambda a: np.ascontiguousarray(np.asarray(a, np.float32).reshape(n, 3))
+    e, g, fw, up = f32(eye), f32(gaze), f32(cam_fwd), f32(cam_up)
+    Z = _ZbParams(int(zb.res), zb.near, zb.far, zb.eps, delta_px, delta_w_rel)
+    vis, amb, ok = (np.zeros(n, np.int8) for _ in range(3))
+    rc = lib().ora_zb_pairs(_p(tri), C.c_int64(len(tri)), C.c_int64(n), _p(sxyz), _p(e), _p(g), _p(fw), _p(up),
+                            C.c_double(theta), C.c_double(cutoff), C.byref(Z), _p(vis), _p(amb), _p(ok),
+                            C.c_int32(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"ora_zb_pairs failed ({rc})")
+    return vis.astype(bool), amb.astype(bool), ok.astype(bool)

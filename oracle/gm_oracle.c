@@ -766,13 +766,12 @@ int ora_zb_frustum(const float* eye, const float* gaze, const float* cam_fwd, co
  * pixels of the centre (at its own depth) lies no deeper than the pixel's depth (plus 1e-6
  * relative), or a hit lies within 1e-5 relative of a clip plane (an FP32 clipper may move the
  * clip edge by that much). zbuf and amb: res * res. */
-int ora_zb_render(const float* tri, int64_t nt, const ora_frustum* F, int32_t res, double delta_px, double* zbuf,
-                  uint8_t* amb)
+static void zb_pixel(const float* tri, int64_t nt, const ora_frustum* F, int32_t res, double delta_px, int32_t px,
+                     int32_t py, double* depth, uint8_t* amb_out)
 {
-    if (!F->ok || res <= 0) return -1;
     double pxw = (F->r - F->l) / res, pxh = (F->t - F->b) / res;
-    for (int32_t py = 0; py < res; ++py) {
-        for (int32_t px = 0; px < res; ++px) {
+    {
+        {
             double x = F->l + (px + 0.5) * pxw, y = F->b + (py + 0.5) * pxh;
             double d[3];
             for (int k = 0; k < 3; ++k) d[k] = x * F->right[k] + y * F->up[k] + F->n * F->fwd[k];
@@ -796,10 +795,19 @@ int ora_zb_render(const float* tri, int64_t nt, const ora_frustum* F, int32_t re
                 }
                 if (nr2 && wp >= F->n * (1.0 - 1e-9) && wp <= F->f * (1.0 + 1e-9) && wp < near_best) near_best = wp;
             }
-            zbuf[(size_t)py * res + px] = best;
-            amb[(size_t)py * res + px] = (uint8_t)(clip_amb || (isfinite(near_best) && near_best <= best * (1.0 + 1e-6)));
+            *depth = best;
+            *amb_out = (uint8_t)(clip_amb || (isfinite(near_best) && near_best <= best * (1.0 + 1e-6)));
         }
     }
+}
+
+int ora_zb_render(const float* tri, int64_t nt, const ora_frustum* F, int32_t res, double delta_px, double* zbuf,
+                  uint8_t* amb)
+{
+    if (!F->ok || res <= 0) return -1;
+    for (int32_t py = 0; py < res; ++py)
+        for (int32_t px = 0; px < res; ++px)
+            zb_pixel(tri, nt, F, res, delta_px, px, py, &zbuf[(size_t)py * res + px], &amb[(size_t)py * res + px]);
     return 0;
 }
 
@@ -836,14 +844,6 @@ static void* render_range(void* arg)
     return NULL;
 }
 
-/* z-buffer visibility of a point of camera-space depth w and near-plane coordinates (xn, yn)
- * in pixel (px, py): |w - Z| <= eps. */
-static int zb_pixel_visible(const double* Z, int32_t res, int32_t px, int32_t py, double w, double eps)
-{
-    double z = Z[(size_t)py * res + px];
-    return isfinite(z) && fabs(w - z) <= eps;
-}
-
 typedef struct {
     const float* tri; int64_t nt;
     const double* sxyz; int64_t s0, s1, ns;
@@ -856,6 +856,70 @@ typedef struct {
     int64_t *ps; int32_t* pf; uint8_t* pflag; double* pg; int64_t np, cap;
     int err;
 } ora_zb_job;
+
+/* The z-buffer visibility of sample sp in frustum F, with the ambiguity bookkeeping: pixel depths
+ * come from `look` (a stored z-buffer, or pixels cast on demand). */
+typedef void (*zb_lookup_fn)(void* ctx, int32_t px, int32_t py, double* depth, uint8_t* amb);
+
+static void zb_decide(const ora_frustum* F, const double sp[3], const ora_zb_params* zp, zb_lookup_fn look, void* ctx,
+                      int* vis_out, int* amb_out)
+{
+    const int32_t res = zp->res;
+    double v[3] = {sp[0] - F->e[0], sp[1] - F->e[1], sp[2] - F->e[2]};
+    double x = v3_dot(v, F->right), y = v3_dot(v, F->up), w = v3_dot(v, F->fwd);
+    int vis = 0, amb_vis = 0;
+    if (fabs(w - F->n) <= 1e-6 * F->n || fabs(w - F->f) <= 1e-6 * F->f) amb_vis = 1;
+    if (w >= F->n && w <= F->f) {
+        double u = (F->n * x / w - F->l) / (F->r - F->l) * res;
+        double q = (F->n * y / w - F->b) / (F->t - F->b) * res;
+        double dp = zp->delta_px;
+        if (u < dp || u > res - dp || q < dp || q > res - dp) {
+            /* on the crop border: inside or filtered out depending on rounding */
+            if (!(u < -dp || u > res + dp || q < -dp || q > res + dp)) amb_vis = 1;
+        }
+        if (u >= 0.0 && u <= res && q >= 0.0 && q <= res) {
+            int32_t cx[2], cy[2];
+            cx[0] = (int32_t)floor(u - dp); cx[1] = (int32_t)floor(u + dp);
+            cy[0] = (int32_t)floor(q - dp); cy[1] = (int32_t)floor(q + dp);
+            for (int k = 0; k < 2; ++k) {
+                if (cx[k] < 0) cx[k] = 0;
+                if (cx[k] > res - 1) cx[k] = res - 1;
+                if (cy[k] < 0) cy[k] = 0;
+                if (cy[k] > res - 1) cy[k] = res - 1;
+            }
+            int32_t px = (int32_t)floor(u), py = (int32_t)floor(q);
+            if (px > res - 1) px = res - 1;
+            if (py > res - 1) py = res - 1;
+            double z0;
+            uint8_t a0;
+            look(ctx, px, py, &z0, &a0);
+            vis = isfinite(z0) && fabs(w - z0) <= zp->eps;
+            double dw = zp->delta_w_rel * w;
+            for (int a = 0; a < 2; ++a) {
+                for (int b = 0; b < 2; ++b) {
+                    double z;
+                    uint8_t am;
+                    look(ctx, cx[a], cy[b], &z, &am);
+                    if (am) amb_vis = 1;
+                    if ((isfinite(z) && fabs(w - z) <= zp->eps) != vis) amb_vis = 1;
+                    if (isfinite(z) && fabs(fabs(w - z) - zp->eps) <= dw) amb_vis = 1;
+                }
+            }
+        }
+    }
+    *vis_out = vis;
+    *amb_out = amb_vis;
+}
+
+typedef struct { const double* Z; const uint8_t* A; int32_t res; } zb_stored;
+
+static void zb_lookup_stored(void* ctx, int32_t px, int32_t py, double* depth, uint8_t* amb)
+{
+    const zb_stored* S = (const zb_stored*)ctx;
+    size_t p = (size_t)py * S->res + px;
+    *depth = S->Z[p];
+    *amb = S->A[p];
+}
 
 static void* zb_accumulate_range(void* arg)
 {
@@ -876,47 +940,9 @@ static void* zb_accumulate_range(void* arg)
             int in = gaussian_pair(sp, e, r, (double)J->dur[f], P->theta, P->cutoff, P->cone_band, &pe);
             if (!in && !pe.edge) continue;
             const ora_frustum* F = &J->F[f];
-            const double* Z = J->Z + npx * f;
-            const uint8_t* A = J->A + npx * f;
-            double v[3] = {sp[0] - F->e[0], sp[1] - F->e[1], sp[2] - F->e[2]};
-            double x = v3_dot(v, F->right), y = v3_dot(v, F->up), w = v3_dot(v, F->fwd);
+            zb_stored S = {J->Z + npx * f, J->A + npx * f, res};
             int vis = 0, amb_vis = 0;
-            if (fabs(w - F->n) <= 1e-6 * F->n || fabs(w - F->f) <= 1e-6 * F->f) amb_vis = 1;
-            if (w >= F->n && w <= F->f) {
-                double u = (F->n * x / w - F->l) / (F->r - F->l) * res;
-                double q = (F->n * y / w - F->b) / (F->t - F->b) * res;
-                double dp = zp->delta_px;
-                if (u < dp || u > res - dp || q < dp || q > res - dp) {
-                    /* on the crop border: inside or filtered out depending on rounding */
-                    if (u < -dp || u > res + dp || q < -dp || q > res + dp) { /* clearly outside */ }
-                    else amb_vis = 1;
-                }
-                if (u >= 0.0 && u <= res && q >= 0.0 && q <= res) {
-                    int32_t cx[2], cy[2];
-                    cx[0] = (int32_t)floor(u - dp); cx[1] = (int32_t)floor(u + dp);
-                    cy[0] = (int32_t)floor(q - dp); cy[1] = (int32_t)floor(q + dp);
-                    for (int k = 0; k < 2; ++k) {
-                        if (cx[k] < 0) cx[k] = 0;
-                        if (cx[k] > res - 1) cx[k] = res - 1;
-                        if (cy[k] < 0) cy[k] = 0;
-                        if (cy[k] > res - 1) cy[k] = res - 1;
-                    }
-                    int32_t px = (int32_t)floor(u), py = (int32_t)floor(q);
-                    if (px > res - 1) px = res - 1;
-                    if (py > res - 1) py = res - 1;
-                    vis = zb_pixel_visible(Z, res, px, py, w, zp->eps);
-                    double dw = zp->delta_w_rel * w;
-                    for (int a = 0; a < 2; ++a) {
-                        for (int b = 0; b < 2; ++b) {
-                            size_t p = (size_t)cy[b] * res + cx[a];
-                            if (A[p]) amb_vis = 1;
-                            if (zb_pixel_visible(Z, res, cx[a], cy[b], w, zp->eps) != vis) amb_vis = 1;
-                            double z = Z[p];
-                            if (isfinite(z) && fabs(fabs(w - z) - zp->eps) <= dw) amb_vis = 1;
-                        }
-                    }
-                }
-            }
+            zb_decide(F, sp, zp, zb_lookup_stored, &S, &vis, &amb_vis);
             size_t o = (size_t)wi * (size_t)J->ns + (size_t)s;
             uint8_t flag = (uint8_t)((in ? PF_IN_CONE : 0) | (vis ? PF_VISIBLE : 0) | (amb_vis ? PF_VIS_AMBIG : 0)
                                      | (pe.edge ? PF_CONE_EDGE : 0));
@@ -1026,4 +1052,70 @@ int ora_zb_accumulate(const float* tri, int64_t nt, const double* sxyz, int64_t 
     if (!zbuf_out) free(Z);
     if (!amb_out) free(A);
     return err;
+}
+
+/* Sampled form of the z-buffer decision for full-size scenes: for each given (sample, fixation)
+ * pair, the fixation's frustum and only the pixels the decision reads, each cast against every
+ * triangle as ora_zb_render does. vis/amb per pair; frustum_ok 0 when the fixation has no crop
+ * window. Threads over pairs. */
+typedef struct {
+    const float* tri; int64_t nt; const ora_frustum* F; int32_t res; double delta_px;
+    int32_t cx[5], cy[5]; double cz[5]; uint8_t ca[5]; int nc;   /* pixels already cast for this pair */
+} zb_cast;
+
+static void zb_lookup_cast(void* ctx, int32_t px, int32_t py, double* depth, uint8_t* amb)
+{
+    zb_cast* C = (zb_cast*)ctx;
+    for (int k = 0; k < C->nc; ++k)
+        if (C->cx[k] == px && C->cy[k] == py) { *depth = C->cz[k]; *amb = C->ca[k]; return; }
+    zb_pixel(C->tri, C->nt, C->F, C->res, C->delta_px, px, py, depth, amb);
+    if (C->nc < 5) { C->cx[C->nc] = px; C->cy[C->nc] = py; C->cz[C->nc] = *depth; C->ca[C->nc] = *amb; ++C->nc; }
+}
+
+typedef struct {
+    const float* tri; int64_t nt; const double* sxyz; const float *eye, *gaze, *fwd, *up;
+    double theta, cutoff; const ora_zb_params* zp; int8_t *vis, *amb, *ok; int64_t p0, p1;
+} zb_pairs_job;
+
+static void* zb_pairs_range(void* arg)
+{
+    zb_pairs_job* J = (zb_pairs_job*)arg;
+    for (int64_t k = J->p0; k < J->p1; ++k) {
+        ora_frustum F;
+        if (ora_zb_frustum(J->eye + 3 * k, J->gaze + 3 * k, J->fwd + 3 * k, J->up + 3 * k, J->theta, J->cutoff,
+                           J->zp->n, J->zp->f, &F) || !F.ok) {
+            J->ok[k] = 0; J->vis[k] = 0; J->amb[k] = 0;
+            continue;
+        }
+        zb_cast C;
+        memset(&C, 0, sizeof(C));
+        C.tri = J->tri; C.nt = J->nt; C.F = &F; C.res = J->zp->res; C.delta_px = J->zp->delta_px;
+        int vis, amb;
+        zb_decide(&F, J->sxyz + 3 * k, J->zp, zb_lookup_cast, &C, &vis, &amb);
+        J->ok[k] = 1; J->vis[k] = (int8_t)vis; J->amb[k] = (int8_t)amb;
+    }
+    return NULL;
+}
+
+int ora_zb_pairs(const float* tri, int64_t nt, int64_t n, const double* sxyz, const float* eye, const float* gaze,
+                 const float* fwd, const float* up, double theta, double cutoff, const ora_zb_params* zp,
+                 int8_t* vis, int8_t* amb, int8_t* ok, int32_t nthreads)
+{
+    int nth = nthreads > 0 ? nthreads : (int)sysconf(_SC_NPROCESSORS_ONLN);
+    if (nth < 1) nth = 1;
+    if (nth > n) nth = n > 0 ? (int)n : 1;
+    zb_pairs_job* jobs = (zb_pairs_job*)calloc((size_t)nth, sizeof(zb_pairs_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)nth, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return -2; }
+    for (int i = 0; i < nth; ++i) {
+        zb_pairs_job* J = &jobs[i];
+        J->tri = tri; J->nt = nt; J->sxyz = sxyz; J->eye = eye; J->gaze = gaze; J->fwd = fwd; J->up = up;
+        J->theta = theta; J->cutoff = cutoff; J->zp = zp; J->vis = vis; J->amb = amb; J->ok = ok;
+        J->p0 = n * i / nth; J->p1 = n * (i + 1) / nth;
+    }
+    for (int i = 1; i < nth; ++i) pthread_create(&th[i], NULL, zb_pairs_range, &jobs[i]);
+    zb_pairs_range(&jobs[0]);
+    for (int i = 1; i < nth; ++i) pthread_join(th[i], NULL);
+    free(jobs); free(th);
+    return 0;
 }

@@ -187,3 +187,28 @@ def test_zbuffer_shadow_of_a_box_on_a_plane():
     assert (sel & deep).sum() > 300 and (sel & clear).sum() > 1000
     assert not vis[sel & deep].any()
     assert vis[sel & clear].all()
+
+
+def test_sampled_pair_form_agrees_with_the_full_form():
+    """zb_pairs (pixels cast on demand, for full-size scenes) reproduces zb_accumulate's recorded
+    decisions pair by pair."""
+    w = synth.tiny_sphere(n_fix=30)
+    w.params = synth.Params(theta_rad=math.radians(3.0))
+    fwd, up = synth.head_frames(w.fixations)
+    zb = oracle.ZBuffer(res=64, eps=0.005)
+    tri = oracle.world_triangles(w)
+    off = oracle.tri_offsets(oracle.areas(tri), oracle.tri_density(w))
+    smp = oracle.samples(tri, off, w.seed, w.session)
+    full = oracle.zb_accumulate(tri, smp.xyz, w.fixations, fwd, up, w.params, zb, record=True)
+    P = full["pairs"]
+    inc = (P["flag"] & oracle.PF_IN_CONE) > 0
+    s_i, f_i = P["sample"][inc], P["fix"][inc]
+    pick = np.random.default_rng(25).choice(len(s_i), size=min(1500, len(s_i)), replace=False)
+    s_i, f_i, flags = s_i[pick], f_i[pick], P["flag"][inc][pick]
+    fx = w.fixations
+    vis, amb, ok = oracle.zb_pairs(tri, smp.xyz[s_i], fx.eye[f_i], fx.gaze[f_i], fwd[f_i], up[f_i],
+                                   w.params.theta_rad, w.params.cutoff_sigmas, zb)
+    assert ok.all()
+    assert np.array_equal(vis, (flags & oracle.PF_VISIBLE) > 0)
+    assert np.array_equal(amb, (flags & oracle.PF_VIS_AMBIG) > 0)
+    assert vis.sum() > 100 and (~vis).sum() > 100
