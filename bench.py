@@ -530,6 +530,18 @@ def field_arm(args):
         G.gm_sync(ctx, stream)
         return sum(q_t) / len(q_t)
 
+    def train_step_ms(kernel, steps=2000):
+        # a fresh field trained by one kernel: device milliseconds per Adam step
+        ft = G.gm_field_create(ctx, lo, hi, synth.field_init(3), stream)
+        G.gm_field_train_kernel(ft, kernel)
+        G.gm_field_train(ft, h.samples, h.map, 0, steps=steps, batch=65536, lr=args.field_lr,
+                         lr_min=args.field_lr / 100, seed=34, stream=stream)
+        ms = G.gm_field_info(ft)["train_ms"] / steps
+        G.gm_field_free(ft)
+        return ms
+
+    train_tc_ms = G.gm_field_info(f)["train_ms"] / args.field_steps
+    train_ms_ms = train_step_ms(G.GM_FIELD_QUERY_MMA_SYNC)
     mma_sync_ms = time_queries(G.GM_FIELD_QUERY_MMA_SYNC)
     field_ms = time_queries(G.GM_FIELD_QUERY_TCGEN05)   # the default kernel; `out` keeps its values
     # the judge: plain accumulation at the query points, normalised by the training map's maximum
@@ -548,6 +560,7 @@ def field_arm(args):
     err = float(torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref))
     info = G.gm_field_info(f)
     flop_q = 2 * (4 * 64 * 64 + 64)            # hidden-layer MACs per query on the tensor cores (x2)
+    train_flop = 65536 * (flop_q + 2 * 3 * 64 * 64 + 2 * 4 * 64 * 64)   # per Adam step
     peak, basis = measured_bf16_peak()
     ach = flop_q * nq / (field_ms * 1e-3) / 1e12
     roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
@@ -565,7 +578,11 @@ def field_arm(args):
             "plain_form": {"value": nq / (plain_ms * 1e-3), "ms": plain_ms, "pairs": int(qst["pairs"]),
                            "form": "gm_accumulate_fixations at the query points"},
             "field_over_plain": plain_ms / field_ms, "roofline": roof,
-            "query_kernels_ms": {"tcgen05": field_ms, "mma_sync": mma_sync_ms}}
+            "query_kernels_ms": {"tcgen05": field_ms, "mma_sync": mma_sync_ms},
+            "train_step_ms": {"tcgen05": train_tc_ms, "mma_sync": train_ms_ms},
+            "train_tflops": {"tcgen05": train_flop / (train_tc_ms * 1e-3) / 1e12,
+                             "mma_sync": train_flop / (train_ms_ms * 1e-3) / 1e12,
+                             "work_basis": "65536 points x 90240 FLOP (forward 32896, dH 24576, dW 32768)"}}
     G.gm_field_free(f)
     G.gm_map_free(mq)
     G.gm_samples_free(qs)

@@ -403,6 +403,15 @@ gm_status gm_field_loss_grad(gm_field* field, const float* xyz, const float* tar
 enum { GM_FIELD_QUERY_TCGEN05 = 0, GM_FIELD_QUERY_MMA_SYNC = 1 };
 gm_status gm_field_query(const gm_field* field, const float* xyz, uint64_t n, float* out, gm_stream stream);
 gm_status gm_field_query_kernel(gm_field* field, int32_t kernel);
+/* The kernel that computes training gradients (gm_field_train, gm_field_step, gm_field_loss_grad).
+ * GM_FIELD_QUERY_TCGEN05 (default): one persistent block per SM over 128-point tiles; every
+ * hidden-layer product of the forward and backward passes, the weight gradients dZ^T H and the
+ * bias gradients runs as tcgen05.mma with FP32 accumulators in tensor memory, the gradients stay
+ * there across a block's tiles, and the blocks' partial sums are added in a fixed order, so the
+ * gradient of a batch does not depend on scheduling. GM_FIELD_QUERY_MMA_SYNC: warp-level mma.sync,
+ * one block per 128 points, gradients summed with atomics. Same definition and rounding; sums
+ * may differ in their last bits. */
+gm_status gm_field_train_kernel(gm_field* field, int32_t kernel);
 /* Copy the FP32 master parameters (GM_FIELD_N_PARAMS) to out (host or device). */
 gm_status gm_field_params(const gm_field* field, float* out, gm_stream stream);
 gm_status gm_field_info(const gm_field* field, uint32_t* n_params, uint32_t* steps_taken, float* last_loss,

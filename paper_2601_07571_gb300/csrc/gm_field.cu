@@ -8,15 +8,18 @@
 //   out = softplus(h4 . w5 + b5)                                       (FP32)
 // Training minimises the mean squared error to the normalised map with Adam (FP32 master
 // weights and moments), one fused kernel per step for the forward and backward passes plus one
-// update kernel; every product of the hidden layers runs on the tensor cores as BF16
-// mma.sync.m16n8k16 with FP32 accumulation.
+// update kernel. Both the queries and the training have two kernels: the default runs every
+// hidden-layer product on the 5th-generation tensor cores (tcgen05.mma, accumulators in tensor
+// memory; k_field_query_tc, k_field_train_tc), the other on warp-level BF16 mma.sync.m16n8k16 with
+// FP32 accumulation (k_field_query, k_field_train).
 //
-// Tensor-core data flow: a warp owns 16 points. Its activations stay in registers between
+// Warp-level data flow: a warp owns 16 points. Its activations stay in registers between
 // layers: the FP32 accumulator fragments of two adjacent n8 tiles, rounded to bf16, are exactly
 // the A fragment of the next k16 step. Weights live in shared memory as bf16 rows of 72 entries
 // (64 + 8 padding), which makes every B-fragment load bank-conflict free. In training, the
 // forward activations are also written transposed to shared memory so that the weight gradients
 // dW_l = dZ_l^T H_{l-1} of the block's 128 points are block-level tensor-core products.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -34,6 +37,8 @@ constexpr int FOCT = 10;             // octaves
 constexpr int WS = 72;               // bf16 row stride of weights in shared memory
 constexpr int TS = 136;              // bf16 row stride of transposed activations (128 points + 8)
 constexpr int NPAR = FD * (FW * FW + FW) + FW + 1;   // 16 705
+constexpr int NPAR_PAD = (NPAR + 3) & ~3;            // partial-sum slices, 16-byte aligned
+static_assert(NPAR_PAD > NPAR, "the slices need a padding slot for the loss");
 constexpr int TRAIN_PTS = 128;       // points per training block (8 warps x 16)
 
 __host__ __device__ constexpr int w_off(int l) { return l * (FW * FW + FW); }
@@ -775,6 +780,404 @@ __global__ void __launch_bounds__(256, 1) k_field_train(const float* __restrict_
     for (int i = threadIdx.x; i < FW; i += blockDim.x) atomicAdd(&grad[W5_OFF + i], S.gw5[i]);
 }
 
+// ---- training on the 5th-generation tensor cores ----------------------------------------------
+// Persistent blocks of 256 threads, one per SM; two threads per point (accumulator row): thread
+// (quarter q, half c) owns point 32 q + lane and the columns [32 c, 32 c + 32). Per tile of 128
+// batch points, every product of the hidden layers is a tcgen05.mma (bf16 x bf16, FP32 in tensor
+// memory):
+//   forward   Z_l = H_l W_l^T + b_l        A = H_l rows (K = inputs),   B = W_l   (N = outputs)
+//   backward  dH_l = dZ_l W_l              A = dZ_l rows (K = outputs), B = W_l^T (N = inputs)
+//             gW_l += dZ_l^T H_l           A = dZ_l^T (K = points),     B = H_l^T (N = inputs)
+//             gb_l += dZ_l^T 1             A = dZ_l^T,                  B = a 16 x 128 block whose row 0 is ones
+// The weight and bias gradients accumulate in tensor memory over all tiles of the block and leave
+// it once, into the block's own slice of a partial-sum buffer that the update kernel reduces in a
+// fixed order (deterministic, no atomics on the gradient). The point-major operands (dZ^T, H^T)
+// are written one 2-byte element per (row, point) into a no-swizzle K-major layout whose core
+// matrices sit 144 bytes apart along the points, so that the 32 lanes of a warp (32 consecutive
+// points) store into 32 different banks. The gradient products have 64 real rows (outputs); the
+// MMA runs with M = 128 and rows 64..127 read the next buffer and are never read back. The output
+// layer (w5, b5) and the loss stay in FP32 on the CUDA cores: w5's gradient is a warp transpose-sum.
+// Waits are bounded; on a timeout the block records GM_DEV_WAIT_TIMEOUT, frees its tensor memory
+// and returns.
+constexpr int TT = 128;                        // points per tile
+constexpr int TT_THREADS = 256;
+constexpr uint32_t TT_TMEM_COLS = 512;
+constexpr uint32_t TT_COL_ACC = 0;             // forward / dH accumulator (64 columns)
+constexpr uint32_t TT_COL_GW = 64;             // weight gradients, 64 columns per layer
+constexpr uint32_t TT_COL_GB = 320;            // bias gradients, 16 columns per layer (column 0 used)
+constexpr int T_LBO = 144;                     // point-major operands: core matrices along the points
+constexpr int T_SBO = 16 * T_LBO;              // ... and along the rows
+constexpr int T_BYTES = 8 * T_SBO;             // 64 rows x 128 points
+
+struct TrainTcSmem {
+    alignas(1024) __nv_bfloat16 A[TT * FW];        // rows = points: H_l (forward) or dZ_l (backward)
+    alignas(1024) __nv_bfloat16 W[FD][FW * FW];    // W_l, rows = outputs
+    alignas(1024) __nv_bfloat16 WT[FD][FW * FW];   // W_l^T, rows = inputs
+    alignas(1024) unsigned char DZT[T_BYTES];      // dZ_l^T; rows 64..127 of its M = 128 read HT[0]
+    alignas(1024) unsigned char HT[FD][T_BYTES];   // H_l^T, l = 0..3
+    alignas(1024) unsigned char ONES[2 * T_SBO];   // 16 rows x 128 points, row 0 = 1
+    alignas(16) float bias[FD * FW];
+    float w5[FW + 1];
+    float gw5w[TT_THREADS / 32][32];   // per warp: w5-gradient sums of its 32 columns
+    float zpart[2][TT];
+    float gb5w[4], lossw[4];           // per warp of the first column half
+    alignas(8) uint64_t mbar;
+    uint32_t tmem;
+    int abort;
+};
+
+// Byte offset of element (row, point) of a point-major operand.
+__device__ __forceinline__ int tp_off(int row, int k) {
+    return (k >> 3) * T_LBO + (row >> 3) * T_SBO + (row & 7) * 16 + (k & 7) * 2;
+}
+
+constexpr uint32_t kIdescN64 = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdescN16 = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+#pragma unroll
+    for (int c0 = 0; c0 < 32; c0 += 16)
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::
+                "r"(taddr + c0),
+            "f"(v[c0]), "f"(v[c0 + 1]), "f"(v[c0 + 2]), "f"(v[c0 + 3]), "f"(v[c0 + 4]), "f"(v[c0 + 5]),
+            "f"(v[c0 + 6]), "f"(v[c0 + 7]), "f"(v[c0 + 8]), "f"(v[c0 + 9]), "f"(v[c0 + 10]), "f"(v[c0 + 11]),
+            "f"(v[c0 + 12]), "f"(v[c0 + 13]), "f"(v[c0 + 14]), "f"(v[c0 + 15]));
+}
+
+// This thread's half row (columns c0 .. c0 + 31, 16 packed bf16 pairs) into the K-major A tile and
+// into column p of a point-major operand.
+__device__ __forceinline__ void store_half(__nv_bfloat16* A, unsigned char* T, int p, int c0, const uint32_t* pk) {
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const int kg = c0 / 8 + g;
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(A) + kg * 2048 + (p >> 3) * 128 + (p & 7) * 16) =
+            make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
+    }
+#pragma unroll
+    for (int j = 0; j < 32; j += 2) {
+        *reinterpret_cast<uint16_t*>(T + tp_off(c0 + j, p)) = (uint16_t)(pk[j / 2] & 0xffffu);
+        *reinterpret_cast<uint16_t*>(T + tp_off(c0 + j + 1, p)) = (uint16_t)(pk[j / 2] >> 16);
+    }
+}
+
+__device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+
+// Lane L ends with the sum over the warp's 32 lanes of v[L].
+__device__ __forceinline__ float warp_transpose_sum(float v[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < o; ++j) {
+            const float send = up ? v[j] : v[j + o];
+            const float keep = up ? v[j + o] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
+__global__ void __launch_bounds__(TT_THREADS, 1) k_field_train_tc(
+    const float* __restrict__ pts, int stride, const float* __restrict__ target, uint64_t n,
+    const uint32_t* __restrict__ idx, uint32_t batch, uint32_t step, uint2 seed, FieldBox B,
+    const __nv_bfloat16* __restrict__ wbf, const __nv_bfloat16* __restrict__ wtbf, const float* __restrict__ theta,
+    float* __restrict__ partial, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char t_smem_raw[];
+    TrainTcSmem& S = *reinterpret_cast<TrainTcSmem*>(t_smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, c = warp >> 2;
+    const int p = 32 * q + lane, c0 = 32 * c;
+    // weights in the core-matrix layout: (n, k) at (k / 8) * 1024 + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2
+    for (int i = tid; i < FD * FW * 8; i += TT_THREADS) {
+        const int l = i / (FW * 8), nn = (i / 8) % FW, kg = i % 8;
+        const size_t src = (size_t)l * FW * FW + nn * FW;
+        const int dst = kg * 1024 + (nn >> 3) * 128 + (nn & 7) * 16;
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(S.W[l]) + dst) = reinterpret_cast<const uint4*>(wbf + src)[kg];
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(S.WT[l]) + dst) =
+            reinterpret_cast<const uint4*>(wtbf + src)[kg];
+    }
+    for (int i = tid; i < 2 * T_SBO / 16; i += TT_THREADS) reinterpret_cast<uint4*>(S.ONES)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < FD * FW; i += TT_THREADS) S.bias[i] = theta[b_off(i / FW) + i % FW];
+    for (int i = tid; i <= FW; i += TT_THREADS) S.w5[i] = theta[W5_OFF + i];
+    S.gw5w[warp][lane] = 0.f;
+    if (tid == 0) {
+        S.abort = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&S.tmem)),
+                     "r"(TT_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    if (tid < TT) *reinterpret_cast<uint16_t*>(S.ONES + tp_off(0, tid)) = 0x3F80;   // bf16 1.0
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tm = S.tmem;
+    const uint32_t row_acc = tm + ((uint32_t)(32 * q) << 16) + TT_COL_ACC + c0;
+    const uint32_t a_addr = smem_addr(S.A), dzt_addr = smem_addr(S.DZT), ones_addr = smem_addr(S.ONES);
+    const uint32_t ntiles = (batch + TT - 1) / TT;
+    const float inv_b = 1.f / (float)batch;
+    uint32_t ph = 0;
+    bool first = true, stop = false;
+    float loss_acc = 0.f, gb5_acc = 0.f;
+    // bounded wait on the block's MMA barrier; every thread takes part
+    auto sync_mma = [&]() {
+        if (!mbar_wait(smem_addr(&S.mbar), ph)) S.abort = 1;
+        ph ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+    };
+    auto block_sync = [&]() {
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        return S.abort != 0;
+    };
+    for (uint32_t tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
+        const uint32_t e = tile * TT + p;
+        uint64_t i = n;
+        if (e < batch) i = idx ? (uint64_t)idx[e] : (uint64_t)(philox_x(step, e, seed.x, seed.y) % (uint32_t)n);
+        float xt[3] = {0.f, 0.f, 0.f};
+        if (i < n) {
+            xt[0] = (pts[stride * i] - B.cx) * B.inv_h;
+            xt[1] = (pts[stride * i + 1] - B.cy) * B.inv_h;
+            xt[2] = (pts[stride * i + 2] - B.cz) * B.inv_h;
+        }
+        uint32_t pk[16];
+        {
+            float v[FW];
+            features_fast(xt, v);
+#pragma unroll
+            for (int j = 0; j < 32; j += 2)   // static indices keep v in registers
+                pk[j / 2] = c ? pack_bf16(v[32 + j], v[33 + j]) : pack_bf16(v[j], v[j + 1]);
+        }
+        store_half(S.A, S.HT[0], p, c0, pk);
+        uint32_t mask[FD];
+        float zp = 0.f;
+#pragma unroll
+        for (int l = 0; l < FD; ++l) {
+            tmem_st32(row_acc, S.bias + l * FW + c0);
+            asm volatile("tcgen05.wait::st.sync.aligned;");
+            if (block_sync()) {
+                stop = true;
+                break;
+            }
+            if (tid == 0) {
+                const uint32_t w_addr = smem_addr(S.W[l]);
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    umma_bf16(tm + TT_COL_ACC, umma_desc(a_addr + s * 4096, 2048, 128),
+                              umma_desc(w_addr + s * 2048, 1024, 128), kIdescN64, 1u);
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_addr(&S.mbar)));
+            }
+            sync_mma();
+            float z[32];
+            tmem_ld16(row_acc, z);
+            tmem_ld16(row_acc + 16, z + 16);
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.f, 0.f);
+            uint32_t m = 0;
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+                __nv_bfloat162 h2 = __hmax2(__floats2bfloat162_rn(z[j], z[j + 1]), zero2);
+                pk[j / 2] = *reinterpret_cast<uint32_t*>(&h2);
+                m |= (z[j] > 0.f ? 1u : 0u) << j;
+                m |= (z[j + 1] > 0.f ? 1u : 0u) << (j + 1);
+            }
+            mask[l] = m;
+            if (l + 1 < FD) {
+                store_half(S.A, S.HT[l + 1], p, c0, pk);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; j += 2) {
+                    zp = fmaf(bf_lo(pk[j / 2]), S.w5[c0 + j], zp);
+                    zp = fmaf(bf_hi(pk[j / 2]), S.w5[c0 + j + 1], zp);
+                }
+            }
+        }
+        if (stop) break;
+        // output layer: both halves form z5 in the same order
+        S.zpart[c][p] = zp;
+        __syncthreads();
+        const float z5 = (S.zpart[0][p] + S.zpart[1][p]) + S.w5[FW];
+        const float y = i < n ? target[i] : 0.f;
+        const float r = e < batch ? softplusf(z5) - y : 0.f;
+        const float dz5 = 2.f * r * inv_b * sigmoidf_(z5);
+        if (c == 0) {
+            loss_acc = fmaf(r, r, loss_acc);
+            gb5_acc += dz5;
+        }
+        {
+            float gv[32];
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+                gv[j] = dz5 * bf_lo(pk[j / 2]);
+                gv[j + 1] = dz5 * bf_hi(pk[j / 2]);
+            }
+            S.gw5w[warp][lane] += warp_transpose_sum(gv);
+        }
+        // dZ_3 = bf16(dz5 w5 . [z_3 > 0])
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) {
+            const float d0 = (mask[FD - 1] >> j) & 1u ? dz5 * S.w5[c0 + j] : 0.f;
+            const float d1 = (mask[FD - 1] >> (j + 1)) & 1u ? dz5 * S.w5[c0 + j + 1] : 0.f;
+            pk[j / 2] = pack_bf16(d0, d1);
+        }
+        store_half(S.A, S.DZT, p, c0, pk);
+#pragma unroll
+        for (int l = FD - 1; l >= 0; --l) {
+            if (block_sync()) {
+                stop = true;
+                break;
+            }
+            if (tid == 0) {
+                const uint32_t ht_addr = smem_addr(S.HT[l]);
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const uint32_t acc = (!first || s > 0) ? 1u : 0u;
+                    const uint64_t da = umma_desc(dzt_addr + s * 2 * T_LBO, T_LBO, T_SBO);
+                    umma_bf16(tm + TT_COL_GW + 64 * l, da, umma_desc(ht_addr + s * 2 * T_LBO, T_LBO, T_SBO),
+                              kIdescN64, acc);
+                    umma_bf16(tm + TT_COL_GB + 16 * l, da, umma_desc(ones_addr + s * 2 * T_LBO, T_LBO, T_SBO),
+                              kIdescN16, acc);
+                }
+                if (l > 0) {
+                    const uint32_t wt_addr = smem_addr(S.WT[l]);
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+                        umma_bf16(tm + TT_COL_ACC, umma_desc(a_addr + s * 4096, 2048, 128),
+                                  umma_desc(wt_addr + s * 2048, 1024, 128), kIdescN64, s > 0 ? 1u : 0u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_addr(&S.mbar)));
+            }
+            sync_mma();
+            if (l > 0) {
+                // dZ_{l-1} = bf16(dH_l . [z_{l-1} > 0])
+                float dh[32];
+                tmem_ld16(row_acc, dh);
+                tmem_ld16(row_acc + 16, dh + 16);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                for (int j = 0; j < 32; j += 2) {
+                    const float d0 = (mask[l - 1] >> j) & 1u ? dh[j] : 0.f;
+                    const float d1 = (mask[l - 1] >> (j + 1)) & 1u ? dh[j + 1] : 0.f;
+                    pk[j / 2] = pack_bf16(d0, d1);
+                }
+                store_half(S.A, S.DZT, p, c0, pk);
+            }
+        }
+        first = false;
+    }
+    // the block's sums into its slice of the partial-sum buffer
+    if (c == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
+            gb5_acc += __shfl_xor_sync(0xffffffffu, gb5_acc, o);
+        }
+        if (lane == 0) {
+            S.lossw[q] = loss_acc;
+            S.gb5w[q] = gb5_acc;
+        }
+    }
+    const bool ok = !block_sync() && !stop;
+    float* P = partial + (size_t)blockIdx.x * NPAR_PAD;
+    if (ok && q < 2) {
+        // accumulator rows 0..63 are the outputs of each layer
+#pragma unroll 1
+        for (int l = 0; l < FD; ++l) {
+            float v[32];
+            const uint32_t ra = tm + ((uint32_t)(32 * q) << 16) + TT_COL_GW + 64 * l + c0;
+            if (first) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = 0.f;
+            } else {
+                tmem_ld16(ra, v);
+                tmem_ld16(ra + 16, v + 16);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+            }
+            float4* dst = reinterpret_cast<float4*>(P + w_off(l) + p * FW + c0);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            if (c == 0) {
+                float gb[16];
+                if (first) gb[0] = 0.f;
+                else {
+                    tmem_ld16(tm + ((uint32_t)(32 * q) << 16) + TT_COL_GB + 16 * l, gb);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+                }
+                P[b_off(l) + p] = gb[0];
+            }
+        }
+    }
+    if (ok) {
+        // warps in a fixed order: the block's sums do not depend on scheduling
+        if (tid < FW) {
+            const int h = tid >> 5, j = tid & 31;
+            P[W5_OFF + tid] = ((S.gw5w[4 * h][j] + S.gw5w[4 * h + 1][j]) + S.gw5w[4 * h + 2][j]) + S.gw5w[4 * h + 3][j];
+        }
+        if (tid == 0) {
+            P[B5_OFF] = ((S.gb5w[0] + S.gb5w[1]) + S.gb5w[2]) + S.gb5w[3];
+            P[NPAR] = ((S.lossw[0] + S.lossw[1]) + S.lossw[2]) + S.lossw[3];   // the padding slot
+        }
+    }
+    if (S.abort && tid == 0) atomicCAS(err, 0, GM_DEV_WAIT_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(TT_TMEM_COLS));
+}
+
+// Gradient = the fixed-order sum of the blocks' partial sums; then either that gradient is
+// stored (grad_out) or one Adam step is taken (and the bf16 copies of the weights refreshed).
+// The blocks' squared-error sums (in the slices' padding slot) go to loss_sum the same way.
+__global__ void k_field_update(const float* __restrict__ partial, int nblk, float* __restrict__ loss_sum,
+                               float* __restrict__ grad_out, float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v, float lr,
+                               float bc1, float bc2, __nv_bfloat16* __restrict__ wbf,
+                               __nv_bfloat16* __restrict__ wtbf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        float l = 0.f;
+        for (int b = 0; b < nblk; ++b) l += partial[(size_t)b * NPAR_PAD + NPAR];
+        *loss_sum = l;
+    }
+    if (i >= NPAR) return;
+    float g = 0.f;
+    for (int b = 0; b < nblk; ++b) g += partial[(size_t)b * NPAR_PAD + i];
+    if (grad_out) {
+        grad_out[i] = g;
+        return;
+    }
+    const float mi = 0.9f * m[i] + 0.1f * g;
+    const float vi = 0.999f * v[i] + 0.001f * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float th = theta[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+    theta[i] = th;
+    const int l = i / (FW * FW + FW), o = i % (FW * FW + FW);
+    if (l < FD && o < FW * FW) {
+        const int r = o / FW, cc = o % FW;
+        const __nv_bfloat16 b = __float2bfloat16_rn(th);
+        wbf[l * FW * FW + r * FW + cc] = b;
+        wtbf[l * FW * FW + cc * FW + r] = b;
+    }
+}
+
 }  // namespace
 
 struct gm_field {
@@ -787,9 +1190,13 @@ struct gm_field {
     float last_loss = 0.f;
     float train_ms = 0.f;
     int32_t query_kernel = GM_FIELD_QUERY_TCGEN05;
+    int32_t train_kernel = GM_FIELD_QUERY_TCGEN05;
+    float* partial = nullptr;   // per-block gradient sums of the tensor-core training kernel
+    int nblk = 0;               // blocks of the last tensor-core gradient launch
 };
 
 static const size_t kTrainSmem = sizeof(TrainSmem);
+static const size_t kTrainTcSmem = sizeof(TrainTcSmem);
 
 extern "C" gm_status gm_field_create(gm_ctx* ctx, const float* box_lo, const float* box_hi, const float* init_params,
                                      gm_stream stream, gm_field** out) {
@@ -823,7 +1230,8 @@ extern "C" gm_status gm_field_create(gm_ctx* ctx, const float* box_lo, const flo
         (st = gm_alloc((void**)&f->grad, sizeof(float) * NPAR, s)) != GM_OK ||
         (st = gm_alloc((void**)&f->loss, sizeof(float) * 4, s)) != GM_OK ||
         (st = gm_alloc((void**)&f->wbf, sizeof(__nv_bfloat16) * FD * FW * FW, s)) != GM_OK ||
-        (st = gm_alloc((void**)&f->wtbf, sizeof(__nv_bfloat16) * FD * FW * FW, s)) != GM_OK)
+        (st = gm_alloc((void**)&f->wtbf, sizeof(__nv_bfloat16) * FD * FW * FW, s)) != GM_OK ||
+        (st = gm_alloc((void**)&f->partial, sizeof(float) * NPAR_PAD * (size_t)std::max(1, ctx->n_sm), s)) != GM_OK)
         return fail(st);
     cudaError_t e = cudaMemcpyAsync(f->theta, init_params, sizeof(float) * NPAR, cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(f->m, 0, sizeof(float) * NPAR, s);
@@ -833,6 +1241,8 @@ extern "C" gm_status gm_field_create(gm_ctx* ctx, const float* box_lo, const flo
     k_field_cast<<<gm_div_up(FD * FW * FW, 256), 256, 0, s>>>(f->theta, f->wbf, f->wtbf);
     ctx->launches += 1;
     e = cudaFuncSetAttribute(k_field_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_field_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainTcSmem);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_field_create"));
     *out = f;
@@ -842,6 +1252,17 @@ extern "C" gm_status gm_field_create(gm_ctx* ctx, const float* box_lo, const flo
 static gm_status field_grad(gm_field* f, const float* pts, int stride, const float* target, uint64_t n,
                             const uint32_t* idx, uint32_t batch, uint32_t step, uint64_t seed, cudaStream_t s) {
     GM_TRY_CUDA(cudaMemsetAsync(f->loss, 0, sizeof(float), s));
+    if (f->train_kernel == GM_FIELD_QUERY_TCGEN05) {
+        const uint32_t ntiles = (batch + TT - 1) / TT;
+        const int grid = (int)std::min<uint32_t>((uint32_t)std::max(1, f->ctx->n_sm), ntiles);
+        k_field_train_tc<<<grid, TT_THREADS, kTrainTcSmem, s>>>(
+            pts, stride, target, n, idx, batch, step, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), f->box,
+            f->wbf, f->wtbf, f->theta, f->partial, f->ctx->dev_err);
+        f->nblk = grid;
+        f->ctx->launches += 1;
+        GM_TRY_CUDA(cudaGetLastError());
+        return GM_OK;
+    }
     k_field_train<<<gm_div_up(batch, TRAIN_PTS), 256, kTrainSmem, s>>>(
         pts, stride, target, n, idx, batch, step, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), f->box, f->wbf,
         f->wtbf, f->theta, f->grad, f->loss);
@@ -854,7 +1275,12 @@ static gm_status field_adam(gm_field* f, float lr, cudaStream_t s) {
     f->t += 1;
     const float bc1 = (float)(1.0 - std::pow(0.9, (double)f->t));
     const float bc2 = (float)(1.0 - std::pow(0.999, (double)f->t));
-    k_field_adam<<<gm_div_up(NPAR, 256), 256, 0, s>>>(f->theta, f->m, f->v, f->grad, lr, bc1, bc2, f->wbf, f->wtbf);
+    if (f->train_kernel == GM_FIELD_QUERY_TCGEN05)
+        k_field_update<<<gm_div_up(NPAR, 256), 256, 0, s>>>(f->partial, f->nblk, f->loss, nullptr, f->theta, f->m,
+                                                            f->v, lr, bc1, bc2, f->wbf, f->wtbf);
+    else
+        k_field_adam<<<gm_div_up(NPAR, 256), 256, 0, s>>>(f->theta, f->m, f->v, f->grad, lr, bc1, bc2, f->wbf,
+                                                          f->wtbf);
     f->ctx->launches += 1;
     GM_TRY_CUDA(cudaGetLastError());
     return GM_OK;
@@ -869,6 +1295,12 @@ extern "C" gm_status gm_field_loss_grad(gm_field* f, const float* xyz, const flo
         return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_loss_grad: inputs must be device memory");
     cudaStream_t s = (cudaStream_t)stream;
     GM_TRY(field_grad(f, xyz, 3, target, n, batch_idx, batch, 0, 0, s));
+    if (f->train_kernel == GM_FIELD_QUERY_TCGEN05) {
+        k_field_update<<<gm_div_up(NPAR, 256), 256, 0, s>>>(f->partial, f->nblk, f->loss, f->grad, nullptr, nullptr,
+                                                            nullptr, 0.f, 1.f, 1.f, nullptr, nullptr);
+        f->ctx->launches += 1;
+        GM_TRY_CUDA(cudaGetLastError());
+    }
     if (grad_out) GM_TRY(gm_copy_out(grad_out, f->grad, sizeof(float) * NPAR, s));
     if (loss_out) {
         float l = 0.f;
@@ -991,6 +1423,14 @@ extern "C" gm_status gm_field_query_kernel(gm_field* f, int32_t kernel) {
     return GM_OK;
 }
 
+extern "C" gm_status gm_field_train_kernel(gm_field* f, int32_t kernel) {
+    if (!f) return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_train_kernel: null field");
+    if (kernel != GM_FIELD_QUERY_TCGEN05 && kernel != GM_FIELD_QUERY_MMA_SYNC)
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_train_kernel: unknown kernel");
+    f->train_kernel = kernel;
+    return GM_OK;
+}
+
 extern "C" gm_status gm_field_params(const gm_field* f, float* out, gm_stream stream) {
     if (!f || !out) return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_params: null argument");
     return gm_copy_out(out, f->theta, sizeof(float) * NPAR, (cudaStream_t)stream);
@@ -1015,5 +1455,6 @@ extern "C" void gm_field_free(gm_field* f) {
     cudaFree(f->loss);
     cudaFree(f->wbf);
     cudaFree(f->wtbf);
+    cudaFree(f->partial);
     delete f;
 }

@@ -138,6 +138,7 @@ _SIGS = {
     "gm_field_loss_grad": (C.c_int, [_P, _P, _P, C.c_uint64, _P, C.c_uint32, _P, C.POINTER(C.c_float), _P]),
     "gm_field_query": (C.c_int, [_P, _P, C.c_uint64, _P, _P]),
     "gm_field_query_kernel": (C.c_int, [_P, C.c_int32]),
+    "gm_field_train_kernel": (C.c_int, [_P, C.c_int32]),
     "gm_field_params": (C.c_int, [_P, _P, _P]),
     "gm_field_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_float),
                                 C.POINTER(C.c_float)]),
@@ -516,6 +517,10 @@ GM_FIELD_QUERY_TCGEN05, GM_FIELD_QUERY_MMA_SYNC = 0, 1
 
 def gm_field_query_kernel(field, kernel: int) -> None:
     _check(lib().gm_field_query_kernel(field, int(kernel)))
+
+
+def gm_field_train_kernel(field, kernel: int) -> None:
+    _check(lib().gm_field_train_kernel(field, int(kernel)))
 
 
 def gm_field_query(field, xyz, n: int, out, stream=None) -> None:
