@@ -800,7 +800,9 @@ __global__ void __launch_bounds__(256, 1) k_field_train(const float* __restrict_
 // Waits are bounded; on a timeout the block records GM_DEV_WAIT_TIMEOUT, frees its tensor memory
 // and returns.
 constexpr int TT = 128;                        // points per tile
-constexpr int TT_THREADS = 256;
+constexpr int TT_CW = 32;                      // accumulator columns per thread (16: 53.9 vs 49.8 us a step)
+constexpr int TT_GROUPS = FW / TT_CW;          // threads per point
+constexpr int TT_THREADS = TT * TT_GROUPS;
 constexpr uint32_t TT_TMEM_COLS = 512;
 constexpr uint32_t TT_COL_ACC = 0;             // forward / dH accumulator (64 columns)
 constexpr uint32_t TT_COL_GW = 64;             // weight gradients, 64 columns per layer
@@ -818,8 +820,8 @@ struct TrainTcSmem {
     alignas(1024) unsigned char ONES[2 * T_SBO];   // 16 rows x 128 points, row 0 = 1
     alignas(16) float bias[FD * FW];
     float w5[FW + 1];
-    float gw5w[TT_THREADS / 32][32];   // per warp: w5-gradient sums of its 32 columns
-    float zpart[2][TT];
+    float gw5w[TT_THREADS / 32][32];   // per warp: w5-gradient sums of its columns
+    float zpart[TT_GROUPS][TT];
     float gb5w[4], lossw[4];           // per warp of the first column half
     alignas(8) uint64_t mbar;
     uint32_t tmem;
@@ -841,9 +843,9 @@ __device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t da, uint64_t db, 
         "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+__device__ __forceinline__ void tmem_st_cw(uint32_t taddr, const float* v) {
 #pragma unroll
-    for (int c0 = 0; c0 < 32; c0 += 16)
+    for (int c0 = 0; c0 < TT_CW; c0 += 16)
         asm volatile(
             "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::
                 "r"(taddr + c0),
@@ -852,17 +854,17 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
             "f"(v[c0 + 12]), "f"(v[c0 + 13]), "f"(v[c0 + 14]), "f"(v[c0 + 15]));
 }
 
-// This thread's half row (columns c0 .. c0 + 31, 16 packed bf16 pairs) into the K-major A tile and
-// into column p of a point-major operand.
-__device__ __forceinline__ void store_half(__nv_bfloat16* A, unsigned char* T, int p, int c0, const uint32_t* pk) {
+// This thread's part of a row (columns c0 .. c0 + TT_CW - 1 as packed bf16 pairs) into the K-major
+// A tile and into column p of a point-major operand.
+__device__ __forceinline__ void store_part(__nv_bfloat16* A, unsigned char* T, int p, int c0, const uint32_t* pk) {
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
+    for (int g = 0; g < TT_CW / 8; ++g) {
         const int kg = c0 / 8 + g;
         *reinterpret_cast<uint4*>(reinterpret_cast<char*>(A) + kg * 2048 + (p >> 3) * 128 + (p & 7) * 16) =
             make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
     }
 #pragma unroll
-    for (int j = 0; j < 32; j += 2) {
+    for (int j = 0; j < TT_CW; j += 2) {
         *reinterpret_cast<uint16_t*>(T + tp_off(c0 + j, p)) = (uint16_t)(pk[j / 2] & 0xffffu);
         *reinterpret_cast<uint16_t*>(T + tp_off(c0 + j + 1, p)) = (uint16_t)(pk[j / 2] >> 16);
     }
@@ -871,11 +873,16 @@ __device__ __forceinline__ void store_half(__nv_bfloat16* A, unsigned char* T, i
 __device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
 
-// Lane L ends with the sum over the warp's 32 lanes of v[L].
-__device__ __forceinline__ float warp_transpose_sum(float v[32]) {
+// Lane L ends with the sum over the warp's 32 lanes of v[L mod TT_CW].
+__device__ __forceinline__ float warp_transpose_sum(float v[TT_CW]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
+    for (int o = 16; o >= TT_CW; o >>= 1) {
+#pragma unroll
+        for (int j = 0; j < TT_CW; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+    }
+#pragma unroll
+    for (int o = TT_CW / 2; o >= 1; o >>= 1) {
         const bool up = (lane & o) != 0;
 #pragma unroll
         for (int j = 0; j < o; ++j) {
@@ -896,7 +903,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_field_train_tc(
     TrainTcSmem& S = *reinterpret_cast<TrainTcSmem*>(t_smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, c = warp >> 2;
-    const int p = 32 * q + lane, c0 = 32 * c;
+    const int p = 32 * q + lane, c0 = TT_CW * c;
     // weights in the core-matrix layout: (n, k) at (k / 8) * 1024 + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2
     for (int i = tid; i < FD * FW * 8; i += TT_THREADS) {
         const int l = i / (FW * 8), nn = (i / 8) % FW, kg = i % 8;
@@ -947,30 +954,52 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_field_train_tc(
         asm volatile("tcgen05.fence::after_thread_sync;");
         return S.abort != 0;
     };
+    // the batch entry of this thread's point in a tile, its position and target; issued one tile
+    // ahead so that the random gathers are in flight while the previous tile computes
+    uint32_t ne = 0;
+    uint64_t ni = n;
+    float nx[3] = {0.f, 0.f, 0.f}, ny = 0.f;
+    auto prefetch = [&](uint32_t t) {
+        ne = t * TT + p;
+        ni = n;
+        if (t < ntiles && ne < batch)
+            ni = idx ? (uint64_t)idx[ne] : (uint64_t)(philox_x(step, ne, seed.x, seed.y) % (uint32_t)n);
+        if (ni < n) {
+            nx[0] = pts[stride * ni];
+            nx[1] = pts[stride * ni + 1];
+            nx[2] = pts[stride * ni + 2];
+            ny = target[ni];
+        }
+    };
+    prefetch(blockIdx.x);
     for (uint32_t tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
-        const uint32_t e = tile * TT + p;
-        uint64_t i = n;
-        if (e < batch) i = idx ? (uint64_t)idx[e] : (uint64_t)(philox_x(step, e, seed.x, seed.y) % (uint32_t)n);
+        const uint32_t e = ne;
+        const uint64_t i = ni;
         float xt[3] = {0.f, 0.f, 0.f};
         if (i < n) {
-            xt[0] = (pts[stride * i] - B.cx) * B.inv_h;
-            xt[1] = (pts[stride * i + 1] - B.cy) * B.inv_h;
-            xt[2] = (pts[stride * i + 2] - B.cz) * B.inv_h;
+            xt[0] = (nx[0] - B.cx) * B.inv_h;
+            xt[1] = (nx[1] - B.cy) * B.inv_h;
+            xt[2] = (nx[2] - B.cz) * B.inv_h;
         }
-        uint32_t pk[16];
+        const float y = i < n ? ny : 0.f;
+        prefetch(tile + gridDim.x);
+        uint32_t pk[TT_CW / 2];
         {
             float v[FW];
             features_fast(xt, v);
 #pragma unroll
-            for (int j = 0; j < 32; j += 2)   // static indices keep v in registers
-                pk[j / 2] = c ? pack_bf16(v[32 + j], v[33 + j]) : pack_bf16(v[j], v[j + 1]);
+            for (int g = 0; g < TT_GROUPS; ++g)   // static indices keep v in registers
+                if (g == c) {
+#pragma unroll
+                    for (int j = 0; j < TT_CW; j += 2) pk[j / 2] = pack_bf16(v[g * TT_CW + j], v[g * TT_CW + j + 1]);
+                }
         }
-        store_half(S.A, S.HT[0], p, c0, pk);
+        store_part(S.A, S.HT[0], p, c0, pk);
         uint32_t mask[FD];
         float zp = 0.f;
 #pragma unroll
         for (int l = 0; l < FD; ++l) {
-            tmem_st32(row_acc, S.bias + l * FW + c0);
+            tmem_st_cw(row_acc, S.bias + l * FW + c0);
             asm volatile("tcgen05.wait::st.sync.aligned;");
             if (block_sync()) {
                 stop = true;
@@ -986,14 +1015,14 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_field_train_tc(
                     smem_addr(&S.mbar)));
             }
             sync_mma();
-            float z[32];
-            tmem_ld16(row_acc, z);
-            tmem_ld16(row_acc + 16, z + 16);
+            float z[TT_CW];
+#pragma unroll
+            for (int j = 0; j < TT_CW; j += 16) tmem_ld16(row_acc + j, z + j);
             asm volatile("tcgen05.wait::ld.sync.aligned;");
             const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.f, 0.f);
             uint32_t m = 0;
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
+            for (int j = 0; j < TT_CW; j += 2) {
                 __nv_bfloat162 h2 = __hmax2(__floats2bfloat162_rn(z[j], z[j + 1]), zero2);
                 pk[j / 2] = *reinterpret_cast<uint32_t*>(&h2);
                 m |= (z[j] > 0.f ? 1u : 0u) << j;
@@ -1001,10 +1030,10 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_field_train_tc(
             }
             mask[l] = m;
             if (l + 1 < FD) {
-                store_half(S.A, S.HT[l + 1], p, c0, pk);
+                store_part(S.A, S.HT[l + 1], p, c0, pk);
             } else {
 #pragma unroll
-                for (int j = 0; j < 32; j += 2) {
+                for (int j = 0; j < TT_CW; j += 2) {
                     zp = fmaf(bf_lo(pk[j / 2]), S.w5[c0 + j], zp);
                     zp = fmaf(bf_hi(pk[j / 2]), S.w5[c0 + j + 1], zp);
                 }
@@ -1014,8 +1043,10 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_field_train_tc(
         // output layer: both halves form z5 in the same order
         S.zpart[c][p] = zp;
         __syncthreads();
-        const float z5 = (S.zpart[0][p] + S.zpart[1][p]) + S.w5[FW];
-        const float y = i < n ? target[i] : 0.f;
+        float z5 = S.zpart[0][p];
+#pragma unroll
+        for (int g = 1; g < TT_GROUPS; ++g) z5 += S.zpart[g][p];
+        z5 += S.w5[FW];
         const float r = e < batch ? softplusf(z5) - y : 0.f;
         const float dz5 = 2.f * r * inv_b * sigmoidf_(z5);
         if (c == 0) {
@@ -1023,9 +1054,9 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_field_train_tc(
             gb5_acc += dz5;
         }
         {
-            float gv[32];
+            float gv[TT_CW];
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
+            for (int j = 0; j < TT_CW; j += 2) {
                 gv[j] = dz5 * bf_lo(pk[j / 2]);
                 gv[j + 1] = dz5 * bf_hi(pk[j / 2]);
             }
@@ -1033,12 +1064,12 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_field_train_tc(
         }
         // dZ_3 = bf16(dz5 w5 . [z_3 > 0])
 #pragma unroll
-        for (int j = 0; j < 32; j += 2) {
+        for (int j = 0; j < TT_CW; j += 2) {
             const float d0 = (mask[FD - 1] >> j) & 1u ? dz5 * S.w5[c0 + j] : 0.f;
             const float d1 = (mask[FD - 1] >> (j + 1)) & 1u ? dz5 * S.w5[c0 + j + 1] : 0.f;
             pk[j / 2] = pack_bf16(d0, d1);
         }
-        store_half(S.A, S.DZT, p, c0, pk);
+        store_part(S.A, S.DZT, p, c0, pk);
 #pragma unroll
         for (int l = FD - 1; l >= 0; --l) {
             if (block_sync()) {
@@ -1069,17 +1100,17 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_field_train_tc(
             sync_mma();
             if (l > 0) {
                 // dZ_{l-1} = bf16(dH_l . [z_{l-1} > 0])
-                float dh[32];
-                tmem_ld16(row_acc, dh);
-                tmem_ld16(row_acc + 16, dh + 16);
+                float dh[TT_CW];
+#pragma unroll
+                for (int j = 0; j < TT_CW; j += 16) tmem_ld16(row_acc + j, dh + j);
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-                for (int j = 0; j < 32; j += 2) {
+                for (int j = 0; j < TT_CW; j += 2) {
                     const float d0 = (mask[l - 1] >> j) & 1u ? dh[j] : 0.f;
                     const float d1 = (mask[l - 1] >> (j + 1)) & 1u ? dh[j + 1] : 0.f;
                     pk[j / 2] = pack_bf16(d0, d1);
                 }
-                store_half(S.A, S.DZT, p, c0, pk);
+                store_part(S.A, S.DZT, p, c0, pk);
             }
         }
         first = false;
@@ -1102,19 +1133,19 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_field_train_tc(
         // accumulator rows 0..63 are the outputs of each layer
 #pragma unroll 1
         for (int l = 0; l < FD; ++l) {
-            float v[32];
+            float v[TT_CW];
             const uint32_t ra = tm + ((uint32_t)(32 * q) << 16) + TT_COL_GW + 64 * l + c0;
             if (first) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = 0.f;
+                for (int j = 0; j < TT_CW; ++j) v[j] = 0.f;
             } else {
-                tmem_ld16(ra, v);
-                tmem_ld16(ra + 16, v + 16);
+#pragma unroll
+                for (int j = 0; j < TT_CW; j += 16) tmem_ld16(ra + j, v + j);
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
             }
             float4* dst = reinterpret_cast<float4*>(P + w_off(l) + p * FW + c0);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            for (int j = 0; j < TT_CW / 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
             if (c == 0) {
                 float gb[16];
                 if (first) gb[0] = 0.f;
@@ -1129,8 +1160,8 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_field_train_tc(
     if (ok) {
         // warps in a fixed order: the block's sums do not depend on scheduling
         if (tid < FW) {
-            const int h = tid >> 5, j = tid & 31;
-            P[W5_OFF + tid] = ((S.gw5w[4 * h][j] + S.gw5w[4 * h + 1][j]) + S.gw5w[4 * h + 2][j]) + S.gw5w[4 * h + 3][j];
+            const int g = tid / TT_CW, j = tid % TT_CW;   // column group and column within it
+            P[W5_OFF + tid] = ((S.gw5w[4 * g][j] + S.gw5w[4 * g + 1][j]) + S.gw5w[4 * g + 2][j]) + S.gw5w[4 * g + 3][j];
         }
         if (tid == 0) {
             P[B5_OFF] = ((S.gb5w[0] + S.gb5w[1]) + S.gb5w[2]) + S.gb5w[3];
@@ -1145,20 +1176,32 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_field_train_tc(
 
 // Gradient = the fixed-order sum of the blocks' partial sums; then either that gradient is
 // stored (grad_out) or one Adam step is taken (and the bf16 copies of the weights refreshed).
-// The blocks' squared-error sums (in the slices' padding slot) go to loss_sum the same way.
-__global__ void k_field_update(const float* __restrict__ partial, int nblk, float* __restrict__ loss_sum,
-                               float* __restrict__ grad_out, float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v, float lr,
-                               float bc1, float bc2, __nv_bfloat16* __restrict__ wbf,
-                               __nv_bfloat16* __restrict__ wtbf) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) {
-        float l = 0.f;
-        for (int b = 0; b < nblk; ++b) l += partial[(size_t)b * NPAR_PAD + NPAR];
-        *loss_sum = l;
-    }
-    if (i >= NPAR) return;
+// A block of 8 warps handles 32 consecutive entries: warp w adds the slices b = w, w + 8, ... in
+// order, then the eight warp sums are added in warp order. Entry NPAR of every slice (padding)
+// holds a block's squared-error sum; its total goes to loss_sum.
+constexpr int UPD_WARPS = 8;
+__global__ void __launch_bounds__(32 * UPD_WARPS) k_field_update(
+    const float* __restrict__ partial, int nblk, float* __restrict__ loss_sum, float* __restrict__ grad_out,
+    float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v, float lr, float bc1, float bc2,
+    __nv_bfloat16* __restrict__ wbf, __nv_bfloat16* __restrict__ wtbf) {
+    __shared__ float red[UPD_WARPS][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 32 + lane;
     float g = 0.f;
-    for (int b = 0; b < nblk; ++b) g += partial[(size_t)b * NPAR_PAD + i];
+    if (i <= NPAR) {
+#pragma unroll 4
+        for (int b = w; b < nblk; b += UPD_WARPS) g += partial[(size_t)b * NPAR_PAD + i];
+    }
+    red[w][lane] = g;
+    __syncthreads();
+    if (w != 0 || i > NPAR) return;
+    g = red[0][lane];
+#pragma unroll
+    for (int k = 1; k < UPD_WARPS; ++k) g += red[k][lane];
+    if (i == NPAR) {
+        *loss_sum = g;
+        return;
+    }
     if (grad_out) {
         grad_out[i] = g;
         return;
@@ -1197,6 +1240,7 @@ struct gm_field {
 
 static const size_t kTrainSmem = sizeof(TrainSmem);
 static const size_t kTrainTcSmem = sizeof(TrainTcSmem);
+static const int kUpdateGrid = (NPAR + 1 + 31) / 32;   // entries 0..NPAR (the last is the loss)
 
 extern "C" gm_status gm_field_create(gm_ctx* ctx, const float* box_lo, const float* box_hi, const float* init_params,
                                      gm_stream stream, gm_field** out) {
@@ -1251,8 +1295,7 @@ extern "C" gm_status gm_field_create(gm_ctx* ctx, const float* box_lo, const flo
 
 static gm_status field_grad(gm_field* f, const float* pts, int stride, const float* target, uint64_t n,
                             const uint32_t* idx, uint32_t batch, uint32_t step, uint64_t seed, cudaStream_t s) {
-    GM_TRY_CUDA(cudaMemsetAsync(f->loss, 0, sizeof(float), s));
-    if (f->train_kernel == GM_FIELD_QUERY_TCGEN05) {
+    if (f->train_kernel == GM_FIELD_QUERY_TCGEN05) {   // the update kernel writes the loss
         const uint32_t ntiles = (batch + TT - 1) / TT;
         const int grid = (int)std::min<uint32_t>((uint32_t)std::max(1, f->ctx->n_sm), ntiles);
         k_field_train_tc<<<grid, TT_THREADS, kTrainTcSmem, s>>>(
@@ -1263,6 +1306,7 @@ static gm_status field_grad(gm_field* f, const float* pts, int stride, const flo
         GM_TRY_CUDA(cudaGetLastError());
         return GM_OK;
     }
+    GM_TRY_CUDA(cudaMemsetAsync(f->loss, 0, sizeof(float), s));
     k_field_train<<<gm_div_up(batch, TRAIN_PTS), 256, kTrainSmem, s>>>(
         pts, stride, target, n, idx, batch, step, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), f->box, f->wbf,
         f->wtbf, f->theta, f->grad, f->loss);
@@ -1276,8 +1320,8 @@ static gm_status field_adam(gm_field* f, float lr, cudaStream_t s) {
     const float bc1 = (float)(1.0 - std::pow(0.9, (double)f->t));
     const float bc2 = (float)(1.0 - std::pow(0.999, (double)f->t));
     if (f->train_kernel == GM_FIELD_QUERY_TCGEN05)
-        k_field_update<<<gm_div_up(NPAR, 256), 256, 0, s>>>(f->partial, f->nblk, f->loss, nullptr, f->theta, f->m,
-                                                            f->v, lr, bc1, bc2, f->wbf, f->wtbf);
+        k_field_update<<<kUpdateGrid, 32 * UPD_WARPS, 0, s>>>(f->partial, f->nblk, f->loss, nullptr, f->theta, f->m,
+                                                               f->v, lr, bc1, bc2, f->wbf, f->wtbf);
     else
         k_field_adam<<<gm_div_up(NPAR, 256), 256, 0, s>>>(f->theta, f->m, f->v, f->grad, lr, bc1, bc2, f->wbf,
                                                           f->wtbf);
@@ -1296,8 +1340,8 @@ extern "C" gm_status gm_field_loss_grad(gm_field* f, const float* xyz, const flo
     cudaStream_t s = (cudaStream_t)stream;
     GM_TRY(field_grad(f, xyz, 3, target, n, batch_idx, batch, 0, 0, s));
     if (f->train_kernel == GM_FIELD_QUERY_TCGEN05) {
-        k_field_update<<<gm_div_up(NPAR, 256), 256, 0, s>>>(f->partial, f->nblk, f->loss, f->grad, nullptr, nullptr,
-                                                            nullptr, 0.f, 1.f, 1.f, nullptr, nullptr);
+        k_field_update<<<kUpdateGrid, 32 * UPD_WARPS, 0, s>>>(f->partial, f->nblk, f->loss, f->grad, nullptr,
+                                                               nullptr, nullptr, 0.f, 1.f, 1.f, nullptr, nullptr);
         f->ctx->launches += 1;
         GM_TRY_CUDA(cudaGetLastError());
     }
