@@ -56,6 +56,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
+// bf16(relu(lo)), bf16(relu(hi)) packed (lo in the low half) by one conversion instruction: rounding
+// to nearest is monotone and keeps 0, so clamping before or after it gives the same value.
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
 __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -498,9 +506,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 3) k_field_query_tc(const float* _
             if (!mbar_wait(smem_addr(&S.mbar_mma[h]), pm)) S.abort = 1;
             pm ^= 1;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // 32 columns at a time: read, round to bf16, ReLU on the packed pairs (rounding is monotone
-            // and keeps 0, so this equals rounding the ReLU), then the next A row or the output dot
-            const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.f, 0.f);
+            // 32 columns at a time: read, ReLU and round to bf16, then the next A row or the output dot
             float acc5 = 0.f;
 #pragma unroll
             for (int c0 = 0; c0 < FW; c0 += 32) {
@@ -510,11 +516,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 3) k_field_query_tc(const float* _
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
                 uint32_t pk[16];
 #pragma unroll
-                for (int c = 0; c < 32; c += 2) {
-                    __nv_bfloat162 q = __floats2bfloat162_rn(va[c], va[c + 1]);
-                    q = __hmax2(q, zero2);
-                    pk[c / 2] = *reinterpret_cast<uint32_t*>(&q);
-                }
+                for (int c = 0; c < 32; c += 2) pk[c / 2] = pack_bf16_relu(va[c], va[c + 1]);
                 if (l + 1 < FD) {
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
@@ -1019,12 +1021,10 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_field_train_tc(
 #pragma unroll
             for (int j = 0; j < TT_CW; j += 16) tmem_ld16(row_acc + j, z + j);
             asm volatile("tcgen05.wait::ld.sync.aligned;");
-            const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.f, 0.f);
             uint32_t m = 0;
 #pragma unroll
             for (int j = 0; j < TT_CW; j += 2) {
-                __nv_bfloat162 h2 = __hmax2(__floats2bfloat162_rn(z[j], z[j + 1]), zero2);
-                pk[j / 2] = *reinterpret_cast<uint32_t*>(&h2);
+                pk[j / 2] = pack_bf16_relu(z[j], z[j + 1]);
                 m |= (z[j] > 0.f ? 1u : 0u) << j;
                 m |= (z[j + 1] > 0.f ? 1u : 0u) << (j + 1);
             }
