@@ -143,6 +143,27 @@ def test_field_tensor_core_gradient_over_many_tiles(env):
     assert F.relative_l2(g1, g3) < 2e-2
 
 
+@pytest.mark.parametrize("batch", [1, 127, 129])
+def test_field_tensor_core_gradient_small_batches(env, batch):
+    """One point, one ragged tile and one full tile plus a single point: the padding rows of a
+    tile add nothing and the mean uses the true batch size."""
+    G, torch, ctx = env
+    theta = synth.field_init(17)
+    f = G.gm_field_create(ctx, BOX_LO, BOX_HI, theta)
+    n = 500
+    x = _points(n, 11)
+    y = np.random.default_rng(12).uniform(0, 1, n).astype(np.float32)
+    idx = np.random.default_rng(13).integers(0, n, batch).astype(np.uint32)
+    dx, dy, di = (torch.from_numpy(a).cuda() for a in (x, y, idx.view(np.int32)))
+    g = np.empty(G.GM_FIELD_N_PARAMS, np.float32)
+    loss = G.gm_field_loss_grad(f, dx, dy, n, di, batch, g)
+    G.gm_field_free(f)
+    feats = F.features(F.normalise(x[idx].astype(np.float64), BOX_LO, BOX_HI))
+    l_ref, g_ref = F.loss_and_grad(theta.astype(np.float64), feats, y[idx].astype(np.float64), emulate_bf16=True)
+    assert abs(loss - l_ref) <= 2e-3 * l_ref
+    assert F.relative_l2(g, g_ref) < 2e-2
+
+
 def test_field_trains_on_the_tiny_sphere_map(env):
     G, torch, ctx = env
     from paper_2601_07571_gb300 import pipeline
