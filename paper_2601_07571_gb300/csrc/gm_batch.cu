@@ -556,7 +556,6 @@ extern "C" gm_status gm_accumulate_batch(gm_ctx* ctx, const gm_session_desc* ss,
 
 extern "C" gm_status gm_batch_autotune(gm_batch* b, gm_stream stream, int32_t* best_flags, float* best_ms) {
     if (!b) return gm_set_error(GM_ERR_INVALID_ARG, "gm_batch_autotune: null batch");
-    cudaStream_t s = (cudaStream_t)stream;
     uint64_t ns_tot = 0, nt_tot = 0;
     for (auto& d : b->host_sess) {
         ns_tot += d.ns;
@@ -594,7 +593,6 @@ extern "C" gm_status gm_batch_autotune(gm_batch* b, gm_stream stream, int32_t* b
     }
     b->flags = best;
     GM_TRY(batch_capture(b));
-    (void)s;
     (void)best_t;
     if (best_flags) *best_flags = best;
     if (best_ms) *best_ms = best_t;
@@ -616,7 +614,6 @@ extern "C" gm_status gm_autotune_accumulate(gm_scene* sc, gm_samples* sm, const 
             return GM_OK;
         }
     }
-    cudaStream_t s = (cudaStream_t)stream;
     gm_fixations sub = *fx;
     sub.n = std::min<uint32_t>(fx->n, 256);   // a prefix of the fixations is enough to rank variants
     int best = 0;
@@ -644,7 +641,6 @@ extern "C" gm_status gm_autotune_accumulate(gm_scene* sc, gm_samples* sm, const 
             best = f;
         }
     }
-    (void)s;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         g_tune[key] = best;

@@ -54,7 +54,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
 }
-__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 // bf16(relu(lo)), bf16(relu(hi)) packed (lo in the low half) by one conversion instruction: rounding
 // to nearest is monotone and keeps 0, so clamping before or after it gives the same value.
@@ -325,14 +324,6 @@ __device__ __forceinline__ void bulk_load(float* dst, const float* src, uint32_t
 __device__ __forceinline__ void half_sync(int h) {
     if (h == 0) asm volatile("bar.sync 1, 128;" ::: "memory");
     else asm volatile("bar.sync 2, 128;" ::: "memory");
-}
-
-// Row t of an A tile from 32 packed bf16 pairs: eight 16-byte stores into the core-matrix layout.
-__device__ __forceinline__ void store_a_row_packed(__nv_bfloat16* A, int t, const uint32_t* pk) {
-#pragma unroll
-    for (int kg = 0; kg < 8; ++kg)
-        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(A) + kg * 2048 + (t >> 3) * 128 + (t & 7) * 16) =
-            make_uint4(pk[4 * kg], pk[4 * kg + 1], pk[4 * kg + 2], pk[4 * kg + 3]);
 }
 
 // The bias of a layer into this thread's accumulator row (the products then add onto it, as the

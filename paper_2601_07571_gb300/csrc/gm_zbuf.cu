@@ -625,6 +625,7 @@ gm_status render_zbuffers(gm_ctx* ctx, gm_scene* sc, const ZbFrustum* frusta, ui
                           unsigned long long* raster_pairs) {
     const size_t npx = (size_t)res * res;
     for (int attempt = 0; attempt < 3; ++attempt) {
+        static_assert(ZB_EMPTY == 0xffffffffu, "a byte-wise 0xff clear writes ZB_EMPTY");
         GM_TRY_CUDA(cudaMemsetAsync(zbuf, 0xff, sizeof(uint32_t) * npx * nfix, s));
         GM_TRY_CUDA(cudaMemsetAsync(rb.counts, 0, sizeof(unsigned long long) * 3, s));
         const dim3 cgrid(gm_div_up(sc->n_tris, ZB_THREADS), std::min<uint32_t>(gm_div_up(nfix, ZB_SMEM_FRUSTA), 65535));
