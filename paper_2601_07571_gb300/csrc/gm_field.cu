@@ -268,9 +268,11 @@ __global__ void __launch_bounds__(256) k_field_query(const float* __restrict__ x
 // point t's 64 features into row t of its A tile (bf16, K-major core-matrix layout: 8 x 8 blocks
 // of 128 bytes); per layer one thread issues four tcgen05.mma (M 128, N 64, K 16, bf16 x bf16 ->
 // FP32 in tensor memory, columns 64 h .. 64 h + 63 for half h) and commits them to the half's
-// mbarrier; every thread then reads its row of the accumulator with tcgen05.ld, adds the bias,
-// applies ReLU, rounds to bf16 and writes the next A row. Waits are bounded: on a timeout the block
-// records GM_DEV_WAIT_TIMEOUT, drains its own copies, frees its tensor memory and returns.
+// mbarrier; every thread then reads its row of the accumulator with tcgen05.ld (the bias was
+// stored there first), applies ReLU, rounds to bf16 and writes the next A row. The output layer is
+// a fifth product with N = 16 whose B rows are the three bf16 parts of w5. Waits are bounded: on a
+// timeout the block records GM_DEV_WAIT_TIMEOUT, drains its own copies, frees its tensor memory and
+// returns.
 constexpr int TQ = 128;                       // points per tile (threads per half)
 constexpr int TQ_THREADS = 2 * TQ;
 constexpr uint32_t TQ_TMEM_COLS = 128;        // two FP32 accumulators of N = 64
@@ -279,6 +281,7 @@ constexpr int TQ_WAIT_ITERS = 1 << 22;
 struct QuerySmem {
     alignas(1024) __nv_bfloat16 A[2][TQ * FW];    // 2 x 16 KB
     alignas(1024) __nv_bfloat16 W[FD][FW * FW];   // 32 KB
+    alignas(1024) __nv_bfloat16 W5[16 * FW];      // output layer as B (N = 16): w5 = hi + mid + lo in rows 0..2
     alignas(16) float bias[FD * FW];
     float w5[FW + 1];
     alignas(16) float xyz[2][2][TQ * 3];          // [half][buffer]
@@ -299,6 +302,17 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lead, uint
 
 // Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major, N = 64, M = 128.
 constexpr uint32_t kQueryIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kQueryIdescN16 = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+// The three bf16 parts of an FP32 value: hi = bf16(w), mid = bf16(w - hi), lo = w - hi - mid. Each
+// difference is exact in FP32 and lo needs at most 8 significant bits, so hi + mid + lo = w exactly;
+// a product with a bf16 activation is then three exact products summed in FP32.
+__device__ __forceinline__ void split3_bf16(float w, __nv_bfloat16 part[3]) {
+    part[0] = __float2bfloat16_rn(w);
+    const float r1 = w - __bfloat162float(part[0]);
+    part[1] = __float2bfloat16_rn(r1);
+    part[2] = __float2bfloat16_rn(r1 - __bfloat162float(part[1]));
+}
 
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
     for (int it = 0; it < TQ_WAIT_ITERS; ++it) {
@@ -409,6 +423,16 @@ __global__ void __launch_bounds__(TQ_THREADS, 3) k_field_query_tc(const float* _
         const uint4 q = reinterpret_cast<const uint4*>(wbf + (size_t)l * FW * FW + nn * FW)[kg];
         *reinterpret_cast<uint4*>(reinterpret_cast<char*>(S.W[l]) + kg * 1024 + (nn >> 3) * 128 + (nn & 7) * 16) = q;
     }
+    // the output layer as a 16 x 64 B operand: rows 0..2 the three bf16 parts of w5, the rest zero;
+    // (n, k) at (k / 8) * 256 + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2
+    for (int e = tid; e < 16 * FW; e += TQ_THREADS) {
+        const int nn = e / FW, k = e % FW;
+        __nv_bfloat16 part[3];
+        split3_bf16(theta[W5_OFF + k], part);
+        const __nv_bfloat16 v = nn < 3 ? part[nn] : __float2bfloat16_rn(0.f);
+        *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(S.W5) + (k >> 3) * 256 + (nn >> 3) * 128 +
+                                          (nn & 7) * 16 + (k & 7) * 2) = v;
+    }
     for (int i = tid; i < FD * FW; i += TQ_THREADS) S.bias[i] = theta[b_off(i / FW) + i % FW];
     for (int i = tid; i <= FW; i += TQ_THREADS) S.w5[i] = theta[W5_OFF + i];
     if (tid == 0) {
@@ -470,7 +494,9 @@ __global__ void __launch_bounds__(TQ_THREADS, 3) k_field_query_tc(const float* _
         features_fast(xt, v);
         store_a_row(A, t, v);
         tmem_st_bias(row_addr, S.bias);   // layer 0's bias (the previous tile's last read is complete)
-        for (int l = 0; l < FD; ++l) {
+        // four hidden layers, then the output layer (l == FD) as one more product: A = h4, B = the
+        // three parts of w5, so z5 - b5 is the sum of the first three accumulator columns
+        for (int l = 0; l <= FD; ++l) {
             asm volatile("tcgen05.wait::st.sync.aligned;");   // the bias is in the accumulator
             asm volatile("fence.proxy.async.shared::cta;");   // this thread's A row, visible to the MMA
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -481,15 +507,28 @@ __global__ void __launch_bounds__(TQ_THREADS, 3) k_field_query_tc(const float* _
                 break;
             }
             if (t == 0) {
-                const uint32_t w_addr = smem_addr(S.W[l]);
+                if (l < FD) {
+                    const uint32_t w_addr = smem_addr(S.W[l]);
 #pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    const uint64_t da = umma_desc(a_addr + s * 4096, 2048, 128);
-                    const uint64_t db = umma_desc(w_addr + s * 2048, 1024, 128);
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_h),
-                        "l"(da), "l"(db), "r"(kQueryIdesc), "r"(1u));
+                    for (int s = 0; s < 4; ++s) {
+                        const uint64_t da = umma_desc(a_addr + s * 4096, 2048, 128);
+                        const uint64_t db = umma_desc(w_addr + s * 2048, 1024, 128);
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_h),
+                            "l"(da), "l"(db), "r"(kQueryIdesc), "r"(1u));
+                    }
+                } else {
+                    const uint32_t w5_addr = smem_addr(S.W5);
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+                        const uint64_t da = umma_desc(a_addr + s * 4096, 2048, 128);
+                        const uint64_t db = umma_desc(w5_addr + s * 512, 256, 128);
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_h),
+                            "l"(da), "l"(db), "r"(kQueryIdescN16), "r"(s > 0 ? 1u : 0u));
+                    }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     smem_addr(&S.mbar_mma[h])));
@@ -497,8 +536,14 @@ __global__ void __launch_bounds__(TQ_THREADS, 3) k_field_query_tc(const float* _
             if (!mbar_wait(smem_addr(&S.mbar_mma[h]), pm)) S.abort = 1;
             pm ^= 1;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // 32 columns at a time: read, ReLU and round to bf16, then the next A row or the output dot
-            float acc5 = 0.f;
+            if (l == FD) {
+                float v[16];
+                tmem_ld16(row_addr, v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (i < n) out[i] = softplusf(((v[0] + v[1]) + v[2]) + S.w5[FW]);
+                break;
+            }
+            // 32 columns at a time: read, ReLU and round to bf16, write the next A row
 #pragma unroll
             for (int c0 = 0; c0 < FW; c0 += 32) {
                 float va[32];
@@ -508,25 +553,14 @@ __global__ void __launch_bounds__(TQ_THREADS, 3) k_field_query_tc(const float* _
                 uint32_t pk[16];
 #pragma unroll
                 for (int c = 0; c < 32; c += 2) pk[c / 2] = pack_bf16_relu(va[c], va[c + 1]);
-                if (l + 1 < FD) {
 #pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        const int kg = c0 / 8 + g;
-                        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(A) + kg * 2048 + (t >> 3) * 128 +
-                                                  (t & 7) * 16) =
-                            make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
-                    }
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 32; c += 2) {
-                        const __nv_bfloat162 q = *reinterpret_cast<const __nv_bfloat162*>(&pk[c / 2]);
-                        acc5 = fmaf(__low2float(q), S.w5[c0 + c], acc5);
-                        acc5 = fmaf(__high2float(q), S.w5[c0 + c + 1], acc5);
-                    }
+                for (int g = 0; g < 4; ++g) {
+                    const int kg = c0 / 8 + g;
+                    *reinterpret_cast<uint4*>(reinterpret_cast<char*>(A) + kg * 2048 + (t >> 3) * 128 + (t & 7) * 16) =
+                        make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
                 }
             }
             if (l + 1 < FD) tmem_st_bias(row_addr, S.bias + (l + 1) * FW);   // next layer's start
-            else if (i < n) out[i] = softplusf(S.w5[FW] + acc5);
         }
     }
     if (S.abort && t == 0) {
