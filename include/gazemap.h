@@ -92,7 +92,9 @@ enum {
     GM_F_REGCAP64 = 32,     /* cap the accumulation kernel at 64 registers (4 blocks per SM) */
     GM_F_TILE_CONSECUTIVE = 64, /* warp tiles of 128 consecutive samples (else four 32-sample runs over 1024) */
     GM_F_STATIC_TILES = 128, /* one warp tile per warp of a full grid (else warps pull tiles from a counter) */
-    GM_F_NO_TILE_CULL = 256  /* test every sample against every fixation (no warp-tile sphere test) */
+    GM_F_NO_TILE_CULL = 256, /* test every sample against every fixation (no warp-tile sphere test) */
+    GM_F_BLOCK128 = 512     /* blocks of 128 threads (7 per SM, 72 registers; 8 per SM with GM_F_REGCAP64)
+                               for the ray-queue binary-tree variant, instead of 256 (3 or 4 per SM) */
 };
 
 typedef struct {
@@ -351,7 +353,8 @@ gm_status gm_accumulate_batch(gm_ctx* ctx, const gm_session_desc* sessions, uint
                               const gm_params* params, gm_stream stream, gm_map** out_per_session);
 /* Pick the fastest accumulation variant for one problem by timing each candidate on its first
  * 256 fixations: ray queue on/off, binary or 4-wide tree, 80- or 64-register cap, spread or
- * consecutive warp tiles, persistent or static scheduling (32 candidates); *best_flags gets the
+ * consecutive warp tiles, persistent or static scheduling (32 candidates), and blocks of 128
+ * instead of 256 threads for the ray-queue binary-tree kernels (8 more); *best_flags gets the
  * GM_F_* variant bits to OR into params->flags. Results are
  * cached per size bucket (log2 of samples, fixations and triangles) for the process and, when the
  * environment variable GM_TUNE_CACHE names a file, in that JSON file across processes. */

@@ -378,7 +378,10 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
                 default: GM_LAUNCH_ACC(true, true, true, 3); break;
             }
         } else {
-            switch (code) {
+            const bool b128 = (prm->flags & GM_F_BLOCK128) != 0;
+            if (b128 && code == 1) GM_LAUNCH_ACC_NT(false, true, false, 7, 128);
+            else if (b128 && code == 5) GM_LAUNCH_ACC_NT(false, true, false, 8, 128);
+            else switch (code) {
                 case 0: GM_LAUNCH_ACC(false, false, false, 3); break;
                 case 1: GM_LAUNCH_ACC(false, true, false, 3); break;
                 case 2: GM_LAUNCH_ACC(false, false, true, 3); break;

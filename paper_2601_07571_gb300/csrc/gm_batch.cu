@@ -619,13 +619,17 @@ extern "C" gm_status gm_autotune_accumulate(gm_scene* sc, gm_samples* sm, const 
     int best = 0;
     float best_t = 1e30f;
     // the three kernel variants of the batched search, times the warp-tile shape (four spread
-    // 32-sample runs or 128 consecutive samples) and the scheduling (persistent or one tile per warp)
+    // 32-sample runs or 128 consecutive samples) and the scheduling (persistent or one tile per warp);
+    // then 128-thread blocks for the two ray-queue binary-tree variants (80- and 64-register caps)
     constexpr int kTileFlags = GM_F_TILE_CONSECUTIVE | GM_F_STATIC_TILES;
-    for (int code = 0; code < 32; ++code) {
+    for (int code = 0; code < 40; ++code) {
         gm_params p = *prm;
-        const int f = flags_of_code(code & 7) | ((code & 8) ? GM_F_TILE_CONSECUTIVE : 0) |
-                      ((code & 16) ? GM_F_STATIC_TILES : 0);
-        p.flags = (prm->flags & ~VARIANT_MASK & ~kTileFlags & ~GM_F_DEBUG_PAIRS) | f | GM_F_TIMING;
+        const int v = code < 32 ? (code & 7) : ((code & 1) ? 5 : 1);
+        const int shape = code < 32 ? code >> 3 : (code - 32) >> 1;
+        const int f = flags_of_code(v) | ((shape & 1) ? GM_F_TILE_CONSECUTIVE : 0) |
+                      ((shape & 2) ? GM_F_STATIC_TILES : 0) | (code >= 32 ? GM_F_BLOCK128 : 0);
+        p.flags = (prm->flags & ~VARIANT_MASK & ~kTileFlags & ~GM_F_BLOCK128 & ~GM_F_DEBUG_PAIRS) | f |
+                  GM_F_TIMING;
         float t = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
             gm_map* m = nullptr;

@@ -426,7 +426,9 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                 if (in) {
                     const int pos = tot + __popc(m & gm_lanemask_lt());
                     qslot[pos] = (uint16_t)(k * 32 + lane);
-                    qg[pos] = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
+                    // the weight is rounded on its own (never fused into the compensated sum), so
+                    // both tracing forms add exactly the same value
+                    qg[pos] = __fmul_rn(F0.w, ex2_approx(-P.C2 * __fdividef(c2, d1s)));
                 }
                 tot += __popc(m);
             }
@@ -475,7 +477,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                     int hit = -1;
                     const bool vis = WIDE ? !occluded4(R, own[k], nodes, tris, err, st.n_node, st.n_tri, hit)
                                           : !occluded(R, own[k], nodes, tris, P.nt, err, st.n_node, st.n_tri, hit);
-                    const float g = F0.w * ex2_approx(-P.C2 * __fdividef(c2, d1s));
+                    const float g = __fmul_rn(F0.w, ex2_approx(-P.C2 * __fdividef(c2, d1s)));
                     if (vis) {
                         ++st.n_vis;
                         const float y = g - cmp[k];

@@ -107,6 +107,31 @@ def test_batch_session_against_oracle(env):
         G.gm_scene_free(sc)
 
 
+def test_batched_variants_agree_bit_for_bit(env):
+    """Every batched kernel variant (ray queue or in-place tracing, binary or 4-wide tree, 80- or
+    64-register cap) gives the same maps: the same additions per sample in the same order, each
+    weight rounded on its own before it enters the compensated sum."""
+    G, pipe, ctx = env
+    ws = _small_sessions(3)
+    hs = _prepare(G, pipe, ctx, ws)
+    ref = None
+    for code in range(8):
+        f = ((0 if code & 1 else G.GM_F_NO_COMPACT) | (G.GM_F_WIDE_BVH if code & 2 else 0)
+             | (G.GM_F_REGCAP64 if code & 4 else 0))
+        b = G.gm_batch_create(ctx, hs, pipe.params_of(ws[0], normalize=False, flags=f))
+        G.gm_batch_run(b)
+        maps = []
+        for i in range(len(ws)):
+            a = np.empty(G.gm_samples_info(hs[i][1]), np.float32)
+            G.gm_map_copy(G.gm_batch_map(b, i), 0, a)
+            maps.append(a.view(np.uint32))
+        G.gm_batch_free(b)
+        if ref is None:
+            ref = maps
+        for a, r in zip(maps, ref):
+            assert np.array_equal(a, r), code
+
+
 def test_autotune_picks_a_variant_and_keeps_results(env, tmp_path, monkeypatch):
     G, pipe, ctx = env
     ws = _small_sessions(3)
@@ -130,7 +155,9 @@ def test_autotune_picks_a_variant_and_keeps_results(env, tmp_path, monkeypatch):
     G.gm_batch_free(b)
     fl2, _ = G.gm_autotune_accumulate(hs[0][0], hs[0][1], *hs[0][2:], prm)
     assert fl2 & ~(G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64 | G.GM_F_TILE_CONSECUTIVE
-                   | G.GM_F_STATIC_TILES) == 0
+                   | G.GM_F_STATIC_TILES | G.GM_F_BLOCK128) == 0
+    if fl2 & G.GM_F_BLOCK128:   # only offered for the ray-queue binary-tree kernels
+        assert not fl2 & (G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH)
     # the tuned variant gives the same map as the default one
     ref = G.gm_accumulate_fixations(hs[0][0], hs[0][1], *hs[0][2:], prm)
     p2 = pipe.params_of(ws[0], normalize=False, flags=fl2)
