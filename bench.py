@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gazemap", "reference"], default="gazemap")
     ap.add_argument("--workload", choices=["paper_scene", "tiny_sphere", "batched", "field", "city", "zbuffer",
-                                           "dynamic"],
+                                           "dynamic", "sampler"],
                     default="paper_scene")
     ap.add_argument("--field-steps", type=int, default=30000, help="Adam steps of the neural field")
     ap.add_argument("--field-lr", type=float, default=3e-3, help="initial learning rate of the field (cosine to 1%%)")
@@ -477,6 +477,104 @@ def dynamic_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def measured_hbm_peak():
+    """HBM copy rate (GB/s) measured by the driver, else the machine's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured copy (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def sampler_arm(args):
+    """Surface sampling and the export record on the paper-shaped scene: the spec sampler
+    (FP64 areas, fixed-point counts, int64 prefix, Philox expansion, Morton work order), the
+    paper's grid sampler (Section 3.1: adaptive integer resolution, (r+1)(r+2)/2 samples per
+    triangle) at the same density, and the per-sample export record (Section 3.3.3) of the Philox
+    samples. Each call is timed with CUDA events (L2 flushed between steps) and its algorithmic
+    bytes are set against the measured HBM copy rate."""
+    import torch
+    from paper_2601_07571_gb300 import build as B
+    B.build()
+    import paper_2601_07571_gb300 as G
+    from paper_2601_07571_gb300 import pipeline
+    torch.cuda.set_device(0)
+    w = make_workload("paper_scene", args.fixations)
+    ctx = G.gm_create(0)
+    stream = torch.cuda.current_stream()
+    sc = G.gm_build_scene(ctx, pipeline.mesh_args(w, to_device=True), stream)
+    dens = [m.density for m in w.meshes]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(fn, release):
+        for _ in range(args.warmup):
+            release(fn())
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            release(r)
+        return sum(ts) / len(ts)
+
+    clocks = ClockSampler()
+    clocks.start()
+    philox_ms = timed(lambda: G.gm_sample_surface(sc, dens, w.seed, w.session, stream), G.gm_samples_free)
+    grid_ms = timed(lambda: G.gm_sample_surface_grid(sc, dens, stream), G.gm_samples_free)
+    sm = G.gm_sample_surface(sc, dens, w.seed, w.session, stream)
+    ns = G.gm_samples_info(sm)
+    gs = G.gm_sample_surface_grid(sc, dens, stream)
+    ng = G.gm_samples_info(gs)
+    G.gm_samples_free(gs)
+    fix = pipeline.fixation_args(w.fixations, to_device=True)
+    m = G.gm_accumulate_fixations(sc, sm, *fix, pipeline.params_of(w, normalize=True), stream)
+    outs = dict(value=torch.empty(ns, dtype=torch.float32, device="cuda"),
+                object_id=torch.empty(ns, dtype=torch.int32, device="cuda"),
+                triangle=torch.empty(ns, dtype=torch.int32, device="cuda"),
+                bary3=torch.empty((ns, 3), dtype=torch.float32, device="cuda"),
+                local_xyz=torch.empty((ns, 3), dtype=torch.float32, device="cuda"),
+                world_xyz=torch.empty((ns, 3), dtype=torch.float32, device="cuda"))
+    export_ms = timed(lambda: G.gm_samples_export(sm, m, 0, stream=stream, **outs), lambda r: None)
+    clk = clocks.stop()
+    ntri = int(G.gm_scene_info(sc)[0])
+    peak, basis = measured_hbm_peak()
+    # algorithmic bytes: world triangles read (3 x float4), offsets written (int64), per sample the
+    # stored record (float4 position + float2 barycentrics) and the work order (float4 + uint32)
+    b_philox = 48 * ntri + 8 * (ntri + 1) + (24 + 20) * ns
+    b_grid = 48 * ntri + 8 * (ntri + 1) + 4 * ntri + (24 + 20) * ng
+    # export: position, barycentrics and map value read; value, object, triangle, 3 barycentrics,
+    # local and world position written
+    b_export = (16 + 8 + 4) * ns + (4 + 4 + 4 + 12 + 12 + 12) * ns
+
+    def roof(bytes_, ms, kernel):
+        ach = bytes_ / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                "kernel": kernel, "peak_basis": basis, "algorithmic_bytes": int(bytes_)}
+
+    line = {"metric": "surface samples/s", "value": ns / (philox_ms * 1e-3), "unit": "samples/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": philox_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+u32", "data": "synthetic",
+            "config": {"workload": w.name + "_sampling", "triangles": ntri, "samples": int(ns),
+                       "grid_samples": int(ng), "l2": "flushed between steps (256 MiB write)",
+                       "inputs": "device-resident"},
+            "roofline": roof(b_philox, philox_ms, "gm_sample_surface (k_tri_counts, scan, k_offsets, k_expand, work order)"),
+            "grid": {"ms": grid_ms, "samples_per_s": ng / (grid_ms * 1e-3),
+                     "roofline": roof(b_grid, grid_ms, "gm_sample_surface_grid")},
+            "export": {"ms": export_ms, "records_per_s": ns / (export_ms * 1e-3),
+                       "roofline": roof(b_export, export_ms, "gm_samples_export (k_export_record)")},
+            "clocks": clk}
+    G.gm_map_free(m)
+    G.gm_samples_free(sm)
+    G.gm_scene_free(sc)
+    G.gm_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def field_arm(args):
     """Neural density field on the paper-shaped scene: train on the normalised map of its 2M
     samples (MSE, Adam, batch 65 536, --field-lr cosine to 1 %, --field-steps steps), then answer
@@ -607,6 +705,9 @@ def main():
         return
     if args.workload == "dynamic":
         dynamic_arm(args)
+        return
+    if args.workload == "sampler":
+        sampler_arm(args)
         return
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
