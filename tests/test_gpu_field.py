@@ -164,6 +164,18 @@ def test_field_tensor_core_gradient_small_batches(env, batch):
     assert F.relative_l2(g, g_ref) < 2e-2
 
 
+def test_field_kernel_selectors_refuse_unknown_kernels(env):
+    G, torch, ctx = env
+    f = G.gm_field_create(ctx, BOX_LO, BOX_HI, synth.field_init(2))
+    with pytest.raises(RuntimeError, match="unknown kernel"):
+        G.gm_field_train_kernel(f, 7)
+    with pytest.raises(RuntimeError, match="unknown kernel"):
+        G.gm_field_query_kernel(f, -1)
+    G.gm_field_train_kernel(f, G.GM_FIELD_QUERY_MMA_SYNC)
+    G.gm_field_train_kernel(f, G.GM_FIELD_QUERY_TCGEN05)
+    G.gm_field_free(f)
+
+
 def test_field_trains_on_the_tiny_sphere_map(env):
     G, torch, ctx = env
     from paper_2601_07571_gb300 import pipeline
