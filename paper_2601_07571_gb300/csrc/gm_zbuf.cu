@@ -193,6 +193,21 @@ __device__ __forceinline__ void to_camera(const ZbFrustum& F, float px, float py
 // ---- cull: (fixation, triangle) pairs whose triangle may meet the fixation's frustum ---------
 // Frustum planes as linear forms through the eye (u in [-1, res + 1] pixels: one pixel of slack),
 // plus near/far with 1e-5 relative slack. FP32; the slack keeps it conservative.
+// True when a sphere (centre c, radius r) lies wholly outside a frustum: beyond its near or far
+// plane or one of its four side planes (these pass through the eye; unit normals in camera
+// coordinates from the pixel mapping with one pixel of slack). The slack covers FP32 rounding.
+__device__ __forceinline__ bool sphere_outside(const ZbFrustum& F, float cx, float cy, float cz, float r, float R) {
+    float xc, yc, wc;
+    to_camera(F, cx, cy, cz, xc, yc, wc);
+    const float slack = r + 1e-4f * (fabsf(xc) + fabsf(yc) + fabsf(wc) + r);
+    const float l0 = F.ox + 1.f, l1 = R + 1.f - F.ox, b0 = F.oy + 1.f, b1 = R + 1.f - F.oy;
+    return wc < F.n - slack || wc > F.f + slack ||
+           fmaf(F.sx, xc, l0 * wc) < -slack * sqrtf(fmaf(F.sx, F.sx, l0 * l0)) ||
+           fmaf(-F.sx, xc, l1 * wc) < -slack * sqrtf(fmaf(F.sx, F.sx, l1 * l1)) ||
+           fmaf(F.sy, yc, b0 * wc) < -slack * sqrtf(fmaf(F.sy, F.sy, b0 * b0)) ||
+           fmaf(-F.sy, yc, b1 * wc) < -slack * sqrtf(fmaf(F.sy, F.sy, b1 * b1));
+}
+
 __global__ void __launch_bounds__(ZB_THREADS) k_zb_cull(const float4* __restrict__ tris, uint32_t nt,
                                                         const ZbFrustum* __restrict__ frusta, uint32_t nfix,
                                                         uint32_t res, PairFT* __restrict__ pairs, uint64_t cap,
@@ -232,6 +247,30 @@ __global__ void __launch_bounds__(ZB_THREADS) k_zb_cull(const float4* __restrict
     const float wR = wbox ? 0.5f * sqrtf((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
                                          (hi[2] - lo[2]) * (hi[2] - lo[2])) * 1.0001f
                           : 0.f;
+    // the block's 256 triangles (also neighbours in leaf order) in one sphere: a frustum that
+    // misses it is skipped by every warp of the block without its own sphere test
+    __shared__ float sBox[ZB_THREADS / 32][6];
+    __shared__ float4 sBlk;
+    __shared__ unsigned sMask[ZB_SMEM_FRUSTA / 32];
+    const int warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sBox[warp][0] = lo[0], sBox[warp][1] = lo[1], sBox[warp][2] = lo[2];
+        sBox[warp][3] = hi[0], sBox[warp][4] = hi[1], sBox[warp][5] = hi[2];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float bl[3] = {INFINITY, INFINITY, INFINITY}, bh[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int w = 0; w < ZB_THREADS / 32; ++w)
+            for (int q = 0; q < 3; ++q) {
+                bl[q] = fminf(bl[q], sBox[w][q]);
+                bh[q] = fmaxf(bh[q], sBox[w][3 + q]);
+            }
+        sBlk = bl[0] <= bh[0]
+                   ? make_float4(0.5f * (bl[0] + bh[0]), 0.5f * (bl[1] + bh[1]), 0.5f * (bl[2] + bh[2]),
+                                 0.5f * sqrtf((bh[0] - bl[0]) * (bh[0] - bl[0]) + (bh[1] - bl[1]) * (bh[1] - bl[1]) +
+                                              (bh[2] - bl[2]) * (bh[2] - bl[2])) * 1.0001f)
+                   : make_float4(0.f, 0.f, 0.f, -1.f);
+    }
     // blockIdx.y picks a group of fixations (one shared-memory load of their frusta); the blocks of
     // one group run together, so the pairs they emit -- and the raster's atomics -- stay on a few
     // z-buffers that fit in L2
@@ -240,23 +279,18 @@ __global__ void __launch_bounds__(ZB_THREADS) k_zb_cull(const float4* __restrict
         __syncthreads();
         for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) sF[k] = frusta[f0 + k];
         __syncthreads();
+        if (threadIdx.x < ZB_SMEM_FRUSTA) {   // whole warps: ZB_SMEM_FRUSTA is a multiple of 32
+            const uint32_t k = threadIdx.x;
+            const float4 bs = sBlk;
+            const bool reach = k < m && sF[k].ok && bs.w >= 0.f && !sphere_outside(sF[k], bs.x, bs.y, bs.z, bs.w, R);
+            const unsigned bits = __ballot_sync(0xffffffffu, reach);
+            if (lane == 0) sMask[k >> 5] = bits;
+        }
+        __syncthreads();
         for (uint32_t k = 0; k < m; ++k) {
+            if (!((sMask[k >> 5] >> (k & 31)) & 1u)) continue;
             const ZbFrustum& F = sF[k];
-            if (!F.ok || !wbox) continue;
-            {
-                // the sphere against the six planes (the side planes pass through the eye; their
-                // unit normals in camera coordinates from the pixel mapping with one pixel of slack)
-                float xc, yc, wc;
-                to_camera(F, wx, wy, wz, xc, yc, wc);
-                const float slack = wR + 1e-4f * (fabsf(xc) + fabsf(yc) + fabsf(wc) + wR);
-                const float l0 = F.ox + 1.f, l1 = R + 1.f - F.ox, b0 = F.oy + 1.f, b1 = R + 1.f - F.oy;
-                const bool out = wc < F.n - slack || wc > F.f + slack ||
-                                 fmaf(F.sx, xc, l0 * wc) < -slack * sqrtf(fmaf(F.sx, F.sx, l0 * l0)) ||
-                                 fmaf(-F.sx, xc, l1 * wc) < -slack * sqrtf(fmaf(F.sx, F.sx, l1 * l1)) ||
-                                 fmaf(F.sy, yc, b0 * wc) < -slack * sqrtf(fmaf(F.sy, F.sy, b0 * b0)) ||
-                                 fmaf(-F.sy, yc, b1 * wc) < -slack * sqrtf(fmaf(F.sy, F.sy, b1 * b1));
-                if (out) continue;
-            }
+            if (!wbox || sphere_outside(F, wx, wy, wz, wR, R)) continue;
             bool keep = false;
             if (valid) {
                 float x[3], y[3], w[3];
