@@ -74,7 +74,9 @@ def parse():
                                            "dynamic", "sampler"],
                     default="paper_scene")
     ap.add_argument("--field-steps", type=int, default=30000, help="Adam steps of the neural field")
-    ap.add_argument("--field-lr", type=float, default=3e-3, help="initial learning rate of the field (cosine to 1%%)")
+    ap.add_argument("--field-lr", type=float, default=1e-3, help="initial learning rate of the field")
+    ap.add_argument("--field-lr-min", type=float, default=None, help="final learning rate (default lr / 100)")
+    ap.add_argument("--no-field", action="store_true", help="leave the neural-field measurement out of the line")
     ap.add_argument("--queries", type=int, default=10_000_000, help="query points of the field workload")
     ap.add_argument("--sessions", type=int, default=64, help="sessions of the batched workload")
     ap.add_argument("--fixations", type=int, default=0, help="use only the first N fixations (profiling)")
@@ -575,50 +577,44 @@ def sampler_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def field_arm(args):
-    """Neural density field on the paper-shaped scene: train on the normalised map of its 2M
-    samples (MSE, Adam, batch 65 536, --field-lr cosine to 1 %, --field-steps steps), then answer
-    --queries fresh surface points (the sampler at 5x density, seed 33) with the field and with the
-    plain accumulation at the same points (the judge); report queries/s of both and the field's
-    relative L2 error against the plain values. (lr 3e-3 with 30 000 steps: rates of 5e-3 and more become unstable or diverge,
-    longer budgets plateau near 0.056 on fresh points.)"""
+def field_measure(G, pipeline, ctx, stream, w, h, steps, lr, lr_min, queries, n_timed, n_warm, kernels=False):
+    """Config 3 on the map `h` of workload `w` (already accumulated and normalised): train the
+    neural density field on its samples (MSE, Adam, batch 65 536, lr cosine from `lr` to `lr_min`
+    over `steps` steps), then answer `queries` fresh surface points (the sampler again, seed 33, the
+    density scaled up) with the field and with the plain accumulation at the same points (the
+    judge). Returns the field's measurement: queries/s of both forms, the field's relative L2 error
+    against the plain values, the query kernel's roofline, the training step time and the clocks
+    sampled while the field kernels ran."""
     import torch
     import synth
-    from paper_2601_07571_gb300 import build as B
-    B.build()
-    import paper_2601_07571_gb300 as G
-    from paper_2601_07571_gb300 import pipeline
-    torch.cuda.set_device(0)
-    w = make_workload("paper_scene", args.fixations)
-    ctx = G.gm_create(0)
-    stream = torch.cuda.current_stream()
-    h = pipeline.run(ctx, w, stream=stream, normalize=True)
     W, ns, st, _ = G.gm_map_info(h.map)
     xyz = torch.empty((ns, 3), dtype=torch.float32, device="cuda")
     G.gm_samples_copy(h.samples, xyz, None, None, None, stream)
     lo, hi = xyz.min(0).values.cpu().numpy(), xyz.max(0).values.cpu().numpy()
-    # query points: the sampler again, another seed, density scaled to reach --queries
-    scale = args.queries / ns
+    scale = queries / ns
     qs = G.gm_sample_surface(h.scene, [m.density * scale for m in w.meshes], 33, 0, stream)
     nq = G.gm_samples_info(qs)
     qxyz = torch.empty((nq, 3), dtype=torch.float32, device="cuda")
     G.gm_samples_copy(qs, qxyz, None, None, None, stream)
-    # the field: train, then query
     f = G.gm_field_create(ctx, lo, hi, synth.field_init(3), stream)
     torch.cuda.synchronize()
+    clocks = ClockSampler()
+    clocks.start()
     t0 = time.perf_counter()
-    loss = G.gm_field_train(f, h.samples, h.map, 0, steps=args.field_steps, batch=65536, lr=args.field_lr,
-                            lr_min=args.field_lr / 100, seed=33, stream=stream)
+    loss = G.gm_field_train(f, h.samples, h.map, 0, steps=steps, batch=65536, lr=lr, lr_min=lr_min, seed=33,
+                            stream=stream)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     out = torch.empty(nq, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def time_queries(kernel):
         G.gm_field_query_kernel(f, kernel)
-        for _ in range(args.warmup):
+        for _ in range(n_warm):
             G.gm_field_query(f, qxyz, nq, out, stream)
         q_t = []
-        for _ in range(args.steps):
+        for _ in range(n_timed):
+            flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             G.gm_field_query(f, qxyz, nq, out, stream)
@@ -628,27 +624,31 @@ def field_arm(args):
         G.gm_sync(ctx, stream)
         return sum(q_t) / len(q_t)
 
-    def train_step_ms(kernel, steps=2000):
+    def train_step_ms(kernel, n=2000):
         # a fresh field trained by one kernel: device milliseconds per Adam step
         ft = G.gm_field_create(ctx, lo, hi, synth.field_init(3), stream)
         G.gm_field_train_kernel(ft, kernel)
-        G.gm_field_train(ft, h.samples, h.map, 0, steps=steps, batch=65536, lr=args.field_lr,
-                         lr_min=args.field_lr / 100, seed=34, stream=stream)
-        ms = G.gm_field_info(ft)["train_ms"] / steps
+        G.gm_field_train(ft, h.samples, h.map, 0, steps=n, batch=65536, lr=lr, lr_min=lr_min, seed=34,
+                         stream=stream)
+        ms = G.gm_field_info(ft)["train_ms"] / n
         G.gm_field_free(ft)
         return ms
 
-    train_tc_ms = G.gm_field_info(f)["train_ms"] / args.field_steps
-    train_ms_ms = train_step_ms(G.GM_FIELD_QUERY_MMA_SYNC)
-    mma_sync_ms = time_queries(G.GM_FIELD_QUERY_MMA_SYNC)
+    train_tc_ms = G.gm_field_info(f)["train_ms"] / steps
+    extra = {}
+    if kernels:
+        extra["train_step_ms_mma_sync"] = train_step_ms(G.GM_FIELD_QUERY_MMA_SYNC)
+        extra["query_ms_mma_sync"] = time_queries(G.GM_FIELD_QUERY_MMA_SYNC)
     field_ms = time_queries(G.GM_FIELD_QUERY_TCGEN05)   # the default kernel; `out` keeps its values
-    # the judge: plain accumulation at the query points, normalised by the training map's maximum
-    # a normalised map keeps its raw maximum: gm_map_copy returns it
+    clk = clocks.stop()
+    # the judge: plain accumulation at the query points, normalised by the training map's raw
+    # maximum (a normalised map keeps it: gm_map_copy returns it)
     raw_max = G.gm_map_copy(h.map, 0, torch.empty(ns, dtype=torch.float32, device="cuda"), stream)
     prm = pipeline.params_of(w, flags=G.GM_F_TIMING, normalize=False)
+    fix = pipeline.fixation_args(w.fixations, True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    mq = G.gm_accumulate_fixations(h.scene, qs, *pipeline.fixation_args(w.fixations, True), prm, stream)
+    mq = G.gm_accumulate_fixations(h.scene, qs, *fix, prm, stream)
     e1.record(stream)
     _, _, qst, _ = G.gm_map_info(mq)
     plain_ms = e0.elapsed_time(e1)
@@ -664,26 +664,49 @@ def field_arm(args):
     roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": None, "kernel": "k_field_query_tc", "peak_basis": basis,
             "work_basis": f"{flop_q} FLOP per query (four 64x64 BF16 layers + output)"}
-    line = {"metric": "neural-field queries/s vs plain", "value": nq / (field_ms * 1e-3), "unit": "queries/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": field_ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": f"field_on_{w.name}", "train_samples": int(ns), "queries": int(nq),
-                       "fixations": w.fixations.n, "field": "64 Fourier features, 4x64 ReLU, softplus",
-                       "train": {"steps": args.field_steps, "batch": 65536,
-                                 "lr": f"{args.field_lr:g} cosine to {args.field_lr / 100:g}"}},
-            "field_rel_l2_vs_plain": err, "train_s": train_s, "train_ms_device": info["train_ms"],
-            "final_batch_mse": loss,
-            "plain_form": {"value": nq / (plain_ms * 1e-3), "ms": plain_ms, "pairs": int(qst["pairs"]),
-                           "form": "gm_accumulate_fixations at the query points"},
-            "field_over_plain": plain_ms / field_ms, "roofline": roof,
-            "query_kernels_ms": {"tcgen05": field_ms, "mma_sync": mma_sync_ms},
-            "train_step_ms": {"tcgen05": train_tc_ms, "mma_sync": train_ms_ms},
-            "train_tflops": {"tcgen05": train_flop / (train_tc_ms * 1e-3) / 1e12,
-                             "mma_sync": train_flop / (train_ms_ms * 1e-3) / 1e12,
-                             "work_basis": "65536 points x 90240 FLOP (forward 32896, dH 24576, dW 32768)"}}
+    res = {"metric": "neural-field queries/s vs plain", "value": nq / (field_ms * 1e-3), "unit": "queries/s",
+           "ms_per_query_batch": field_ms, "dtype": "bf16",
+           "config": {"workload": f"field_on_{w.name}", "train_samples": int(ns), "queries": int(nq),
+                      "fixations": w.fixations.n, "field": "64 Fourier features (10 octaves), 4x64 ReLU, softplus",
+                      "train": {"steps": steps, "batch": 65536, "lr": f"{lr:g} cosine to {lr_min:g}",
+                                "optimizer": "Adam (0.9, 0.999)", "loss": "MSE on the max-normalised map"},
+                      "l2": "flushed between query batches (256 MiB write)"},
+           "rel_l2_vs_plain": err, "rel_l2_target": 1e-2, "train_s": train_s, "train_ms_device": info["train_ms"],
+           "final_batch_mse": loss,
+           "plain_form": {"value": nq / (plain_ms * 1e-3), "ms": plain_ms, "pairs": int(qst["pairs"]),
+                          "form": "gm_accumulate_fixations at the query points"},
+           "field_over_plain": plain_ms / field_ms, "roofline": roof,
+           "train_step_ms": train_tc_ms,
+           "train_tflops": train_flop / (train_tc_ms * 1e-3) / 1e12,
+           "train_work_basis": "65536 points x 90240 FLOP (forward 32896, dH 24576, dW 32768)",
+           "clocks": clk, **extra}
     G.gm_field_free(f)
     G.gm_map_free(mq)
     G.gm_samples_free(qs)
+    return res
+
+
+def field_arm(args):
+    """Neural density field on the paper-shaped scene as its own line (config 3 with the step
+    budget and learning rate of the command line), plus the warp-level mma.sync kernels timed
+    beside the tensor-core ones."""
+    import torch
+    from paper_2601_07571_gb300 import build as B
+    B.build()
+    import paper_2601_07571_gb300 as G
+    from paper_2601_07571_gb300 import pipeline
+    torch.cuda.set_device(0)
+    w = make_workload("paper_scene", args.fixations)
+    ctx = G.gm_create(0)
+    stream = torch.cuda.current_stream()
+    h = pipeline.run(ctx, w, stream=stream, normalize=True)
+    r = field_measure(G, pipeline, ctx, stream, w, h, args.field_steps, args.field_lr,
+                      args.field_lr_min if args.field_lr_min is not None else args.field_lr / 100,
+                      args.queries, args.steps, args.warmup, kernels=True)
+    line = {"metric": r.pop("metric"), "value": r.pop("value"), "unit": r.pop("unit"), "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r.pop("ms_per_query_batch"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": r.pop("dtype"),
+            "data": "synthetic", "config": r.pop("config"), **r}
     h.free()
     G.gm_destroy(ctx)
     print(json.dumps(line), flush=True)
@@ -852,6 +875,13 @@ def main():
             "e2e": {"value": whole_job_rate(pairs, world, e2e_s), "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(out.numel() * 4), "ms_per_step": e2e_s * 1e3},
             "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_field and args.workload == "paper_scene" and not args.fixations:
+        # the metric's second half: config 3 on this workload's map, with its own clock record
+        hf = pipeline.run(ctx, w, stream=stream, normalize=True)
+        line["field"] = field_measure(G, pipeline, ctx, stream, w, hf, args.field_steps, args.field_lr,
+                                      args.field_lr_min if args.field_lr_min is not None else args.field_lr / 100,
+                                      args.queries, args.steps, args.warmup)
+        hf.free()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         dt, p, n = calibrated_oracle(w, args.cpu_seconds, cores)

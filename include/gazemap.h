@@ -233,10 +233,14 @@ gm_status gm_samples_export(const gm_samples* s, const gm_map* map, uint32_t win
  * launching anything. Every call shares that array and it keeps the last call's contents;
  * nothing in it needs to start at zero (each call writes every partial it reads), but calls
  * that overlap on the GPU (different streams, or other threads) race on it and must be
- * serialised by the caller. The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call before any stream
- * capture. Densities that are negative, NaN or give a triangle 2^31 or more samples set that
- * triangle's count to 0 and are reported by the next gm_sync. */
+ * serialised by the caller. The first call with each gm_ctx looks up the array's device address
+ * (cudaGetSymbolAddress, with the context's device current); make that first call before any
+ * stream capture. Densities that are negative, NaN or give a triangle 2^31 or more samples set that
+ * triangle's count to 0 and are reported by the next gm_sync (GM_ERR_INTERNAL). A scene whose
+ * expected total (the FP64 sum of k A over its triangles) exceeds 2^31 - 16 samples would wrap
+ * the int64 prefix: then every offset is written as 0 and the next gm_sync returns
+ * GM_ERR_UNSUPPORTED. The scratch address is looked up per gm_ctx: after a cudaDeviceReset,
+ * create a new context (the old one's device memory is gone anyway) and it looks it up again. */
 gm_status gm_tri_offsets_noalloc(gm_ctx* ctx, const float* tri_xyz, const double* density_per_tri,
                                  uint32_t n_tris, int64_t* offsets, gm_stream stream);
 

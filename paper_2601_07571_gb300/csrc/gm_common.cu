@@ -120,7 +120,11 @@ extern "C" gm_status gm_sync(gm_ctx* c, gm_stream stream) {
         return gm_set_error(GM_ERR_INTERNAL, "device: BVH traversal stack overflow");
     if (err == GM_DEV_WAIT_TIMEOUT) {
         cudaMemset(c->dev_err, 0, sizeof(int));
-        return gm_set_error(GM_ERR_INTERNAL, "device: an asynchronous copy or tensor-core product did not complete in time");
+        return gm_set_error(GM_ERR_TIMEOUT, "device: an asynchronous copy or tensor-core product did not complete in time");
+    }
+    if (err == GM_DEV_TOO_MANY_SAMPLES) {
+        cudaMemset(c->dev_err, 0, sizeof(int));
+        return gm_set_error(GM_ERR_UNSUPPORTED, "device: the scene needs 2^31 - 16 or more samples (offsets set to 0)");
     }
     if (err != 0) return gm_set_error(GM_ERR_INTERNAL, "device: consistency check failed (" + std::to_string(err) + ")");
     return GM_OK;

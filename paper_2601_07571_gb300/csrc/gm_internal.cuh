@@ -27,13 +27,15 @@ gm_status gm_cuda_error(cudaError_t e, const char* what);
     } while (0)
 
 // Device-side fault codes written to gm_ctx::dev_err (first writer wins).
-enum { GM_DEV_OK = 0, GM_DEV_STACK_OVERFLOW = 1, GM_DEV_BAD_INDEX = 2, GM_DEV_WAIT_TIMEOUT = 4 };
+enum { GM_DEV_OK = 0, GM_DEV_STACK_OVERFLOW = 1, GM_DEV_BAD_INDEX = 2, GM_DEV_WAIT_TIMEOUT = 4,
+       GM_DEV_TOO_MANY_SAMPLES = 8 };
 
 struct gm_ctx {
     int device = 0;
     int n_sm = 0;
     int* dev_err = nullptr;      // one int in device memory, zero when healthy
     unsigned long long launches = 0;  // kernels launched through this context (host count)
+    void* noalloc_scratch = nullptr;  // device address of the allocation-free entry point's array
 };
 
 struct gm_scene {

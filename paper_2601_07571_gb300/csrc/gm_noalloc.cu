@@ -10,11 +10,17 @@
 // the prefix buffer, and the one scratch buffer -- the per-block partial sums of the prefix --
 // is the file-scope device array below, which every GPU that loads this library holds until the
 // process exits.
+//
+// The 32.32 fixed-point prefix is an int64 and would wrap once the scene needs about 2^31 samples;
+// each scan block therefore also sums its k A in FP64, and when a block or the whole scene
+// exceeds 2^31 - 16 expected samples every partial sum is marked negative, every offset is written
+// as 0 and the device error word reports it (gm_sync: GM_ERR_UNSUPPORTED).
 #include <cmath>
 #include <mutex>
 #include <string>
 
 #include "gm_internal.cuh"
+#include "gm_scan.cuh"
 
 namespace {
 
@@ -30,49 +36,21 @@ static __device__ __align__(256) int64_t g_noalloc_scan_part[NA_MAX_BLOCKS];
 
 namespace {
 
-constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_setup_mutex;
-int64_t* g_part_addr[NA_MAX_DEVICES] = {};
 
-template <typename T>
-__device__ __forceinline__ T na_warp_incl(T v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        T u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
-    }
-    return v;
-}
+// Expected samples (FP64 sum of k A) above which the int64 prefix could wrap: the FP64 sums are
+// within a few samples of the exact ones, and (2^31 - 16 + 4) 2^32 + n_tris / 2 < 2^63.
+constexpr double NA_MAX_EXPECTED = 2147483632.0;
 
-template <typename T, int NT>
-__device__ __forceinline__ T na_block_excl(T v, T* total) {
-    __shared__ T warp_tot[NT / 32];
-    __shared__ T tot_sh;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T inc = na_warp_incl(v);
-    if (lane == 31) warp_tot[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        T w = lane < NT / 32 ? warp_tot[lane] : T(0);
-        T wi = na_warp_incl(w);
-        if (lane < NT / 32) warp_tot[lane] = wi - w;
-        if (lane == NT / 32 - 1) tot_sh = wi;
-    }
-    __syncthreads();
-    T res = warp_tot[warp] + inc - v;
-    *total = tot_sh;
-    __syncthreads();
-    return res;
-}
-
-// q_i = rint(k_i A_i 2^32) into off[i + 1]; then the partial sum of each tile.
+// q_i = rint(k_i A_i 2^32) into off[i + 1]; then the partial sum of each tile, or -1 when the
+// tile's FP64 sum of k A is too large for the int64 sum.
 __global__ void __launch_bounds__(NA_THREADS) na_counts_reduce(const float* __restrict__ tri,
                                                                const double* __restrict__ dens, uint32_t nt,
                                                                int64_t* __restrict__ off, int64_t* __restrict__ part,
                                                                int* __restrict__ err) {
     const uint32_t base = blockIdx.x * (uint32_t)NA_TILE;
-    int64_t s = 0;
+    uint64_t s = 0;   // unsigned: a tile that is too large may wrap it (it is then marked, not used)
+    double ks = 0.0;
 #pragma unroll
     for (int it = 0; it < NA_ITEMS; ++it) {
         const uint32_t i = base + it * NA_THREADS + threadIdx.x;
@@ -91,23 +69,42 @@ __global__ void __launch_bounds__(NA_THREADS) na_counts_reduce(const float* __re
         }
         const int64_t q = __double2ll_rn(__dmul_rn(k, 4294967296.0));
         off[i + 1] = q;
-        s += q;
+        s += (uint64_t)q;
+        ks += k;
     }
-    int64_t tot;
-    na_block_excl<int64_t, NA_THREADS>(s, &tot);
-    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    double ktot;
+    block_excl_scan<double, NA_THREADS>(ks, &ktot);
+    uint64_t tot;
+    block_excl_scan<uint64_t, NA_THREADS>(s, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = ktot <= NA_MAX_EXPECTED ? (int64_t)tot : (int64_t)-1;
 }
 
-// Exclusive scan of the partial sums (one block).
-__global__ void __launch_bounds__(1024) na_scan_parts(int64_t* __restrict__ part, uint32_t nb) {
+// Exclusive scan of the partial sums (one block). First the FP64 total of the partials: when a
+// partial is marked or the total exceeds the limit, every partial becomes -1 and the error word
+// is set; else the exact int64 scan (no partial prefix can then reach 2^63).
+__global__ void __launch_bounds__(1024) na_scan_parts(int64_t* __restrict__ part, uint32_t nb, int* __restrict__ err) {
     __shared__ int64_t carry;
+    double acc = 0.0;
+    int bad = 0;
+    for (uint32_t i = threadIdx.x; i < nb; i += 1024) {
+        const int64_t v = part[i];
+        bad |= v < 0;
+        acc += (double)v;
+    }
+    double total;
+    block_excl_scan<double, 1024>(acc, &total);
+    if (__syncthreads_or(bad) || !(total <= NA_MAX_EXPECTED * 4294967296.0)) {
+        for (uint32_t i = threadIdx.x; i < nb; i += 1024) part[i] = -1;
+        if (threadIdx.x == 0) atomicCAS(err, 0, GM_DEV_TOO_MANY_SAMPLES);
+        return;
+    }
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (uint32_t b0 = 0; b0 < nb; b0 += 1024) {
         const uint32_t i = b0 + threadIdx.x;
         const int64_t v = i < nb ? part[i] : 0;
         int64_t tot;
-        const int64_t ex = na_block_excl<int64_t, 1024>(v, &tot);
+        const int64_t ex = block_excl_scan<int64_t, 1024>(v, &tot);
         if (i < nb) part[i] = carry + ex;
         __syncthreads();
         if (threadIdx.x == 0) carry += tot;
@@ -120,6 +117,12 @@ __global__ void __launch_bounds__(NA_THREADS) na_scan_down(int64_t* __restrict__
                                                            const int64_t* __restrict__ part) {
     __shared__ int64_t tile[NA_TILE];
     const uint32_t base = blockIdx.x * (uint32_t)NA_TILE;
+    if (blockIdx.x == 0 && threadIdx.x == 0) off[0] = 0;
+    if (part[blockIdx.x] < 0) {
+        // the scene needs too many samples: no offsets (the error word says why)
+        for (uint32_t i = base + threadIdx.x; i < nt && i < base + NA_TILE; i += NA_THREADS) off[i + 1] = 0;
+        return;
+    }
 #pragma unroll
     for (int it = 0; it < NA_ITEMS; ++it) {
         const uint32_t i = base + it * NA_THREADS + threadIdx.x;
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(NA_THREADS) na_scan_down(int64_t* __restrict__
         v[it] = s;
     }
     int64_t tot;
-    const int64_t ex = na_block_excl<int64_t, NA_THREADS>(s, &tot) + part[blockIdx.x];
+    const int64_t ex = block_excl_scan<int64_t, NA_THREADS>(s, &tot) + part[blockIdx.x];
 #pragma unroll
     for (int it = 0; it < NA_ITEMS; ++it) tile[threadIdx.x * NA_ITEMS + it] = v[it] + ex;
     __syncthreads();
@@ -142,7 +145,6 @@ __global__ void __launch_bounds__(NA_THREADS) na_scan_down(int64_t* __restrict__
         const uint32_t i = base + it * NA_THREADS + threadIdx.x;
         if (i < nt) off[i + 1] = (tile[it * NA_THREADS + threadIdx.x] + ((int64_t)1 << 31)) >> 32;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) off[0] = 0;
 }
 
 }  // namespace
@@ -159,20 +161,19 @@ extern "C" gm_status gm_tri_offsets_noalloc(gm_ctx* ctx, const float* tri_xyz, c
                                 std::to_string(NA_MAX_BLOCKS) + " partial sums)");
     if (!gm_is_device_ptr(offsets) || (n_tris > 0 && (!gm_is_device_ptr(tri_xyz) || !gm_is_device_ptr(density_per_tri))))
         return gm_set_error(GM_ERR_INVALID_ARG, "gm_tri_offsets_noalloc: every buffer must be device memory");
-    if (ctx->device < 0 || ctx->device >= NA_MAX_DEVICES)
-        return gm_set_error(GM_ERR_UNSUPPORTED, "gm_tri_offsets_noalloc: device ordinal too large");
     GM_TRY_CUDA(cudaSetDevice(ctx->device));
     int64_t* part = nullptr;
     {
-        // once per device, with that device current: the device address of the scratch array
+        // once per context, with its device current: the device address of the scratch array. A
+        // context made after a reset of the device (cudaDeviceReset) looks it up again.
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_part_addr[ctx->device]) {
+        if (!ctx->noalloc_scratch) {
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scan_part);
             if (e != cudaSuccess) return gm_cuda_error(e, "gm_tri_offsets_noalloc: cudaGetSymbolAddress");
-            g_part_addr[ctx->device] = static_cast<int64_t*>(p);
+            ctx->noalloc_scratch = p;
         }
-        part = g_part_addr[ctx->device];
+        part = static_cast<int64_t*>(ctx->noalloc_scratch);
     }
     cudaStream_t s = (cudaStream_t)stream;
     if (n_tris == 0) {
@@ -180,7 +181,7 @@ extern "C" gm_status gm_tri_offsets_noalloc(gm_ctx* ctx, const float* tri_xyz, c
         return GM_OK;
     }
     na_counts_reduce<<<(uint32_t)nb, NA_THREADS, 0, s>>>(tri_xyz, density_per_tri, n_tris, offsets, part, ctx->dev_err);
-    na_scan_parts<<<1, 1024, 0, s>>>(part, (uint32_t)nb);
+    na_scan_parts<<<1, 1024, 0, s>>>(part, (uint32_t)nb, ctx->dev_err);
     na_scan_down<<<(uint32_t)nb, NA_THREADS, 0, s>>>(offsets, n_tris, part);
     ctx->launches += 3;
     GM_TRY_CUDA(cudaGetLastError());

@@ -18,25 +18,43 @@
 
 namespace {
 
-__global__ void k_tri_counts(const float4* __restrict__ tri, const uint32_t* __restrict__ tri_mesh,
-                             const double* __restrict__ dens, uint32_t nt, int64_t* __restrict__ q,
-                             int* __restrict__ err) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nt) return;
-    float4 a = tri[3 * i], b = tri[3 * i + 1], c = tri[3 * i + 2];
-    double e1x = __dsub_rn(b.x, a.x), e1y = __dsub_rn(b.y, a.y), e1z = __dsub_rn(b.z, a.z);
-    double e2x = __dsub_rn(c.x, a.x), e2y = __dsub_rn(c.y, a.y), e2z = __dsub_rn(c.z, a.z);
-    double cx = __dsub_rn(__dmul_rn(e1y, e2z), __dmul_rn(e1z, e2y));
-    double cy = __dsub_rn(__dmul_rn(e1z, e2x), __dmul_rn(e1x, e2z));
-    double cz = __dsub_rn(__dmul_rn(e1x, e2y), __dmul_rn(e1y, e2x));
-    double n2 = __dadd_rn(__dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)), __dmul_rn(cz, cz));
-    double A = __dmul_rn(0.5, __dsqrt_rn(n2));
-    double k = __dmul_rn(dens[tri_mesh[i]], A);
-    if (!(k >= 0.0) || k >= 2147483648.0) {
-        atomicCAS(err, 0, GM_DEV_BAD_INDEX);
-        k = 0.0;
+// q_i = rint(k_i A_i 2^32) per triangle. The int64 prefix of the q_i wraps once the scene needs
+// about 2^31 samples in total, so every block also adds its FP64 sum of k_i A_i into *ksum (one
+// atomic per block); the host refuses the scene when that sum exceeds 2^31 - 16 before it trusts
+// the prefix.
+__global__ void __launch_bounds__(256) k_tri_counts(const float4* __restrict__ tri, const uint32_t* __restrict__ tri_mesh,
+                                                   const double* __restrict__ dens, uint32_t nt,
+                                                   int64_t* __restrict__ q, double* __restrict__ ksum,
+                                                   int* __restrict__ err) {
+    __shared__ double wsum[8];
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    double k = 0.0;
+    if (i < nt) {
+        float4 a = tri[3 * i], b = tri[3 * i + 1], c = tri[3 * i + 2];
+        double e1x = __dsub_rn(b.x, a.x), e1y = __dsub_rn(b.y, a.y), e1z = __dsub_rn(b.z, a.z);
+        double e2x = __dsub_rn(c.x, a.x), e2y = __dsub_rn(c.y, a.y), e2z = __dsub_rn(c.z, a.z);
+        double cx = __dsub_rn(__dmul_rn(e1y, e2z), __dmul_rn(e1z, e2y));
+        double cy = __dsub_rn(__dmul_rn(e1z, e2x), __dmul_rn(e1x, e2z));
+        double cz = __dsub_rn(__dmul_rn(e1x, e2y), __dmul_rn(e1y, e2x));
+        double n2 = __dadd_rn(__dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)), __dmul_rn(cz, cz));
+        double A = __dmul_rn(0.5, __dsqrt_rn(n2));
+        k = __dmul_rn(dens[tri_mesh[i]], A);
+        if (!(k >= 0.0) || k >= 2147483648.0) {
+            atomicCAS(err, 0, GM_DEV_BAD_INDEX);
+            k = 0.0;
+        }
+        q[i] = __double2ll_rn(__dmul_rn(k, 4294967296.0));
     }
-    q[i] = __double2ll_rn(__dmul_rn(k, 4294967296.0));
+    double v = k;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += wsum[w];
+        if (b > 0.0) atomicAdd(ksum, b);
+    }
 }
 
 __global__ void k_offsets(const int64_t* __restrict__ S, uint32_t nt, int64_t* __restrict__ off) {
@@ -238,19 +256,25 @@ extern "C" gm_status gm_sample_surface(gm_scene* sc, const double* density_per_m
         return st;
     };
     gm_status st;
-    if ((st = gm_alloc((void**)&dens, sizeof(double) * sc->n_meshes, s)) != GM_OK) return fail(st);
+    // dens[0 .. n_meshes) the per-mesh densities, dens[n_meshes] the FP64 sum of k A over triangles
+    if ((st = gm_alloc((void**)&dens, sizeof(double) * (sc->n_meshes + 1), s)) != GM_OK) return fail(st);
     if ((st = gm_alloc((void**)&q, sizeof(int64_t) * nt, s)) != GM_OK) return fail(st);
     if ((st = gm_alloc((void**)&sm->tri_offset, sizeof(int64_t) * (nt + 1), s)) != GM_OK) return fail(st);
     cudaError_t e = cudaMemcpyAsync(dens, density_per_mesh, sizeof(double) * sc->n_meshes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(gm_cuda_error(e, "density upload"));
+    if ((e = cudaMemsetAsync(dens + sc->n_meshes, 0, sizeof(double), s)) != cudaSuccess)
+        return fail(gm_cuda_error(e, "gm_sample_surface"));
     int launches = 0;
-    k_tri_counts<<<gm_div_up(nt, 256), 256, 0, s>>>(sc->tri_canon, sc->tri_mesh, dens, nt, q, sc->ctx->dev_err);
+    k_tri_counts<<<gm_div_up(nt, 256), 256, 0, s>>>(sc->tri_canon, sc->tri_mesh, dens, nt, q, dens + sc->n_meshes,
+                                                    sc->ctx->dev_err);
     if ((st = gm_inclusive_scan_i64(q, nt, s, &launches)) != GM_OK) return fail(st);
     k_offsets<<<gm_div_up(nt, 256), 256, 0, s>>>(q, nt, sm->tri_offset);
     launches += 2;
     int64_t total = 0;
+    double ksum = 0.0;
     int herr = 0;
     if ((e = cudaMemcpyAsync(&total, sm->tri_offset + nt, sizeof(int64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&ksum, dens + sc->n_meshes, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(&herr, sc->ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return fail(gm_cuda_error(e, "gm_sample_surface"));
@@ -262,7 +286,11 @@ extern "C" gm_status gm_sample_surface(gm_scene* sc, const double* density_per_m
         cudaMemsetAsync(sc->ctx->dev_err, 0, sizeof(int), s);
         return fail(gm_set_error(GM_ERR_UNSUPPORTED, "gm_sample_surface: a triangle needs 2^31 or more samples"));
     }
-    if (total > 0x7fffffffLL)
+    // The FP64 sum is within 4 samples of the exact one (at most 2^24 block atomics of relative
+    // error 2^-53 on a sum below 2^31), so sum k A <= 2^31 - 16 keeps the 32.32 prefix below
+    // (2^31 - 12) 2^32 + n_tris / 2 < 2^63: no wrap. Beyond it the prefix may have wrapped and
+    // the sum decides.
+    if (!(ksum <= 2147483632.0) || total < 0 || total > 0x7fffffffLL)
         return fail(gm_set_error(GM_ERR_UNSUPPORTED, "gm_sample_surface: more than 2^31-1 samples"));
     sm->n = (uint64_t)total;
     const uint32_t n = (uint32_t)total;

@@ -327,8 +327,27 @@ def gm_samples_free(samples) -> None:
 
 
 def gm_tri_offsets_noalloc(ctx, tri_xyz, density_per_tri, n_tris: int, offsets, stream=None) -> None:
-    """Per-triangle offsets from caller-owned device buffers, allocating nothing (see the header)."""
-    _check(lib().gm_tri_offsets_noalloc(ctx, _ptr(tri_xyz), _ptr(density_per_tri), C.c_uint32(n_tris),
+    """Per-triangle offsets from caller-owned device buffers, allocating nothing (see the header).
+
+    The C entry point cannot see buffer sizes, so they are checked here: tri_xyz float32 with at
+    least 9 * n_tris elements, density_per_tri float64 with at least n_tris, offsets int64 with at
+    least n_tris + 1, all on a CUDA device. Sizes beyond the fixed scratch are left to the library,
+    which refuses them before launching anything."""
+    import torch
+    n = int(n_tris)
+    if n < 0 or n > 0xFFFFFFFF:
+        raise ValueError("gm_tri_offsets_noalloc: n_tris must fit in uint32")
+    need = n if n <= 65536 * 2048 else 0   # oversized requests reach the library's own refusal
+    for name, t, dt, cnt in (("tri_xyz", tri_xyz, torch.float32, 9 * need),
+                             ("density_per_tri", density_per_tri, torch.float64, need),
+                             ("offsets", offsets, torch.int64, need + 1)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"gm_tri_offsets_noalloc: {name} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"gm_tri_offsets_noalloc: {name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous() or t.numel() < cnt:
+            raise ValueError(f"gm_tri_offsets_noalloc: {name} must be contiguous with at least {cnt} elements")
+    _check(lib().gm_tri_offsets_noalloc(ctx, _ptr(tri_xyz), _ptr(density_per_tri), C.c_uint32(n),
                                         _ptr(offsets), _stream(stream)))
 
 
