@@ -317,7 +317,9 @@ def test_paper_scene_full_size_sampled(G, ctx, pipe):
     which = np.array(sorted(pick), np.int64)
     pts = s_all.xyz.astype(np.float32)
     stri = s_all.tri.astype(np.uint32)
-    ora = oracle.accumulate(tri, pts[which].astype(np.float64), s_all.tri[which], fx, w.params, delta_abs=3e-5,
+    # grazing margin: 16 ulp of the 4-5 m eye-to-vertex distances of this scene (the FP32
+    # watertight test decides within a few ulp of them)
+    ora = oracle.accumulate(tri, pts[which].astype(np.float64), s_all.tri[which], fx, w.params, delta_abs=8e-6,
                             cone_band=1e-4)
     d, amb, sens = ora["density"][0], ora["amb"][0], ora["sens"][0]
     assert (d > 0).sum() >= 100
