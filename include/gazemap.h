@@ -93,8 +93,11 @@ enum {
     GM_F_TILE_CONSECUTIVE = 64, /* warp tiles of 128 consecutive samples (else four 32-sample runs over 1024) */
     GM_F_STATIC_TILES = 128, /* one warp tile per warp of a full grid (else warps pull tiles from a counter) */
     GM_F_NO_TILE_CULL = 256, /* test every sample against every fixation (no warp-tile sphere test) */
-    GM_F_BLOCK128 = 512     /* blocks of 128 threads (7 per SM, 72 registers; 8 per SM with GM_F_REGCAP64)
+    GM_F_BLOCK128 = 512,    /* blocks of 128 threads (7 per SM, 72 registers; 8 per SM with GM_F_REGCAP64)
                                for the ray-queue binary-tree variant, instead of 256 (3 or 4 per SM) */
+    GM_F_BVH = 1024,        /* occlusion rays walk the BVH instead of the eye grid (the flags NO_COMPACT,
+                               WIDE_BVH, REGCAP64 and BLOCK128 select BVH variants and imply it) */
+    GM_F_GRID64 = 2048      /* eye grid of 64 x 64 cells per fixation instead of 128 x 128 */
 };
 
 typedef struct {
@@ -107,8 +110,12 @@ typedef struct {
     float accumulate_ms;      /* cone + occlusion + Gaussian + store + max kernel */
     float normalize_ms;
     uint32_t launches;        /* kernels this call launched */
-    uint64_t nodes_visited;   /* BVH nodes fetched by all occlusion rays */
+    uint64_t nodes_visited;   /* BVH nodes fetched by all occlusion rays (eye grid: cell entries read) */
     uint64_t tris_tested;     /* ray/triangle tests performed by all occlusion rays */
+    uint64_t pairs_tested;    /* sample x fixation cone tests evaluated (pairs of warp tiles whose bounding
+                                 sphere the cone misses are skipped without a per-sample test) */
+    float grid_ms;            /* eye-grid frames, counts and (first chunk's) cell lists (GM_F_TIMING) */
+    uint32_t grid_chunks;     /* fixation chunks the eye grid was built in (0: BVH occlusion) */
 } gm_map_stats;
 
 /* ---- context ------------------------------------------------------------------------ */
@@ -253,7 +260,16 @@ gm_status gm_tri_offsets_noalloc(gm_ctx* ctx, const float* tri_xyz, const double
  *   then value[window(f)][s] += t_f / (sigma sqrt(2 pi)) exp(-(d2/d1)^2 / (2 sigma^2)).
  * Sums are compensated (Kahan) FP32 in fixation order. The maximum of each window's map is
  * kept; with params->normalize the map is divided by it in place (max 0 => map stays 0 and
- * the call returns GM_WARN_EMPTY at gm_map_info). */
+ * the call returns GM_WARN_EMPTY at gm_map_info).
+ * Occlusion: by default each fixation gets an eye grid -- the triangles that can meet its cone,
+ * binned by their image in the gaze frame into 128 x 128 cells (GM_F_GRID64: 64 x 64) and sorted
+ * by depth -- and a segment tests the triangles of its own cell; GM_F_BVH walks the scene's BVH
+ * instead. Both give the same maps (the same triangle test over every triangle it can report).
+ * The grid's memory is taken on the stream for the call: at most a third of the free device
+ * memory for the cell lists of one chunk of fixations (more fixations run in several chunks) and
+ * 1 GiB of offset tables; the environment variable GM_EYEGRID_CHUNK_ENTRIES, read at each call,
+ * lowers the per-chunk entry budget. The call reads the per-fixation list sizes back once (it
+ * synchronises the stream). */
 gm_status gm_accumulate_fixations(gm_scene* scene, gm_samples* samples, const gm_fixations* fix,
                                   const gm_params* params, gm_stream stream, gm_map** out);
 /* The same accumulation for a scene whose meshes move from window to window (params->window_s > 0

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgazemap.so")
 SOURCES = ["gm_common.cu", "gm_sort.cu", "gm_scene.cu", "gm_sampler.cu", "gm_accum.cu", "gm_batch.cu",
-           "gm_field.cu", "gm_noalloc.cu", "gm_zbuf.cu"]
+           "gm_field.cu", "gm_noalloc.cu", "gm_zbuf.cu", "gm_eyegrid.cu"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",
               "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 

@@ -10,9 +10,11 @@
 // streams the fixation list through shared memory in tiles; for each fixation every thread
 // runs the 4-sigma cone test on its samples (p = s - e, d1 = p.r^, c = p x r^,
 // in-cone <=> d1 > 0 and |c|^2 <= (cutoff tan theta)^2 d1^2, about 20 FP32 instructions per
-// pair) and, for in-cone pairs only, traces the occlusion segment e -> e + (1 - eps) p through
-// the BVH (any-hit, early exit, the sample's own triangle skipped) with the watertight
-// ray/triangle test of Woop, Benthin and Wald (JCGT 2013). A visible pair adds
+// pair) and, for in-cone pairs only, traces the occlusion segment e -> e + (1 - eps) p (any-hit,
+// early exit, the sample's own triangle skipped) with the watertight ray/triangle test of Woop,
+// Benthin and Wald (JCGT 2013), over the triangles of the segment's cell in the fixation's eye
+// grid (gm_eyegrid.cu) or, with GM_F_BVH, through the BVH. With more fixations than one eye-grid
+// chunk holds, the kernel runs once per chunk and the compensated sums carry over. A visible pair adds
 // g = w exp(-(|c|/d1)^2 / (2 tan^2 theta)), i.e. the paper's t/(sigma sqrt(2 pi)) *
 // exp(-sigma_k^2 / (2 sigma^2)) with sigma_k = d2 / d1, d2 = |c|, in fixation order (Kahan).
 // When the window id of the next fixation changes (block-uniform), the block stores its sums
@@ -22,6 +24,7 @@
 // Normalisation (Section 3.2.3) is a separate streaming kernel: v / max per window.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -86,7 +89,7 @@ __global__ void k_fix_pack(const uint32_t* __restrict__ keys, const uint32_t* __
 // rays (densely gazed patches) spread over the whole run instead of forming a tail. MINB is the
 // minimum number of resident blocks per SM the register allocation must allow (3: up to 80
 // registers, 4: up to 64).
-template <bool DEBUG, bool COMPACT, bool WIDE, int MINB, int NT = ACC_THREADS>
+template <bool DEBUG, bool COMPACT, bool WIDE, int MINB, int NT = ACC_THREADS, bool GRID = false>
 __global__ void __launch_bounds__(NT, MINB) k_accumulate(
     const float4* __restrict__ spos, const uint32_t* __restrict__ sidx, const float4* __restrict__ fix,
     const uint32_t* __restrict__ n_fix_dev, const float4* __restrict__ nodes, const float4* __restrict__ tris,
@@ -114,18 +117,18 @@ __global__ void __launch_bounds__(NT, MINB) k_accumulate(
             tile = blockIdx.x * (NT / 32) + warp;
         }
         if (tile >= n_tiles) break;
-        warp_tile<DEBUG, COMPACT, WIDE>(tile, spos, sidx, fix, nf, nodes, tris, P, out, max_bits, wsmp + wb, wacc + wb,
-                                        qslot + wb, qg + wb, wbox + warp, &counters[2], dbg, err, st);
+        warp_tile<DEBUG, COMPACT, WIDE, GRID>(tile, spos, sidx, fix, nf, nodes, tris, P, out, max_bits, wsmp + wb,
+                                              wacc + wb, qslot + wb, qg + wb, wbox + warp, &counters[2], dbg, err, st);
     }
     warp_stats_commit(st, counters);
 }
 
 // (The driver's default shared-memory carveout is kept: preferring the largest L1 leaves room for
 // fewer blocks per SM and measured 316 vs 253 ms at the paper scene.)
-template <bool D, bool Cm, bool Wd, int Mb, int NT = ACC_THREADS>
+template <bool D, bool Cm, bool Wd, int Mb, int NT = ACC_THREADS, bool Gr = false>
 int acc_occupancy() {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_accumulate<D, Cm, Wd, Mb, NT>, NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_accumulate<D, Cm, Wd, Mb, NT, Gr>, NT, 0);
     return b > 0 ? b : 1;
 }
 
@@ -248,8 +251,10 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
         mp->stats.n_windows = (uint32_t)W;
     }
     std::vector<void*> tmp;
+    EyeGrid* egp = nullptr;   // set once the eye grid exists, freed with the temporaries
     auto fail = [&](gm_status st) {
         for (void* p : tmp) cudaFreeAsync(p, s);
+        if (egp) eg_free(egp, s);
         if (!into) gm_map_free(mp);
         return st;
     };
@@ -264,7 +269,7 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
 
     const bool timing = mp->timing && !into;
     if (timing) {
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 6; ++i) {
             cudaError_t e = cudaEventCreate(&mp->ev[i]);
             if (e != cudaSuccess) return fail(gm_cuda_error(e, "cudaEventCreate"));
         }
@@ -338,6 +343,9 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
     P.nt = sc->n_tris;
     P.dbg_cap = mp->dbg_cap;
     DebugOut dbg{mp->dbg_sample, mp->dbg_fix, mp->dbg_vis, mp->dbg_g, orig};
+    EyeGrid eg;
+    egp = &eg;
+    float2* carry = nullptr;
     const bool reorder = !(prm->flags & GM_F_NO_REORDER) && sm->work_pos;
     uint32_t* ident = nullptr;
     const float4* spos = reorder ? sm->work_pos : sm->pos;
@@ -357,44 +365,92 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
         const bool compact = !(prm->flags & GM_F_NO_COMPACT);
         const bool wide = (prm->flags & GM_F_WIDE_BVH) && sc->nodes4;
         const bool occ4 = (prm->flags & GM_F_REGCAP64) != 0;
+        const bool b128 = (prm->flags & GM_F_BLOCK128) != 0;
+        // the eye grid traces from the ray queue of the default kernel shape; the BVH variants
+        // (in place, 4-wide, register caps, 128-thread blocks) keep the tree
+        const bool grid = !(prm->flags & GM_F_BVH) && compact && !wide && !occ4 && !b128 && nf > 0;
         const float4* tree = wide ? sc->nodes4 : sc->nodes;
         const int code = (compact ? 1 : 0) | (wide ? 2 : 0) | (occ4 ? 4 : 0);
         // persistent grid: every resident block slot once, never more blocks than tiles need
-#define GM_LAUNCH_ACC_NT(D, Cm, Wd, Mb, NT)                                                                    \
-    do {                                                                                                       \
-        const uint32_t all = gm_div_up(n_tiles, NT / 32);                                                      \
-        const uint32_t grid =                                                                                  \
-            persistent ? std::min<uint32_t>((uint32_t)ctx->n_sm * acc_occupancy<D, Cm, Wd, Mb, NT>(), all) : all; \
-        k_accumulate<D, Cm, Wd, Mb, NT><<<grid, NT, 0, s>>>(spos, sidx, packed, n_valid, tree, sc->bvh_tris,    \
-                                                                P, n_tiles, persistent, mp->values,            \
-                                                                mp->max_bits, mp->counters, ctx->dev_err, dbg); \
+#define GM_LAUNCH_ACC_NT(D, Cm, Wd, Mb, NT, Gr)                                                                   \
+    do {                                                                                                          \
+        const uint32_t all = gm_div_up(n_tiles, NT / 32);                                                         \
+        const uint32_t grd =                                                                                      \
+            persistent ? std::min<uint32_t>((uint32_t)ctx->n_sm * acc_occupancy<D, Cm, Wd, Mb, NT, Gr>(), all)     \
+                       : all;                                                                                     \
+        k_accumulate<D, Cm, Wd, Mb, NT, Gr><<<grd, NT, 0, s>>>(spos, sidx, packed, n_valid, tree, sc->bvh_tris, P, \
+                                                               n_tiles, persistent, mp->values, mp->max_bits,     \
+                                                               mp->counters, ctx->dev_err, dbg);                  \
     } while (0)
-#define GM_LAUNCH_ACC(D, Cm, Wd, Mb) GM_LAUNCH_ACC_NT(D, Cm, Wd, Mb, ACC_THREADS)
-        if (debug) {
-            switch (code & 3) {
-                case 0: GM_LAUNCH_ACC(true, false, false, 3); break;
-                case 1: GM_LAUNCH_ACC(true, true, false, 3); break;
-                case 2: GM_LAUNCH_ACC(true, false, true, 3); break;
-                default: GM_LAUNCH_ACC(true, true, true, 3); break;
+#define GM_LAUNCH_ACC(D, Cm, Wd, Mb) GM_LAUNCH_ACC_NT(D, Cm, Wd, Mb, ACC_THREADS, false)
+        if (grid) {
+            const uint32_t R = (prm->flags & GM_F_GRID64) ? 64u : 128u;
+            size_t fr = 0, tot = 0;
+            GM_TRY_CUDA(cudaMemGetInfo(&fr, &tot));
+            // entries of one chunk: at most a third of the free memory (8 bytes each), or fewer when
+            // GM_EYEGRID_CHUNK_ENTRIES says so (smaller chunks: tighter memory, more launches)
+            uint64_t budget = std::max<uint64_t>(1u << 20, (uint64_t)fr / 3 / sizeof(uint2));
+            if (const char* env = std::getenv("GM_EYEGRID_CHUNK_ENTRIES")) {
+                const unsigned long long v = std::strtoull(env, nullptr, 10);
+                if (v > 0) budget = std::min<uint64_t>(budget, v);
             }
+            if ((st = eg_prepare(sc, packed, n_valid, nf, (float)std::sqrt((double)P.K), R, budget, s, &eg,
+                                 &launches)) != GM_OK)
+                return fail(st);
+            const uint32_t nchunk = (uint32_t)eg.chunk.size() - 1;
+            if (nchunk > 1) TMP_ALLOC(carry, sizeof(float2) * ns);
+            P.carry = carry;
+            P.eg_basis = eg.basis;
+            P.eg_cells = eg.cells;
+            P.eg_ent = eg.ent;
+            P.eg_R = R;
+            P.eg_s = eg.s;
+            if (timing) cudaEventRecord(mp->ev[4], s);
+            for (uint32_t k = 0; k < std::max<uint32_t>(1u, nchunk); ++k) {
+                if (nchunk > 0) {
+                    if ((st = eg_build_chunk(sc, packed, &eg, k, s, &launches)) != GM_OK) return fail(st);
+                    P.f0 = eg.chunk[k];
+                    P.f1 = eg.chunk[k + 1];
+                    P.carry_in = k > 0;
+                    P.carry_out = k + 1 < nchunk;
+                }
+                if (timing && k == 0) cudaEventRecord(mp->ev[5], s);
+                if (k > 0) GM_TRY_CUDA(cudaMemsetAsync(&mp->counters[6], 0, sizeof(unsigned long long), s));
+                if (debug) GM_LAUNCH_ACC_NT(true, true, false, 3, ACC_THREADS, true);
+                else GM_LAUNCH_ACC_NT(false, true, false, 3, ACC_THREADS, true);
+                ++launches;
+            }
+            mp->stats.grid_chunks = std::max<uint32_t>(1u, nchunk);
         } else {
-            const bool b128 = (prm->flags & GM_F_BLOCK128) != 0;
-            if (b128 && code == 1) GM_LAUNCH_ACC_NT(false, true, false, 7, 128);
-            else if (b128 && code == 5) GM_LAUNCH_ACC_NT(false, true, false, 8, 128);
-            else switch (code) {
-                case 0: GM_LAUNCH_ACC(false, false, false, 3); break;
-                case 1: GM_LAUNCH_ACC(false, true, false, 3); break;
-                case 2: GM_LAUNCH_ACC(false, false, true, 3); break;
-                case 3: GM_LAUNCH_ACC(false, true, true, 3); break;
-                case 4: GM_LAUNCH_ACC(false, false, false, 4); break;
-                case 5: GM_LAUNCH_ACC(false, true, false, 4); break;
-                case 6: GM_LAUNCH_ACC(false, false, true, 4); break;
-                default: GM_LAUNCH_ACC(false, true, true, 4); break;
+            if (timing) {
+                cudaEventRecord(mp->ev[4], s);
+                cudaEventRecord(mp->ev[5], s);
             }
+            if (debug) {
+                switch (code & 3) {
+                    case 0: GM_LAUNCH_ACC(true, false, false, 3); break;
+                    case 1: GM_LAUNCH_ACC(true, true, false, 3); break;
+                    case 2: GM_LAUNCH_ACC(true, false, true, 3); break;
+                    default: GM_LAUNCH_ACC(true, true, true, 3); break;
+                }
+            } else {
+                if (b128 && code == 1) GM_LAUNCH_ACC_NT(false, true, false, 7, 128, false);
+                else if (b128 && code == 5) GM_LAUNCH_ACC_NT(false, true, false, 8, 128, false);
+                else switch (code) {
+                    case 0: GM_LAUNCH_ACC(false, false, false, 3); break;
+                    case 1: GM_LAUNCH_ACC(false, true, false, 3); break;
+                    case 2: GM_LAUNCH_ACC(false, false, true, 3); break;
+                    case 3: GM_LAUNCH_ACC(false, true, true, 3); break;
+                    case 4: GM_LAUNCH_ACC(false, false, false, 4); break;
+                    case 5: GM_LAUNCH_ACC(false, true, false, 4); break;
+                    case 6: GM_LAUNCH_ACC(false, false, true, 4); break;
+                    default: GM_LAUNCH_ACC(false, true, true, 4); break;
+                }
+            }
+            ++launches;
         }
 #undef GM_LAUNCH_ACC
 #undef GM_LAUNCH_ACC_NT
-        ++launches;
     }
     if (timing) cudaEventRecord(mp->ev[2], s);
     if (prm->normalize && !into) launches += launch_normalize(mp, ctx->n_sm, s) > 0 ? 1 : 0;
@@ -409,6 +465,7 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_accumulate_fixations launch"));
     for (void* p : tmp) cudaFreeAsync(p, s);
+    eg_free(&eg, s);
     mp->stats.launches = (into ? mp->stats.launches : 0) + (uint32_t)launches;
     ctx->launches += launches;
     if (out) *out = mp;
@@ -484,12 +541,23 @@ extern "C" gm_status gm_map_info(gm_map* mp, uint32_t* n_windows, uint64_t* n_sa
     mp->stats.pairs = (uint64_t)nvalid * mp->ns;
     mp->stats.nodes_visited = c[4];
     mp->stats.tris_tested = c[5];
+    mp->stats.pairs_tested = c[7];
     if (mp->timing) {
-        float a = 0, b = 0, d = 0;
+        float a = 0, b = 0, d = 0, g = 0;
         cudaEventElapsedTime(&a, mp->ev[0], mp->ev[1]);
-        cudaEventElapsedTime(&b, mp->ev[1], mp->ev[2]);
+        if (mp->ev[4] && mp->ev[5]) {
+            // ev[1] .. ev[4]: eye-grid frames and counts; ev[4] .. ev[5]: the first chunk's build
+            float g0 = 0, g1 = 0;
+            cudaEventElapsedTime(&g0, mp->ev[1], mp->ev[4]);
+            cudaEventElapsedTime(&g1, mp->ev[4], mp->ev[5]);
+            g = g0 + g1;
+            cudaEventElapsedTime(&b, mp->ev[5], mp->ev[2]);
+        } else {
+            cudaEventElapsedTime(&b, mp->ev[1], mp->ev[2]);
+        }
         cudaEventElapsedTime(&d, mp->ev[2], mp->ev[3]);
         mp->stats.prep_ms = a;
+        mp->stats.grid_ms = g;
         mp->stats.accumulate_ms = b;
         mp->stats.normalize_ms = d;
     }

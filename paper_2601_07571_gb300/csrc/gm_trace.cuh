@@ -1,10 +1,12 @@
 // gm_trace.cuh -- device code shared by the single-map and the batched accumulation kernels:
-// the occlusion query (binary and 4-wide BVH, watertight triangle test) and the per-warp tile
-// body that runs the cone test, the ray queue, the Gaussian and the compensated sums for 32*SPT
-// consecutive work-order samples over a whole fixation list.
+// the occlusion queries (binary and 4-wide BVH, or the per-fixation eye grid; one watertight
+// triangle test for all of them) and the per-warp tile body that runs the cone test, the ray
+// queue, the Gaussian and the compensated sums for 32*SPT consecutive work-order samples over a
+// range of the fixation list.
 #pragma once
 
 #include "gm_internal.cuh"
+#include "gm_eyegrid.cuh"
 
 namespace {
 
@@ -28,6 +30,18 @@ struct AccParams {
     uint32_t group = 1;
     uint32_t tile_cull = 1;   // skip fixations whose cone misses the warp tile's bounding sphere
     float tanphi = 0.f;       // cutoff tan theta, slightly enlarged (the sphere test's cone)
+    // fixations [f0, min(f1, n_valid)) of the sorted list are processed by this launch; with
+    // carry_in the sums start from `carry` (and the window of fixation f0 - 1 is still open),
+    // with carry_out they are saved there instead of being flushed at the end
+    uint32_t f0 = 0, f1 = 0xffffffffu;
+    uint32_t carry_in = 0, carry_out = 0;
+    float2* carry = nullptr;  // per work-order sample: (sum, compensation)
+    // eye grid of the fixations [f0, f1) (occlusion by cell lists instead of the BVH)
+    const float4* eg_basis = nullptr;   // per fixation (global index): (u, 0), (v, 0)
+    const uint32_t* eg_cells = nullptr; // per fixation of the launch: R*R + 2 entry offsets
+    const uint2* eg_ent = nullptr;      // (leaf slot, depth lower bound bits), depth-sorted per cell
+    uint32_t eg_R = 0;
+    float eg_s = 0.f;                   // cells per unit of x/w: R / (2 T)
 };
 
 struct DebugOut {
@@ -243,6 +257,40 @@ __device__ bool occluded4(const Ray& R, uint32_t own, const float4* __restrict__
     }
 }
 
+// Any-hit query of the segment through the eye grid of its fixation: the triangles binned in the
+// ray's cell (and the fixation's near list, cell R*R) are every triangle the segment can meet,
+// stored with a lower bound of their depth along the gaze and sorted by it; the walk stops at
+// the first hit or at the first entry that lies wholly beyond the sample (wlim).
+__device__ __forceinline__ bool eg_list_hit(const Ray& R, uint32_t own, uint32_t b, uint32_t e, float wlim,
+                                            const uint2* __restrict__ ent, const float4* __restrict__ tris,
+                                            uint32_t& n_ent, uint32_t& n_tri, int& hit_slot) {
+    uint2 nx = b < e ? __ldg(&ent[b]) : make_uint2(0u, 0u);
+    for (uint32_t k = b; k < e; ++k) {
+        const uint2 t = nx;
+        if (k + 1 < e) nx = __ldg(&ent[k + 1]);   // the next entry is in flight while this one is tested
+        ++n_ent;
+        if (__uint_as_float(t.y) > wlim) break;
+        if (leaf_hit(R, tris, (int)t.x, own, n_tri)) {
+            hit_slot = (int)t.x;
+            return true;
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool occluded_grid(const Ray& R, uint32_t own, float w_s, int cell, int R2,
+                                              const uint32_t* __restrict__ cs, const uint2* __restrict__ ent,
+                                              const float4* __restrict__ tris, uint32_t& n_ent, uint32_t& n_tri,
+                                              int& hit_slot) {
+    // a triangle can hold the hit only if part of it lies nearer than the sample (t < 1); the
+    // stored bounds are conservative and 1e-5 covers the rounding of the sample's own depth
+    const float wlim = w_s * 1.00001f;
+    const uint32_t nb = __ldg(&cs[R2]), ne = __ldg(&cs[R2 + 1]);
+    const uint32_t cb = __ldg(&cs[cell]), ce = __ldg(&cs[cell + 1]);
+    if (nb < ne && eg_list_hit(R, own, nb, ne, wlim, ent, tris, n_ent, n_tri, hit_slot)) return true;
+    return eg_list_hit(R, own, cb, ce, wlim, ent, tris, n_ent, n_tri, hit_slot);
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -273,6 +321,7 @@ struct DebugOut;
 struct TileStats {
     unsigned long long n_in = 0, n_vis = 0;
     uint32_t n_node = 0, n_tri = 0;
+    unsigned long long n_tested = 0;   // sample x fixation cone tests evaluated (not skipped by a tile sphere)
 };
 
 // Debug record of one traced pair (sample index in stored order, fixation in input order).
@@ -288,12 +337,16 @@ __device__ __forceinline__ void record_pair(unsigned long long* cursor, const De
     }
 }
 
-// One warp processes the work-order samples [tile * WARP_TILE, (tile + 1) * WARP_TILE) against
-// fixations [0, nf) of `fix` (packed (e, w), (r^, window), sorted by window). Sums are written to
-// out[window * P.ns + sidx[j]] when a window ends; each window's maximum is folded into
-// max_bits[window] with one atomicMax per warp. The warp's shared-memory regions (WARP_TILE
-// entries each) are used only when COMPACT. No block-wide synchronisation.
-template <bool DEBUG, bool COMPACT, bool WIDE>
+// One warp processes the work-order samples of warp tile `tile` (see AccParams::group) against
+// fixations [P.f0, min(P.f1, nf)) of `fix` (packed (e, w), (r^, window), sorted by window). Sums are
+// written to out[window * P.ns + sidx[j]] when a window ends; each window's maximum is folded into
+// max_bits[window] with one atomicMax per warp. With P.carry_in the compensated sums start from
+// P.carry and the window of fixation f0 - 1 continues; with P.carry_out the open sums are saved to
+// P.carry at the end instead of being written (a later launch continues them). The warp's
+// shared-memory regions (WARP_TILE entries each) are used only when COMPACT. Occlusion: the BVH
+// (binary or, WIDE, 4-wide) or, GRID, the eye grid of P (COMPACT only). No block-wide
+// synchronisation. *tested counts the sample x fixation cone tests actually evaluated.
+template <bool DEBUG, bool COMPACT, bool WIDE, bool GRID = false>
 __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restrict__ spos,
                                           const uint32_t* __restrict__ sidx, const float4* __restrict__ fix,
                                           uint32_t nf, const float4* __restrict__ nodes,
@@ -302,14 +355,17 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                                           float4* wsmp, float2* wacc, uint16_t* qslot, float* qg, float4* wbox,
                                           unsigned long long* __restrict__ dbg_cursor, const DebugOut& dbg,
                                           int* __restrict__ err, TileStats& st) {
+    static_assert(!GRID || COMPACT, "the eye grid traces from the ray queue");
     const int lane = threadIdx.x & 31;
     const uint32_t G = P.group;
     const uint32_t stride = 32u * G;
     const uint32_t base0 = (tile / G) * (uint32_t)WARP_TILE * G + (tile % G) * 32u;
     const uint32_t base = base0 + lane;
+    const uint32_t i_end = min(nf, P.f1);
     float sx[SPT], sy[SPT], sz[SPT], sum[SPT], cmp[SPT];
     uint32_t own[SPT];
     float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    uint32_t live = 0;
 #pragma unroll
     for (int k = 0; k < SPT; ++k) {
         const uint32_t j = base + k * stride;
@@ -317,6 +373,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
         const float4 p = j < P.ns ? spos[j]
                                   : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, __uint_as_float(0xffffffffu));
         if (j < P.ns) {
+            ++live;
             blo[0] = fminf(blo[0], p.x);
             blo[1] = fminf(blo[1], p.y);
             blo[2] = fminf(blo[2], p.z);
@@ -324,11 +381,12 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
             bhi[1] = fmaxf(bhi[1], p.y);
             bhi[2] = fmaxf(bhi[2], p.z);
         }
-        sum[k] = 0.f;
-        cmp[k] = 0.f;
+        const float2 c0 = (P.carry_in && j < P.ns) ? P.carry[j] : make_float2(0.f, 0.f);
+        sum[k] = c0.x;
+        cmp[k] = c0.y;
         if (COMPACT) {
             wsmp[k * 32 + lane] = p;
-            wacc[k * 32 + lane] = make_float2(0.f, 0.f);
+            wacc[k * 32 + lane] = c0;
         } else {
             sx[k] = p.x;
             sy[k] = p.y;
@@ -356,7 +414,9 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                                                     (bhi[2] - blo[2]) * (bhi[2] - blo[2])) * 1.0001f
                                      : -1.f);
     __syncwarp();
+    // the open window: none, or (continuing a previous launch) the window of fixation f0 - 1
     uint32_t cur = 0xffffffffu;
+    if (P.carry_in && P.f0 > 0) cur = __float_as_uint(__ldg(&fix[2 * (P.f0 - 1) + 1]).w);
 
     auto flush = [&](uint32_t w) {
         float m = 0.f;
@@ -378,11 +438,12 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
         if (lane == 0 && m > 0.f) atomicMax(&max_bits[w], __float_as_uint(m));
     };
 
-    float4 nF0 = nf > 0 ? __ldg(&fix[0]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 nF1 = nf > 0 ? __ldg(&fix[1]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (uint32_t i = 0; i < nf; ++i) {
+    const uint32_t i_beg = P.f0;
+    float4 nF0 = i_beg < i_end ? __ldg(&fix[2 * i_beg]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 nF1 = i_beg < i_end ? __ldg(&fix[2 * i_beg + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (uint32_t i = i_beg; i < i_end; ++i) {
         const float4 F0 = nF0, F1 = nF1;
-        if (i + 1 < nf) {
+        if (i + 1 < i_end) {
             nF0 = __ldg(&fix[2 * (i + 1)]);
             nF1 = __ldg(&fix[2 * (i + 1) + 1]);
         }
@@ -407,6 +468,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
             const float lim = bR + fmaf(P.tanphi, fmaxf(reach, 0.f), margin);
             if (reach <= -margin || fmaf(ux, ux, fmaf(uy, uy, uz * uz)) > lim * lim) continue;
         }
+        st.n_tested += live;
         if (COMPACT) {
             int tot = 0;
 #pragma unroll
@@ -434,6 +496,14 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
             }
             if (tot == 0) continue;
             __syncwarp();
+            // the eye grid of this fixation (warp-uniform): its gaze frame and its cell offsets
+            float4 gU = make_float4(0.f, 0.f, 0.f, 0.f), gV = gU;
+            const uint32_t* cs = nullptr;
+            if (GRID) {
+                gU = __ldg(&P.eg_basis[2 * i]);
+                gV = __ldg(&P.eg_basis[2 * i + 1]);
+                cs = P.eg_cells + (size_t)(i - P.f0) * (P.eg_R * P.eg_R + 2u);
+            }
             // the queue is traced 32 rays at a time: rays of one batch leave one eye toward neighbouring
             // samples and walk the tree nearly in step (node fetches are shared); a queue-refill
             // variant that let lanes run out of phase measured 28 % slower
@@ -445,13 +515,24 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                     const float g = qg[e];
                     ++st.n_in;
                     Ray R;
-                    make_ray(R, make_float3(F0.x, F0.y, F0.z), make_float3(sp.x - F0.x, sp.y - F0.y, sp.z - F0.z),
-                             P.tmax);
+                    const float3 d = make_float3(sp.x - F0.x, sp.y - F0.y, sp.z - F0.z);
+                    make_ray(R, make_float3(F0.x, F0.y, F0.z), d, P.tmax);
                     int hit = -1;
-                    const bool vis = WIDE ? !occluded4(R, __float_as_uint(sp.w), nodes, tris, err, st.n_node,
-                                                       st.n_tri, hit)
-                                          : !occluded(R, __float_as_uint(sp.w), nodes, tris, P.nt, err, st.n_node,
-                                                      st.n_tri, hit);
+                    bool vis;
+                    if (GRID) {
+                        // the ray's cell: its direction in the fixation's gaze frame
+                        const float w_s = fmaf(d.x, F1.x, fmaf(d.y, F1.y, d.z * F1.z));
+                        const float xs = __fdividef(fmaf(d.x, gU.x, fmaf(d.y, gU.y, d.z * gU.z)), w_s);
+                        const float ys = __fdividef(fmaf(d.x, gV.x, fmaf(d.y, gV.y, d.z * gV.z)), w_s);
+                        const int RR = (int)P.eg_R;
+                        const int cell = eg_cell_coord(ys, P.eg_s, RR) * RR + eg_cell_coord(xs, P.eg_s, RR);
+                        vis = !occluded_grid(R, __float_as_uint(sp.w), w_s, cell, RR * RR, cs, P.eg_ent, tris,
+                                             st.n_node, st.n_tri, hit);
+                    } else {
+                        vis = WIDE ? !occluded4(R, __float_as_uint(sp.w), nodes, tris, err, st.n_node, st.n_tri, hit)
+                                   : !occluded(R, __float_as_uint(sp.w), nodes, tris, P.nt, err, st.n_node,
+                                               st.n_tri, hit);
+                    }
                     if (vis) {
                         ++st.n_vis;
                         kahan_slot(wacc, slot, g);
@@ -498,25 +579,40 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
             }
         }
     }
+    if (P.carry_out) {
+        // the window goes on in the next launch: keep the open sums
+        if (COMPACT) __syncwarp();
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+            const uint32_t j = base + k * stride;
+            if (j < P.ns) P.carry[j] = COMPACT ? wacc[k * 32 + lane] : make_float2(sum[k], cmp[k]);
+        }
+        if (COMPACT) __syncwarp();
+        return;
+    }
     if (cur != 0xffffffffu) flush(cur);
     else if (P.W == 1) flush(0);   // no fixation at all: window 0 is written as zeros
 }
 
 // Sum a warp's tile statistics into counters [0] in-cone, [1] visible, [4] nodes, [5] triangles.
 __device__ __forceinline__ void warp_stats_commit(TileStats st, unsigned long long* __restrict__ counters) {
-    unsigned long long a = st.n_in, b = st.n_vis, c = st.n_node, d = st.n_tri;
+    unsigned long long a = st.n_in, b = st.n_vis, c = st.n_node, d = st.n_tri, t = st.n_tested;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
         b += __shfl_xor_sync(0xffffffffu, b, o);
         c += __shfl_xor_sync(0xffffffffu, c, o);
         d += __shfl_xor_sync(0xffffffffu, d, o);
+        t += __shfl_xor_sync(0xffffffffu, t, o);
     }
-    if ((threadIdx.x & 31) == 0 && (a | b)) {
-        atomicAdd(&counters[0], a);
-        atomicAdd(&counters[1], b);
-        atomicAdd(&counters[4], c);
-        atomicAdd(&counters[5], d);
+    if ((threadIdx.x & 31) == 0) {
+        if (a | b) {
+            atomicAdd(&counters[0], a);
+            atomicAdd(&counters[1], b);
+            atomicAdd(&counters[4], c);
+            atomicAdd(&counters[5], d);
+        }
+        if (t) atomicAdd(&counters[7], t);
     }
 }
 

@@ -18,6 +18,7 @@ GM_OK, GM_ERR_INVALID_ARG, GM_ERR_CUDA, GM_ERR_OOM, GM_ERR_TIMEOUT = 0, 1, 2, 3,
 GM_ERR_UNSUPPORTED, GM_ERR_INTERNAL, GM_WARN_EMPTY = 5, 6, 100
 GM_F_TIMING, GM_F_DEBUG_PAIRS, GM_F_NO_REORDER, GM_F_NO_COMPACT, GM_F_WIDE_BVH = 1, 2, 4, 8, 16
 GM_F_REGCAP64, GM_F_TILE_CONSECUTIVE, GM_F_STATIC_TILES, GM_F_NO_TILE_CULL, GM_F_BLOCK128 = 32, 64, 128, 256, 512
+GM_F_BVH, GM_F_GRID64 = 1024, 2048
 GM_Q_SAMPLE, GM_Q_PLAIN, GM_Q_FIELD = 0, 1, 2
 
 
@@ -73,7 +74,8 @@ class gm_map_stats(C.Structure):
     _fields_ = [("pairs", C.c_uint64), ("in_cone", C.c_uint64), ("visible", C.c_uint64),
                 ("n_windows", C.c_uint32), ("n_fixations_used", C.c_uint32), ("prep_ms", C.c_float),
                 ("accumulate_ms", C.c_float), ("normalize_ms", C.c_float), ("launches", C.c_uint32),
-                ("nodes_visited", C.c_uint64), ("tris_tested", C.c_uint64)]
+                ("nodes_visited", C.c_uint64), ("tris_tested", C.c_uint64), ("pairs_tested", C.c_uint64),
+                ("grid_ms", C.c_float), ("grid_chunks", C.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1,0 +1,149 @@
+"""The eye grid (per-fixation angular cell lists) against the BVH: identical maps.
+
+The eye grid lists, for every cell of a fixation's gaze-frame grid, every triangle the
+watertight triangle test can report for a segment of that cell, so the occlusion decisions --
+and therefore the compensated sums and the maps -- must equal those of the BVH walk bit for bit,
+at both grid resolutions, in one chunk of fixations or several (the sums carry across chunks and
+windows close where they should), and with geometry close to the eye (the near list) or crossing
+the eye's plane (the FP64 clip)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2601_07571_gb300 import build
+    build.build()
+    import paper_2601_07571_gb300 as G
+    return G
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    c = G.gm_create(0)
+    yield c
+    G.gm_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def pipe(G):
+    from paper_2601_07571_gb300 import pipeline
+    return pipeline
+
+
+def _maps(G, pipe, ctx, w, flags, windows=1):
+    h = pipe.run(ctx, w, normalize=False, flags=flags | G.GM_F_DEBUG_PAIRS | G.GM_F_TIMING, debug_pair_cap=4_000_000)
+    W, ns, stats, _ = G.gm_map_info(h.map)
+    vals = np.stack([pipe.map_array(h, k)[0] for k in range(W)])
+    mx = [pipe.map_array(h, k)[1] for k in range(W)]
+    pairs = G.gm_map_debug_pairs(h.map, 4_000_000)
+    h.free()
+    key = np.sort(pairs["sample"].astype(np.int64) * (1 << 32) + pairs["fix"])
+    vis = pairs["visible"][np.argsort(pairs["sample"].astype(np.int64) * (1 << 32) + pairs["fix"])]
+    return vals, mx, key, vis, stats
+
+
+def _same(a, b):
+    va, ma, ka, sa, _ = a
+    vb, mb, kb, sb, _ = b
+    assert np.array_equal(va.view(np.uint32), vb.view(np.uint32))
+    assert ma == mb
+    assert np.array_equal(ka, kb) and np.array_equal(sa, sb)
+
+
+@pytest.mark.parametrize("which", ["tiny", "session", "windows"])
+@pytest.mark.parametrize("res", ["grid128", "grid64"])
+def test_eye_grid_equals_bvh(G, ctx, pipe, which, res):
+    if which == "tiny":
+        w = synth.tiny_sphere()
+    elif which == "session":
+        w = synth.session(5)
+        w.fixations = w.fixations.subset(slice(0, 300))
+    else:
+        w = synth.tiny_sphere(n_fix=300)
+        ts = w.fixations.timestamp_s
+        w.params = synth.Params(t_begin=1.0, t_end=float(ts.max()) * 0.95, window_s=4.0)
+    flag = 0 if res == "grid128" else G.GM_F_GRID64
+    grid = _maps(G, pipe, ctx, w, flag)
+    bvh = _maps(G, pipe, ctx, w, G.GM_F_BVH)
+    _same(grid, bvh)
+    st = grid[4]
+    assert st["grid_chunks"] == 1 and bvh[4]["grid_chunks"] == 0
+    assert st["in_cone"] == bvh[4]["in_cone"] > 1000
+    print(f"EYEGRID {which} {res}: {st['in_cone']} rays, {st['nodes_visited'] / st['in_cone']:.1f} entries and "
+          f"{st['tris_tested'] / st['in_cone']:.1f} triangle tests per ray (BVH {bvh[4]['nodes_visited'] / st['in_cone']:.1f}"
+          f" nodes, {bvh[4]['tris_tested'] / st['in_cone']:.1f} triangles)")
+
+
+@pytest.mark.parametrize("budget", [20_000, 200_000])
+def test_eye_grid_in_chunks_carries_sums_across_launches(G, ctx, pipe, budget):
+    """Small per-chunk budgets split the fixations into many launches; sums carry over, windows
+    that span a chunk boundary are written once, and the maps equal the single-chunk ones."""
+    w = synth.tiny_sphere(n_fix=300)
+    ts = w.fixations.timestamp_s
+    w.params = synth.Params(t_begin=0.0, t_end=float(ts.max()) + 1.0, window_s=7.0)
+    one = _maps(G, pipe, ctx, w, 0)
+    os.environ["GM_EYEGRID_CHUNK_ENTRIES"] = str(budget)
+    try:
+        many = _maps(G, pipe, ctx, w, 0)
+    finally:
+        del os.environ["GM_EYEGRID_CHUNK_ENTRIES"]
+    _same(one, many)
+    assert one[4]["grid_chunks"] == 1 and many[4]["grid_chunks"] > 2
+    # single window, chunked
+    w.params = synth.Params()
+    os.environ["GM_EYEGRID_CHUNK_ENTRIES"] = str(budget)
+    try:
+        many = _maps(G, pipe, ctx, w, 0)
+    finally:
+        del os.environ["GM_EYEGRID_CHUNK_ENTRIES"]
+    _same(_maps(G, pipe, ctx, w, G.GM_F_BVH), many)
+
+
+def test_eye_grid_geometry_at_the_eye(G, ctx, pipe):
+    """Eyes 5 mm and 3 cm from a large tilted plate (near list, FP64 clip of triangles that cross
+    the eye's plane), a floor under the eyes, and a sphere behind the plate: grid and BVH agree."""
+    rng = np.random.default_rng(8)
+    sph = synth.tiny_sphere()
+    # a plate of 2 x 2 m in 20 x 20 quads, tilted, through x = 1.6 between the sphere and the eyes
+    n = 20
+    u = np.linspace(-1.0, 1.0, n + 1)
+    gy, gz = np.meshgrid(u, u, indexing="ij")
+    verts = np.stack([1.6 + 0.2 * gy, gy, gz], -1).reshape(-1, 3).astype(np.float32)
+    idx = []
+    for i in range(n):
+        for j in range(n):
+            a, b, c, d = i * (n + 1) + j, i * (n + 1) + j + 1, (i + 1) * (n + 1) + j, (i + 1) * (n + 1) + j + 1
+            if (i + j) % 3:   # holes in the plate: some rays pass
+                idx += [[a, b, d], [a, d, c]]
+    plate = synth.Mesh(verts, np.array(idx, np.uint32), synth.identity(), 5, 300.0)
+    fv = np.array([[-4, -1.2, -4], [4, -1.2, -4], [4, -1.2, 4], [-4, -1.2, 4]], np.float32)
+    floor = synth.Mesh(fv, np.array([[0, 1, 2], [0, 2, 3]], np.uint32), synth.identity(), 6, 50.0)
+    meshes = list(sph.meshes) + [plate, floor]
+    nf = 60
+    eye = np.zeros((nf, 3), np.float32)
+    gaze = np.zeros((nf, 3), np.float32)
+    for k in range(nf):
+        y, z = rng.uniform(-0.8, 0.8, 2)
+        x_plate = 1.6 + 0.2 * y
+        dist = [0.005, 0.03, 0.4][k % 3]
+        eye[k] = (x_plate + dist, y, z)
+        tgt = rng.normal(size=3)
+        tgt /= np.linalg.norm(tgt)
+        g = tgt - eye[k]
+        gaze[k] = g / np.linalg.norm(g)
+    fx = synth.Fixations(eye, gaze, rng.uniform(0.1, 0.6, nf).astype(np.float32), np.arange(nf, dtype=np.float64))
+    w = synth.Workload("eye_near_plate", meshes, fx, synth.Params(theta_rad=math.radians(3.0)), seed=4)
+    grid = _maps(G, pipe, ctx, w, 0)
+    bvh = _maps(G, pipe, ctx, w, G.GM_F_BVH)
+    _same(grid, bvh)
+    assert grid[4]["in_cone"] > 1000 and 0 < grid[4]["visible"] < grid[4]["in_cone"]
