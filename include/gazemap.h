@@ -126,6 +126,11 @@ void gm_destroy(gm_ctx* ctx);
 const char* gm_last_error(void);
 /* Wait for `stream`, then report any device-side fault recorded by library kernels. */
 gm_status gm_sync(gm_ctx* ctx, gm_stream stream);
+/* Failure-detection check of the bounded device waits (not in the paper): one block waits, with
+ * the wait the tensor-core field kernels use, on an mbarrier that nothing completes, gives up
+ * after `iterations` polls (1 .. 2^16) and records the timeout; the next gm_sync returns
+ * GM_ERR_TIMEOUT and clears it, and the context stays usable. Nothing hangs or faults. */
+gm_status gm_debug_wait_timeout(gm_ctx* ctx, uint32_t iterations, gm_stream stream);
 /* Number of kernels this context has launched so far (every library launch site counts). */
 gm_status gm_ctx_launches(const gm_ctx* ctx, uint64_t* kernel_launches);
 
@@ -437,6 +442,16 @@ gm_status gm_field_query_kernel(gm_field* field, int32_t kernel);
 gm_status gm_field_train_kernel(gm_field* field, int32_t kernel);
 /* Copy the FP32 master parameters (GM_FIELD_N_PARAMS) to out (host or device). */
 gm_status gm_field_params(const gm_field* field, float* out, gm_stream stream);
+/* Checkpoint and resume of training (the field is not in the paper): the FP32 parameters, the two
+ * Adam moment vectors (GM_FIELD_N_PARAMS floats each, the layout of gm_field_params) and the number
+ * of Adam steps taken, which sets both the bias corrections and the batch draws of the next
+ * gm_field_train. Buffers host or device; get: any pointer may be NULL (that part is skipped);
+ * set: all three are required, the bf16 weight copies are refreshed from theta. A field restored
+ * from a checkpoint and trained on continues exactly as the original would. */
+gm_status gm_field_get_state(const gm_field* field, float* theta, float* m, float* v, uint32_t* steps,
+                             gm_stream stream);
+gm_status gm_field_set_state(gm_field* field, const float* theta, const float* m, const float* v, uint32_t steps,
+                             gm_stream stream);
 gm_status gm_field_info(const gm_field* field, uint32_t* n_params, uint32_t* steps_taken, float* last_loss,
                         float* train_ms);
 void gm_field_free(gm_field* field);

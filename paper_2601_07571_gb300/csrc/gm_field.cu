@@ -314,6 +314,20 @@ __device__ __forceinline__ void split3_bf16(float w, __nv_bfloat16 part[3]) {
     part[2] = __float2bfloat16_rn(r1 - __bfloat162float(part[1]));
 }
 
+// Bounded wait on an mbarrier phase: false after `iters` polls without completion.
+__device__ __forceinline__ bool mbar_wait_n(uint32_t addr, uint32_t parity, uint32_t iters) {
+    for (uint32_t it = 0; it < iters; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
     for (int it = 0; it < TQ_WAIT_ITERS; ++it) {
         uint32_t done;
@@ -1482,6 +1496,59 @@ extern "C" gm_status gm_field_query(const gm_field* f, const float* xyz, uint64_
     }
     if (ox) cudaFreeAsync(dx, s);
     return st;
+}
+
+// One block waits, with the field kernels' bounded wait, on an mbarrier that nothing completes (no
+// thread arrives, no copy is issued): the wait gives up after `iters` polls and the block records
+// the timeout in the error word, as the field kernels do.
+__global__ void k_wait_timeout(uint32_t iters, int* __restrict__ err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar)), "r"(1u) : "memory");
+    __syncthreads();
+    const bool ok = mbar_wait_n(smem_addr(&bar), 0u, iters);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!ok) atomicCAS(err, 0, GM_DEV_WAIT_TIMEOUT);
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(&bar)) : "memory");
+    }
+}
+
+extern "C" gm_status gm_debug_wait_timeout(gm_ctx* ctx, uint32_t iterations, gm_stream stream) {
+    if (!ctx) return gm_set_error(GM_ERR_INVALID_ARG, "gm_debug_wait_timeout: null context");
+    if (iterations == 0 || iterations > (1u << 16))
+        return gm_set_error(GM_ERR_INVALID_ARG, "gm_debug_wait_timeout: iterations must be in [1, 2^16]");
+    GM_TRY_CUDA(cudaSetDevice(ctx->device));
+    k_wait_timeout<<<1, 32, 0, (cudaStream_t)stream>>>(iterations, ctx->dev_err);
+    ctx->launches += 1;
+    GM_TRY_CUDA(cudaGetLastError());
+    return GM_OK;
+}
+
+extern "C" gm_status gm_field_get_state(const gm_field* f, float* theta, float* m, float* v, uint32_t* steps,
+                                        gm_stream stream) {
+    if (!f) return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_get_state: null field");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (theta) GM_TRY(gm_copy_out(theta, f->theta, sizeof(float) * NPAR, s));
+    if (m) GM_TRY(gm_copy_out(m, f->m, sizeof(float) * NPAR, s));
+    if (v) GM_TRY(gm_copy_out(v, f->v, sizeof(float) * NPAR, s));
+    if (steps) *steps = f->t;
+    return GM_OK;
+}
+
+extern "C" gm_status gm_field_set_state(gm_field* f, const float* theta, const float* m, const float* v,
+                                        uint32_t steps, gm_stream stream) {
+    if (!f || !theta || !m || !v) return gm_set_error(GM_ERR_INVALID_ARG, "gm_field_set_state: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    GM_TRY_CUDA(cudaMemcpyAsync(f->theta, theta, sizeof(float) * NPAR, cudaMemcpyDefault, s));
+    GM_TRY_CUDA(cudaMemcpyAsync(f->m, m, sizeof(float) * NPAR, cudaMemcpyDefault, s));
+    GM_TRY_CUDA(cudaMemcpyAsync(f->v, v, sizeof(float) * NPAR, cudaMemcpyDefault, s));
+    // the bf16 copies the kernels read follow the restored parameters
+    k_field_cast<<<gm_div_up(FD * FW * FW, 256), 256, 0, s>>>(f->theta, f->wbf, f->wtbf);
+    f->ctx->launches += 1;
+    GM_TRY_CUDA(cudaGetLastError());
+    f->t = steps;
+    return GM_OK;
 }
 
 extern "C" gm_status gm_field_query_kernel(gm_field* f, int32_t kernel) {

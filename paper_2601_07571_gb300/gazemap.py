@@ -145,6 +145,9 @@ _SIGS = {
     "gm_field_info": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_float),
                                 C.POINTER(C.c_float)]),
     "gm_field_free": (None, [_P]),
+    "gm_field_get_state": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_uint32), _P]),
+    "gm_field_set_state": (C.c_int, [_P, _P, _P, _P, C.c_uint32, _P]),
+    "gm_debug_wait_timeout": (C.c_int, [_P, C.c_uint32, _P]),
 }
 
 
@@ -550,6 +553,21 @@ def gm_field_query(field, xyz, n: int, out, stream=None) -> None:
 
 def gm_field_params(field, out, stream=None) -> None:
     _check(lib().gm_field_params(field, _ptr(out), _stream(stream)))
+
+
+def gm_field_get_state(field, theta=None, m=None, v=None, stream=None) -> int:
+    """Copy parameters and Adam moments out (any of them may be None); returns the steps taken."""
+    t = C.c_uint32()
+    _check(lib().gm_field_get_state(field, _ptr(theta), _ptr(m), _ptr(v), C.byref(t), _stream(stream)))
+    return t.value
+
+
+def gm_field_set_state(field, theta, m, v, steps: int, stream=None) -> None:
+    _check(lib().gm_field_set_state(field, _ptr(theta), _ptr(m), _ptr(v), C.c_uint32(int(steps)), _stream(stream)))
+
+
+def gm_debug_wait_timeout(ctx, iterations: int, stream=None) -> None:
+    _check(lib().gm_debug_wait_timeout(ctx, C.c_uint32(int(iterations)), _stream(stream)))
 
 
 def gm_field_info(field):

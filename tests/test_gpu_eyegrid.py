@@ -47,17 +47,25 @@ def _maps(G, pipe, ctx, w, flags, windows=1):
     mx = [pipe.map_array(h, k)[1] for k in range(W)]
     pairs = G.gm_map_debug_pairs(h.map, 4_000_000)
     h.free()
-    key = np.sort(pairs["sample"].astype(np.int64) * (1 << 32) + pairs["fix"])
-    vis = pairs["visible"][np.argsort(pairs["sample"].astype(np.int64) * (1 << 32) + pairs["fix"])]
+    if pairs["n"] > 4_000_000:
+        # more in-cone pairs than the record holds: which ones were recorded depends on scheduling
+        key = vis = None
+    else:
+        order = np.argsort(pairs["sample"].astype(np.int64) * (1 << 32) + pairs["fix"])
+        key = (pairs["sample"].astype(np.int64) * (1 << 32) + pairs["fix"])[order]
+        vis = pairs["visible"][order]
     return vals, mx, key, vis, stats
 
 
 def _same(a, b):
-    va, ma, ka, sa, _ = a
-    vb, mb, kb, sb, _ = b
+    va, ma, ka, sa, ta = a
+    vb, mb, kb, sb, tb = b
     assert np.array_equal(va.view(np.uint32), vb.view(np.uint32))
     assert ma == mb
-    assert np.array_equal(ka, kb) and np.array_equal(sa, sb)
+    assert ta["in_cone"] == tb["in_cone"] and ta["visible"] == tb["visible"]
+    assert (ka is None) == (kb is None)
+    if ka is not None:
+        assert np.array_equal(ka, kb) and np.array_equal(sa, sb)
 
 
 @pytest.mark.parametrize("which", ["tiny", "session", "windows"])

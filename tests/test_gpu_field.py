@@ -197,3 +197,68 @@ def test_field_trains_on_the_tiny_sphere_map(env):
     h.free()
     assert info["steps"] == 1500 and np.isfinite(loss)
     assert e1 < 0.5 * e0 and e1 < 0.6, (e0, e1)
+
+
+def test_field_checkpoint_resumes_training_exactly(env):
+    """Parameters, both Adam moments and the step count saved after one training call and
+    restored into a fresh field: the next call continues bit for bit as on the original."""
+    G, torch, ctx = env
+    from paper_2601_07571_gb300 import pipeline
+    w = synth.tiny_sphere()
+    h = pipeline.run(ctx, w, normalize=True)
+    xyz, _, _, _ = pipeline.samples_arrays(h)
+    lo, hi = xyz.min(0), xyz.max(0)
+    n = G.GM_FIELD_N_PARAMS
+    a = G.gm_field_create(ctx, lo, hi, synth.field_init(3))
+    G.gm_field_train(a, h.samples, h.map, 0, steps=300, batch=4096, lr=3e-3, lr_min=1e-3, seed=9)
+    th, m, v = (np.empty(n, np.float32) for _ in range(3))
+    steps = G.gm_field_get_state(a, th, m, v)
+    assert steps == 300 and np.abs(m).max() > 0 and v.min() >= 0 and v.max() > 0
+    b = G.gm_field_create(ctx, lo, hi, synth.field_init(4))   # other initial parameters, zero moments
+    G.gm_field_set_state(b, th, m, v, steps)
+    for f in (a, b):
+        G.gm_field_train(f, h.samples, h.map, 0, steps=200, batch=4096, lr=1e-3, lr_min=1e-4, seed=9)
+    ta, ma, va = (np.empty(n, np.float32) for _ in range(3))
+    tb, mb, vb = (np.empty(n, np.float32) for _ in range(3))
+    sa = G.gm_field_get_state(a, ta, ma, va)
+    sb = G.gm_field_get_state(b, tb, mb, vb)
+    qa, qb = np.empty(len(xyz), np.float32), np.empty(len(xyz), np.float32)
+    G.gm_field_query(a, xyz, len(xyz), qa)
+    G.gm_field_query(b, xyz, len(xyz), qb)
+    G.gm_field_free(a)
+    G.gm_field_free(b)
+    h.free()
+    assert sa == sb == 500
+    for x, y in ((ta, tb), (ma, mb), (va, vb), (qa, qb)):
+        assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+    # device buffers work too, and set_state refuses missing parts
+    dth = torch.from_numpy(th).cuda()
+    c = G.gm_field_create(ctx, lo, hi, synth.field_init(3))
+    G.gm_field_set_state(c, dth, torch.from_numpy(m).cuda(), torch.from_numpy(v).cuda(), 300)
+    back = np.empty(n, np.float32)
+    assert G.gm_field_get_state(c, back) == 300 and np.array_equal(back, th)
+    with pytest.raises(G.GazeMapError):
+        G.gm_field_set_state(c, th, None, v, 1)
+    G.gm_field_free(c)
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable(env):
+    """A wait on an mbarrier that nothing completes gives up after its poll budget; gm_sync
+    reports GM_ERR_TIMEOUT once, and the context keeps working."""
+    G, torch, ctx = env
+    G.gm_debug_wait_timeout(ctx, 2000)
+    with pytest.raises(G.GazeMapError) as ei:
+        G.gm_sync(ctx)
+    assert ei.value.status == G.GM_ERR_TIMEOUT
+    G.gm_sync(ctx)   # cleared
+    f = G.gm_field_create(ctx, BOX_LO, BOX_HI, synth.field_init(11))
+    x = _points(1000, 5)
+    out = np.empty(len(x), np.float32)
+    G.gm_field_query(f, x, len(x), out)
+    G.gm_sync(ctx)
+    G.gm_field_free(f)
+    feats = F.features(F.normalise(x.astype(np.float64), BOX_LO, BOX_HI))
+    ref, _ = F.forward(synth.field_init(11).astype(np.float64), feats, emulate_bf16=True)
+    assert np.all(np.isfinite(out)) and np.abs(out - ref).max() <= 1e-2 * np.abs(ref).max() + 1e-6
+    with pytest.raises(G.GazeMapError):
+        G.gm_debug_wait_timeout(ctx, 0)
