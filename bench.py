@@ -9,9 +9,10 @@ buffers with the copies in and the map copy out inside the timed region.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl gazemap|reference] [--workload ...]
 
-Under torchrun (N > 1) every rank runs an independent replica of the workload (weak scaling:
-the path shards by sample or by session with no data-path exchange); timing is the max over
-ranks. `--impl reference` times the FP64 CPU oracle on this host's cores on a bounded sample
+Under torchrun (N > 1) the path is sharded by samples: every rank builds the scene, takes one
+contiguous slice of the samples and accumulates it; the ranks exchange one maximum per window
+(all-reduce) and normalise their slices by it (strong scaling: the workload is fixed); timing is
+the max over ranks. `--impl reference` times the FP64 CPU oracle on this host's cores on a bounded sample
 of the same workload (rank 0 only).
 """
 from __future__ import annotations
@@ -101,6 +102,16 @@ def reduce_max(x: float, dist=None, device="cpu") -> float:
     import torch
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, dist=None, device="cpu") -> float:
+    """Sum of a per-rank value over all ranks (identity without torch.distributed)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -761,7 +772,16 @@ def main():
 
     builder = {"default": None, "lbvh": G.GM_BUILD_LBVH, "ploc": G.GM_BUILD_PLOC}[args.builder]
 
+    # one GPU: the whole path; several: the sample-sharded path (each rank its slice of the samples,
+    # one all-reduce of the per-window maxima before the normalisation)
+    sharded = world > 1
+    from paper_2601_07571_gb300 import shard
+
     def step(meshes, fix):
+        if sharded:
+            sc, sm, mp, _, _ = shard.run_sharded(ctx, w, rank, world, dist, stream, flags=G.GM_F_TIMING | args.flags,
+                                                 device="cuda", meshes=meshes, fixations=fix)
+            return sc, sm, mp
         sc = G.gm_build_scene(ctx, meshes, stream, builder=builder, ploc_radius=args.ploc_radius)
         sm = G.gm_sample_surface(sc, dens, w.seed, w.session, stream)
         mp = G.gm_accumulate_fixations(sc, sm, *fix, prm, stream)
@@ -811,7 +831,9 @@ def main():
     clk = clocks.stop()
     step_ms = reduce_max(sum(times) / len(times), dist, "cuda")
     pairs = stats["pairs"]
-    value = whole_job_rate(pairs, world, step_ms * 1e-3)
+    # every rank's pairs (its slice of the samples x all fixations)
+    total_pairs = int(reduce_sum(pairs, dist, "cuda")) if sharded else world * pairs
+    value = total_pairs / (step_ms * 1e-3)
 
     # ---- end to end from pinned host buffers -------------------------------------------------
     host_meshes = [(torch.from_numpy(np.ascontiguousarray(v)).pin_memory(),
@@ -869,12 +891,15 @@ def main():
                              "work_basis": f"{FP32_INSTR_PER_PAIR} FP32 instructions per nominal pair"}
 
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "strong" if sharded else "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "triangles": w.n_tris, "samples": int(ns),
+            "config": {"workload": w.name, "triangles": w.n_tris, "samples": int(ns if not sharded else
+                                                                                   reduce_sum(ns, dist, "cuda")),
                        "fixations": w.fixations.n, "pairs_per_step": int(pairs),
                        "l2": "flushed between steps (256 MiB write)", "inputs": "device-resident",
-                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "parallelism": (f"samples{world}: each rank a contiguous slice of the samples, "
+                                       "all-reduce MAX of the per-window maxima") if sharded else "single",
                        "accumulate_flags": args.flags, "builder": args.builder, "eps_rel": w.params.eps_rel,
                        "ploc_radius": args.ploc_radius or 8},
             "stages_ms": {"accumulate": acc, "eye_grid": gms, "fixation_prep": sum(prep_ms) / len(prep_ms),
@@ -889,7 +914,7 @@ def main():
             ("grid_entries_per_ray" if grid_on else "nodes_per_ray"): stats["nodes_visited"] / max(1, stats["in_cone"]),
             "tris_per_ray": stats["tris_tested"] / max(1, stats["in_cone"]),
             "roofline": roof,
-            "e2e": {"value": whole_job_rate(pairs, world, e2e_s), "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+            "e2e": {"value": total_pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(out.numel() * 4), "ms_per_step": e2e_s * 1e3},
             "gpu_launches": int(launches), "clocks": clk}
     if rank == 0 and world == 1 and not args.no_field and args.workload == "paper_scene" and not args.fixations:

@@ -116,6 +116,7 @@ typedef struct {
                                  sphere the cone misses are skipped without a per-sample test) */
     float grid_ms;            /* eye-grid frames, counts and (first chunk's) cell lists (GM_F_TIMING) */
     uint32_t grid_chunks;     /* fixation chunks the eye grid was built in (0: BVH occlusion) */
+    uint32_t grid_launches;   /* accumulation launches over runs of fixations (eye grid) */
 } gm_map_stats;
 
 /* ---- context ------------------------------------------------------------------------ */
@@ -208,6 +209,12 @@ gm_status gm_samples_offsets(const gm_samples* s, int64_t* dst, gm_stream stream
  * obj n object ids (Section 3.3.3 export fields). */
 gm_status gm_samples_copy(const gm_samples* s, float* xyz, uint32_t* tri, float* bary2,
                           uint32_t* obj, gm_stream stream);
+/* Samples [begin, end) of `src` in its stored order, as a sample set of their own (positions and
+ * barycentrics copied, a spatial work order of their own): the slice one GPU takes when the path
+ * is sharded by samples (each sample's value depends on no other sample, so the slices' maps are
+ * the whole map's values, bit for bit). The slice is a set of fixed points: it has no per-triangle
+ * offsets and does not follow re-posed meshes. */
+gm_status gm_samples_slice(const gm_samples* src, uint64_t begin, uint64_t end, gm_stream stream, gm_samples** out);
 void gm_samples_free(gm_samples* s);
 /* Re-place a Philox or grid sample set on its scene's current pose: same triangle, same
  * barycentrics (same counts per triangle: the densities of the first pose stand), positions from
@@ -273,7 +280,9 @@ gm_status gm_tri_offsets_noalloc(gm_ctx* ctx, const float* tri_xyz, const double
  * The grid's memory is taken on the stream for the call: at most a third of the free device
  * memory for the cell lists of one chunk of fixations (more fixations run in several chunks) and
  * 1 GiB of offset tables; the environment variable GM_EYEGRID_CHUNK_ENTRIES, read at each call,
- * lowers the per-chunk entry budget. The call reads the per-fixation list sizes back once (it
+ * lowers the per-chunk entry budget (a chunk always takes at least one fixation). Within a chunk
+ * the accumulation runs once per run of fixations whose lists fit in L2 together
+ * (GM_EYEGRID_L2_ENTRIES entries of 8 bytes, 4M by default), carrying the sums over. The call reads the per-fixation list sizes back once (it
  * synchronises the stream). */
 gm_status gm_accumulate_fixations(gm_scene* scene, gm_samples* samples, const gm_fixations* fix,
                                   const gm_params* params, gm_stream stream, gm_map** out);
@@ -332,6 +341,15 @@ gm_status gm_map_info(gm_map* map, uint32_t* n_windows, uint64_t* n_samples, gm_
  * device), and its maximum to *max_out (may be NULL). Values are normalised iff the map was
  * accumulated with params->normalize. */
 gm_status gm_map_copy(const gm_map* map, uint32_t window, float* dst, float* max_out, gm_stream stream);
+/* The maximum of every window (n_windows floats, host or device): the map's own raw maxima, or
+ * those it was normalised by. */
+gm_status gm_map_max(const gm_map* map, float* out, gm_stream stream);
+/* Divide every window of a raw map (accumulated with params.normalize = 0) by `maxima` (n_windows
+ * floats >= 0, host or device; NULL: the map's own maxima) and keep those as the map's maxima;
+ * windows whose maximum is 0 stay 0. Section 3.2.3's normalisation when the maximum comes from
+ * elsewhere: the ranks of a sample-sharded run normalise their slices by the maximum over all
+ * ranks. Call it once per map. */
+gm_status gm_map_normalize(gm_map* map, const float* maxima, gm_stream stream);
 /* Device pointer to the map values (n_windows x n_samples FP32, window-major), owned by map. */
 const float* gm_map_device_values(const gm_map* map);
 /* Recorded in-cone pairs (GM_F_DEBUG_PAIRS), in no particular order: sample index (stored

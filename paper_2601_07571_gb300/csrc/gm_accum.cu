@@ -398,29 +398,58 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
                                  &launches)) != GM_OK)
                 return fail(st);
             const uint32_t nchunk = (uint32_t)eg.chunk.size() - 1;
-            if (nchunk > 1) TMP_ALLOC(carry, sizeof(float2) * ns);
+            // accumulation launches: within a build chunk, runs of fixations whose cell lists fit in
+            // L2 together (GM_EYEGRID_L2_ENTRIES entries, 4M = 32 MB by default), so that every
+            // launch reads its grids from L2; the sums carry from launch to launch
+            uint64_t l2_entries = 4u << 20;
+            if (const char* env = std::getenv("GM_EYEGRID_L2_ENTRIES")) {
+                const unsigned long long v = std::strtoull(env, nullptr, 10);
+                if (v > 0) l2_entries = v;
+            }
+            std::vector<std::pair<uint32_t, uint32_t>> runs;   // [a, b) per launch
+            std::vector<uint32_t> run_chunk;
+            for (uint32_t k = 0; k < nchunk; ++k) {
+                uint32_t a = eg.chunk[k];
+                uint64_t acc = 0;
+                for (uint32_t f = eg.chunk[k]; f < eg.chunk[k + 1]; ++f) {
+                    if (f > a && acc + eg.h_tot[f] > l2_entries) {
+                        runs.emplace_back(a, f);
+                        run_chunk.push_back(k);
+                        a = f;
+                        acc = 0;
+                    }
+                    acc += eg.h_tot[f];
+                }
+                runs.emplace_back(a, eg.chunk[k + 1]);
+                run_chunk.push_back(k);
+            }
+            if (runs.size() > 1) TMP_ALLOC(carry, sizeof(float2) * ns);
             P.carry = carry;
             P.eg_basis = eg.basis;
-            P.eg_cells = eg.cells;
             P.eg_ent = eg.ent;
             P.eg_R = R;
             P.eg_s = eg.s;
             if (timing) cudaEventRecord(mp->ev[4], s);
-            for (uint32_t k = 0; k < std::max<uint32_t>(1u, nchunk); ++k) {
-                if (nchunk > 0) {
-                    if ((st = eg_build_chunk(sc, packed, &eg, k, s, &launches)) != GM_OK) return fail(st);
-                    P.f0 = eg.chunk[k];
-                    P.f1 = eg.chunk[k + 1];
-                    P.carry_in = k > 0;
-                    P.carry_out = k + 1 < nchunk;
+            const size_t per_fix = (size_t)R * R + 2;
+            for (size_t q = 0; q < std::max<size_t>(1, runs.size()); ++q) {
+                if (!runs.empty()) {
+                    const uint32_t k = run_chunk[q];
+                    if (q == 0 || run_chunk[q - 1] != k)
+                        if ((st = eg_build_chunk(sc, packed, &eg, k, s, &launches)) != GM_OK) return fail(st);
+                    P.f0 = runs[q].first;
+                    P.f1 = runs[q].second;
+                    P.eg_cells = eg.cells + (size_t)(runs[q].first - eg.chunk[k]) * per_fix;
+                    P.carry_in = q > 0;
+                    P.carry_out = q + 1 < runs.size();
                 }
-                if (timing && k == 0) cudaEventRecord(mp->ev[5], s);
-                if (k > 0) GM_TRY_CUDA(cudaMemsetAsync(&mp->counters[6], 0, sizeof(unsigned long long), s));
+                if (timing && q == 0) cudaEventRecord(mp->ev[5], s);
+                if (q > 0) GM_TRY_CUDA(cudaMemsetAsync(&mp->counters[6], 0, sizeof(unsigned long long), s));
                 if (debug) GM_LAUNCH_ACC_NT(true, true, false, 3, ACC_THREADS, true);
                 else GM_LAUNCH_ACC_NT(false, true, false, 3, ACC_THREADS, true);
                 ++launches;
             }
             mp->stats.grid_chunks = std::max<uint32_t>(1u, nchunk);
+            mp->stats.grid_launches = (uint32_t)std::max<size_t>(1, runs.size());
         } else {
             if (timing) {
                 cudaEventRecord(mp->ev[4], s);
@@ -587,6 +616,31 @@ extern "C" gm_status gm_map_copy(const gm_map* mp, uint32_t window, float* dst, 
 }
 
 extern "C" const float* gm_map_device_values(const gm_map* mp) { return mp ? mp->values : nullptr; }
+
+extern "C" gm_status gm_map_max(const gm_map* mp, float* out, gm_stream stream) {
+    if (!mp || !out) return gm_set_error(GM_ERR_INVALID_ARG, "gm_map_max: null argument");
+    // the maxima are kept as the bit patterns of non-negative floats: the bytes are the floats
+    return gm_copy_out(out, mp->max_bits, sizeof(float) * mp->W, (cudaStream_t)stream);
+}
+
+extern "C" gm_status gm_map_normalize(gm_map* mp, const float* maxima, gm_stream stream) {
+    if (!mp) return gm_set_error(GM_ERR_INVALID_ARG, "gm_map_normalize: null map");
+    cudaStream_t s = (cudaStream_t)stream;
+    GM_TRY_CUDA(cudaSetDevice(mp->ctx->device));
+    if (maxima) {
+        if (!gm_is_device_ptr(maxima)) {
+            for (uint32_t w = 0; w < mp->W; ++w)
+                if (!(maxima[w] >= 0.f) || !std::isfinite(maxima[w]))
+                    return gm_set_error(GM_ERR_INVALID_ARG, "gm_map_normalize: maxima must be finite and >= 0");
+        }
+        GM_TRY_CUDA(cudaMemcpyAsync(mp->max_bits, maxima, sizeof(float) * mp->W, cudaMemcpyDefault, s));
+    }
+    const int l = launch_normalize(mp, mp->ctx->n_sm, s);
+    mp->ctx->launches += l;
+    mp->stats.launches += (uint32_t)l;
+    GM_TRY_CUDA(cudaGetLastError());
+    return GM_OK;
+}
 
 extern "C" gm_status gm_map_debug_pairs(const gm_map* mp, uint32_t* sample, uint32_t* fix, uint8_t* vis, float* g,
                                         uint64_t cap, uint64_t* n) {

@@ -295,8 +295,37 @@ __global__ void __launch_bounds__(EG_THREADS) k_eg_count(const float4* __restric
     if (threadIdx.x == 0) totals[f] = tot;
 }
 
-// In-place shell sort of one cell's entries by depth bound (gaps 701 ... 1: insertion sort for
-// the short lists that are the rule).
+constexpr int EG_SORT_MAX = 256;     // cells up to this long are sorted by one warp in shared memory
+
+// One warp sorts one cell's entries (n <= EG_SORT_MAX) by depth bound: a bitonic network over the
+// next power of two (at least 32) in the warp's shared-memory slot, padded with +inf keys.
+__device__ void eg_warp_sort(uint2* __restrict__ a, uint32_t n, uint2* sw) {
+    const int lane = threadIdx.x & 31;
+    uint32_t P = 32;
+    while (P < n) P <<= 1;
+    for (uint32_t i = lane; i < P; i += 32) sw[i] = i < n ? a[i] : make_uint2(0u, 0x7f800000u);
+    __syncwarp();
+    for (uint32_t k = 2; k <= P; k <<= 1)
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = lane; i < P; i += 32) {
+                const uint32_t ixj = i ^ j;
+                if (ixj > i) {
+                    const uint2 x = sw[i], y = sw[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((__uint_as_float(x.y) > __uint_as_float(y.y)) == up) {
+                        sw[i] = y;
+                        sw[ixj] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    for (uint32_t i = lane; i < n; i += 32) a[i] = sw[i];
+    __syncwarp();
+}
+
+// In-place shell sort of one cell's entries by depth bound (the rare cells longer than
+// EG_SORT_MAX, one thread).
 __device__ void eg_sort(uint2* a, uint32_t n) {
     const uint32_t gaps[8] = {701, 301, 132, 57, 23, 10, 4, 1};
 #pragma unroll 1
@@ -367,25 +396,30 @@ __global__ void __launch_bounds__(EG_THREADS) k_eg_build(const float4* __restric
     __syncthreads();
     eg_pass<R, true>(F, G, spheres, n_blocks, tris, nt, cnt, blist, &nsurv, e, min(all, tot), err);
     __syncthreads();
-    // after the fill cnt[c] is the end of cell c, i.e. the start of cell c + 1
-    for (int c = threadIdx.x; c < NC; c += EG_THREADS) {
+    // after the fill cnt[c] is the end of cell c, i.e. the start of cell c + 1; one warp per cell
+    uint2* sw = reinterpret_cast<uint2*>(eg_sm + (((size_t)R * R + 1 + EG_BATCH + 1) & ~(size_t)1)) +
+                (threadIdx.x >> 5) * EG_SORT_MAX;
+    for (int c = threadIdx.x >> 5; c < NC; c += EG_THREADS / 32) {
         const uint32_t st = c == 0 ? 0u : cnt[c - 1], en = cnt[c];
-        if (en > st + 1 && en <= all) eg_sort(e + st, en - st);
+        if (en <= st + 1 || en > all) continue;
+        if (en - st <= (uint32_t)EG_SORT_MAX) eg_warp_sort(e + st, en - st, sw);
+        else if ((threadIdx.x & 31) == 0) eg_sort(e + st, en - st);
     }
 }
 
+// counts (R*R + 1), the surviving-block list, and (build only) one sort slot per warp
 template <int R>
-size_t eg_smem() {
-    return sizeof(uint32_t) * ((size_t)R * R + 1 + EG_BATCH);
+size_t eg_smem(bool build) {
+    const size_t b = sizeof(uint32_t) * ((size_t)R * R + 1 + EG_BATCH);
+    return build ? ((b + 7) & ~(size_t)7) + sizeof(uint2) * (EG_THREADS / 32) * EG_SORT_MAX : b;
 }
 
 template <int R>
 gm_status eg_configure(int device) {
     static int done = -1;
     if (done == device) return GM_OK;
-    const int smem = (int)eg_smem<R>();
-    GM_TRY_CUDA(cudaFuncSetAttribute(k_eg_count<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    GM_TRY_CUDA(cudaFuncSetAttribute(k_eg_build<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    GM_TRY_CUDA(cudaFuncSetAttribute(k_eg_count<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eg_smem<R>(false)));
+    GM_TRY_CUDA(cudaFuncSetAttribute(k_eg_build<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eg_smem<R>(true)));
     done = device;
     return GM_OK;
 }
@@ -421,11 +455,11 @@ gm_status eg_prepare(gm_scene* sc, const float4* fix, const uint32_t* n_valid_de
     }
     if (nf > 0) {
         if (R == 64)
-            k_eg_count<64><<<nf, EG_THREADS, eg_smem<64>(), s>>>(fix, n_valid_dev, g->spheres, g->n_blocks,
+            k_eg_count<64><<<nf, EG_THREADS, eg_smem<64>(false), s>>>(fix, n_valid_dev, g->spheres, g->n_blocks,
                                                                   sc->bvh_tris, nt, G, g->basis, g->totals,
                                                                   sc->ctx->dev_err);
         else
-            k_eg_count<128><<<nf, EG_THREADS, eg_smem<128>(), s>>>(fix, n_valid_dev, g->spheres, g->n_blocks,
+            k_eg_count<128><<<nf, EG_THREADS, eg_smem<128>(false), s>>>(fix, n_valid_dev, g->spheres, g->n_blocks,
                                                                     sc->bvh_tris, nt, G, g->basis, g->totals,
                                                                     sc->ctx->dev_err);
         ++*launches;
@@ -450,9 +484,10 @@ gm_status eg_prepare(gm_scene* sc, const float4* fix, const uint32_t* n_valid_de
     g->max_fix = 0;
     for (uint32_t f = 0; f < nv; ++f) {
         const uint64_t t = g->h_tot[f];
-        if (t > ent_cap)
-            return gm_set_error(GM_ERR_OOM, "eye grid: one fixation needs " + std::to_string(t) +
-                                                " entries, more than the budget of " + std::to_string(ent_cap));
+        if (t > 0x7fffffffull)
+            return gm_set_error(GM_ERR_UNSUPPORTED, "eye grid: one fixation needs " + std::to_string(t) +
+                                                        " entries (limit 2^31 - 1)");
+        // a chunk holds at least one fixation, however large
         if (f > c_begin && (acc + t > ent_cap || f - c_begin >= fix_cap)) {
             g->chunk.push_back(f);
             g->max_entries = std::max(g->max_entries, acc);
@@ -484,11 +519,11 @@ gm_status eg_build_chunk(gm_scene* sc, const float4* fix, EyeGrid* g, uint32_t k
     GM_TRY_CUDA(cudaMemcpyAsync(g->base, g->h_base.data() + f0, sizeof(uint32_t) * (f1 - f0), cudaMemcpyHostToDevice, s));
     const EgGeom G = eg_geom(*g);
     if (g->R == 64)
-        k_eg_build<64><<<f1 - f0, EG_THREADS, eg_smem<64>(), s>>>(fix, f0, g->spheres, g->n_blocks, sc->bvh_tris,
+        k_eg_build<64><<<f1 - f0, EG_THREADS, eg_smem<64>(true), s>>>(fix, f0, g->spheres, g->n_blocks, sc->bvh_tris,
                                                                    sc->n_tris, G, g->basis, g->base, g->totals,
                                                                    g->cells, g->ent, sc->ctx->dev_err);
     else
-        k_eg_build<128><<<f1 - f0, EG_THREADS, eg_smem<128>(), s>>>(fix, f0, g->spheres, g->n_blocks, sc->bvh_tris,
+        k_eg_build<128><<<f1 - f0, EG_THREADS, eg_smem<128>(true), s>>>(fix, f0, g->spheres, g->n_blocks, sc->bvh_tris,
                                                                      sc->n_tris, G, g->basis, g->base, g->totals,
                                                                      g->cells, g->ent, sc->ctx->dev_err);
     ++*launches;

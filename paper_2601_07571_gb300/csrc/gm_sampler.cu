@@ -582,6 +582,38 @@ extern "C" gm_status gm_samples_follow(gm_samples* sm, gm_stream stream) {
     return GM_OK;
 }
 
+extern "C" gm_status gm_samples_slice(const gm_samples* src, uint64_t begin, uint64_t end, gm_stream stream,
+                                      gm_samples** out) {
+    if (!src || !out) return gm_set_error(GM_ERR_INVALID_ARG, "gm_samples_slice: null argument");
+    *out = nullptr;
+    if (begin > end || end > src->n) return gm_set_error(GM_ERR_INVALID_ARG, "gm_samples_slice: range outside the set");
+    cudaStream_t s = (cudaStream_t)stream;
+    GM_TRY_CUDA(cudaSetDevice(src->scene->ctx->device));
+    gm_samples* sm = new gm_samples();
+    sm->scene = src->scene;
+    sm->n = end - begin;
+    sm->kind = GM_SAMPLES_POINTS;   // fixed points: no offsets of their own, they do not follow poses
+    auto fail = [&](gm_status st) {
+        gm_samples_free(sm);
+        return st;
+    };
+    gm_status st;
+    const size_t n = (size_t)sm->n;
+    if ((st = gm_alloc((void**)&sm->pos, sizeof(float4) * n, s)) != GM_OK) return fail(st);
+    cudaError_t e = n ? cudaMemcpyAsync(sm->pos, src->pos + begin, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s)
+                      : cudaSuccess;
+    if (e == cudaSuccess && src->bary && n) {
+        if ((st = gm_alloc((void**)&sm->bary, sizeof(float2) * n, s)) != GM_OK) return fail(st);
+        e = cudaMemcpyAsync(sm->bary, src->bary + begin, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s);
+    }
+    if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_samples_slice"));
+    int launches = 0;
+    if ((st = build_work_order(sm, s, &launches)) != GM_OK) return fail(st);
+    sm->scene->ctx->launches += launches;
+    *out = sm;
+    return GM_OK;
+}
+
 extern "C" void gm_samples_free(gm_samples* sm) {
     if (!sm) return;
     cudaFree(sm->pos);

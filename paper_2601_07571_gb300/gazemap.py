@@ -75,7 +75,7 @@ class gm_map_stats(C.Structure):
                 ("n_windows", C.c_uint32), ("n_fixations_used", C.c_uint32), ("prep_ms", C.c_float),
                 ("accumulate_ms", C.c_float), ("normalize_ms", C.c_float), ("launches", C.c_uint32),
                 ("nodes_visited", C.c_uint64), ("tris_tested", C.c_uint64), ("pairs_tested", C.c_uint64),
-                ("grid_ms", C.c_float), ("grid_chunks", C.c_uint32)]
+                ("grid_ms", C.c_float), ("grid_chunks", C.c_uint32), ("grid_launches", C.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -146,6 +146,9 @@ _SIGS = {
                                 C.POINTER(C.c_float)]),
     "gm_field_free": (None, [_P]),
     "gm_field_get_state": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_uint32), _P]),
+    "gm_samples_slice": (C.c_int, [_P, C.c_uint64, C.c_uint64, _P, C.POINTER(_P)]),
+    "gm_map_max": (C.c_int, [_P, _P, _P]),
+    "gm_map_normalize": (C.c_int, [_P, _P, _P]),
     "gm_field_set_state": (C.c_int, [_P, _P, _P, _P, C.c_uint32, _P]),
     "gm_debug_wait_timeout": (C.c_int, [_P, C.c_uint32, _P]),
 }
@@ -578,3 +581,17 @@ def gm_field_info(field):
 
 def gm_field_free(field) -> None:
     lib().gm_field_free(field)
+
+
+def gm_samples_slice(samples, begin: int, end: int, stream=None):
+    h = _P()
+    _check(lib().gm_samples_slice(samples, C.c_uint64(int(begin)), C.c_uint64(int(end)), _stream(stream), C.byref(h)))
+    return h
+
+
+def gm_map_max(m, out, stream=None) -> None:
+    _check(lib().gm_map_max(m, _ptr(out), _stream(stream)))
+
+
+def gm_map_normalize(m, maxima=None, stream=None) -> None:
+    _check(lib().gm_map_normalize(m, _ptr(maxima), _stream(stream)))

@@ -54,6 +54,15 @@ def fixation_args(fixations, to_device: bool = False):
     return arrs
 
 
+def n_windows(workload) -> int:
+    """Maps a call makes: ceil((t_end - t_begin) / window_s) windows when window_s > 0, else one."""
+    import math
+    p = workload.params
+    if p.window_s > 0:
+        return max(1, int(math.ceil((p.t_end - p.t_begin) / p.window_s)))
+    return 1
+
+
 def params_of(workload, flags: int = 0, normalize: Optional[bool] = None, debug_pair_cap: int = 0):
     p = workload.params
     return G.make_params(p.theta_rad, p.cutoff_sigmas, p.eps_rel, p.t_begin, p.t_end, p.window_s,

@@ -92,28 +92,31 @@ def test_eye_grid_equals_bvh(G, ctx, pipe, which, res):
           f" nodes, {bvh[4]['tris_tested'] / st['in_cone']:.1f} triangles)")
 
 
-@pytest.mark.parametrize("budget", [20_000, 200_000])
+@pytest.mark.parametrize("budget", [("GM_EYEGRID_CHUNK_ENTRIES", 20_000), ("GM_EYEGRID_CHUNK_ENTRIES", 200_000),
+                                    ("GM_EYEGRID_L2_ENTRIES", 30_000)])
 def test_eye_grid_in_chunks_carries_sums_across_launches(G, ctx, pipe, budget):
-    """Small per-chunk budgets split the fixations into many launches; sums carry over, windows
-    that span a chunk boundary are written once, and the maps equal the single-chunk ones."""
+    """Small budgets split the fixations into many build chunks (a chunk takes at least one
+    fixation, however large) or many accumulation launches; sums carry over, windows that span a
+    boundary are written once, and the maps equal the single-launch ones."""
+    var, budget = budget
     w = synth.tiny_sphere(n_fix=300)
     ts = w.fixations.timestamp_s
     w.params = synth.Params(t_begin=0.0, t_end=float(ts.max()) + 1.0, window_s=7.0)
     one = _maps(G, pipe, ctx, w, 0)
-    os.environ["GM_EYEGRID_CHUNK_ENTRIES"] = str(budget)
+    os.environ[var] = str(budget)
     try:
         many = _maps(G, pipe, ctx, w, 0)
     finally:
-        del os.environ["GM_EYEGRID_CHUNK_ENTRIES"]
+        del os.environ[var]
     _same(one, many)
-    assert one[4]["grid_chunks"] == 1 and many[4]["grid_chunks"] > 2
-    # single window, chunked
+    assert one[4]["grid_chunks"] == 1 and one[4]["grid_launches"] == 1 and many[4]["grid_launches"] > 2
+    # single window, split
     w.params = synth.Params()
-    os.environ["GM_EYEGRID_CHUNK_ENTRIES"] = str(budget)
+    os.environ[var] = str(budget)
     try:
         many = _maps(G, pipe, ctx, w, 0)
     finally:
-        del os.environ["GM_EYEGRID_CHUNK_ENTRIES"]
+        del os.environ[var]
     _same(_maps(G, pipe, ctx, w, G.GM_F_BVH), many)
 
 
