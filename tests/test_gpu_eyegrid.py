@@ -109,7 +109,7 @@ def test_eye_grid_in_chunks_carries_sums_across_launches(G, ctx, pipe, budget):
     finally:
         del os.environ[var]
     _same(one, many)
-    assert one[4]["grid_chunks"] == 1 and one[4]["grid_launches"] == 1 and many[4]["grid_launches"] > 2
+    assert one[4]["grid_chunks"] == 1 and many[4]["grid_launches"] > max(2, one[4]["grid_launches"])
     # single window, split
     w.params = synth.Params()
     os.environ[var] = str(budget)
