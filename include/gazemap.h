@@ -94,10 +94,14 @@ enum {
     GM_F_STATIC_TILES = 128, /* one warp tile per warp of a full grid (else warps pull tiles from a counter) */
     GM_F_NO_TILE_CULL = 256, /* test every sample against every fixation (no warp-tile sphere test) */
     GM_F_BLOCK128 = 512,    /* blocks of 128 threads (7 per SM, 72 registers; 8 per SM with GM_F_REGCAP64)
-                               for the ray-queue binary-tree variant, instead of 256 (3 or 4 per SM) */
+                               for the ray-queue binary-tree variant, instead of 256 (3 or 4 per SM);
+                               with the eye grid: 128-thread blocks, 6 per SM */
     GM_F_BVH = 1024,        /* occlusion rays walk the BVH instead of the eye grid (the flags NO_COMPACT,
                                WIDE_BVH, REGCAP64 and BLOCK128 select BVH variants and imply it) */
-    GM_F_GRID64 = 2048      /* eye grid of 64 x 64 cells per fixation instead of 128 x 128 */
+    GM_F_GRID64 = 2048,     /* eye grid of 64 x 64 cells per fixation instead of 128 x 128 */
+    GM_F_SPT1 = 4096,       /* eye grid: warp tiles of 32 samples (1 per thread) instead of 128 (4 per thread) */
+    GM_F_SPT2 = 8192,       /* eye grid: warp tiles of 64 samples (2 per thread) */
+    GM_F_BLOCK512 = 16384   /* eye grid: blocks of 512 threads (with 1 or 2 samples per thread) */
 };
 
 typedef struct {
@@ -394,11 +398,15 @@ void gm_batch_free(gm_batch* batch);
  * gm_map_free). */
 gm_status gm_accumulate_batch(gm_ctx* ctx, const gm_session_desc* sessions, uint32_t n_sessions,
                               const gm_params* params, gm_stream stream, gm_map** out_per_session);
-/* Pick the fastest accumulation variant for one problem by timing each candidate on its first
- * 256 fixations: ray queue on/off, binary or 4-wide tree, 80- or 64-register cap, spread or
- * consecutive warp tiles, persistent or static scheduling (32 candidates), and blocks of 128
- * instead of 256 threads for the ray-queue binary-tree kernels (8 more); *best_flags gets the
- * GM_F_* variant bits to OR into params->flags. Results are
+/* Pick the fastest accumulation variant for one problem. Candidates: with the BVH (GM_F_BVH), ray
+ * queue on/off, binary or 4-wide tree, 80- or 64-register cap, spread or consecutive warp tiles,
+ * persistent or static scheduling (32), and blocks of 128 instead of 256 threads for the
+ * ray-queue binary-tree kernels (8 more); with the eye grid, 128 or 64 cells a side times the
+ * warp-tile and block shape (4, 2 or 1 samples per thread; 256, 128 or 512 threads) times spread
+ * or consecutive tiles (28). Each is timed (fixation prep + eye grid + accumulation, best of two)
+ * on a prefix of the fixations (a sixteenth, at least 256); the two fastest are timed again on
+ * all of them and the faster is kept. *best_flags gets the GM_F_* variant bits to OR into
+ * params->flags. Results are
  * cached per size bucket (log2 of samples, fixations and triangles) for the process and, when the
  * environment variable GM_TUNE_CACHE names a file, in that JSON file across processes. */
 gm_status gm_autotune_accumulate(gm_scene* scene, gm_samples* samples, const gm_fixations* fix,

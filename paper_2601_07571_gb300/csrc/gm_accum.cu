@@ -89,13 +89,13 @@ __global__ void k_fix_pack(const uint32_t* __restrict__ keys, const uint32_t* __
 // rays (densely gazed patches) spread over the whole run instead of forming a tail. MINB is the
 // minimum number of resident blocks per SM the register allocation must allow (3: up to 80
 // registers, 4: up to 64).
-template <bool DEBUG, bool COMPACT, bool WIDE, int MINB, int NT = ACC_THREADS, bool GRID = false>
+template <bool DEBUG, bool COMPACT, bool WIDE, int MINB, int NT = ACC_THREADS, bool GRID = false, int S = SPT>
 __global__ void __launch_bounds__(NT, MINB) k_accumulate(
     const float4* __restrict__ spos, const uint32_t* __restrict__ sidx, const float4* __restrict__ fix,
     const uint32_t* __restrict__ n_fix_dev, const float4* __restrict__ nodes, const float4* __restrict__ tris,
     AccParams P, uint32_t n_tiles, int persistent, float* __restrict__ out, unsigned int* __restrict__ max_bits,
     unsigned long long* __restrict__ counters, int* __restrict__ err, DebugOut dbg) {
-    constexpr int QN = COMPACT ? NT * SPT : 1;
+    constexpr int QN = COMPACT ? NT * S : 1;
     __shared__ float4 wsmp[QN];     // per warp: its WARP_TILE samples (x, y, z, own triangle)
     __shared__ float2 wacc[QN];     // per warp: (sum, compensation) of each sample
     __shared__ float4 wbox[NT / 32];   // per warp: its tile's bounding sphere
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(NT, MINB) k_accumulate(
     __shared__ float qg[QN];        // per warp: their weights
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int wb = COMPACT ? warp * WARP_TILE : 0;
+    const int wb = COMPACT ? warp * 32 * S : 0;
     const uint32_t nf = *n_fix_dev;
     unsigned int* next = reinterpret_cast<unsigned int*>(&counters[6]);
     TileStats st;
@@ -117,18 +117,19 @@ __global__ void __launch_bounds__(NT, MINB) k_accumulate(
             tile = blockIdx.x * (NT / 32) + warp;
         }
         if (tile >= n_tiles) break;
-        warp_tile<DEBUG, COMPACT, WIDE, GRID>(tile, spos, sidx, fix, nf, nodes, tris, P, out, max_bits, wsmp + wb,
-                                              wacc + wb, qslot + wb, qg + wb, wbox + warp, &counters[2], dbg, err, st);
+        warp_tile<DEBUG, COMPACT, WIDE, GRID, S>(tile, spos, sidx, fix, nf, nodes, tris, P, out, max_bits, wsmp + wb,
+                                                 wacc + wb, qslot + wb, qg + wb, wbox + warp, &counters[2], dbg, err,
+                                                 st);
     }
     warp_stats_commit(st, counters);
 }
 
 // (The driver's default shared-memory carveout is kept: preferring the largest L1 leaves room for
 // fewer blocks per SM and measured 316 vs 253 ms at the paper scene.)
-template <bool D, bool Cm, bool Wd, int Mb, int NT = ACC_THREADS, bool Gr = false>
+template <bool D, bool Cm, bool Wd, int Mb, int NT = ACC_THREADS, bool Gr = false, int S = SPT>
 int acc_occupancy() {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_accumulate<D, Cm, Wd, Mb, NT, Gr>, NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_accumulate<D, Cm, Wd, Mb, NT, Gr, S>, NT, 0);
     return b > 0 ? b : 1;
 }
 
@@ -368,20 +369,22 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
         const bool b128 = (prm->flags & GM_F_BLOCK128) != 0;
         // the eye grid traces from the ray queue of the default kernel shape; the BVH variants
         // (in place, 4-wide, register caps, 128-thread blocks) keep the tree
-        const bool grid = !(prm->flags & GM_F_BVH) && compact && !wide && !occ4 && !b128 && nf > 0;
+        const bool grid = !(prm->flags & GM_F_BVH) && compact && !wide && !occ4 && nf > 0;
         const float4* tree = wide ? sc->nodes4 : sc->nodes;
         const int code = (compact ? 1 : 0) | (wide ? 2 : 0) | (occ4 ? 4 : 0);
         // persistent grid: every resident block slot once, never more blocks than tiles need
-#define GM_LAUNCH_ACC_NT(D, Cm, Wd, Mb, NT, Gr)                                                                   \
+#define GM_LAUNCH_ACC_S(D, Cm, Wd, Mb, NT, Gr, S_)                                                                \
     do {                                                                                                          \
-        const uint32_t all = gm_div_up(n_tiles, NT / 32);                                                         \
+        const uint32_t nt_s = gm_div_up(ns, (uint64_t)32 * (S_) * P.group) * P.group;                             \
+        const uint32_t all = gm_div_up(nt_s, NT / 32);                                                            \
         const uint32_t grd =                                                                                      \
-            persistent ? std::min<uint32_t>((uint32_t)ctx->n_sm * acc_occupancy<D, Cm, Wd, Mb, NT, Gr>(), all)     \
+            persistent ? std::min<uint32_t>((uint32_t)ctx->n_sm * acc_occupancy<D, Cm, Wd, Mb, NT, Gr, S_>(), all) \
                        : all;                                                                                     \
-        k_accumulate<D, Cm, Wd, Mb, NT, Gr><<<grd, NT, 0, s>>>(spos, sidx, packed, n_valid, tree, sc->bvh_tris, P, \
-                                                               n_tiles, persistent, mp->values, mp->max_bits,     \
-                                                               mp->counters, ctx->dev_err, dbg);                  \
+        k_accumulate<D, Cm, Wd, Mb, NT, Gr, S_><<<grd, NT, 0, s>>>(spos, sidx, packed, n_valid, tree, sc->bvh_tris, \
+                                                                   P, nt_s, persistent, mp->values, mp->max_bits, \
+                                                                   mp->counters, ctx->dev_err, dbg);              \
     } while (0)
+#define GM_LAUNCH_ACC_NT(D, Cm, Wd, Mb, NT, Gr) GM_LAUNCH_ACC_S(D, Cm, Wd, Mb, NT, Gr, SPT)
 #define GM_LAUNCH_ACC(D, Cm, Wd, Mb) GM_LAUNCH_ACC_NT(D, Cm, Wd, Mb, ACC_THREADS, false)
         if (grid) {
             const uint32_t R = (prm->flags & GM_F_GRID64) ? 64u : 128u;
@@ -444,8 +447,19 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
                 }
                 if (timing && q == 0) cudaEventRecord(mp->ev[5], s);
                 if (q > 0) GM_TRY_CUDA(cudaMemsetAsync(&mp->counters[6], 0, sizeof(unsigned long long), s));
-                if (debug) GM_LAUNCH_ACC_NT(true, true, false, 3, ACC_THREADS, true);
-                else GM_LAUNCH_ACC_NT(false, true, false, 3, ACC_THREADS, true);
+                // shape: samples per thread (GM_F_SPT1 / GM_F_SPT2, else 4) and block size
+                // (GM_F_BLOCK128 / GM_F_BLOCK512, else 256); 80 registers a thread in every shape
+                const int spt = (prm->flags & GM_F_SPT1) ? 1 : (prm->flags & GM_F_SPT2) ? 2 : 4;
+                const int nth = b128 ? 128 : (prm->flags & GM_F_BLOCK512) ? 512 : 256;
+                if (debug) GM_LAUNCH_ACC_S(true, true, false, 3, 256, true, 4);
+                else if (nth == 256 && spt == 4) GM_LAUNCH_ACC_S(false, true, false, 3, 256, true, 4);
+                else if (nth == 256 && spt == 2) GM_LAUNCH_ACC_S(false, true, false, 3, 256, true, 2);
+                else if (nth == 256) GM_LAUNCH_ACC_S(false, true, false, 3, 256, true, 1);
+                else if (nth == 128 && spt == 4) GM_LAUNCH_ACC_S(false, true, false, 6, 128, true, 4);
+                else if (nth == 128 && spt == 2) GM_LAUNCH_ACC_S(false, true, false, 6, 128, true, 2);
+                else if (nth == 128) GM_LAUNCH_ACC_S(false, true, false, 6, 128, true, 1);
+                else if (spt == 1) GM_LAUNCH_ACC_S(false, true, false, 1, 512, true, 1);
+                else GM_LAUNCH_ACC_S(false, true, false, 1, 512, true, 2);   // 512 x 4 exceeds static shared memory
                 ++launches;
             }
             mp->stats.grid_chunks = std::max<uint32_t>(1u, nchunk);
@@ -480,6 +494,7 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
         }
 #undef GM_LAUNCH_ACC
 #undef GM_LAUNCH_ACC_NT
+#undef GM_LAUNCH_ACC_S
     }
     if (timing) cudaEventRecord(mp->ev[2], s);
     if (prm->normalize && !into) launches += launch_normalize(mp, ctx->n_sm, s) > 0 ? 1 : 0;

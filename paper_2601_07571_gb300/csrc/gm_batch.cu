@@ -614,36 +614,67 @@ extern "C" gm_status gm_autotune_accumulate(gm_scene* sc, gm_samples* sm, const 
             return GM_OK;
         }
     }
+    // Candidates are ranked on a prefix of the fixations (a sixteenth, at least 256), by the time
+    // of the whole call (fixation prep, eye grid, accumulation); the two best are then timed on the
+    // full list and the faster is kept, so a prefix that ranks them wrongly costs nothing.
     gm_fixations sub = *fx;
-    sub.n = std::min<uint32_t>(fx->n, 256);   // a prefix of the fixations is enough to rank variants
-    int best = 0;
-    float best_t = 1e30f;
-    // the three kernel variants of the batched search, times the warp-tile shape (four spread
+    sub.n = std::min<uint32_t>(fx->n, std::max<uint32_t>(256, fx->n / 16));
+    constexpr int kTileFlags = GM_F_TILE_CONSECUTIVE | GM_F_STATIC_TILES;
+    constexpr int kShapeFlags = GM_F_BLOCK128 | GM_F_BLOCK512 | GM_F_SPT1 | GM_F_SPT2 | GM_F_GRID64 | GM_F_BVH;
+    std::vector<int> cand;
+    // BVH: the three kernel variants of the batched search, times the warp-tile shape (four spread
     // 32-sample runs or 128 consecutive samples) and the scheduling (persistent or one tile per warp);
     // then 128-thread blocks for the two ray-queue binary-tree variants (80- and 64-register caps)
-    constexpr int kTileFlags = GM_F_TILE_CONSECUTIVE | GM_F_STATIC_TILES;
     for (int code = 0; code < 40; ++code) {
-        gm_params p = *prm;
         const int v = code < 32 ? (code & 7) : ((code & 1) ? 5 : 1);
         const int shape = code < 32 ? code >> 3 : (code - 32) >> 1;
-        const int f = flags_of_code(v) | ((shape & 1) ? GM_F_TILE_CONSECUTIVE : 0) |
-                      ((shape & 2) ? GM_F_STATIC_TILES : 0) | (code >= 32 ? GM_F_BLOCK128 : 0);
-        p.flags = (prm->flags & ~VARIANT_MASK & ~kTileFlags & ~GM_F_BLOCK128 & ~GM_F_DEBUG_PAIRS) | f |
-                  GM_F_TIMING;
+        cand.push_back(GM_F_BVH | flags_of_code(v) | ((shape & 1) ? GM_F_TILE_CONSECUTIVE : 0) |
+                       ((shape & 2) ? GM_F_STATIC_TILES : 0) | (code >= 32 ? GM_F_BLOCK128 : 0));
+    }
+    // eye grid: 128 or 64 cells a side, samples per thread and block size, spread or consecutive tiles
+    const int grid_shapes[7] = {0, GM_F_SPT2, GM_F_SPT1, GM_F_BLOCK128, GM_F_BLOCK128 | GM_F_SPT2,
+                                GM_F_BLOCK512 | GM_F_SPT2, GM_F_BLOCK512 | GM_F_SPT1};
+    for (int res = 0; res < 2; ++res)
+        for (int sh = 0; sh < 7; ++sh)
+            for (int tl = 0; tl < 2; ++tl)
+                cand.push_back((res ? GM_F_GRID64 : 0) | grid_shapes[sh] | (tl ? GM_F_TILE_CONSECUTIVE : 0));
+    auto time_of = [&](int f, const gm_fixations* fs, float* out_ms) -> gm_status {
+        gm_params p = *prm;
+        p.flags = (prm->flags & ~VARIANT_MASK & ~kTileFlags & ~kShapeFlags & ~GM_F_DEBUG_PAIRS) | f | GM_F_TIMING;
+        p.normalize = 0;
         float t = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
             gm_map* m = nullptr;
-            GM_TRY(gm_accumulate_fixations(sc, sm, &sub, &p, stream, &m));
+            GM_TRY(gm_accumulate_fixations(sc, sm, fs, &p, stream, &m));
             gm_map_stats stt;
             gm_status st = gm_map_info(m, nullptr, nullptr, &stt);
             gm_map_free(m);
             if (st != GM_OK && st != GM_WARN_EMPTY) return st;
-            t = std::min(t, stt.accumulate_ms);
+            t = std::min(t, stt.prep_ms + stt.grid_ms + stt.accumulate_ms);
         }
-        if (t < best_t) {
-            best_t = t;
-            best = f;
+        *out_ms = t;
+        return GM_OK;
+    };
+    int b1 = cand[0], b2 = cand[0];
+    float t1 = 1e30f, t2 = 1e30f;
+    for (int f : cand) {
+        float t;
+        GM_TRY(time_of(f, &sub, &t));
+        if (t < t1) {
+            b2 = b1, t2 = t1;
+            b1 = f, t1 = t;
+        } else if (t < t2) {
+            b2 = f, t2 = t;
         }
+    }
+    int best = b1;
+    float best_t = t1;
+    if (sub.n < fx->n) {
+        float f1, f2 = 1e30f;
+        GM_TRY(time_of(b1, fx, &f1));
+        if (b2 != b1) GM_TRY(time_of(b2, fx, &f2));
+        best = f2 < f1 ? b2 : b1;
+        best_t = std::min(f1, f2);
     }
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);

@@ -337,7 +337,7 @@ __device__ __forceinline__ void record_pair(unsigned long long* cursor, const De
     }
 }
 
-// One warp processes the work-order samples of warp tile `tile` (see AccParams::group) against
+// One warp processes the S x 32 work-order samples of warp tile `tile` (see AccParams::group) against
 // fixations [P.f0, min(P.f1, nf)) of `fix` (packed (e, w), (r^, window), sorted by window). Sums are
 // written to out[window * P.ns + sidx[j]] when a window ends; each window's maximum is folded into
 // max_bits[window] with one atomicMax per warp. With P.carry_in the compensated sums start from
@@ -346,7 +346,7 @@ __device__ __forceinline__ void record_pair(unsigned long long* cursor, const De
 // shared-memory regions (WARP_TILE entries each) are used only when COMPACT. Occlusion: the BVH
 // (binary or, WIDE, 4-wide) or, GRID, the eye grid of P (COMPACT only). No block-wide
 // synchronisation. *tested counts the sample x fixation cone tests actually evaluated.
-template <bool DEBUG, bool COMPACT, bool WIDE, bool GRID = false>
+template <bool DEBUG, bool COMPACT, bool WIDE, bool GRID = false, int S = SPT>
 __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restrict__ spos,
                                           const uint32_t* __restrict__ sidx, const float4* __restrict__ fix,
                                           uint32_t nf, const float4* __restrict__ nodes,
@@ -359,15 +359,15 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
     const int lane = threadIdx.x & 31;
     const uint32_t G = P.group;
     const uint32_t stride = 32u * G;
-    const uint32_t base0 = (tile / G) * (uint32_t)WARP_TILE * G + (tile % G) * 32u;
+    const uint32_t base0 = (tile / G) * (uint32_t)(32 * S) * G + (tile % G) * 32u;
     const uint32_t base = base0 + lane;
     const uint32_t i_end = min(nf, P.f1);
-    float sx[SPT], sy[SPT], sz[SPT], sum[SPT], cmp[SPT];
-    uint32_t own[SPT];
+    float sx[S], sy[S], sz[S], sum[S], cmp[S];
+    uint32_t own[S];
     float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
     uint32_t live = 0;
 #pragma unroll
-    for (int k = 0; k < SPT; ++k) {
+    for (int k = 0; k < S; ++k) {
         const uint32_t j = base + k * stride;
         // padding lanes hold NaN positions: every cone test on them is false
         const float4 p = j < P.ns ? spos[j]
@@ -422,7 +422,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
         float m = 0.f;
         if (COMPACT) __syncwarp();
 #pragma unroll
-        for (int k = 0; k < SPT; ++k) {
+        for (int k = 0; k < S; ++k) {
             if (COMPACT) {
                 sum[k] = wacc[k * 32 + lane].x;
                 wacc[k * 32 + lane] = make_float2(0.f, 0.f);
@@ -472,7 +472,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
         if (COMPACT) {
             int tot = 0;
 #pragma unroll
-            for (int k = 0; k < SPT; ++k) {
+            for (int k = 0; k < S; ++k) {
                 // the tile's samples are read from shared memory (they are there for the ray queue
                 // anyway), which keeps 4 x 4 registers free for occupancy
                 const float4 q = wsmp[k * 32 + lane];
@@ -543,7 +543,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
             __syncwarp();
         } else {
 #pragma unroll
-            for (int k = 0; k < SPT; ++k) {
+            for (int k = 0; k < S; ++k) {
                 const float px = sx[k] - F0.x, py = sy[k] - F0.y, pz = sz[k] - F0.z;
                 const float d1 = fmaf(px, F1.x, fmaf(py, F1.y, pz * F1.z));
                 const float cx = fmaf(py, F1.z, -pz * F1.y);
@@ -583,7 +583,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
         // the window goes on in the next launch: keep the open sums
         if (COMPACT) __syncwarp();
 #pragma unroll
-        for (int k = 0; k < SPT; ++k) {
+        for (int k = 0; k < S; ++k) {
             const uint32_t j = base + k * stride;
             if (j < P.ns) P.carry[j] = COMPACT ? wacc[k * 32 + lane] : make_float2(sum[k], cmp[k]);
         }

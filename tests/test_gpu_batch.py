@@ -154,10 +154,15 @@ def test_autotune_picks_a_variant_and_keeps_results(env, tmp_path, monkeypatch):
         assert np.array_equal(a.view(np.uint32), before[i].view(np.uint32))
     G.gm_batch_free(b)
     fl2, _ = G.gm_autotune_accumulate(hs[0][0], hs[0][1], *hs[0][2:], prm)
-    assert fl2 & ~(G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64 | G.GM_F_TILE_CONSECUTIVE
-                   | G.GM_F_STATIC_TILES | G.GM_F_BLOCK128) == 0
-    if fl2 & G.GM_F_BLOCK128:   # only offered for the ray-queue binary-tree kernels
-        assert not fl2 & (G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH)
+    shape = (G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64 | G.GM_F_TILE_CONSECUTIVE | G.GM_F_STATIC_TILES
+             | G.GM_F_BLOCK128 | G.GM_F_BVH | G.GM_F_GRID64 | G.GM_F_SPT1 | G.GM_F_SPT2 | G.GM_F_BLOCK512)
+    assert fl2 & ~shape == 0
+    if fl2 & G.GM_F_BVH:
+        assert not fl2 & (G.GM_F_GRID64 | G.GM_F_SPT1 | G.GM_F_SPT2 | G.GM_F_BLOCK512)
+        if fl2 & G.GM_F_BLOCK128:   # only offered for the ray-queue binary-tree kernels
+            assert not fl2 & (G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH)
+    else:                            # eye-grid shapes only
+        assert not fl2 & (G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64 | G.GM_F_STATIC_TILES)
     # the tuned variant gives the same map as the default one
     ref = G.gm_accumulate_fixations(hs[0][0], hs[0][1], *hs[0][2:], prm)
     p2 = pipe.params_of(ws[0], normalize=False, flags=fl2)

@@ -158,3 +158,25 @@ def test_eye_grid_geometry_at_the_eye(G, ctx, pipe):
     bvh = _maps(G, pipe, ctx, w, G.GM_F_BVH)
     _same(grid, bvh)
     assert grid[4]["in_cone"] > 1000 and 0 < grid[4]["visible"] < grid[4]["in_cone"]
+
+
+@pytest.mark.parametrize("shape", ["spt2", "spt1", "block128", "block128_spt2", "block512_spt2", "block512_spt1",
+                                   "consecutive"])
+def test_eye_grid_kernel_shapes_agree_bit_for_bit(G, ctx, pipe, shape):
+    """Samples per thread, block size and tile layout only change which warp handles which
+    sample; every sample still gets its additions in fixation order."""
+    flag = {"spt2": G.GM_F_SPT2, "spt1": G.GM_F_SPT1, "block128": G.GM_F_BLOCK128,
+            "block128_spt2": G.GM_F_BLOCK128 | G.GM_F_SPT2, "block512_spt2": G.GM_F_BLOCK512 | G.GM_F_SPT2,
+            "block512_spt1": G.GM_F_BLOCK512 | G.GM_F_SPT1, "consecutive": G.GM_F_TILE_CONSECUTIVE}[shape]
+    w = synth.session(5)
+    w.fixations = w.fixations.subset(slice(0, 150))
+    h = pipe.run(ctx, w, normalize=False)
+    a, _ = pipe.map_array(h)
+    _, _, sa, _ = G.gm_map_info(h.map)
+    h.free()
+    h = pipe.run(ctx, w, normalize=False, flags=flag)
+    b, _ = pipe.map_array(h)
+    _, _, sb, _ = G.gm_map_info(h.map)
+    h.free()
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    assert sa["in_cone"] == sb["in_cone"] and sa["visible"] == sb["visible"]
