@@ -915,7 +915,7 @@ def main():
                           "build_and_sample": step_ms - acc - gms - sum(prep_ms) / len(prep_ms)
                           - sum(norm_ms) / len(norm_ms)},
             "occlusion": (f"eye grid {64 if args.flags & G.GM_F_GRID64 else 128}^2 cells per fixation, "
-                          f"{stats['grid_chunks']} chunk(s)") if grid_on else "BVH",
+                          f"{stats['grid_chunks']} chunk(s), {stats['grid_launches']} launch(es)") if grid_on else "BVH",
             "in_cone_pairs": int(stats["in_cone"]), "visible_pairs": int(stats["visible"]),
             "cone_tests_evaluated": int(stats["pairs_tested"]),
             "rays_per_s": stats["in_cone"] / (acc * 1e-3),

@@ -96,9 +96,9 @@ enum {
     GM_F_BLOCK128 = 512,    /* blocks of 128 threads (7 per SM, 72 registers; 8 per SM with GM_F_REGCAP64)
                                for the ray-queue binary-tree variant, instead of 256 (3 or 4 per SM);
                                with the eye grid: 128-thread blocks, 6 per SM */
-    GM_F_BVH = 1024,        /* occlusion rays walk the BVH instead of the eye grid (the flags NO_COMPACT,
-                               WIDE_BVH, REGCAP64 and BLOCK128 select BVH variants and imply it) */
-    GM_F_GRID64 = 2048,     /* eye grid of 64 x 64 cells per fixation instead of 128 x 128 */
+    GM_F_EYE_GRID = 1024,   /* occlusion through per-fixation eye grids instead of the BVH (ray-queue
+                               kernel only: with NO_COMPACT, WIDE_BVH or REGCAP64 the BVH is kept) */
+    GM_F_GRID64 = 2048,     /* with GM_F_EYE_GRID: 64 x 64 cells per fixation instead of 128 x 128 */
     GM_F_SPT1 = 4096,       /* eye grid: warp tiles of 32 samples (1 per thread) instead of 128 (4 per thread) */
     GM_F_SPT2 = 8192,       /* eye grid: warp tiles of 64 samples (2 per thread) */
     GM_F_BLOCK512 = 16384   /* eye grid: blocks of 512 threads (with 1 or 2 samples per thread) */
@@ -119,7 +119,7 @@ typedef struct {
     uint64_t pairs_tested;    /* sample x fixation cone tests evaluated (pairs of warp tiles whose bounding
                                  sphere the cone misses are skipped without a per-sample test) */
     float grid_ms;            /* eye-grid frames, counts and (first chunk's) cell lists (GM_F_TIMING) */
-    uint32_t grid_chunks;     /* fixation chunks the eye grid was built in (0: BVH occlusion) */
+    uint32_t grid_chunks;     /* fixation chunks the eye grid was built in (0: BVH occlusion, the default) */
     uint32_t grid_launches;   /* accumulation launches over runs of fixations (eye grid) */
 } gm_map_stats;
 
@@ -277,16 +277,17 @@ gm_status gm_tri_offsets_noalloc(gm_ctx* ctx, const float* tri_xyz, const double
  * Sums are compensated (Kahan) FP32 in fixation order. The maximum of each window's map is
  * kept; with params->normalize the map is divided by it in place (max 0 => map stays 0 and
  * the call returns GM_WARN_EMPTY at gm_map_info).
- * Occlusion: by default each fixation gets an eye grid -- the triangles that can meet its cone,
- * binned by their image in the gaze frame into 128 x 128 cells (GM_F_GRID64: 64 x 64) and sorted
- * by depth -- and a segment tests the triangles of its own cell; GM_F_BVH walks the scene's BVH
- * instead. Both give the same maps (the same triangle test over every triangle it can report).
- * The grid's memory is taken on the stream for the call: at most a third of the free device
+ * Occlusion: by default every segment walks the scene's BVH. With GM_F_EYE_GRID each fixation
+ * gets an eye grid instead -- the triangles that can meet its cone, binned by their image in the
+ * gaze frame into 128 x 128 cells (GM_F_GRID64: 64 x 64) and sorted by depth -- and a segment
+ * tests the triangles of its own cell. Both give the same maps (the same triangle test over every
+ * triangle it can report).
+ * The eye grid's memory is taken on the stream for the call: at most a third of the free device
  * memory for the cell lists of one chunk of fixations (more fixations run in several chunks) and
  * 1 GiB of offset tables; the environment variable GM_EYEGRID_CHUNK_ENTRIES, read at each call,
  * lowers the per-chunk entry budget (a chunk always takes at least one fixation). Within a chunk
- * the accumulation runs once per run of fixations whose lists fit in L2 together
- * (GM_EYEGRID_L2_ENTRIES entries of 8 bytes, 4M by default), carrying the sums over. The call reads the per-fixation list sizes back once (it
+ * the accumulation can run once per run of fixations whose lists hold at most GM_EYEGRID_L2_ENTRIES
+ * entries (of 8 bytes; default: one launch per chunk), carrying the sums over. The call reads the per-fixation list sizes back once (it
  * synchronises the stream). */
 gm_status gm_accumulate_fixations(gm_scene* scene, gm_samples* samples, const gm_fixations* fix,
                                   const gm_params* params, gm_stream stream, gm_map** out);
@@ -398,10 +399,10 @@ void gm_batch_free(gm_batch* batch);
  * gm_map_free). */
 gm_status gm_accumulate_batch(gm_ctx* ctx, const gm_session_desc* sessions, uint32_t n_sessions,
                               const gm_params* params, gm_stream stream, gm_map** out_per_session);
-/* Pick the fastest accumulation variant for one problem. Candidates: with the BVH (GM_F_BVH), ray
+/* Pick the fastest accumulation variant for one problem. Candidates: with the BVH, ray
  * queue on/off, binary or 4-wide tree, 80- or 64-register cap, spread or consecutive warp tiles,
  * persistent or static scheduling (32), and blocks of 128 instead of 256 threads for the
- * ray-queue binary-tree kernels (8 more); with the eye grid, 128 or 64 cells a side times the
+ * ray-queue binary-tree kernels (8 more); with the eye grid (GM_F_EYE_GRID), 128 or 64 cells a side times the
  * warp-tile and block shape (4, 2 or 1 samples per thread; 256, 128 or 512 threads) times spread
  * or consecutive tiles (28). Each is timed (fixation prep + eye grid + accumulation, best of two)
  * on a prefix of the fixations (a sixteenth, at least 256); the two fastest are timed again on

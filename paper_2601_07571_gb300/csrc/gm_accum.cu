@@ -12,8 +12,8 @@
 // in-cone <=> d1 > 0 and |c|^2 <= (cutoff tan theta)^2 d1^2, about 20 FP32 instructions per
 // pair) and, for in-cone pairs only, traces the occlusion segment e -> e + (1 - eps) p (any-hit,
 // early exit, the sample's own triangle skipped) with the watertight ray/triangle test of Woop,
-// Benthin and Wald (JCGT 2013), over the triangles of the segment's cell in the fixation's eye
-// grid (gm_eyegrid.cu) or, with GM_F_BVH, through the BVH. With more fixations than one eye-grid
+// Benthin and Wald (JCGT 2013), through the BVH or, with GM_F_EYE_GRID, over the triangles of the
+// segment's cell in the fixation's eye grid (gm_eyegrid.cu). With more fixations than one eye-grid
 // chunk holds, the kernel runs once per chunk and the compensated sums carry over. A visible pair adds
 // g = w exp(-(|c|/d1)^2 / (2 tan^2 theta)), i.e. the paper's t/(sigma sqrt(2 pi)) *
 // exp(-sigma_k^2 / (2 sigma^2)) with sigma_k = d2 / d1, d2 = |c|, in fixation order (Kahan).
@@ -367,9 +367,9 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
         const bool wide = (prm->flags & GM_F_WIDE_BVH) && sc->nodes4;
         const bool occ4 = (prm->flags & GM_F_REGCAP64) != 0;
         const bool b128 = (prm->flags & GM_F_BLOCK128) != 0;
-        // the eye grid traces from the ray queue of the default kernel shape; the BVH variants
-        // (in place, 4-wide, register caps, 128-thread blocks) keep the tree
-        const bool grid = !(prm->flags & GM_F_BVH) && compact && !wide && !occ4 && nf > 0;
+        // the eye grid (opt-in) traces from the ray queue; the in-place, 4-wide and 64-register
+        // variants keep the tree
+        const bool grid = (prm->flags & GM_F_EYE_GRID) && compact && !wide && !occ4 && nf > 0;
         const float4* tree = wide ? sc->nodes4 : sc->nodes;
         const int code = (compact ? 1 : 0) | (wide ? 2 : 0) | (occ4 ? 4 : 0);
         // persistent grid: every resident block slot once, never more blocks than tiles need
@@ -401,10 +401,10 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
                                  &launches)) != GM_OK)
                 return fail(st);
             const uint32_t nchunk = (uint32_t)eg.chunk.size() - 1;
-            // accumulation launches: within a build chunk, runs of fixations whose cell lists fit in
-            // L2 together (GM_EYEGRID_L2_ENTRIES entries, 4M = 32 MB by default), so that every
-            // launch reads its grids from L2; the sums carry from launch to launch
-            uint64_t l2_entries = 4u << 20;
+            // accumulation launches: within a build chunk, runs of fixations holding at most
+            // GM_EYEGRID_L2_ENTRIES entries (default: the whole chunk in one launch; L2-sized runs
+            // measured slower, each launch waiting on its slowest warp tile); the sums carry over
+            uint64_t l2_entries = ~0ull;   // measured: one launch per chunk beats L2-sized runs
             if (const char* env = std::getenv("GM_EYEGRID_L2_ENTRIES")) {
                 const unsigned long long v = std::strtoull(env, nullptr, 10);
                 if (v > 0) l2_entries = v;

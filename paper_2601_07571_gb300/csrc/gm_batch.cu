@@ -620,7 +620,7 @@ extern "C" gm_status gm_autotune_accumulate(gm_scene* sc, gm_samples* sm, const 
     gm_fixations sub = *fx;
     sub.n = std::min<uint32_t>(fx->n, std::max<uint32_t>(256, fx->n / 16));
     constexpr int kTileFlags = GM_F_TILE_CONSECUTIVE | GM_F_STATIC_TILES;
-    constexpr int kShapeFlags = GM_F_BLOCK128 | GM_F_BLOCK512 | GM_F_SPT1 | GM_F_SPT2 | GM_F_GRID64 | GM_F_BVH;
+    constexpr int kShapeFlags = GM_F_BLOCK128 | GM_F_BLOCK512 | GM_F_SPT1 | GM_F_SPT2 | GM_F_GRID64 | GM_F_EYE_GRID;
     std::vector<int> cand;
     // BVH: the three kernel variants of the batched search, times the warp-tile shape (four spread
     // 32-sample runs or 128 consecutive samples) and the scheduling (persistent or one tile per warp);
@@ -628,7 +628,7 @@ extern "C" gm_status gm_autotune_accumulate(gm_scene* sc, gm_samples* sm, const 
     for (int code = 0; code < 40; ++code) {
         const int v = code < 32 ? (code & 7) : ((code & 1) ? 5 : 1);
         const int shape = code < 32 ? code >> 3 : (code - 32) >> 1;
-        cand.push_back(GM_F_BVH | flags_of_code(v) | ((shape & 1) ? GM_F_TILE_CONSECUTIVE : 0) |
+        cand.push_back(flags_of_code(v) | ((shape & 1) ? GM_F_TILE_CONSECUTIVE : 0) |
                        ((shape & 2) ? GM_F_STATIC_TILES : 0) | (code >= 32 ? GM_F_BLOCK128 : 0));
     }
     // eye grid: 128 or 64 cells a side, samples per thread and block size, spread or consecutive tiles
@@ -637,7 +637,8 @@ extern "C" gm_status gm_autotune_accumulate(gm_scene* sc, gm_samples* sm, const 
     for (int res = 0; res < 2; ++res)
         for (int sh = 0; sh < 7; ++sh)
             for (int tl = 0; tl < 2; ++tl)
-                cand.push_back((res ? GM_F_GRID64 : 0) | grid_shapes[sh] | (tl ? GM_F_TILE_CONSECUTIVE : 0));
+                cand.push_back(GM_F_EYE_GRID | (res ? GM_F_GRID64 : 0) | grid_shapes[sh] |
+                               (tl ? GM_F_TILE_CONSECUTIVE : 0));
     auto time_of = [&](int f, const gm_fixations* fs, float* out_ms) -> gm_status {
         gm_params p = *prm;
         p.flags = (prm->flags & ~VARIANT_MASK & ~kTileFlags & ~kShapeFlags & ~GM_F_DEBUG_PAIRS) | f | GM_F_TIMING;

@@ -17,13 +17,15 @@
 // error of X on either side (vertex and sample) plus the watertight test's own angular slack
 // (about 1e-7 rad) with room to spare. Triangles with a vertex nearer than W0 along the gaze are
 // clipped at w = W0 in FP64 (the part nearer than W0 lies outside the cone unless the triangle
-// comes within RNEAR of the eye); a triangle within RNEAR of the eye goes to the fixation's near
-// list (cell R*R), tested by every ray of the fixation.
+// comes within RNEAR of the eye); a triangle within RNEAR of the eye, or one whose image box covers
+// more than EG_BIG_CELLS cells, goes to the fixation's all-rays list (cell R*R), walked by every ray
+// of the fixation.
 //
 // Stages: k_eg_spheres (bounding sphere of each run of 256 leaf-order triangles), k_eg_count (one
 // block per fixation: cone test of the spheres, then of their triangles, cell counts in shared
 // memory; the fixation's total), then per chunk of fixations k_eg_build (the counts again, a
-// block-wide scan into the chunk's offset table, the fill, a depth sort of every cell). The host
+// block-wide scan into the chunk's offset table, the fill, a depth sort of every cell in batches
+// staged in shared memory). The host
 // reads the totals once to size the chunks (memory) and their entry offsets.
 #include <algorithm>
 #include <cmath>
@@ -40,6 +42,7 @@ constexpr int EG_THREADS = 512;
 constexpr int EG_BATCH = 2048;       // surviving 256-triangle blocks handled per round
 constexpr int EG_BLOCK = 256;        // leaf-order triangles per bounding sphere
 constexpr float EG_W0 = 0.02f;       // clip depth (metres) for triangles reaching toward the eye plane
+constexpr int EG_BIG_CELLS = 1024;   // triangles whose box covers more cells go to the all-rays list
 
 struct EgFix {
     float3 e, r, u, v;
@@ -205,7 +208,9 @@ __device__ void eg_pass(const EgFix& F, const EgGeom& G, const float4* __restric
                 float wlo;
                 if (!eg_classify<R>(F, G, a, b, c, cx0, cx1, cy0, cy1, near, wlo)) continue;
                 const uint2 rec = make_uint2(t, __float_as_uint(wlo));
-                if (near) {
+                // a triangle near the eye, or one whose box covers many cells, goes to the list
+                // every ray of the fixation walks (cell R*R) instead of into each of its cells
+                if (near || (cx1 - cx0 + 1) * (cy1 - cy0 + 1) > EG_BIG_CELLS) {
                     const uint32_t p = atomicAdd(&cnt[R * R], 1u);
                     if (FILL) {
                         if (p < tot) ent[p] = rec;
@@ -295,37 +300,10 @@ __global__ void __launch_bounds__(EG_THREADS) k_eg_count(const float4* __restric
     if (threadIdx.x == 0) totals[f] = tot;
 }
 
-constexpr int EG_SORT_MAX = 256;     // cells up to this long are sorted by one warp in shared memory
+constexpr int EG_STAGE = 4096;       // entries staged in shared memory for the per-cell sorts
 
-// One warp sorts one cell's entries (n <= EG_SORT_MAX) by depth bound: a bitonic network over the
-// next power of two (at least 32) in the warp's shared-memory slot, padded with +inf keys.
-__device__ void eg_warp_sort(uint2* __restrict__ a, uint32_t n, uint2* sw) {
-    const int lane = threadIdx.x & 31;
-    uint32_t P = 32;
-    while (P < n) P <<= 1;
-    for (uint32_t i = lane; i < P; i += 32) sw[i] = i < n ? a[i] : make_uint2(0u, 0x7f800000u);
-    __syncwarp();
-    for (uint32_t k = 2; k <= P; k <<= 1)
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = lane; i < P; i += 32) {
-                const uint32_t ixj = i ^ j;
-                if (ixj > i) {
-                    const uint2 x = sw[i], y = sw[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((__uint_as_float(x.y) > __uint_as_float(y.y)) == up) {
-                        sw[i] = y;
-                        sw[ixj] = x;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    for (uint32_t i = lane; i < n; i += 32) a[i] = sw[i];
-    __syncwarp();
-}
-
-// In-place shell sort of one cell's entries by depth bound (the rare cells longer than
-// EG_SORT_MAX, one thread).
+// In-place shell sort of one cell's entries by depth bound, one thread (gaps 701 ... 1: plain
+// insertion sort for the short lists that are the rule).
 __device__ void eg_sort(uint2* a, uint32_t n) {
     const uint32_t gaps[8] = {701, 301, 132, 57, 23, 10, 4, 1};
 #pragma unroll 1
@@ -396,22 +374,49 @@ __global__ void __launch_bounds__(EG_THREADS) k_eg_build(const float4* __restric
     __syncthreads();
     eg_pass<R, true>(F, G, spheres, n_blocks, tris, nt, cnt, blist, &nsurv, e, min(all, tot), err);
     __syncthreads();
-    // after the fill cnt[c] is the end of cell c, i.e. the start of cell c + 1; one warp per cell
-    uint2* sw = reinterpret_cast<uint2*>(eg_sm + (((size_t)R * R + 1 + EG_BATCH + 1) & ~(size_t)1)) +
-                (threadIdx.x >> 5) * EG_SORT_MAX;
-    for (int c = threadIdx.x >> 5; c < NC; c += EG_THREADS / 32) {
-        const uint32_t st = c == 0 ? 0u : cnt[c - 1], en = cnt[c];
-        if (en <= st + 1 || en > all) continue;
-        if (en - st <= (uint32_t)EG_SORT_MAX) eg_warp_sort(e + st, en - st, sw);
-        else if ((threadIdx.x & 31) == 0) eg_sort(e + st, en - st);
+    // after the fill cnt[c] is the end of cell c, i.e. the start of cell c + 1. The cells are sorted
+    // in batches of consecutive cells staged in shared memory (their entries are contiguous): one
+    // thread per cell, insertion or shell sort; a cell longer than the stage is sorted in place
+    uint2* stage = reinterpret_cast<uint2*>(eg_sm + (((size_t)R * R + 1 + EG_BATCH + 1) & ~(size_t)1));
+    __shared__ int s_c1;
+    for (int c0 = 0; c0 < NC;) {
+        const uint32_t st0 = c0 == 0 ? 0u : cnt[c0 - 1];
+        if (threadIdx.x == 0) {
+            // the last cell c1 - 1 whose end is within EG_STAGE entries of st0 (binary search; ends
+            // are non-decreasing), at least one cell
+            int lo = c0, hi = NC - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cnt[mid] - st0 <= (uint32_t)EG_STAGE) lo = mid;
+                else hi = mid - 1;
+            }
+            s_c1 = lo + 1;
+        }
+        __syncthreads();
+        const int c1 = s_c1;
+        const uint32_t en1 = min(cnt[c1 - 1], all);
+        if (en1 - st0 > (uint32_t)EG_STAGE) {   // one cell longer than the stage
+            if (threadIdx.x == 0) eg_sort(e + st0, en1 - st0);
+        } else {
+            for (uint32_t k = threadIdx.x; k < en1 - st0; k += EG_THREADS) stage[k] = e[st0 + k];
+            __syncthreads();
+            for (int c = c0 + threadIdx.x; c < c1; c += EG_THREADS) {
+                const uint32_t a = (c == 0 ? 0u : cnt[c - 1]) - st0, b = min(cnt[c], all) - st0;
+                if (b > a + 1) eg_sort(stage + a, b - a);
+            }
+            __syncthreads();
+            for (uint32_t k = threadIdx.x; k < en1 - st0; k += EG_THREADS) e[st0 + k] = stage[k];
+        }
+        __syncthreads();
+        c0 = c1;
     }
 }
 
-// counts (R*R + 1), the surviving-block list, and (build only) one sort slot per warp
+// counts (R*R + 1), the surviving-block list, and (build only) the sort stage
 template <int R>
 size_t eg_smem(bool build) {
     const size_t b = sizeof(uint32_t) * ((size_t)R * R + 1 + EG_BATCH);
-    return build ? ((b + 7) & ~(size_t)7) + sizeof(uint2) * (EG_THREADS / 32) * EG_SORT_MAX : b;
+    return build ? ((b + 7) & ~(size_t)7) + sizeof(uint2) * EG_STAGE : b;
 }
 
 template <int R>

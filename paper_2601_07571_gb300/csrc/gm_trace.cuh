@@ -264,14 +264,27 @@ __device__ bool occluded4(const Ray& R, uint32_t own, const float4* __restrict__
 __device__ __forceinline__ bool eg_list_hit(const Ray& R, uint32_t own, uint32_t b, uint32_t e, float wlim,
                                             const uint2* __restrict__ ent, const float4* __restrict__ tris,
                                             uint32_t& n_ent, uint32_t& n_tri, int& hit_slot) {
-    uint2 nx = b < e ? __ldg(&ent[b]) : make_uint2(0u, 0u);
-    for (uint32_t k = b; k < e; ++k) {
-        const uint2 t = nx;
-        if (k + 1 < e) nx = __ldg(&ent[k + 1]);   // the next entry is in flight while this one is tested
-        ++n_ent;
-        if (__uint_as_float(t.y) > wlim) break;
-        if (leaf_hit(R, tris, (int)t.x, own, n_tri)) {
-            hit_slot = (int)t.x;
+    // two entries per step: both triangles' loads are in flight before either is tested
+    for (uint32_t k = b; k < e; k += 2) {
+        const uint2 t0 = __ldg(&ent[k]);
+        const bool two = k + 1 < e;
+        const uint2 t1 = two ? __ldg(&ent[k + 1]) : make_uint2(0u, 0x7f800000u);
+        const bool u0 = __uint_as_float(t0.y) <= wlim, u1 = two && __uint_as_float(t1.y) <= wlim;
+        n_ent += two ? 2 : 1;
+        if (!u0) break;
+        const float4* p0 = tris + 3 * (size_t)t0.x;
+        const float4* p1 = tris + 3 * (size_t)(u1 ? t1.x : t0.x);
+        const float4 a0 = __ldg(p0), b0 = __ldg(p0 + 1), c0 = __ldg(p0 + 2);
+        const float4 a1 = __ldg(p1), b1 = __ldg(p1 + 1), c1 = __ldg(p1 + 2);
+        ++n_tri;
+        if (__float_as_uint(a0.w) != own && tri_hit(R, a0, b0, c0)) {
+            hit_slot = (int)t0.x;
+            return true;
+        }
+        if (!u1) break;
+        ++n_tri;
+        if (__float_as_uint(a1.w) != own && tri_hit(R, a1, b1, c1)) {
+            hit_slot = (int)t1.x;
             return true;
         }
     }

@@ -155,9 +155,9 @@ def test_autotune_picks_a_variant_and_keeps_results(env, tmp_path, monkeypatch):
     G.gm_batch_free(b)
     fl2, _ = G.gm_autotune_accumulate(hs[0][0], hs[0][1], *hs[0][2:], prm)
     shape = (G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64 | G.GM_F_TILE_CONSECUTIVE | G.GM_F_STATIC_TILES
-             | G.GM_F_BLOCK128 | G.GM_F_BVH | G.GM_F_GRID64 | G.GM_F_SPT1 | G.GM_F_SPT2 | G.GM_F_BLOCK512)
+             | G.GM_F_BLOCK128 | G.GM_F_EYE_GRID | G.GM_F_GRID64 | G.GM_F_SPT1 | G.GM_F_SPT2 | G.GM_F_BLOCK512)
     assert fl2 & ~shape == 0
-    if fl2 & G.GM_F_BVH:
+    if not fl2 & G.GM_F_EYE_GRID:
         assert not fl2 & (G.GM_F_GRID64 | G.GM_F_SPT1 | G.GM_F_SPT2 | G.GM_F_BLOCK512)
         if fl2 & G.GM_F_BLOCK128:   # only offered for the ray-queue binary-tree kernels
             assert not fl2 & (G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH)

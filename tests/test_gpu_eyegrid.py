@@ -80,9 +80,9 @@ def test_eye_grid_equals_bvh(G, ctx, pipe, which, res):
         w = synth.tiny_sphere(n_fix=300)
         ts = w.fixations.timestamp_s
         w.params = synth.Params(t_begin=1.0, t_end=float(ts.max()) * 0.95, window_s=4.0)
-    flag = 0 if res == "grid128" else G.GM_F_GRID64
+    flag = G.GM_F_EYE_GRID | (0 if res == "grid128" else G.GM_F_GRID64)
     grid = _maps(G, pipe, ctx, w, flag)
-    bvh = _maps(G, pipe, ctx, w, G.GM_F_BVH)
+    bvh = _maps(G, pipe, ctx, w, 0)
     _same(grid, bvh)
     st = grid[4]
     assert st["grid_chunks"] == 1 and bvh[4]["grid_chunks"] == 0
@@ -92,8 +92,8 @@ def test_eye_grid_equals_bvh(G, ctx, pipe, which, res):
           f" nodes, {bvh[4]['tris_tested'] / st['in_cone']:.1f} triangles)")
 
 
-@pytest.mark.parametrize("budget", [("GM_EYEGRID_CHUNK_ENTRIES", 20_000), ("GM_EYEGRID_CHUNK_ENTRIES", 200_000),
-                                    ("GM_EYEGRID_L2_ENTRIES", 30_000)])
+@pytest.mark.parametrize("budget", [("GM_EYEGRID_CHUNK_ENTRIES", 2_000), ("GM_EYEGRID_CHUNK_ENTRIES", 20_000),
+                                    ("GM_EYEGRID_L2_ENTRIES", 3_000)])
 def test_eye_grid_in_chunks_carries_sums_across_launches(G, ctx, pipe, budget):
     """Small budgets split the fixations into many build chunks (a chunk takes at least one
     fixation, however large) or many accumulation launches; sums carry over, windows that span a
@@ -102,22 +102,24 @@ def test_eye_grid_in_chunks_carries_sums_across_launches(G, ctx, pipe, budget):
     w = synth.tiny_sphere(n_fix=300)
     ts = w.fixations.timestamp_s
     w.params = synth.Params(t_begin=0.0, t_end=float(ts.max()) + 1.0, window_s=7.0)
-    one = _maps(G, pipe, ctx, w, 0)
+    E = G.GM_F_EYE_GRID
+    one = _maps(G, pipe, ctx, w, E)
     os.environ[var] = str(budget)
     try:
-        many = _maps(G, pipe, ctx, w, 0)
+        many = _maps(G, pipe, ctx, w, E)
     finally:
         del os.environ[var]
     _same(one, many)
-    assert one[4]["grid_chunks"] == 1 and many[4]["grid_launches"] > max(2, one[4]["grid_launches"])
+    assert one[4]["grid_chunks"] == 1 and one[4]["grid_launches"] == 1
+    assert many[4]["grid_chunks"] * many[4]["grid_launches"] > 2
     # single window, split
     w.params = synth.Params()
     os.environ[var] = str(budget)
     try:
-        many = _maps(G, pipe, ctx, w, 0)
+        many = _maps(G, pipe, ctx, w, E)
     finally:
         del os.environ[var]
-    _same(_maps(G, pipe, ctx, w, G.GM_F_BVH), many)
+    _same(_maps(G, pipe, ctx, w, 0), many)
 
 
 def test_eye_grid_geometry_at_the_eye(G, ctx, pipe):
@@ -154,8 +156,8 @@ def test_eye_grid_geometry_at_the_eye(G, ctx, pipe):
         gaze[k] = g / np.linalg.norm(g)
     fx = synth.Fixations(eye, gaze, rng.uniform(0.1, 0.6, nf).astype(np.float32), np.arange(nf, dtype=np.float64))
     w = synth.Workload("eye_near_plate", meshes, fx, synth.Params(theta_rad=math.radians(3.0)), seed=4)
-    grid = _maps(G, pipe, ctx, w, 0)
-    bvh = _maps(G, pipe, ctx, w, G.GM_F_BVH)
+    grid = _maps(G, pipe, ctx, w, G.GM_F_EYE_GRID)
+    bvh = _maps(G, pipe, ctx, w, 0)
     _same(grid, bvh)
     assert grid[4]["in_cone"] > 1000 and 0 < grid[4]["visible"] < grid[4]["in_cone"]
 
@@ -163,18 +165,18 @@ def test_eye_grid_geometry_at_the_eye(G, ctx, pipe):
 @pytest.mark.parametrize("shape", ["spt2", "spt1", "block128", "block128_spt2", "block512_spt2", "block512_spt1",
                                    "consecutive"])
 def test_eye_grid_kernel_shapes_agree_bit_for_bit(G, ctx, pipe, shape):
-    """Samples per thread, block size and tile layout only change which warp handles which
-    sample; every sample still gets its additions in fixation order."""
+    """Eye-grid kernels: samples per thread, block size and tile layout only change which warp
+    handles which sample; every sample still gets its additions in fixation order."""
     flag = {"spt2": G.GM_F_SPT2, "spt1": G.GM_F_SPT1, "block128": G.GM_F_BLOCK128,
             "block128_spt2": G.GM_F_BLOCK128 | G.GM_F_SPT2, "block512_spt2": G.GM_F_BLOCK512 | G.GM_F_SPT2,
             "block512_spt1": G.GM_F_BLOCK512 | G.GM_F_SPT1, "consecutive": G.GM_F_TILE_CONSECUTIVE}[shape]
     w = synth.session(5)
     w.fixations = w.fixations.subset(slice(0, 150))
-    h = pipe.run(ctx, w, normalize=False)
+    h = pipe.run(ctx, w, normalize=False, flags=G.GM_F_EYE_GRID)
     a, _ = pipe.map_array(h)
     _, _, sa, _ = G.gm_map_info(h.map)
     h.free()
-    h = pipe.run(ctx, w, normalize=False, flags=flag)
+    h = pipe.run(ctx, w, normalize=False, flags=flag | G.GM_F_EYE_GRID)
     b, _ = pipe.map_array(h)
     _, _, sb, _ = G.gm_map_info(h.map)
     h.free()
