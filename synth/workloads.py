@@ -276,29 +276,60 @@ def city_block(seed: int = 4, n_fix: int = 100_000, n_samples: float = 20e6,
     for m in meshes:
         m.density = n_samples / area
     centers = np.asarray(centers)
-    # random walk of the viewer, one step per fixation
+    # object extents for gaze targets: boxes (half sizes) first, then spheres (radius)
+    n_box = len(parts)
+    ext = np.zeros((len(centers), 3))
+    rad = np.zeros(len(centers))
+    box_half = np.array([(pp[0].max(0) - pp[0].min(0)) / 2 for pp in parts])
+    ext[:n_box] = box_half
+    for i in range(n_spheres):
+        rad[n_box + i] = centers[n_box + i][1]
+    # the viewer walks the 2 m streets between blocks (x or z a multiple of the pitch), one step
+    # of 0.3 m per fixation, turning at crossings, and steps around the spheres on the crossings
     pos = np.zeros((n_fix, 3))
-    p = np.array([0.0, 1.7, 0.0])
     half = grid * pitch / 2
-    heading = rng.uniform(0, 2 * np.pi)
+    lines = np.arange(-grid // 2 + 1, grid // 2) * pitch          # interior streets
+    along = 0                                                      # 0: moving along x, 1: along z
+    line = rng.choice(lines)
+    coord = rng.uniform(-half + pitch, half - pitch)
+    sign = 1.0
+    sph_c = centers[n_box:, [0, 2]]
+    sph_r = rad[n_box:]
     for i in range(n_fix):
-        heading += rng.normal(0, 0.15)
-        p = p + 0.3 * np.array([np.cos(heading), 0.0, np.sin(heading)])
-        if abs(p[0]) > half or abs(p[2]) > half:
-            heading += np.pi
-            p = np.clip(p, -half, half)
-        pos[i] = p
-    pos[:, 1] = 1.7
-    # gaze at a random point of a nearby object (one of the 8 closest centres)
-    d2 = ((pos[:, None, [0, 2]] - centers[None, :, [0, 2]]) ** 2).sum(-1) if n_fix * len(centers) < 5e8 else None
+        coord += sign * 0.3
+        if abs(coord) > half - pitch:
+            sign = -sign
+            coord = np.clip(coord, -half + pitch, half - pitch)
+        # at a crossing, turn onto the cross street half of the time
+        near_cross = np.abs(coord - np.round(coord / pitch) * pitch) < 0.15
+        if near_cross and rng.random() < 0.5:
+            c = np.round(coord / pitch) * pitch
+            if abs(c) < half - pitch / 2:
+                along, line, coord = 1 - along, c, line
+                sign = rng.choice([-1.0, 1.0])
+        off = rng.uniform(-0.6, 0.6)
+        xz = np.array([coord, line + off]) if along == 0 else np.array([line + off, coord])
+        # outside every sphere (in plan, with half a metre to spare)
+        d = xz[None, :] - sph_c
+        dist = np.sqrt((d ** 2).sum(1))
+        j = np.argmin(dist - sph_r)
+        if dist[j] < sph_r[j] + 0.5:
+            xz = sph_c[j] + d[j] / max(dist[j], 1e-6) * (sph_r[j] + 0.5)
+        pos[i] = (xz[0], 1.7, xz[1])
+    # gaze at a point on the surface of one of the 8 nearest objects
     tgt = np.zeros((n_fix, 3))
     for i0 in range(0, n_fix, 2000):
         sl = slice(i0, min(n_fix, i0 + 2000))
+        m = sl.stop - sl.start
         dd = ((pos[sl, None, :] - centers[None, :, :]) ** 2).sum(-1)
         near = np.argsort(dd, axis=1)[:, :8]
-        pick = near[np.arange(near.shape[0]), rng.integers(0, 8, size=near.shape[0])]
-        tgt[sl] = centers[pick] + rng.normal(0, 0.5, size=(near.shape[0], 3))
-    del d2
+        pick = near[np.arange(m), rng.integers(0, 8, size=m)]
+        u = rng.normal(size=(m, 3))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        is_box = pick < n_box
+        h = np.where(is_box[:, None], ext[pick], 1.0)
+        scale = np.where(is_box, 1.0 / np.max(np.abs(u) / np.maximum(h, 1e-9), axis=1), rad[pick])
+        tgt[sl] = centers[pick] + u * scale[:, None]
     gaze = _jitter(rng, tgt - pos, math.radians(1.0))
     ts = np.sort(rng.uniform(0.0, duration_s, size=n_fix))
     dur = rng.uniform(0.1, 0.6, size=n_fix).astype(np.float32)
