@@ -1,6 +1,15 @@
 """The neural density field on the GPU against the FP64 field oracle (which emulates the bf16
 rounding the definition fixes): queries, the loss gradient, one Adam step, and a short training
-run on the tiny sphere's map."""
+run on the tiny sphere's map.
+
+Element-wise bars: the definition fixes every bf16 rounding but neither the order of the FP32
+additions of a layer (or of a batch sum) nor the evaluation of the features' sines and cosines;
+where a value to be rounded lies near a bf16 boundary, two correct implementations round it
+apart and the later layers carry the difference on. The oracle's enclosures (forward_bounds,
+loss_and_grad_bounds: interval arithmetic through every rounding, FP32 sums as chains with one
+unit of error per addition, features within 1e-5) bound every value such an implementation can
+produce; each GPU value must lie inside its own. The median agreement checks beside them are
+empirical (typical values agree far better than the worst case)."""
 import numpy as np
 import pytest
 
@@ -30,6 +39,33 @@ def _points(n, seed):
     return rng.uniform(BOX_LO, BOX_HI, size=(n, 3)).astype(np.float32)
 
 
+def _xt(x):
+    return F.normalise32(x, BOX_LO, BOX_HI)
+
+
+def _inside(v, lo, hi, rel=2e-6, what=""):
+    """v within [lo, hi], widened by the FP32 evaluation of the final softplus / sigmoid."""
+    v = np.asarray(v, np.float64)
+    slack = rel * np.maximum(np.abs(lo), np.abs(hi)) + 1e-12
+    bad = (v < lo - slack) | (v > hi + slack)
+    assert not bad.any(), f"{what}: {bad.sum()} of {v.size} outside their enclosures"
+
+
+def _chain_tc(batch):
+    """Longest FP32 addition chain of a batch sum in the tensor-core training kernel: the tiles of
+    one block accumulate in tensor memory, then the blocks' sums are added in block order."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    tiles = -(-batch // 128)
+    nblk = min(n_sm, tiles)
+    return -(-tiles // nblk) * 128 + nblk + 1
+
+
+def _chain_mma(batch):
+    """The warp-level kernel: 128 points a block, the blocks' sums added by atomics."""
+    return 128 + -(-batch // 128) + 1
+
+
 def test_field_query_matches_oracle(env):
     G, torch, ctx = env
     theta = synth.field_init(11)
@@ -38,10 +74,11 @@ def test_field_query_matches_oracle(env):
     x = _points(5000, 2)
     out = np.empty(len(x), np.float32)
     G.gm_field_query(f, x, len(x), out)
-    feats = F.features(F.normalise(x.astype(np.float64), BOX_LO, BOX_HI))
+    feats = F.features(_xt(x))
     ref, _ = F.forward(theta.astype(np.float64), feats, emulate_bf16=True)
+    lo, hi, _ = F.forward_bounds(theta.astype(np.float64), _xt(x))
+    _inside(out, lo, hi, what="tcgen05 queries")
     err = np.abs(out - ref)
-    assert err.max() <= 1e-2 * np.abs(ref).max()
     assert np.median(err / np.maximum(np.abs(ref), 1e-6)) < 2e-3
     # the same through gm_query_density
     out2 = np.empty(len(x), np.float32)
@@ -52,8 +89,7 @@ def test_field_query_matches_oracle(env):
     G.gm_field_query_kernel(f, G.GM_FIELD_QUERY_MMA_SYNC)
     out3 = np.empty(len(x), np.float32)
     G.gm_field_query(f, x, len(x), out3)
-    err3 = np.abs(out3 - ref)
-    assert err3.max() <= 1e-2 * np.abs(ref).max()
+    _inside(out3, lo, hi, what="mma.sync queries")
     assert np.median(np.abs(out3 - out) / np.maximum(np.abs(ref), 1e-6)) < 1e-3
     G.gm_field_query_kernel(f, G.GM_FIELD_QUERY_TCGEN05)
     G.gm_sync(ctx)
@@ -79,11 +115,10 @@ def test_field_query_tiles_tails_and_alignment(env, n, offset):
     G.gm_field_query(f, dx, n, out_ms)
     G.gm_sync(ctx)
     a, b = out_tc.cpu().numpy(), out_ms.cpu().numpy()
-    feats = F.features(F.normalise(x.astype(np.float64), BOX_LO, BOX_HI))
-    ref, _ = F.forward(theta.astype(np.float64), feats, emulate_bf16=True)
+    lo, hi, _ = F.forward_bounds(theta.astype(np.float64), _xt(x))
     assert np.all(np.isfinite(a))
-    assert np.abs(a - ref).max() <= 1e-2 * max(np.abs(ref).max(), 1e-3)
-    assert np.abs(a - b).max() <= 1e-2 * max(np.abs(ref).max(), 1e-3)
+    _inside(a, lo, hi, what="tcgen05 queries")
+    _inside(b, lo, hi, what="mma.sync queries")
     G.gm_field_free(f)
 
 
@@ -100,16 +135,26 @@ def test_field_gradient_and_adam_step_match_oracle(env, kernel):
     dx, dy, di = (torch.from_numpy(a).cuda() for a in (x, y, idx.view(np.int32)))
     g = np.empty(G.GM_FIELD_N_PARAMS, np.float32)
     loss = G.gm_field_loss_grad(f, dx, dy, n, di, len(idx), g)
-    feats = F.features(F.normalise(x[idx].astype(np.float64), BOX_LO, BOX_HI))
+    feats = F.features(_xt(x[idx]))
     l_ref, g_ref = F.loss_and_grad(theta.astype(np.float64), feats, y[idx].astype(np.float64), emulate_bf16=True)
-    assert abs(loss - l_ref) <= 2e-3 * l_ref
+    chain = _chain_tc(len(idx)) if kernel == "TCGEN05" else _chain_mma(len(idx))
+    (llo, lhi), glo, ghi = F.loss_and_grad_bounds(theta.astype(np.float64), _xt(x[idx]), y[idx].astype(np.float64),
+                                                  chain)
+    _inside([loss], [llo], [lhi], rel=1e-5, what="loss")
+    _inside(g, glo, ghi, rel=1e-5, what="gradient")
     assert F.relative_l2(g, g_ref) < 2e-2
-    # one Adam step: the first update is lr * g / (|g| + eps), i.e. +-lr wherever |g| is not tiny
+    # one Adam step from zero moments: theta - lr g / (|g| + eps) (bias-corrected), increasing in g,
+    # so the enclosure of g gives the enclosure of the step; plus the FP32 update's own rounding
     lr = 1e-3
     G.gm_field_step(f, dx, dy, n, di, len(idx), lr)
     after = np.empty(G.GM_FIELD_N_PARAMS, np.float32)
     G.gm_field_params(f, after)
-    th_ref, _, _ = F.adam_step(theta.astype(np.float64), 0.0, 0.0, g_ref, 1, lr)
+    t64 = theta.astype(np.float64)
+    step = lambda gg: gg / (np.abs(gg) + 1e-8)
+    a_lo, a_hi = t64 - lr * step(ghi), t64 - lr * step(glo)
+    rnd = 4 * 2.0 ** -24 * (np.abs(t64) + lr)
+    assert np.all((after >= a_lo - rnd) & (after <= a_hi + rnd))
+    th_ref, _, _ = F.adam_step(t64, 0.0, 0.0, g_ref, 1, lr)
     sure = np.abs(g_ref) > 1e-3 * np.abs(g_ref).max()
     assert sure.sum() > 1000
     assert np.allclose(after[sure], th_ref[sure], rtol=0, atol=1e-6)
@@ -135,9 +180,14 @@ def test_field_tensor_core_gradient_over_many_tiles(env):
     G.gm_field_train_kernel(f, G.GM_FIELD_QUERY_MMA_SYNC)
     l3 = G.gm_field_loss_grad(f, dx, dy, n, di, batch, g3)
     G.gm_field_free(f)
-    feats = F.features(F.normalise(x[idx].astype(np.float64), BOX_LO, BOX_HI))
+    feats = F.features(_xt(x[idx]))
     l_ref, g_ref = F.loss_and_grad(theta.astype(np.float64), feats, y[idx].astype(np.float64), emulate_bf16=True)
     assert np.array_equal(g1, g2) and l1 == l2
+    for g, l, chain, what in ((g1, l1, _chain_tc(batch), "tcgen05"), (g3, l3, _chain_mma(batch), "mma.sync")):
+        (llo, lhi), glo, ghi = F.loss_and_grad_bounds(theta.astype(np.float64), _xt(x[idx]),
+                                                      y[idx].astype(np.float64), chain)
+        _inside([l], [llo], [lhi], rel=1e-5, what=what + " loss")
+        _inside(g, glo, ghi, rel=1e-5, what=what + " gradient")
     assert abs(l1 - l_ref) <= 2e-3 * l_ref and abs(l3 - l_ref) <= 2e-3 * l_ref
     assert F.relative_l2(g1, g_ref) < 2e-2
     assert F.relative_l2(g1, g3) < 2e-2
@@ -158,8 +208,12 @@ def test_field_tensor_core_gradient_small_batches(env, batch):
     g = np.empty(G.GM_FIELD_N_PARAMS, np.float32)
     loss = G.gm_field_loss_grad(f, dx, dy, n, di, batch, g)
     G.gm_field_free(f)
-    feats = F.features(F.normalise(x[idx].astype(np.float64), BOX_LO, BOX_HI))
+    feats = F.features(_xt(x[idx]))
     l_ref, g_ref = F.loss_and_grad(theta.astype(np.float64), feats, y[idx].astype(np.float64), emulate_bf16=True)
+    (llo, lhi), glo, ghi = F.loss_and_grad_bounds(theta.astype(np.float64), _xt(x[idx]), y[idx].astype(np.float64),
+                                                  _chain_tc(batch))
+    _inside([loss], [llo], [lhi], rel=1e-5, what="loss")
+    _inside(g, glo, ghi, rel=1e-5, what="gradient")
     assert abs(loss - l_ref) <= 2e-3 * l_ref
     assert F.relative_l2(g, g_ref) < 2e-2
 
@@ -257,8 +311,8 @@ def test_bounded_wait_runs_out_and_the_context_stays_usable(env):
     G.gm_field_query(f, x, len(x), out)
     G.gm_sync(ctx)
     G.gm_field_free(f)
-    feats = F.features(F.normalise(x.astype(np.float64), BOX_LO, BOX_HI))
-    ref, _ = F.forward(synth.field_init(11).astype(np.float64), feats, emulate_bf16=True)
-    assert np.all(np.isfinite(out)) and np.abs(out - ref).max() <= 1e-2 * np.abs(ref).max() + 1e-6
+    lo, hi, _ = F.forward_bounds(synth.field_init(11).astype(np.float64), _xt(x))
+    assert np.all(np.isfinite(out))
+    _inside(out, lo, hi, what="queries after the timeout")
     with pytest.raises(G.GazeMapError):
         G.gm_debug_wait_timeout(ctx, 0)

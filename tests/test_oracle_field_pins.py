@@ -97,3 +97,85 @@ def test_bf16_emulated_forward_stays_close_to_exact():
     a, _ = F.forward(theta, feats, emulate_bf16=True)
     b, _ = F.forward(theta, feats, emulate_bf16=False)
     assert F.relative_l2(a, b) < 2e-2
+
+
+# ---- enclosures of admissible implementations (element-wise bars of the GPU field tests) ----
+def _emulate_fp32(theta, xt, rng, feat_eps):
+    """One admissible implementation: features perturbed within feat_eps (FP32), every layer's
+    products (exact in FP32) added to the bias in a random order in FP32, the output layer's FP32
+    products added in a random order, softplus in FP32."""
+    Ws, bs, w5, b5 = F.unpack(theta)
+    f = F.features(xt)
+    noise = rng.uniform(-feat_eps, feat_eps, f.shape)
+    noise[:, :3] = 0.0
+    noise[:, 63] = 0.0
+    h = F.bf16((f + noise).astype(np.float32))
+    for W, b in zip(Ws, bs):
+        Wq = F.bf16(W)
+        prod = (h[:, None, :] * Wq[None, :, :]).astype(np.float32)        # exact: bf16 x bf16
+        acc = np.broadcast_to(np.float32(b), (len(h), F.WIDTH)).astype(np.float32).copy()
+        for j in rng.permutation(F.WIDTH):
+            acc = (acc + prod[:, :, j]).astype(np.float32)
+        h = F.bf16(np.maximum(acc, np.float32(0)))
+    p5 = (h.astype(np.float32) * np.float32(w5)).astype(np.float32)
+    acc = np.full(len(h), np.float32(b5), np.float32)
+    for j in rng.permutation(F.WIDTH):
+        acc = (acc + p5[:, j]).astype(np.float32)
+    z = acc.astype(np.float32)
+    return np.where(z > 30, z, np.log1p(np.exp(np.minimum(z, 30)).astype(np.float32))).astype(np.float64)
+
+
+def test_forward_bounds_enclose_admissible_implementations():
+    theta = synth.field_init(12).astype(np.float64)
+    lo_box, hi_box = np.array([-2.0, -1.0, -1.5], np.float32), np.array([2.0, 1.5, 1.0], np.float32)
+    x = np.random.default_rng(2).uniform(lo_box, hi_box, size=(600, 3)).astype(np.float32)
+    xt = F.normalise32(x, lo_box, hi_box)
+    lo, hi, _ = F.forward_bounds(theta, xt)
+    exact, _ = F.forward(theta, F.features(xt))
+    assert np.all((lo <= exact) & (exact <= hi))
+    rng = np.random.default_rng(7)
+    for _ in range(4):
+        e = _emulate_fp32(theta, xt, rng, F.FEAT_EPS)
+        slack = 2e-6 * np.abs(e) + 1e-12          # the FP32 softplus itself
+        assert np.all((e >= lo - slack) & (e <= hi + slack))
+    # each term is needed: with exact features, FP32 sums in random orders leave the bounds that
+    # omit the accumulation term, and stay inside the ones that keep it
+    lo_a, hi_a, _ = F.forward_bounds(theta, xt, feat_eps=0.0)
+    lo_0, hi_0, _ = F.forward_bounds(theta, xt, feat_eps=0.0, acc_u=0.0)
+    outside = 0
+    for _ in range(4):
+        e = _emulate_fp32(theta, xt, rng, 0.0)
+        slack = 2e-6 * np.abs(e) + 1e-12
+        assert np.all((e >= lo_a - slack) & (e <= hi_a + slack))
+        outside += int(((e < lo_0 - slack) | (e > hi_0 + slack)).sum())
+    assert outside > 0
+    # and feature errors alone move outputs beyond the bounds that omit them
+    lo_f, hi_f, _ = F.forward_bounds(theta, xt, feat_eps=0.0, acc_u=0.0)
+    e_f = [F.forward(theta, np.where(np.arange(64) < 3, F.features(xt), F.features(xt) + d))[0]
+           for d in (3e-5, -3e-5)]
+    assert any(((v < lo_f - 1e-12) | (v > hi_f + 1e-12)).any() for v in e_f)
+
+
+def test_normalise32_is_the_fp32_definition():
+    lo_box, hi_box = np.array([-2.0, -1.0, -1.5], np.float32), np.array([2.0, 1.5, 1.0], np.float32)
+    x = np.random.default_rng(3).uniform(lo_box, hi_box, size=(1000, 3)).astype(np.float32)
+    a = F.normalise32(x, lo_box, hi_box)
+    b = F.normalise(x, lo_box, hi_box)
+    # the FP32 evaluation is within a few FP32 roundings of the exact value, and inside [-1, 1]
+    assert np.abs(a - b).max() <= 4 * 2.0 ** -24 * 2 and np.abs(a).max() <= 1.0 + 1e-6
+    assert np.array_equal(a, a.astype(np.float32).astype(np.float64))
+
+
+def test_grad_bounds_enclose_the_exact_sums():
+    theta = synth.field_init(12).astype(np.float64)
+    lo_box, hi_box = np.array([-2.0, -1.0, -1.5], np.float32), np.array([2.0, 1.5, 1.0], np.float32)
+    x = np.random.default_rng(2).uniform(lo_box, hi_box, size=(256, 3)).astype(np.float32)
+    xt = F.normalise32(x, lo_box, hi_box)
+    y = np.random.default_rng(4).uniform(0, 1, 256)
+    l, g = F.loss_and_grad(theta, F.features(xt), y)
+    (llo, lhi), glo, ghi = F.loss_and_grad_bounds(theta, xt, y, chain=256 + 2)
+    assert llo <= l <= lhi
+    assert np.all((glo <= g) & (g <= ghi))
+    # and they are not vacuous: most weight gradients are pinned to within their own size
+    w = (ghi - glo) / np.maximum(np.abs(g), 1e-30)
+    assert np.median(w) < 10
