@@ -169,19 +169,26 @@ __device__ bool occluded(const Ray& R, uint32_t own, const float4* __restrict__ 
         const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
         float tl = slab(R, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
         float tr = slab(R, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
+        // leaf children reached by the segment are tested at once, left first, from one call
+        // site (one copy of the triangle test in the loop keeps the loop's code small)
+        int l0 = -1, l1 = -1;
         if (tl < INFINITY && cl < 0) {
-            if (leaf_hit(R, tris, ~cl, own, n_tri)) {
-                hit_slot = ~cl;
-                return true;
-            }
+            l0 = ~cl;
             tl = INFINITY;
         }
         if (tr < INFINITY && cr < 0) {
-            if (leaf_hit(R, tris, ~cr, own, n_tri)) {
-                hit_slot = ~cr;
+            if (l0 < 0) l0 = ~cr;
+            else l1 = ~cr;
+            tr = INFINITY;
+        }
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {
+            const int slot = q ? l1 : l0;
+            if (slot < 0) break;
+            if (leaf_hit(R, tris, slot, own, n_tri)) {
+                hit_slot = slot;
                 return true;
             }
-            tr = INFINITY;
         }
         if (tl < INFINITY && tr < INFINITY) {
             if (sp >= STACK) {
@@ -353,9 +360,10 @@ __device__ __forceinline__ void record_pair(unsigned long long* cursor, const De
 // One warp processes the S x 32 work-order samples of warp tile `tile` (see AccParams::group) against
 // fixations [P.f0, min(P.f1, nf)) of `fix` (packed (e, w), (r^, window), sorted by window). Sums are
 // written to out[window * P.ns + sidx[j]] when a window ends; each window's maximum is folded into
-// max_bits[window] with one atomicMax per warp. With P.carry_in the compensated sums start from
-// P.carry and the window of fixation f0 - 1 continues; with P.carry_out the open sums are saved to
-// P.carry at the end instead of being written (a later launch continues them). The warp's
+// max_bits[window] with one atomicMax per warp. Eye-grid kernels only: with P.carry_in the
+// compensated sums start from P.carry and the window of fixation f0 - 1 continues; with
+// P.carry_out the open sums are saved to P.carry at the end instead of being written (a later
+// launch continues them); the BVH kernels take the whole list [0, nf). The warp's
 // shared-memory regions (WARP_TILE entries each) are used only when COMPACT. Occlusion: the BVH
 // (binary or, WIDE, 4-wide) or, GRID, the eye grid of P (COMPACT only). No block-wide
 // synchronisation. *tested counts the sample x fixation cone tests actually evaluated.
@@ -369,12 +377,15 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                                           unsigned long long* __restrict__ dbg_cursor, const DebugOut& dbg,
                                           int* __restrict__ err, TileStats& st) {
     static_assert(!GRID || COMPACT, "the eye grid traces from the ray queue");
+    // fixation ranges and sums carried across launches exist for the eye grid's chunks only; the
+    // BVH kernels cover the whole list in one launch and keep none of that code
+    constexpr bool CH = GRID;
     const int lane = threadIdx.x & 31;
     const uint32_t G = P.group;
     const uint32_t stride = 32u * G;
     const uint32_t base0 = (tile / G) * (uint32_t)(32 * S) * G + (tile % G) * 32u;
     const uint32_t base = base0 + lane;
-    const uint32_t i_end = min(nf, P.f1);
+    const uint32_t i_end = CH ? min(nf, P.f1) : nf;
     float sx[S], sy[S], sz[S], sum[S], cmp[S];
     uint32_t own[S];
     float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -394,7 +405,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
             bhi[1] = fmaxf(bhi[1], p.y);
             bhi[2] = fmaxf(bhi[2], p.z);
         }
-        const float2 c0 = (P.carry_in && j < P.ns) ? P.carry[j] : make_float2(0.f, 0.f);
+        const float2 c0 = (CH && P.carry_in && j < P.ns) ? P.carry[j] : make_float2(0.f, 0.f);
         sum[k] = c0.x;
         cmp[k] = c0.y;
         if (COMPACT) {
@@ -429,7 +440,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
     __syncwarp();
     // the open window: none, or (continuing a previous launch) the window of fixation f0 - 1
     uint32_t cur = 0xffffffffu;
-    if (P.carry_in && P.f0 > 0) cur = __float_as_uint(__ldg(&fix[2 * (P.f0 - 1) + 1]).w);
+    if (CH && P.carry_in && P.f0 > 0) cur = __float_as_uint(__ldg(&fix[2 * (P.f0 - 1) + 1]).w);
 
     auto flush = [&](uint32_t w) {
         float m = 0.f;
@@ -451,7 +462,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
         if (lane == 0 && m > 0.f) atomicMax(&max_bits[w], __float_as_uint(m));
     };
 
-    const uint32_t i_beg = P.f0;
+    const uint32_t i_beg = CH ? P.f0 : 0u;
     float4 nF0 = i_beg < i_end ? __ldg(&fix[2 * i_beg]) : make_float4(0.f, 0.f, 0.f, 0.f);
     float4 nF1 = i_beg < i_end ? __ldg(&fix[2 * i_beg + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
     for (uint32_t i = i_beg; i < i_end; ++i) {
@@ -592,7 +603,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
             }
         }
     }
-    if (P.carry_out) {
+    if (CH && P.carry_out) {
         // the window goes on in the next launch: keep the open sums
         if (COMPACT) __syncwarp();
 #pragma unroll
