@@ -169,26 +169,19 @@ __device__ bool occluded(const Ray& R, uint32_t own, const float4* __restrict__ 
         const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
         float tl = slab(R, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
         float tr = slab(R, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
-        // leaf children reached by the segment are tested at once, left first, from one call
-        // site (one copy of the triangle test in the loop keeps the loop's code small)
-        int l0 = -1, l1 = -1;
         if (tl < INFINITY && cl < 0) {
-            l0 = ~cl;
+            if (leaf_hit(R, tris, ~cl, own, n_tri)) {
+                hit_slot = ~cl;
+                return true;
+            }
             tl = INFINITY;
         }
         if (tr < INFINITY && cr < 0) {
-            if (l0 < 0) l0 = ~cr;
-            else l1 = ~cr;
-            tr = INFINITY;
-        }
-#pragma unroll 1
-        for (int q = 0; q < 2; ++q) {
-            const int slot = q ? l1 : l0;
-            if (slot < 0) break;
-            if (leaf_hit(R, tris, slot, own, n_tri)) {
-                hit_slot = slot;
+            if (leaf_hit(R, tris, ~cr, own, n_tri)) {
+                hit_slot = ~cr;
                 return true;
             }
+            tr = INFINITY;
         }
         if (tl < INFINITY && tr < INFINITY) {
             if (sp >= STACK) {
