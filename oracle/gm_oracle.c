@@ -764,8 +764,17 @@ int ora_zb_frustum(const float* eye, const float* gaze, const float* cam_fwd, co
  * is the smallest w = t n over triangles that the ray e + t (x right + y up + n fwd) meets with
  * n <= w <= f (+inf when none). amb[p] is set when a triangle whose edge passes within delta_px
  * pixels of the centre (at its own depth) lies no deeper than the pixel's depth (plus 1e-6
- * relative), or a hit lies within 1e-5 relative of a clip plane (an FP32 clipper may move the
- * clip edge by that much). zbuf and amb: res * res. */
+ * relative), or a hit lies within zb_depth_band of a clip plane: a clipper that computes camera
+ * depths in FP32 may place the clip edge that far from the exact plane. zbuf and amb: res * res. */
+/* How far a camera depth w = (p - e).fwd evaluated in FP32 (from FP32 p and e, an FP32 copy of
+ * fwd: one subtraction and three multiply-adds per coordinate) can lie from the exact one: six
+ * units of 2^-24 of ||p - e||_1; doubled here to cover a clip point interpolated between two such
+ * depths. Absolute (metres), so it grows with the distance of the geometry, not of the plane. */
+static double zb_depth_band(const double q[3], const double e[3])
+{
+    return 12.0 * 5.9604644775390625e-8 * (fabs(q[0] - e[0]) + fabs(q[1] - e[1]) + fabs(q[2] - e[2]));
+}
+
 static void zb_pixel(const float* tri, int64_t nt, const ora_frustum* F, int32_t res, double delta_px, int32_t px,
                      int32_t py, double* depth, uint8_t* amb_out)
 {
@@ -790,7 +799,14 @@ static void zb_pixel(const float* tri, int64_t nt, const ora_frustum* F, int32_t
                 double tt, tp2;
                 ray_tri_t(F->e, d, tri + 9 * j, dw * (wp > 0.0 ? wp : 0.0), &tt, &nr2, &tp2);
                 if (hit) {
-                    if (fabs(w - F->n) <= 1e-5 * F->n || fabs(w - F->f) <= 1e-5 * F->f) clip_amb = 1;
+                    const float* T = tri + 9 * j;
+                    double band = 0.0;
+                    for (int k = 0; k < 3; ++k) {
+                        const double v[3] = {T[3 * k], T[3 * k + 1], T[3 * k + 2]};
+                        const double bk = zb_depth_band(v, F->e);
+                        if (bk > band) band = bk;
+                    }
+                    if (fabs(w - F->n) <= band || fabs(w - F->f) <= band) clip_amb = 1;
                     if (w >= F->n && w <= F->f && w < best) best = w;
                 }
                 if (nr2 && wp >= F->n * (1.0 - 1e-9) && wp <= F->f * (1.0 + 1e-9) && wp < near_best) near_best = wp;
@@ -868,7 +884,10 @@ static void zb_decide(const ora_frustum* F, const double sp[3], const ora_zb_par
     double v[3] = {sp[0] - F->e[0], sp[1] - F->e[1], sp[2] - F->e[2]};
     double x = v3_dot(v, F->right), y = v3_dot(v, F->up), w = v3_dot(v, F->fwd);
     int vis = 0, amb_vis = 0;
-    if (fabs(w - F->n) <= 1e-6 * F->n || fabs(w - F->f) <= 1e-6 * F->f) amb_vis = 1;
+    {
+        const double band = zb_depth_band(sp, F->e);   /* the sample's own FP32 camera depth */
+        if (fabs(w - F->n) <= band || fabs(w - F->f) <= band) amb_vis = 1;
+    }
     if (w >= F->n && w <= F->f) {
         double u = (F->n * x / w - F->l) / (F->r - F->l) * res;
         double q = (F->n * y / w - F->b) / (F->t - F->b) * res;

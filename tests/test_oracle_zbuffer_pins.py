@@ -212,3 +212,29 @@ def test_sampled_pair_form_agrees_with_the_full_form():
     assert np.array_equal(vis, (flags & oracle.PF_VISIBLE) > 0)
     assert np.array_equal(amb, (flags & oracle.PF_VIS_AMBIG) > 0)
     assert vis.sum() > 100 and (~vis).sum() > 100
+
+
+def test_fp32_camera_depth_error_bound():
+    """The clip-plane ambiguity band of the oracle's z-buffer bookkeeping is twice a bound on the
+    error of a camera depth w = (p - e).fwd evaluated in FP32 from FP32 inputs (subtraction, then a
+    chain of multiply-adds with an FP32 copy of the unit axis): six units of 2^-24 of ||p - e||_1.
+    Checked against FP32 evaluations of random points up to 200 m from random eyes."""
+    rng = np.random.default_rng(12)
+    n = 200_000
+    e = rng.uniform(-100, 100, (n, 3)).astype(np.float32)
+    p = (e.astype(np.float64) + rng.normal(0, 60, (n, 3))).astype(np.float32)
+    f64 = rng.normal(size=(n, 3))
+    f64 /= np.linalg.norm(f64, axis=1, keepdims=True)
+    f32 = f64.astype(np.float32)
+
+    def fma32(a, b, c):   # a*b is exact in FP64 for FP32 a, b; one rounding of the sum to FP32
+        return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(np.float32)
+
+    d = (p - e).astype(np.float32)
+    w32 = fma32(d[:, 0], f32[:, 0], fma32(d[:, 1], f32[:, 1], (d[:, 2] * f32[:, 2]).astype(np.float32)))
+    dx = p.astype(np.float64) - e.astype(np.float64)
+    w64 = (dx * f64).sum(1)
+    bound = 6 * 2.0 ** -24 * np.abs(dx).sum(1)
+    err = np.abs(w32.astype(np.float64) - w64)
+    assert np.all(err <= bound)
+    assert err.max() > 0.1 * bound.max() / 6    # the bound is not vacuous: errors of a unit occur
