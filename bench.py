@@ -312,6 +312,7 @@ def batched_arm(args):
     clk = clocks.stop()
     launches = G.gm_ctx_launches(ctx) - l0
     info = G.gm_batch_info(b)
+    buckets = G.gm_batch_buckets(b)
     ms = sum(batch_t) / len(batch_t)
     pms = sum(plain_t) / len(plain_t)
     line = {"metric": METRIC, "value": pairs / (ms * 1e-3), "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
@@ -322,7 +323,11 @@ def batched_arm(args):
                        "l2": "flushed between steps (256 MiB write)", "inputs": "device-resident"},
             "plain_form": {"value": pairs / (pms * 1e-3), "ms_per_step": pms,
                            "form": "one gm_accumulate_fixations per session"},
-            "batched_over_plain": pms / ms, "gpu_launches": int(launches), "clocks": clk}
+            "batched_over_plain": pms / ms,
+            "size_buckets": [{"triangles": rng, "sessions": x["sessions"], "work_items": x["work_items"],
+                              "variant_flags": x["flags"], "launch_ms": x["ms"]}
+                             for rng, x in zip(("< 2^14", "2^14 .. 2^17", ">= 2^17"), buckets)],
+            "gpu_launches": int(launches), "clocks": clk}
     G.gm_batch_free(b)
     for sc, sm, *_ in hs:
         G.gm_samples_free(sm)

@@ -391,9 +391,17 @@ gm_status gm_batch_map(gm_batch* batch, uint32_t session, gm_map** map);
 /* Plan facts; *last_ms is the device time of the last completed run (0 if none). */
 gm_status gm_batch_info(gm_batch* batch, uint32_t* n_sessions, uint64_t* n_work_items, uint64_t* pairs,
                         float* last_ms, int32_t* variant_flags);
-/* Time every accumulation variant on the plan, keep the fastest (re-capturing the graph) and
- * return its flags and time. Cached per size bucket; see gm_autotune_accumulate. */
+/* The plan groups its sessions into three size buckets (fewer than 2^14, fewer than 2^17, more
+ * triangles); each bucket's work items run in their own persistent launch of the graph, with
+ * their own variant. gm_batch_autotune times every accumulation variant on every bucket's own
+ * launch (events recorded in the graph), keeps each bucket's fastest (re-capturing the graph) and
+ * returns the flags of the bucket with the most work and the time of a replay with the chosen
+ * variants. Cached per bucket and size; see gm_autotune_accumulate. */
 gm_status gm_batch_autotune(gm_batch* batch, gm_stream stream, int32_t* best_flags, float* best_ms);
+/* Per bucket (3): its variant flags, sessions, work items and the device time of its launch in
+ * the last completed replay (0 if none). Any output may be NULL. */
+gm_status gm_batch_buckets(gm_batch* batch, uint32_t* n_buckets, int32_t* flags, uint32_t* sessions,
+                           uint32_t* work_items, float* last_ms);
 void gm_batch_free(gm_batch* batch);
 /* One-shot form: plan, run once, hand every session's map to the caller (free each with
  * gm_map_free). */

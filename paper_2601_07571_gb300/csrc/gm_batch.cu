@@ -3,17 +3,19 @@
 //
 // A session is (scene, samples, fixations); all sessions share the generation parameters. At
 // plan creation every session's fixations are staged into one device buffer and a work list
-// of warp tiles (session, 32*SPT consecutive work-order samples) is built on the host, ordered
-// by decreasing cost (fixations per tile, i.e. longest processing time first). The plan then
-// captures into one CUDA graph: the counter resets, the batched fixation prep (window keys per
-// session, one stable radix sort, packing), the persistent accumulation kernel whose warps pull
-// work items from a global counter until the list is exhausted, and the batched normalisation.
-// gm_batch_run replays the graph: no host work and one launch per call.
+// of warp tiles (session, 32*SPT consecutive work-order samples) is built on the host: sessions
+// grouped into three size buckets by triangle count, within a bucket ordered by decreasing cost
+// (fixations per tile, i.e. longest processing time first). The plan then captures into one
+// CUDA graph: the counter resets, the batched fixation prep (window keys per session, one stable
+// radix sort, packing), one persistent accumulation launch per bucket (its warps pull the
+// bucket's work items from the bucket's counter; each bucket has its own kernel variant and
+// events around its launch), and the batched normalisation. gm_batch_run replays the graph: no
+// host work and one graph launch per call.
 //
 // Autotuning: the candidates are the accumulation variants (per-warp ray queue on/off, binary
-// or 4-wide tree, 80- or 64-register cap). Each is timed on the real data and the fastest is
-// kept; results are cached per size bucket (log2 of samples, fixations, triangles) in memory
-// and in the JSON file named by GM_TUNE_CACHE, if set.
+// or 4-wide tree, 80- or 64-register cap). Each is timed on every bucket's own launch and each
+// bucket keeps its fastest; results are cached per bucket and size (log2 of samples, fixations,
+// triangles) in memory and in the JSON file named by GM_TUNE_CACHE, if set.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -93,6 +95,9 @@ struct AccConst {
 
 // Warp tiles of the batch use the spread layout (four 32-sample runs over 1024 samples).
 constexpr uint32_t BATCH_GROUP = 8;
+constexpr int BATCH_BUCKETS = 3;   // sessions of < 2^14, < 2^17 and more triangles
+
+int bucket_of_tris(uint32_t nt) { return nt < (1u << 14) ? 0 : nt < (1u << 17) ? 1 : 2; }
 
 // Persistent: every warp pulls work items (session, warp tile) from `work` until none is left.
 template <bool COMPACT, bool WIDE, int MINB>
@@ -259,6 +264,12 @@ struct gm_batch {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int launches_per_run = 0;
+    // size buckets (by triangles): each a contiguous run of the work list, its own counter, its
+    // own kernel variant and its own persistent launch, timed by events recorded in the graph
+    uint32_t bucket_begin[BATCH_BUCKETS + 1] = {};
+    uint32_t bucket_sessions[BATCH_BUCKETS] = {};
+    int bflags[BATCH_BUCKETS] = {};
+    cudaEvent_t bev[BATCH_BUCKETS][2] = {};
 };
 
 static void batch_release_graph(gm_batch* b) {
@@ -271,10 +282,11 @@ static void batch_release_graph(gm_batch* b) {
 // Capture the whole batched call into a graph for the variant in b->flags.
 static gm_status batch_capture(gm_batch* b) {
     batch_release_graph(b);
-    // the session table points at the tree the variant traverses
+    // the session table points at the tree its bucket's variant traverses
     for (uint32_t i = 0; i < b->n; ++i) {
         const gm_scene* sc = b->scenes[i];
-        b->host_sess[i].nodes = (b->flags & GM_F_WIDE_BVH) && sc->nodes4 ? sc->nodes4 : sc->nodes;
+        const int f = b->bflags[bucket_of_tris(sc->n_tris)];
+        b->host_sess[i].nodes = (f & GM_F_WIDE_BVH) && sc->nodes4 ? sc->nodes4 : sc->nodes;
     }
     GM_TRY_CUDA(cudaMemcpy(b->sess, b->host_sess.data(), sizeof(SessionDev) * b->n, cudaMemcpyHostToDevice));
     cudaStream_t cs;
@@ -284,7 +296,7 @@ static gm_status batch_capture(gm_batch* b) {
     const double tan_t = std::tan((double)b->prm.theta_rad);
     gm_status st = GM_OK;
     if (e == cudaSuccess) {
-        cudaMemsetAsync(b->work, 0, sizeof(unsigned int), cs);
+        cudaMemsetAsync(b->work, 0, sizeof(unsigned int) * BATCH_BUCKETS, cs);
         cudaMemsetAsync(b->n_valid, 0, sizeof(uint32_t) * b->n, cs);
         for (uint32_t i = 0; i < b->n; ++i) {
             gm_map* m = b->maps[i];
@@ -312,10 +324,17 @@ static gm_status batch_capture(gm_batch* b) {
             C.C2 = (float)(1.4426950408889634 / (2.0 * tan_t * tan_t));
             C.K = (float)((double)b->prm.cutoff_sigmas * tan_t * (double)b->prm.cutoff_sigmas * tan_t);
             C.tmax = 1.0f - b->prm.eps_rel;
-            const int code = code_of_flags(b->flags);
-            const int grid = b->ctx->n_sm * batch_occupancy(code);
-            launch_batch(code, grid, cs, b->sess, b->items, b->n_items, b->work, C, b->ctx->dev_err);
-            ++launches;
+            for (int k = 0; k < BATCH_BUCKETS; ++k) {
+                const uint32_t i0 = b->bucket_begin[k], i1 = b->bucket_begin[k + 1];
+                if (i1 <= i0) continue;
+                const int code = code_of_flags(b->bflags[k]);
+                const int grid = (int)std::min<uint64_t>((uint64_t)b->ctx->n_sm * batch_occupancy(code),
+                                                         gm_div_up(i1 - i0, ACC_THREADS / 32));
+                cudaEventRecord(b->bev[k][0], cs);
+                launch_batch(code, grid, cs, b->sess, b->items + i0, i1 - i0, b->work + k, C, b->ctx->dev_err);
+                cudaEventRecord(b->bev[k][1], cs);
+                ++launches;
+            }
         }
         if (b->prm.normalize) {
             dim3 g(std::max(1, b->ctx->n_sm * 8 / (int)std::max<uint32_t>(1, b->n)), b->n);
@@ -335,6 +354,10 @@ static gm_status batch_capture(gm_batch* b) {
 }
 
 extern "C" void gm_batch_free(gm_batch* b) {
+    if (b)
+        for (int k = 0; k < BATCH_BUCKETS; ++k)
+            for (int q = 0; q < 2; ++q)
+                if (b->bev[k][q]) cudaEventDestroy(b->bev[k][q]);
     if (!b) return;
     batch_release_graph(b);
     for (gm_map* m : b->maps) gm_map_free(m);
@@ -389,6 +412,7 @@ extern "C" gm_status gm_batch_create(gm_ctx* ctx, const gm_session_desc* ss, uin
     b->prm = *prm;
     b->W = (uint32_t)W;
     b->flags = prm->flags & VARIANT_MASK;
+    for (int k = 0; k < BATCH_BUCKETS; ++k) b->bflags[k] = b->flags;
     auto fail = [&](gm_status st) {
         cudaStreamSynchronize(s);
         gm_batch_free(b);
@@ -426,7 +450,7 @@ extern "C" gm_status gm_batch_create(gm_ctx* ctx, const gm_session_desc* ss, uin
         (st = gm_alloc((void**)&b->hist, sizeof(uint32_t) * gm_radix_sort_u32_hist_words(nf ? nf : 1), s)) != GM_OK ||
         (st = gm_alloc((void**)&b->packed, sizeof(float4) * 2 * nfa, s)) != GM_OK ||
         (st = gm_alloc((void**)&b->n_valid, sizeof(uint32_t) * n, s)) != GM_OK ||
-        (st = gm_alloc((void**)&b->work, sizeof(unsigned int), s)) != GM_OK ||
+        (st = gm_alloc((void**)&b->work, sizeof(unsigned int) * BATCH_BUCKETS, s)) != GM_OK ||
         (st = gm_alloc((void**)&b->sess, sizeof(SessionDev) * n, s)) != GM_OK)
         return fail(st);
     // stage fixations (host or device sources) into the concatenated buffers
@@ -469,14 +493,20 @@ extern "C" gm_status gm_batch_create(gm_ctx* ctx, const gm_session_desc* ss, uin
     }
     e = cudaMemcpyAsync(b->sess, b->host_sess.data(), sizeof(SessionDev) * n, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_batch_create: session table"));
-    // work list: longest processing time first
+    // work list: by size bucket, within a bucket longest processing time first
     std::vector<uint32_t> order(n);
     std::iota(order.begin(), order.end(), 0u);
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) { return ss[a].fix.n > ss[c].fix.n; });
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) {
+        const int ba = bucket_of_tris(ss[a].scene->n_tris), bc = bucket_of_tris(ss[c].scene->n_tris);
+        return ba != bc ? ba < bc : ss[a].fix.n > ss[c].fix.n;
+    });
     std::vector<uint2> items;
     for (uint32_t i : order) {
+        const int k = bucket_of_tris(ss[i].scene->n_tris);
+        ++b->bucket_sessions[k];
         const uint32_t tiles = gm_div_up(ss[i].samples->n, (uint64_t)WARP_TILE * BATCH_GROUP) * BATCH_GROUP;
         for (uint32_t t = 0; t < tiles; ++t) items.push_back(make_uint2(i, t));
+        for (int q = k + 1; q <= BATCH_BUCKETS; ++q) b->bucket_begin[q] = (uint32_t)items.size();
     }
     b->n_items = (uint32_t)items.size();
     if ((st = gm_alloc((void**)&b->items, sizeof(uint2) * (items.empty() ? 1 : items.size()), s)) != GM_OK) return fail(st);
@@ -486,6 +516,10 @@ extern "C" gm_status gm_batch_create(gm_ctx* ctx, const gm_session_desc* ss, uin
     }
     if ((e = cudaEventCreate(&b->ev0)) != cudaSuccess || (e = cudaEventCreate(&b->ev1)) != cudaSuccess)
         return fail(gm_cuda_error(e, "gm_batch_create: events"));
+    for (int k = 0; k < BATCH_BUCKETS; ++k)
+        for (int q = 0; q < 2; ++q)
+            if ((e = cudaEventCreate(&b->bev[k][q])) != cudaSuccess)
+                return fail(gm_cuda_error(e, "gm_batch_create: events"));
     // everything above is stream-ordered on s; the graph replays on any stream after it
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(gm_cuda_error(e, "gm_batch_create"));
     if ((st = batch_capture(b)) != GM_OK) return fail(st);
@@ -511,7 +545,13 @@ extern "C" gm_status gm_batch_info(gm_batch* b, uint32_t* n_sessions, uint64_t* 
     if (n_sessions) *n_sessions = b->n;
     if (n_items) *n_items = b->n_items;
     if (pairs) *pairs = b->pairs;
-    if (variant_flags) *variant_flags = b->flags;
+    if (variant_flags) {
+        // the variant of the bucket with the most work items
+        int kb = 0;
+        for (int k = 1; k < BATCH_BUCKETS; ++k)
+            if (b->bucket_begin[k + 1] - b->bucket_begin[k] > b->bucket_begin[kb + 1] - b->bucket_begin[kb]) kb = k;
+        *variant_flags = b->bflags[kb];
+    }
     if (last_ms) {
         *last_ms = 0.f;
         if (cudaEventQuery(b->ev1) != cudaErrorNotReady) {
@@ -556,46 +596,87 @@ extern "C" gm_status gm_accumulate_batch(gm_ctx* ctx, const gm_session_desc* ss,
 
 extern "C" gm_status gm_batch_autotune(gm_batch* b, gm_stream stream, int32_t* best_flags, float* best_ms) {
     if (!b) return gm_set_error(GM_ERR_INVALID_ARG, "gm_batch_autotune: null batch");
-    uint64_t ns_tot = 0, nt_tot = 0;
-    for (auto& d : b->host_sess) {
-        ns_tot += d.ns;
-        nt_tot += d.nt;
+    // per bucket: its totals for the cache key, then every variant timed on its own launch (events
+    // recorded in the graph around each bucket's launch), the fastest kept
+    uint64_t ns_k[BATCH_BUCKETS] = {}, nf_k[BATCH_BUCKETS] = {}, nt_k[BATCH_BUCKETS] = {};
+    for (uint32_t i = 0; i < b->n; ++i) {
+        const int k = bucket_of_tris(b->host_sess[i].nt);
+        ns_k[k] += b->host_sess[i].ns;
+        nf_k[k] += b->fix_off[i + 1] - b->fix_off[i];
+        nt_k[k] += b->host_sess[i].nt;
     }
-    const std::string key = bucket_key("batch", ns_tot, b->nf_total, nt_tot);
-    int best = -1;
-    float best_t = 0.f;
+    int best[BATCH_BUCKETS];
+    float best_t[BATCH_BUCKETS];
+    bool todo = false;
+    std::string keys[BATCH_BUCKETS];
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         tune_load_locked();
-        auto it = g_tune.find(key);
-        if (it != g_tune.end()) best = it->second;
+        for (int k = 0; k < BATCH_BUCKETS; ++k) {
+            keys[k] = bucket_key(("batch" + std::to_string(k)).c_str(), ns_k[k], nf_k[k], nt_k[k]);
+            auto it = g_tune.find(keys[k]);
+            best[k] = it != g_tune.end() ? it->second : -1;
+            best_t[k] = 1e30f;
+            todo |= best[k] < 0 && b->bucket_begin[k + 1] > b->bucket_begin[k];
+        }
     }
-    if (best < 0) {
+    if (todo) {
         for (int code = 0; code < 8; ++code) {
-            b->flags = flags_of_code(code);
+            for (int k = 0; k < BATCH_BUCKETS; ++k) b->bflags[k] = flags_of_code(code);
             GM_TRY(batch_capture(b));
-            float t = 1e30f;
+            float t[BATCH_BUCKETS] = {1e30f, 1e30f, 1e30f};
             for (int rep = 0; rep < 2; ++rep) {
                 GM_TRY(gm_batch_run(b, stream));
-                float ms = 0.f;
                 GM_TRY_CUDA(cudaEventSynchronize(b->ev1));
-                GM_TRY_CUDA(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
-                t = std::min(t, ms);
+                for (int k = 0; k < BATCH_BUCKETS; ++k) {
+                    if (b->bucket_begin[k + 1] <= b->bucket_begin[k]) continue;
+                    float ms = 0.f;
+                    GM_TRY_CUDA(cudaEventElapsedTime(&ms, b->bev[k][0], b->bev[k][1]));
+                    t[k] = std::min(t[k], ms);
+                }
             }
-            if (best < 0 || t < best_t) {
-                best = b->flags;
-                best_t = t;
-            }
+            for (int k = 0; k < BATCH_BUCKETS; ++k)
+                if (t[k] < best_t[k]) {
+                    best_t[k] = t[k];
+                    best[k] = flags_of_code(code);
+                }
         }
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tune[key] = best;
+        for (int k = 0; k < BATCH_BUCKETS; ++k)
+            if (b->bucket_begin[k + 1] > b->bucket_begin[k]) g_tune[keys[k]] = best[k];
         tune_store_locked();
     }
-    b->flags = best;
+    for (int k = 0; k < BATCH_BUCKETS; ++k) b->bflags[k] = best[k] >= 0 ? best[k] : b->flags;
     GM_TRY(batch_capture(b));
-    (void)best_t;
-    if (best_flags) *best_flags = best;
-    if (best_ms) *best_ms = best_t;
+    // the whole replay with the chosen variants
+    float total = 0.f;
+    GM_TRY(gm_batch_run(b, stream));
+    GM_TRY_CUDA(cudaEventSynchronize(b->ev1));
+    GM_TRY_CUDA(cudaEventElapsedTime(&total, b->ev0, b->ev1));
+    if (best_flags) GM_TRY(gm_batch_info(b, nullptr, nullptr, nullptr, nullptr, best_flags));
+    if (best_ms) *best_ms = total;
+    return GM_OK;
+}
+
+extern "C" gm_status gm_batch_buckets(gm_batch* b, uint32_t* n_buckets, int32_t* flags, uint32_t* sessions,
+                                      uint32_t* work_items, float* last_ms) {
+    if (!b) return gm_set_error(GM_ERR_INVALID_ARG, "gm_batch_buckets: null batch");
+    if (n_buckets) *n_buckets = BATCH_BUCKETS;
+    bool done = last_ms && cudaEventQuery(b->ev1) != cudaErrorNotReady;
+    if (done) GM_TRY_CUDA(cudaEventSynchronize(b->ev1));
+    for (int k = 0; k < BATCH_BUCKETS; ++k) {
+        if (flags) flags[k] = b->bflags[k];
+        if (sessions) sessions[k] = b->bucket_sessions[k];
+        if (work_items) work_items[k] = b->bucket_begin[k + 1] - b->bucket_begin[k];
+        if (last_ms) {
+            last_ms[k] = 0.f;
+            if (done && b->bucket_begin[k + 1] > b->bucket_begin[k] &&
+                cudaEventElapsedTime(&last_ms[k], b->bev[k][0], b->bev[k][1]) != cudaSuccess) {
+                cudaGetLastError();
+                last_ms[k] = 0.f;
+            }
+        }
+    }
     return GM_OK;
 }
 

@@ -130,6 +130,7 @@ _SIGS = {
                                 C.POINTER(C.c_float), C.POINTER(C.c_int32)]),
     "gm_batch_autotune": (C.c_int, [_P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
     "gm_batch_free": (None, [_P]),
+    "gm_batch_buckets": (C.c_int, [_P, C.POINTER(C.c_uint32), _P, _P, _P, _P]),
     "gm_accumulate_batch": (C.c_int, [_P, C.POINTER(gm_session_desc), C.c_uint32, C.POINTER(gm_params), _P,
                                       C.POINTER(_P)]),
     "gm_autotune_accumulate": (C.c_int, [_P, _P, C.POINTER(gm_fixations), C.POINTER(gm_params), _P,
@@ -595,3 +596,14 @@ def gm_map_max(m, out, stream=None) -> None:
 
 def gm_map_normalize(m, maxima=None, stream=None) -> None:
     _check(lib().gm_map_normalize(m, _ptr(maxima), _stream(stream)))
+
+
+def gm_batch_buckets(b):
+    """Per size bucket: variant flags, sessions, work items and the last replay's launch time (ms)."""
+    n = C.c_uint32()
+    fl = np.zeros(3, np.int32)
+    se = np.zeros(3, np.uint32)
+    it = np.zeros(3, np.uint32)
+    ms = np.zeros(3, np.float32)
+    _check(lib().gm_batch_buckets(b, C.byref(n), _ptr(fl), _ptr(se), _ptr(it), _ptr(ms)))
+    return [dict(flags=int(fl[k]), sessions=int(se[k]), work_items=int(it[k]), ms=float(ms[k])) for k in range(n.value)]

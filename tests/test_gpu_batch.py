@@ -148,6 +148,15 @@ def test_autotune_picks_a_variant_and_keeps_results(env, tmp_path, monkeypatch):
     assert flags & ~(G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64) == 0 and ms > 0
     assert G.gm_batch_info(b)["variant_flags"] == flags
     G.gm_batch_run(b)
+    G.gm_sync(ctx)
+    bk = G.gm_batch_buckets(b)
+    # sessions of 2k-20k triangles fall in the two smaller buckets; each bucket's launch is timed
+    assert sum(x["sessions"] for x in bk) == len(ws)
+    assert sum(x["work_items"] for x in bk) == G.gm_batch_info(b)["n_work_items"]
+    assert sum(1 for x in bk if x["sessions"]) >= 2
+    for x in bk:
+        assert x["flags"] & ~(G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64) == 0
+        assert (x["ms"] > 0) == (x["work_items"] > 0)
     for i in range(len(ws)):
         a = np.empty_like(before[i])
         G.gm_map_copy(G.gm_batch_map(b, i), 0, a)
