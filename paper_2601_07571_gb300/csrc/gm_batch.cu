@@ -330,9 +330,11 @@ static gm_status batch_capture(gm_batch* b) {
                 const int code = code_of_flags(b->bflags[k]);
                 const int grid = (int)std::min<uint64_t>((uint64_t)b->ctx->n_sm * batch_occupancy(code),
                                                          gm_div_up(i1 - i0, ACC_THREADS / 32));
-                cudaEventRecord(b->bev[k][0], cs);
+                // external event records: the graph records them when it runs (a plain record in a
+                // capture only orders the work)
+                cudaEventRecordWithFlags(b->bev[k][0], cs, cudaEventRecordExternal);
                 launch_batch(code, grid, cs, b->sess, b->items + i0, i1 - i0, b->work + k, C, b->ctx->dev_err);
-                cudaEventRecord(b->bev[k][1], cs);
+                cudaEventRecordWithFlags(b->bev[k][1], cs, cudaEventRecordExternal);
                 ++launches;
             }
         }
@@ -631,7 +633,11 @@ extern "C" gm_status gm_batch_autotune(gm_batch* b, gm_stream stream, int32_t* b
                 for (int k = 0; k < BATCH_BUCKETS; ++k) {
                     if (b->bucket_begin[k + 1] <= b->bucket_begin[k]) continue;
                     float ms = 0.f;
-                    GM_TRY_CUDA(cudaEventElapsedTime(&ms, b->bev[k][0], b->bev[k][1]));
+                    const cudaError_t e = cudaEventElapsedTime(&ms, b->bev[k][0], b->bev[k][1]);
+                    if (e != cudaSuccess) {
+                        cudaGetLastError();   // leave no error behind for the next launch check
+                        return gm_cuda_error(e, "gm_batch_autotune: bucket timing");
+                    }
                     t[k] = std::min(t[k], ms);
                 }
             }
