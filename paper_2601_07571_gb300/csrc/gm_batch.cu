@@ -7,9 +7,10 @@
 // grouped into three size buckets by triangle count, within a bucket ordered by decreasing cost
 // (fixations per tile, i.e. longest processing time first). The plan then captures into one
 // CUDA graph: the counter resets, the batched fixation prep (window keys per session, one stable
-// radix sort, packing), one persistent accumulation launch per bucket (its warps pull the
-// bucket's work items from the bucket's counter; each bucket has its own kernel variant and
-// events around its launch), and the batched normalisation. gm_batch_run replays the graph: no
+// radix sort, packing), one persistent accumulation launch per bucket on forked streams (its
+// warps pull the bucket's work items from the bucket's counter; each bucket has its own kernel
+// variant and events around its launch; a bucket's tail overlaps the next one's start), and the
+// batched normalisation. gm_batch_run replays the graph: no
 // host work and one graph launch per call.
 //
 // Autotuning: the candidates are the accumulation variants (per-warp ray queue on/off, binary
@@ -270,6 +271,8 @@ struct gm_batch {
     uint32_t bucket_sessions[BATCH_BUCKETS] = {};
     int bflags[BATCH_BUCKETS] = {};
     cudaEvent_t bev[BATCH_BUCKETS][2] = {};
+    cudaStream_t bs[BATCH_BUCKETS] = {};       // capture-time fork streams of the bucket launches
+    cudaEvent_t fork = nullptr, join[BATCH_BUCKETS] = {};
 };
 
 static void batch_release_graph(gm_batch* b) {
@@ -279,8 +282,10 @@ static void batch_release_graph(gm_batch* b) {
     b->graph = nullptr;
 }
 
-// Capture the whole batched call into a graph for the variant in b->flags.
-static gm_status batch_capture(gm_batch* b) {
+// Capture the whole batched call into a graph with the variants in b->bflags. concurrent: the
+// buckets' launches run on forked streams (one bucket's tail overlaps the next one's start);
+// else one after another (the autotuner times each bucket alone).
+static gm_status batch_capture(gm_batch* b, bool concurrent = true) {
     batch_release_graph(b);
     // the session table points at the tree its bucket's variant traverses
     for (uint32_t i = 0; i < b->n; ++i) {
@@ -324,18 +329,28 @@ static gm_status batch_capture(gm_batch* b) {
             C.C2 = (float)(1.4426950408889634 / (2.0 * tan_t * tan_t));
             C.K = (float)((double)b->prm.cutoff_sigmas * tan_t * (double)b->prm.cutoff_sigmas * tan_t);
             C.tmax = 1.0f - b->prm.eps_rel;
+            if (concurrent) {
+                cudaEventRecord(b->fork, cs);   // (inside the capture: an ordering edge only)
+                for (int k = 0; k < BATCH_BUCKETS; ++k) cudaStreamWaitEvent(b->bs[k], b->fork, 0);
+            }
             for (int k = 0; k < BATCH_BUCKETS; ++k) {
                 const uint32_t i0 = b->bucket_begin[k], i1 = b->bucket_begin[k + 1];
-                if (i1 <= i0) continue;
-                const int code = code_of_flags(b->bflags[k]);
-                const int grid = (int)std::min<uint64_t>((uint64_t)b->ctx->n_sm * batch_occupancy(code),
-                                                         gm_div_up(i1 - i0, ACC_THREADS / 32));
-                // external event records: the graph records them when it runs (a plain record in a
-                // capture only orders the work)
-                cudaEventRecordWithFlags(b->bev[k][0], cs, cudaEventRecordExternal);
-                launch_batch(code, grid, cs, b->sess, b->items + i0, i1 - i0, b->work + k, C, b->ctx->dev_err);
-                cudaEventRecordWithFlags(b->bev[k][1], cs, cudaEventRecordExternal);
-                ++launches;
+                cudaStream_t ks = concurrent ? b->bs[k] : cs;
+                if (i1 > i0) {
+                    const int code = code_of_flags(b->bflags[k]);
+                    const int grid = (int)std::min<uint64_t>((uint64_t)b->ctx->n_sm * batch_occupancy(code),
+                                                             gm_div_up(i1 - i0, ACC_THREADS / 32));
+                    // external event records: the graph records them when it runs (a plain record in
+                    // a capture only orders the work)
+                    cudaEventRecordWithFlags(b->bev[k][0], ks, cudaEventRecordExternal);
+                    launch_batch(code, grid, ks, b->sess, b->items + i0, i1 - i0, b->work + k, C, b->ctx->dev_err);
+                    cudaEventRecordWithFlags(b->bev[k][1], ks, cudaEventRecordExternal);
+                    ++launches;
+                }
+                if (concurrent) {
+                    cudaEventRecord(b->join[k], ks);
+                    cudaStreamWaitEvent(cs, b->join[k], 0);
+                }
             }
         }
         if (b->prm.normalize) {
@@ -356,10 +371,15 @@ static gm_status batch_capture(gm_batch* b) {
 }
 
 extern "C" void gm_batch_free(gm_batch* b) {
-    if (b)
-        for (int k = 0; k < BATCH_BUCKETS; ++k)
+    if (b) {
+        for (int k = 0; k < BATCH_BUCKETS; ++k) {
             for (int q = 0; q < 2; ++q)
                 if (b->bev[k][q]) cudaEventDestroy(b->bev[k][q]);
+            if (b->join[k]) cudaEventDestroy(b->join[k]);
+            if (b->bs[k]) cudaStreamDestroy(b->bs[k]);
+        }
+        if (b->fork) cudaEventDestroy(b->fork);
+    }
     if (!b) return;
     batch_release_graph(b);
     for (gm_map* m : b->maps) gm_map_free(m);
@@ -518,10 +538,16 @@ extern "C" gm_status gm_batch_create(gm_ctx* ctx, const gm_session_desc* ss, uin
     }
     if ((e = cudaEventCreate(&b->ev0)) != cudaSuccess || (e = cudaEventCreate(&b->ev1)) != cudaSuccess)
         return fail(gm_cuda_error(e, "gm_batch_create: events"));
-    for (int k = 0; k < BATCH_BUCKETS; ++k)
+    for (int k = 0; k < BATCH_BUCKETS; ++k) {
         for (int q = 0; q < 2; ++q)
             if ((e = cudaEventCreate(&b->bev[k][q])) != cudaSuccess)
                 return fail(gm_cuda_error(e, "gm_batch_create: events"));
+        if ((e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&b->bs[k], cudaStreamNonBlocking)) != cudaSuccess)
+            return fail(gm_cuda_error(e, "gm_batch_create: streams"));
+    }
+    if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess)
+        return fail(gm_cuda_error(e, "gm_batch_create: events"));
     // everything above is stream-ordered on s; the graph replays on any stream after it
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(gm_cuda_error(e, "gm_batch_create"));
     if ((st = batch_capture(b)) != GM_OK) return fail(st);
@@ -625,7 +651,7 @@ extern "C" gm_status gm_batch_autotune(gm_batch* b, gm_stream stream, int32_t* b
     if (todo) {
         for (int code = 0; code < 8; ++code) {
             for (int k = 0; k < BATCH_BUCKETS; ++k) b->bflags[k] = flags_of_code(code);
-            GM_TRY(batch_capture(b));
+            GM_TRY(batch_capture(b, false));   // buckets one after another: each timed alone
             float t[BATCH_BUCKETS] = {1e30f, 1e30f, 1e30f};
             for (int rep = 0; rep < 2; ++rep) {
                 GM_TRY(gm_batch_run(b, stream));

@@ -150,10 +150,13 @@ def test_autotune_picks_a_variant_and_keeps_results(env, tmp_path, monkeypatch):
     G.gm_batch_run(b)
     G.gm_sync(ctx)
     bk = G.gm_batch_buckets(b)
-    # sessions of 2k-20k triangles fall in the two smaller buckets; each bucket's launch is timed
-    assert sum(x["sessions"] for x in bk) == len(ws)
+    # every session in the bucket of its triangle count (< 2^14, < 2^17, more); each bucket's
+    # launch is timed
+    nts = [G.gm_scene_info(h[0])[0] for h in hs]
+    want = [sum(1 for nt in nts if (nt < 2 ** 14 if k == 0 else 2 ** 14 <= nt < 2 ** 17 if k == 1 else nt >= 2 ** 17))
+            for k in range(3)]
+    assert [x["sessions"] for x in bk] == want
     assert sum(x["work_items"] for x in bk) == G.gm_batch_info(b)["n_work_items"]
-    assert sum(1 for x in bk if x["sessions"]) >= 2
     for x in bk:
         assert x["flags"] & ~(G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64) == 0
         assert (x["ms"] > 0) == (x["work_items"] > 0)
