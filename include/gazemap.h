@@ -101,7 +101,9 @@ enum {
     GM_F_GRID64 = 2048,     /* with GM_F_EYE_GRID: 64 x 64 cells per fixation instead of 128 x 128 */
     GM_F_SPT1 = 4096,       /* eye grid: warp tiles of 32 samples (1 per thread) instead of 128 (4 per thread) */
     GM_F_SPT2 = 8192,       /* eye grid: warp tiles of 64 samples (2 per thread) */
-    GM_F_BLOCK512 = 16384   /* eye grid: blocks of 512 threads (with 1 or 2 samples per thread) */
+    GM_F_BLOCK512 = 16384,  /* eye grid: blocks of 512 threads (with 1 or 2 samples per thread) */
+    GM_F_FIX_SMEM = 32768   /* default BVH kernel: each warp stages its fixations 32 at a time in shared
+                               memory (coalesced loads) instead of reading them one by one through L1 */
 };
 
 typedef struct {

@@ -89,7 +89,8 @@ __global__ void k_fix_pack(const uint32_t* __restrict__ keys, const uint32_t* __
 // rays (densely gazed patches) spread over the whole run instead of forming a tail. MINB is the
 // minimum number of resident blocks per SM the register allocation must allow (3: up to 80
 // registers, 4: up to 64).
-template <bool DEBUG, bool COMPACT, bool WIDE, int MINB, int NT = ACC_THREADS, bool GRID = false, int S = SPT>
+template <bool DEBUG, bool COMPACT, bool WIDE, int MINB, int NT = ACC_THREADS, bool GRID = false, int S = SPT,
+          bool FSM = false>
 __global__ void __launch_bounds__(NT, MINB) k_accumulate(
     const float4* __restrict__ spos, const uint32_t* __restrict__ sidx, const float4* __restrict__ fix,
     const uint32_t* __restrict__ n_fix_dev, const float4* __restrict__ nodes, const float4* __restrict__ tris,
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(NT, MINB) k_accumulate(
     __shared__ float4 wbox[NT / 32];   // per warp: its tile's bounding sphere
     __shared__ uint16_t qslot[QN];  // per warp: queue of in-cone sample slots
     __shared__ float qg[QN];        // per warp: their weights
+    __shared__ float4 wfix[FSM ? (NT / 32) * 64 : 1];   // per warp: 32 staged fixations
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int wb = COMPACT ? warp * 32 * S : 0;
@@ -117,19 +119,19 @@ __global__ void __launch_bounds__(NT, MINB) k_accumulate(
             tile = blockIdx.x * (NT / 32) + warp;
         }
         if (tile >= n_tiles) break;
-        warp_tile<DEBUG, COMPACT, WIDE, GRID, S>(tile, spos, sidx, fix, nf, nodes, tris, P, out, max_bits, wsmp + wb,
-                                                 wacc + wb, qslot + wb, qg + wb, wbox + warp, &counters[2], dbg, err,
-                                                 st);
+        warp_tile<DEBUG, COMPACT, WIDE, GRID, S, FSM>(tile, spos, sidx, fix, nf, nodes, tris, P, out, max_bits,
+                                                      wsmp + wb, wacc + wb, qslot + wb, qg + wb, wbox + warp,
+                                                      &counters[2], dbg, err, st, FSM ? wfix + warp * 64 : nullptr);
     }
     warp_stats_commit(st, counters);
 }
 
 // (The driver's default shared-memory carveout is kept: preferring the largest L1 leaves room for
 // fewer blocks per SM and measured 316 vs 253 ms at the paper scene.)
-template <bool D, bool Cm, bool Wd, int Mb, int NT = ACC_THREADS, bool Gr = false, int S = SPT>
+template <bool D, bool Cm, bool Wd, int Mb, int NT = ACC_THREADS, bool Gr = false, int S = SPT, bool Fs = false>
 int acc_occupancy() {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_accumulate<D, Cm, Wd, Mb, NT, Gr, S>, NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_accumulate<D, Cm, Wd, Mb, NT, Gr, S, Fs>, NT, 0);
     return b > 0 ? b : 1;
 }
 
@@ -373,17 +375,20 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
         const float4* tree = wide ? sc->nodes4 : sc->nodes;
         const int code = (compact ? 1 : 0) | (wide ? 2 : 0) | (occ4 ? 4 : 0);
         // persistent grid: every resident block slot once, never more blocks than tiles need
-#define GM_LAUNCH_ACC_S(D, Cm, Wd, Mb, NT, Gr, S_)                                                                \
+#define GM_LAUNCH_ACC_F(D, Cm, Wd, Mb, NT, Gr, S_, Fs)                                                           \
     do {                                                                                                          \
         const uint32_t nt_s = gm_div_up(ns, (uint64_t)32 * (S_) * P.group) * P.group;                             \
         const uint32_t all = gm_div_up(nt_s, NT / 32);                                                            \
-        const uint32_t grd =                                                                                      \
-            persistent ? std::min<uint32_t>((uint32_t)ctx->n_sm * acc_occupancy<D, Cm, Wd, Mb, NT, Gr, S_>(), all) \
-                       : all;                                                                                     \
-        k_accumulate<D, Cm, Wd, Mb, NT, Gr, S_><<<grd, NT, 0, s>>>(spos, sidx, packed, n_valid, tree, sc->bvh_tris, \
-                                                                   P, nt_s, persistent, mp->values, mp->max_bits, \
-                                                                   mp->counters, ctx->dev_err, dbg);              \
+        const uint32_t grd = persistent ? std::min<uint32_t>(                                                     \
+                                              (uint32_t)ctx->n_sm * acc_occupancy<D, Cm, Wd, Mb, NT, Gr, S_, Fs>(), \
+                                              all)                                                                \
+                                        : all;                                                                    \
+        k_accumulate<D, Cm, Wd, Mb, NT, Gr, S_, Fs><<<grd, NT, 0, s>>>(spos, sidx, packed, n_valid, tree,          \
+                                                                       sc->bvh_tris, P, nt_s, persistent,         \
+                                                                       mp->values, mp->max_bits, mp->counters,    \
+                                                                       ctx->dev_err, dbg);                        \
     } while (0)
+#define GM_LAUNCH_ACC_S(D, Cm, Wd, Mb, NT, Gr, S_) GM_LAUNCH_ACC_F(D, Cm, Wd, Mb, NT, Gr, S_, false)
 #define GM_LAUNCH_ACC_NT(D, Cm, Wd, Mb, NT, Gr) GM_LAUNCH_ACC_S(D, Cm, Wd, Mb, NT, Gr, SPT)
 #define GM_LAUNCH_ACC(D, Cm, Wd, Mb) GM_LAUNCH_ACC_NT(D, Cm, Wd, Mb, ACC_THREADS, false)
         if (grid) {
@@ -481,7 +486,10 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
                 else if (b128 && code == 5) GM_LAUNCH_ACC_NT(false, true, false, 8, 128, false);
                 else switch (code) {
                     case 0: GM_LAUNCH_ACC(false, false, false, 3); break;
-                    case 1: GM_LAUNCH_ACC(false, true, false, 3); break;
+                    case 1:
+                        if (prm->flags & GM_F_FIX_SMEM) GM_LAUNCH_ACC_F(false, true, false, 3, 256, false, SPT, true);
+                        else GM_LAUNCH_ACC(false, true, false, 3);
+                        break;
                     case 2: GM_LAUNCH_ACC(false, false, true, 3); break;
                     case 3: GM_LAUNCH_ACC(false, true, true, 3); break;
                     case 4: GM_LAUNCH_ACC(false, false, false, 4); break;
@@ -495,6 +503,7 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
 #undef GM_LAUNCH_ACC
 #undef GM_LAUNCH_ACC_NT
 #undef GM_LAUNCH_ACC_S
+#undef GM_LAUNCH_ACC_F
     }
     if (timing) cudaEventRecord(mp->ev[2], s);
     if (prm->normalize && !into) launches += launch_normalize(mp, ctx->n_sm, s) > 0 ? 1 : 0;

@@ -359,8 +359,10 @@ __device__ __forceinline__ void record_pair(unsigned long long* cursor, const De
 // launch continues them); the BVH kernels take the whole list [0, nf). The warp's
 // shared-memory regions (WARP_TILE entries each) are used only when COMPACT. Occlusion: the BVH
 // (binary or, WIDE, 4-wide) or, GRID, the eye grid of P (COMPACT only). No block-wide
-// synchronisation. *tested counts the sample x fixation cone tests actually evaluated.
-template <bool DEBUG, bool COMPACT, bool WIDE, bool GRID = false, int S = SPT>
+// synchronisation. *tested counts the sample x fixation cone tests actually evaluated. FSM: the
+// fixations are staged 32 at a time in the warp's slot wfix (64 float4) instead of being read
+// one by one through L1.
+template <bool DEBUG, bool COMPACT, bool WIDE, bool GRID = false, int S = SPT, bool FSM = false>
 __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restrict__ spos,
                                           const uint32_t* __restrict__ sidx, const float4* __restrict__ fix,
                                           uint32_t nf, const float4* __restrict__ nodes,
@@ -368,7 +370,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                                           float* __restrict__ out, unsigned int* __restrict__ max_bits,
                                           float4* wsmp, float2* wacc, uint16_t* qslot, float* qg, float4* wbox,
                                           unsigned long long* __restrict__ dbg_cursor, const DebugOut& dbg,
-                                          int* __restrict__ err, TileStats& st) {
+                                          int* __restrict__ err, TileStats& st, float4* wfix = nullptr) {
     static_assert(!GRID || COMPACT, "the eye grid traces from the ray queue");
     // fixation ranges and sums carried across launches exist for the eye grid's chunks only; the
     // BVH kernels cover the whole list in one launch and keep none of that code
@@ -456,14 +458,10 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
     };
 
     const uint32_t i_beg = CH ? P.f0 : 0u;
-    float4 nF0 = i_beg < i_end ? __ldg(&fix[2 * i_beg]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 nF1 = i_beg < i_end ? __ldg(&fix[2 * i_beg + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (uint32_t i = i_beg; i < i_end; ++i) {
-        const float4 F0 = nF0, F1 = nF1;
-        if (i + 1 < i_end) {
-            nF0 = __ldg(&fix[2 * (i + 1)]);
-            nF1 = __ldg(&fix[2 * (i + 1) + 1]);
-        }
+    float4 nF0 = !FSM && i_beg < i_end ? __ldg(&fix[2 * i_beg]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 nF1 = !FSM && i_beg < i_end ? __ldg(&fix[2 * i_beg + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    // the work of one fixation (window change, tile sphere test, cone tests, ray queue)
+    auto per_fixation = [&](const uint32_t i, const float4 F0, const float4 F1) {
         const uint32_t win = __float_as_uint(F1.w);
         if (win != cur) {
             if (cur != 0xffffffffu) flush(cur);
@@ -483,7 +481,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
             const float margin = 1e-4f * (fabsf(qx) + fabsf(qy) + fabsf(qz) + bR);
             const float reach = d1c + bR;
             const float lim = bR + fmaf(P.tanphi, fmaxf(reach, 0.f), margin);
-            if (reach <= -margin || fmaf(ux, ux, fmaf(uy, uy, uz * uz)) > lim * lim) continue;
+            if (reach <= -margin || fmaf(ux, ux, fmaf(uy, uy, uz * uz)) > lim * lim) return;
         }
         st.n_tested += live;
         if (COMPACT) {
@@ -511,7 +509,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                 }
                 tot += __popc(m);
             }
-            if (tot == 0) continue;
+            if (tot == 0) return;
             __syncwarp();
             // the eye grid of this fixation (warp-uniform): its gaze frame and its cell offsets
             float4 gU = make_float4(0.f, 0.f, 0.f, 0.f), gV = gU;
@@ -594,6 +592,30 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                     }
                 }
             }
+        }
+        };
+    if (FSM) {
+        // fixations staged 32 at a time in the warp's shared-memory slot (one coalesced load per
+        // lane), then read from there
+        for (uint32_t c0 = i_beg; c0 < i_end; c0 += 32) {
+            const uint32_t m = min(32u, i_end - c0);
+            __syncwarp();
+            if ((uint32_t)lane < m) {
+                wfix[2 * lane] = __ldg(&fix[2 * (c0 + lane)]);
+                wfix[2 * lane + 1] = __ldg(&fix[2 * (c0 + lane) + 1]);
+            }
+            __syncwarp();
+            for (uint32_t k = 0; k < m; ++k) per_fixation(c0 + k, wfix[2 * k], wfix[2 * k + 1]);
+        }
+    } else {
+        // fixations read through L1 as warp-wide broadcasts, the next one in flight
+        for (uint32_t i = i_beg; i < i_end; ++i) {
+            const float4 F0 = nF0, F1 = nF1;
+            if (i + 1 < i_end) {
+                nF0 = __ldg(&fix[2 * (i + 1)]);
+                nF1 = __ldg(&fix[2 * (i + 1) + 1]);
+            }
+            per_fixation(i, F0, F1);
         }
     }
     if (CH && P.carry_out) {
