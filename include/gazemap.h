@@ -102,8 +102,8 @@ enum {
     GM_F_SPT1 = 4096,       /* eye grid: warp tiles of 32 samples (1 per thread) instead of 128 (4 per thread) */
     GM_F_SPT2 = 8192,       /* eye grid: warp tiles of 64 samples (2 per thread) */
     GM_F_BLOCK512 = 16384,  /* eye grid: blocks of 512 threads (with 1 or 2 samples per thread) */
-    GM_F_FIX_SMEM = 32768   /* default BVH kernel: each warp stages its fixations 32 at a time in shared
-                               memory (coalesced loads) instead of reading them one by one through L1 */
+    GM_F_FIX_L1 = 32768     /* default BVH kernel: read the fixations one by one through L1 (warp-wide
+                               broadcasts) instead of staging them 32 at a time in each warp's shared memory */
 };
 
 typedef struct {

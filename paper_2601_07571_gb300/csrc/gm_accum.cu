@@ -486,9 +486,9 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
                 else if (b128 && code == 5) GM_LAUNCH_ACC_NT(false, true, false, 8, 128, false);
                 else switch (code) {
                     case 0: GM_LAUNCH_ACC(false, false, false, 3); break;
-                    case 1:
-                        if (prm->flags & GM_F_FIX_SMEM) GM_LAUNCH_ACC_F(false, true, false, 3, 256, false, SPT, true);
-                        else GM_LAUNCH_ACC(false, true, false, 3);
+                    case 1:   // the default: fixations staged in shared memory (GM_F_FIX_L1: through L1)
+                        if (prm->flags & GM_F_FIX_L1) GM_LAUNCH_ACC(false, true, false, 3);
+                        else GM_LAUNCH_ACC_F(false, true, false, 3, 256, false, SPT, true);
                         break;
                     case 2: GM_LAUNCH_ACC(false, false, true, 3); break;
                     case 3: GM_LAUNCH_ACC(false, true, true, 3); break;

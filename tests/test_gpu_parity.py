@@ -345,7 +345,7 @@ def test_paper_scene_full_size_sampled(G, ctx, pipe):
 
 
 @pytest.mark.parametrize("other", ["in_place", "wide_tree", "tile_consecutive", "static_tiles", "no_tile_cull",
-                                   "block128", "block128_regcap64", "fix_smem"])
+                                   "block128", "block128_regcap64", "fix_l1"])
 def test_accumulate_variants_agree_bit_for_bit(G, ctx, pipe, other):
     """The per-warp ray queue only reorders which lane traces which ray, and the 4-wide tree
     only skips intermediate boxes (every box is conservative, so every hitting triangle is
@@ -354,7 +354,7 @@ def test_accumulate_variants_agree_bit_for_bit(G, ctx, pipe, other):
     flag = {"in_place": G.GM_F_NO_COMPACT, "wide_tree": G.GM_F_WIDE_BVH, "tile_consecutive": G.GM_F_TILE_CONSECUTIVE,
             "static_tiles": G.GM_F_STATIC_TILES, "no_tile_cull": G.GM_F_NO_TILE_CULL,
             "block128": G.GM_F_BLOCK128, "block128_regcap64": G.GM_F_BLOCK128 | G.GM_F_REGCAP64,
-            "fix_smem": G.GM_F_FIX_SMEM}[other]
+            "fix_l1": G.GM_F_FIX_L1}[other]
     s5 = synth.session(5)
     s5.fixations = s5.fixations.subset(slice(0, 150))
     cap = 4_000_000
