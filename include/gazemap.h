@@ -99,11 +99,16 @@ enum {
     GM_F_EYE_GRID = 1024,   /* occlusion through per-fixation eye grids instead of the BVH (ray-queue
                                kernel only: with NO_COMPACT, WIDE_BVH or REGCAP64 the BVH is kept) */
     GM_F_GRID64 = 2048,     /* with GM_F_EYE_GRID: 64 x 64 cells per fixation instead of 128 x 128 */
-    GM_F_SPT1 = 4096,       /* eye grid: warp tiles of 32 samples (1 per thread) instead of 128 (4 per thread) */
-    GM_F_SPT2 = 8192,       /* eye grid: warp tiles of 64 samples (2 per thread) */
-    GM_F_BLOCK512 = 16384,  /* eye grid: blocks of 512 threads (with 1 or 2 samples per thread) */
-    GM_F_FIX_L1 = 32768     /* default BVH kernel: read the fixations one by one through L1 (warp-wide
-                               broadcasts) instead of staging them 32 at a time in each warp's shared memory */
+    GM_F_SPT1 = 4096,       /* warp tiles of 32 samples (1 per thread); the default of the ray-queue
+                               binary-tree kernel (the eye grid's default is 4 per thread) */
+    GM_F_SPT2 = 8192,       /* warp tiles of 64 samples (2 per thread): ray-queue binary tree and eye grid */
+    GM_F_BLOCK512 = 16384,  /* blocks of 512 threads: eye grid (1 or 2 samples per thread) and the
+                               one-sample ray-queue binary-tree kernel */
+    GM_F_FIX_L1 = 32768,    /* ray-queue binary-tree kernel: read the fixations one by one through L1
+                               (warp-wide broadcasts) instead of staging them 32 at a time in each
+                               warp's shared memory */
+    GM_F_SPT4 = 65536       /* warp tiles of 128 samples (4 per thread): the ray-queue binary-tree kernel
+                               (the in-place and 4-wide kernels always take 4) */
 };
 
 typedef struct {

@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(NT, MINB) k_accumulate(
         }
         if (tile >= n_tiles) break;
         warp_tile<DEBUG, COMPACT, WIDE, GRID, S, FSM>(tile, spos, sidx, fix, nf, nodes, tris, P, out, max_bits,
-                                                      wsmp + wb, wacc + wb, qslot + wb, qg + wb, wbox + warp,
-                                                      &counters[2], dbg, err, st, FSM ? wfix + warp * 64 : nullptr);
+                                                          wsmp + wb, wacc + wb, qslot + wb, qg + wb, wbox + warp,
+                                                          &counters[2], dbg, err, st, FSM ? wfix + warp * 64 : nullptr);
     }
     warp_stats_commit(st, counters);
 }
@@ -454,7 +454,7 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
                 if (q > 0) GM_TRY_CUDA(cudaMemsetAsync(&mp->counters[6], 0, sizeof(unsigned long long), s));
                 // shape: samples per thread (GM_F_SPT1 / GM_F_SPT2, else 4) and block size
                 // (GM_F_BLOCK128 / GM_F_BLOCK512, else 256); 80 registers a thread in every shape
-                const int spt = (prm->flags & GM_F_SPT1) ? 1 : (prm->flags & GM_F_SPT2) ? 2 : 4;
+                const int spt = (prm->flags & GM_F_SPT1) ? 1 : (prm->flags & GM_F_SPT2) ? 2 : 4;   // default 4
                 const int nth = b128 ? 128 : (prm->flags & GM_F_BLOCK512) ? 512 : 256;
                 if (debug) GM_LAUNCH_ACC_S(true, true, false, 3, 256, true, 4);
                 else if (nth == 256 && spt == 4) GM_LAUNCH_ACC_S(false, true, false, 3, 256, true, 4);
@@ -482,18 +482,35 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
                     default: GM_LAUNCH_ACC(true, true, true, 3); break;
                 }
             } else {
-                if (b128 && code == 1) GM_LAUNCH_ACC_NT(false, true, false, 7, 128, false);
+                // the ray-queue binary-tree kernels: samples per thread 1 (the default), 2 or 4; the
+                // one-sample tiles fit 64 registers (4 blocks per SM) and stage their fixations in
+                // shared memory
+                const int qspt = (prm->flags & GM_F_SPT4) ? 4 : (prm->flags & GM_F_SPT2) ? 2 : 1;
+                const bool b512 = (prm->flags & GM_F_BLOCK512) != 0;
+                if ((code == 1 || code == 5) && qspt == 1) {
+                    if (b128) GM_LAUNCH_ACC_F(false, true, false, 8, 128, false, 1, true);
+                    else if (b512) GM_LAUNCH_ACC_F(false, true, false, 2, 512, false, 1, true);
+                    else if (prm->flags & GM_F_FIX_L1) GM_LAUNCH_ACC_F(false, true, false, 4, 256, false, 1, false);
+                    else GM_LAUNCH_ACC_F(false, true, false, 4, 256, false, 1, true);
+                } else if ((code == 1 || code == 5) && qspt == 2) {
+                    if (code == 5) GM_LAUNCH_ACC_F(false, true, false, 4, 256, false, 2, true);
+                    else GM_LAUNCH_ACC_F(false, true, false, 3, 256, false, 2, true);
+                } else if (b128 && code == 1) GM_LAUNCH_ACC_NT(false, true, false, 7, 128, false);
                 else if (b128 && code == 5) GM_LAUNCH_ACC_NT(false, true, false, 8, 128, false);
                 else switch (code) {
                     case 0: GM_LAUNCH_ACC(false, false, false, 3); break;
-                    case 1:   // the default: fixations staged in shared memory (GM_F_FIX_L1: through L1)
+                    case 1:   // 4 samples per thread: fixations staged in shared memory (GM_F_FIX_L1: through L1)
                         if (prm->flags & GM_F_FIX_L1) GM_LAUNCH_ACC(false, true, false, 3);
                         else GM_LAUNCH_ACC_F(false, true, false, 3, 256, false, SPT, true);
                         break;
                     case 2: GM_LAUNCH_ACC(false, false, true, 3); break;
                     case 3: GM_LAUNCH_ACC(false, true, true, 3); break;
                     case 4: GM_LAUNCH_ACC(false, false, false, 4); break;
-                    case 5: GM_LAUNCH_ACC(false, true, false, 4); break;
+                    case 5:
+                        if (prm->flags & GM_F_SPT1) GM_LAUNCH_ACC_F(false, true, false, 4, 256, false, 1, true);
+                        else if (prm->flags & GM_F_SPT2) GM_LAUNCH_ACC_F(false, true, false, 4, 256, false, 2, true);
+                        else GM_LAUNCH_ACC(false, true, false, 4);
+                        break;
                     case 6: GM_LAUNCH_ACC(false, false, true, 4); break;
                     default: GM_LAUNCH_ACC(false, true, true, 4); break;
                 }

@@ -100,20 +100,26 @@ constexpr int BATCH_BUCKETS = 3;   // sessions of < 2^14, < 2^17 and more triang
 
 int bucket_of_tris(uint32_t nt) { return nt < (1u << 14) ? 0 : nt < (1u << 17) ? 1 : 2; }
 
-// Persistent: every warp pulls work items (session, warp tile) from `work` until none is left.
-template <bool COMPACT, bool WIDE, int MINB>
+// Warp-tile sizes of the batched kernels, by tile index: 4, 2 or 1 samples per thread.
+constexpr int BATCH_TILES = 3;
+constexpr int BATCH_TILE_SPT[BATCH_TILES] = {4, 2, 1};
+
+// Persistent: every warp pulls work items (session, warp tile of 32 S samples per run) from `work`
+// until none is left. FSM: fixations staged in the warp's shared memory.
+template <bool COMPACT, bool WIDE, int MINB, int S = SPT, bool FSM = false>
 __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate_batch(const SessionDev* __restrict__ sess,
                                                                         const uint2* __restrict__ items,
                                                                         uint32_t n_items, unsigned int* __restrict__ work,
                                                                         AccConst C, int* __restrict__ err) {
-    constexpr int QN = COMPACT ? ACC_THREADS * SPT : 1;
+    constexpr int QN = COMPACT ? ACC_THREADS * S : 1;
     __shared__ float4 wsmp[QN];
     __shared__ float2 wacc[QN];
     __shared__ float4 wbox[ACC_THREADS / 32];
     __shared__ uint16_t qslot[QN];
     __shared__ float qg[QN];
+    __shared__ float4 wfix[FSM ? (ACC_THREADS / 32) * 64 : 1];
     const int lane = threadIdx.x & 31;
-    const int wb = COMPACT ? (threadIdx.x >> 5) * WARP_TILE : 0;
+    const int wb = COMPACT ? (threadIdx.x >> 5) * 32 * S : 0;
     const DebugOut dbg{nullptr, nullptr, nullptr, nullptr, nullptr};
     for (;;) {
         uint32_t it = 0;
@@ -121,22 +127,23 @@ __global__ void __launch_bounds__(ACC_THREADS, MINB) k_accumulate_batch(const Se
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
         const uint2 wi = items[it];
-        const SessionDev S = sess[wi.x];
+        const SessionDev Sd = sess[wi.x];
         AccParams P;
         P.C2 = C.C2;
         P.K = C.K;
         P.tmax = C.tmax;
-        P.ns = S.ns;
-        P.W = S.W;
-        P.nt = S.nt;
+        P.ns = Sd.ns;
+        P.W = Sd.W;
+        P.nt = Sd.nt;
         P.dbg_cap = 0;
         P.group = BATCH_GROUP;
         P.tanphi = sqrtf(C.K) * 1.00001f;
         TileStats st;
-        warp_tile<false, COMPACT, WIDE>(wi.y, S.spos, S.sidx, S.fix, *S.n_fix, S.nodes, S.tris, P, S.out, S.max_bits,
-                                        wsmp + wb, wacc + wb, qslot + wb, qg + wb, wbox + (threadIdx.x >> 5), nullptr,
-                                        dbg, err, st);
-        warp_stats_commit(st, S.counters);
+        warp_tile<false, COMPACT, WIDE, false, S, FSM>(wi.y, Sd.spos, Sd.sidx, Sd.fix, *Sd.n_fix, Sd.nodes, Sd.tris, P,
+                                                       Sd.out, Sd.max_bits, wsmp + wb, wacc + wb, qslot + wb, qg + wb,
+                                                       wbox + (threadIdx.x >> 5), nullptr, dbg, err, st,
+                                                       FSM ? wfix + (threadIdx.x >> 5) * 64 : nullptr);
+        warp_stats_commit(st, Sd.counters);
     }
 }
 
@@ -155,31 +162,42 @@ __global__ void k_bcount(const SessionDev* __restrict__ sess, uint32_t n) {
     if (i < n) sess[i].counters[3] = *sess[i].n_fix;
 }
 
-template <bool Cm, bool Wd, int Mb>
+template <bool Cm, bool Wd, int Mb, int S = SPT, bool Fs = false>
 int occupancy_of() {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_accumulate_batch<Cm, Wd, Mb>, ACC_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_accumulate_batch<Cm, Wd, Mb, S, Fs>, ACC_THREADS, 0);
     return std::max(b, 1);
 }
 
+// Variant codes: bits 0-2 the kernel (ray queue, 4-wide tree, 64-register cap), 8 x the tile index
+// (ray-queue binary tree only: 2 samples per thread with fixations staged in shared memory, or 1,
+// which also takes 64 registers).
 void launch_batch(int code, int grid, cudaStream_t s, const SessionDev* sess, const uint2* items, uint32_t n_items,
                   unsigned int* work, AccConst C, int* err) {
-#define GM_B(Cm, Wd, Mb) k_accumulate_batch<Cm, Wd, Mb><<<grid, ACC_THREADS, 0, s>>>(sess, items, n_items, work, C, err)
-    switch (code) {
-        case 0: GM_B(false, false, 3); break;
-        case 1: GM_B(true, false, 3); break;
-        case 2: GM_B(false, true, 3); break;
-        case 3: GM_B(true, true, 3); break;
-        case 4: GM_B(false, false, 4); break;
-        case 5: GM_B(true, false, 4); break;
-        case 6: GM_B(false, true, 4); break;
-        default: GM_B(true, true, 4); break;
+#define GM_B(Cm, Wd, Mb, S_, Fs) \
+    k_accumulate_batch<Cm, Wd, Mb, S_, Fs><<<grid, ACC_THREADS, 0, s>>>(sess, items, n_items, work, C, err)
+    const int t = code >> 3;
+    if (t == 2) GM_B(true, false, 4, 1, true);
+    else if (t == 1 && (code & 7) == 5) GM_B(true, false, 4, 2, true);
+    else if (t == 1) GM_B(true, false, 3, 2, true);
+    else switch (code & 7) {
+        case 0: GM_B(false, false, 3, SPT, false); break;
+        case 1: GM_B(true, false, 3, SPT, false); break;
+        case 2: GM_B(false, true, 3, SPT, false); break;
+        case 3: GM_B(true, true, 3, SPT, false); break;
+        case 4: GM_B(false, false, 4, SPT, false); break;
+        case 5: GM_B(true, false, 4, SPT, false); break;
+        case 6: GM_B(false, true, 4, SPT, false); break;
+        default: GM_B(true, true, 4, SPT, false); break;
     }
 #undef GM_B
 }
 
 int batch_occupancy(int code) {
-    switch (code) {
+    const int t = code >> 3;
+    if (t == 2) return occupancy_of<true, false, 4, 1, true>();
+    if (t == 1) return (code & 7) == 5 ? occupancy_of<true, false, 4, 2, true>() : occupancy_of<true, false, 3, 2, true>();
+    switch (code & 7) {
         case 0: return occupancy_of<false, false, 3>();
         case 1: return occupancy_of<true, false, 3>();
         case 2: return occupancy_of<false, true, 3>();
@@ -191,14 +209,24 @@ int batch_occupancy(int code) {
     }
 }
 
-// variant code <-> GM_F_* flags
+// variant code <-> GM_F_* flags (the ray-queue binary tree takes 1 sample per thread by default)
 int code_of_flags(int flags) {
-    return ((flags & GM_F_NO_COMPACT) ? 0 : 1) | ((flags & GM_F_WIDE_BVH) ? 2 : 0) | ((flags & GM_F_REGCAP64) ? 4 : 0);
+    const int base =
+        ((flags & GM_F_NO_COMPACT) ? 0 : 1) | ((flags & GM_F_WIDE_BVH) ? 2 : 0) | ((flags & GM_F_REGCAP64) ? 4 : 0);
+    if ((base & 3) != 1) return base;
+    if (flags & GM_F_SPT4) return base;
+    if (flags & GM_F_SPT2) return base + 8;
+    return 1 + 16;
 }
 int flags_of_code(int code) {
-    return ((code & 1) ? 0 : GM_F_NO_COMPACT) | ((code & 2) ? GM_F_WIDE_BVH : 0) | ((code & 4) ? GM_F_REGCAP64 : 0);
+    const int t = code >> 3, base = code & 7;
+    return ((base & 1) ? 0 : GM_F_NO_COMPACT) | ((base & 2) ? GM_F_WIDE_BVH : 0) | ((base & 4) ? GM_F_REGCAP64 : 0) |
+           ((base & 3) == 1 ? (t == 0 ? GM_F_SPT4 : t == 1 ? GM_F_SPT2 : 0) : 0);
 }
-constexpr int VARIANT_MASK = GM_F_NO_COMPACT | GM_F_WIDE_BVH | GM_F_REGCAP64;
+// the codes the batched autotuner times
+constexpr int BATCH_CODES[] = {0, 1, 2, 3, 4, 5, 6, 7, 9, 13, 17};
+int tile_of_code(int code) { return code >> 3; }
+constexpr int VARIANT_MASK = GM_F_NO_COMPACT | GM_F_WIDE_BVH | GM_F_REGCAP64 | GM_F_SPT1 | GM_F_SPT2 | GM_F_SPT4;
 
 // ---- tuning cache ------------------------------------------------------------------------------
 std::mutex g_tune_mutex;
@@ -252,8 +280,8 @@ struct gm_batch {
     std::vector<uint32_t> fix_off;
     std::vector<SessionDev> host_sess;
     SessionDev* sess = nullptr;
-    uint2* items = nullptr;
-    uint32_t n_items = 0;
+    uint2* items[BATCH_TILES] = {};   // the work list for each warp-tile size
+    uint32_t n_items[BATCH_TILES] = {};
     unsigned int* work = nullptr;
     uint32_t* n_valid = nullptr;
     float *eye = nullptr, *gaze = nullptr, *dur = nullptr;
@@ -267,13 +295,21 @@ struct gm_batch {
     int launches_per_run = 0;
     // size buckets (by triangles): each a contiguous run of the work list, its own counter, its
     // own kernel variant and its own persistent launch, timed by events recorded in the graph
-    uint32_t bucket_begin[BATCH_BUCKETS + 1] = {};
+    uint32_t bucket_begin[BATCH_TILES][BATCH_BUCKETS + 1] = {};
     uint32_t bucket_sessions[BATCH_BUCKETS] = {};
     int bflags[BATCH_BUCKETS] = {};
     cudaEvent_t bev[BATCH_BUCKETS][2] = {};
     cudaStream_t bs[BATCH_BUCKETS] = {};       // capture-time fork streams of the bucket launches
     cudaEvent_t fork = nullptr, join[BATCH_BUCKETS] = {};
 };
+
+// work items of bucket k in the work list of its variant's tile size
+static uint32_t bucket_items(const gm_batch* b, int k) {
+    const int tk = tile_of_code(code_of_flags(b->bflags[k]));
+    return b->bucket_begin[tk][k + 1] - b->bucket_begin[tk][k];
+}
+// whether bucket k holds any sample (the same for every tile size)
+static bool bucket_busy(const gm_batch* b, int k) { return b->bucket_begin[0][k + 1] > b->bucket_begin[0][k]; }
 
 static void batch_release_graph(gm_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -324,7 +360,7 @@ static gm_status batch_capture(gm_batch* b, bool concurrent = true) {
                                                                       b->nf_total, b->W, wnorm, b->packed);
             ++launches;
         }
-        if (b->n_items > 0) {
+        if (b->n_items[0] > 0) {
             AccConst C;
             C.C2 = (float)(1.4426950408889634 / (2.0 * tan_t * tan_t));
             C.K = (float)((double)b->prm.cutoff_sigmas * tan_t * (double)b->prm.cutoff_sigmas * tan_t);
@@ -334,16 +370,17 @@ static gm_status batch_capture(gm_batch* b, bool concurrent = true) {
                 for (int k = 0; k < BATCH_BUCKETS; ++k) cudaStreamWaitEvent(b->bs[k], b->fork, 0);
             }
             for (int k = 0; k < BATCH_BUCKETS; ++k) {
-                const uint32_t i0 = b->bucket_begin[k], i1 = b->bucket_begin[k + 1];
+                const int code = code_of_flags(b->bflags[k]);
+                const int tk = tile_of_code(code);
+                const uint32_t i0 = b->bucket_begin[tk][k], i1 = b->bucket_begin[tk][k + 1];
                 cudaStream_t ks = concurrent ? b->bs[k] : cs;
                 if (i1 > i0) {
-                    const int code = code_of_flags(b->bflags[k]);
                     const int grid = (int)std::min<uint64_t>((uint64_t)b->ctx->n_sm * batch_occupancy(code),
                                                              gm_div_up(i1 - i0, ACC_THREADS / 32));
                     // external event records: the graph records them when it runs (a plain record in
                     // a capture only orders the work)
                     cudaEventRecordWithFlags(b->bev[k][0], ks, cudaEventRecordExternal);
-                    launch_batch(code, grid, ks, b->sess, b->items + i0, i1 - i0, b->work + k, C, b->ctx->dev_err);
+                    launch_batch(code, grid, ks, b->sess, b->items[tk] + i0, i1 - i0, b->work + k, C, b->ctx->dev_err);
                     cudaEventRecordWithFlags(b->bev[k][1], ks, cudaEventRecordExternal);
                     ++launches;
                 }
@@ -384,7 +421,7 @@ extern "C" void gm_batch_free(gm_batch* b) {
     batch_release_graph(b);
     for (gm_map* m : b->maps) gm_map_free(m);
     cudaFree(b->sess);
-    cudaFree(b->items);
+    for (int t = 0; t < BATCH_TILES; ++t) cudaFree(b->items[t]);
     cudaFree(b->work);
     cudaFree(b->n_valid);
     cudaFree(b->eye);
@@ -522,19 +559,24 @@ extern "C" gm_status gm_batch_create(gm_ctx* ctx, const gm_session_desc* ss, uin
         const int ba = bucket_of_tris(ss[a].scene->n_tris), bc = bucket_of_tris(ss[c].scene->n_tris);
         return ba != bc ? ba < bc : ss[a].fix.n > ss[c].fix.n;
     });
-    std::vector<uint2> items;
-    for (uint32_t i : order) {
-        const int k = bucket_of_tris(ss[i].scene->n_tris);
-        ++b->bucket_sessions[k];
-        const uint32_t tiles = gm_div_up(ss[i].samples->n, (uint64_t)WARP_TILE * BATCH_GROUP) * BATCH_GROUP;
-        for (uint32_t t = 0; t < tiles; ++t) items.push_back(make_uint2(i, t));
-        for (int q = k + 1; q <= BATCH_BUCKETS; ++q) b->bucket_begin[q] = (uint32_t)items.size();
-    }
-    b->n_items = (uint32_t)items.size();
-    if ((st = gm_alloc((void**)&b->items, sizeof(uint2) * (items.empty() ? 1 : items.size()), s)) != GM_OK) return fail(st);
-    if (!items.empty()) {
-        e = cudaMemcpyAsync(b->items, items.data(), sizeof(uint2) * items.size(), cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_batch_create: work list"));
+    for (uint32_t i : order) ++b->bucket_sessions[bucket_of_tris(ss[i].scene->n_tris)];
+    std::vector<uint2> items[BATCH_TILES];
+    for (int tk = 0; tk < BATCH_TILES; ++tk) {
+        const uint64_t per_tile = 32ull * BATCH_TILE_SPT[tk] * BATCH_GROUP;
+        for (uint32_t i : order) {
+            const int k = bucket_of_tris(ss[i].scene->n_tris);
+            const uint32_t tiles = (uint32_t)(gm_div_up(ss[i].samples->n, per_tile) * BATCH_GROUP);
+            for (uint32_t t = 0; t < tiles; ++t) items[tk].push_back(make_uint2(i, t));
+            for (int q = k + 1; q <= BATCH_BUCKETS; ++q) b->bucket_begin[tk][q] = (uint32_t)items[tk].size();
+        }
+        b->n_items[tk] = (uint32_t)items[tk].size();
+        const size_t nb = sizeof(uint2) * (items[tk].empty() ? 1 : items[tk].size());
+        if ((st = gm_alloc((void**)&b->items[tk], nb, s)) != GM_OK) return fail(st);
+        if (!items[tk].empty()) {
+            e = cudaMemcpyAsync(b->items[tk], items[tk].data(), sizeof(uint2) * items[tk].size(),
+                                cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return fail(gm_cuda_error(e, "gm_batch_create: work list"));
+        }
     }
     if ((e = cudaEventCreate(&b->ev0)) != cudaSuccess || (e = cudaEventCreate(&b->ev1)) != cudaSuccess)
         return fail(gm_cuda_error(e, "gm_batch_create: events"));
@@ -571,13 +613,17 @@ extern "C" gm_status gm_batch_info(gm_batch* b, uint32_t* n_sessions, uint64_t* 
                                    float* last_ms, int32_t* variant_flags) {
     if (!b) return gm_set_error(GM_ERR_INVALID_ARG, "gm_batch_info: null batch");
     if (n_sessions) *n_sessions = b->n;
-    if (n_items) *n_items = b->n_items;
+    if (n_items) {
+        *n_items = 0;
+        for (int k = 0; k < BATCH_BUCKETS; ++k) *n_items += bucket_items(b, k);
+    }
     if (pairs) *pairs = b->pairs;
     if (variant_flags) {
-        // the variant of the bucket with the most work items
+        // the variant of the bucket with the most samples
         int kb = 0;
         for (int k = 1; k < BATCH_BUCKETS; ++k)
-            if (b->bucket_begin[k + 1] - b->bucket_begin[k] > b->bucket_begin[kb + 1] - b->bucket_begin[kb]) kb = k;
+            if (b->bucket_begin[0][k + 1] - b->bucket_begin[0][k] > b->bucket_begin[0][kb + 1] - b->bucket_begin[0][kb])
+                kb = k;
         *variant_flags = b->bflags[kb];
     }
     if (last_ms) {
@@ -645,11 +691,11 @@ extern "C" gm_status gm_batch_autotune(gm_batch* b, gm_stream stream, int32_t* b
             auto it = g_tune.find(keys[k]);
             best[k] = it != g_tune.end() ? it->second : -1;
             best_t[k] = 1e30f;
-            todo |= best[k] < 0 && b->bucket_begin[k + 1] > b->bucket_begin[k];
+            todo |= best[k] < 0 && bucket_busy(b, k);
         }
     }
     if (todo) {
-        for (int code = 0; code < 8; ++code) {
+        for (const int code : BATCH_CODES) {
             for (int k = 0; k < BATCH_BUCKETS; ++k) b->bflags[k] = flags_of_code(code);
             GM_TRY(batch_capture(b, false));   // buckets one after another: each timed alone
             float t[BATCH_BUCKETS] = {1e30f, 1e30f, 1e30f};
@@ -657,7 +703,7 @@ extern "C" gm_status gm_batch_autotune(gm_batch* b, gm_stream stream, int32_t* b
                 GM_TRY(gm_batch_run(b, stream));
                 GM_TRY_CUDA(cudaEventSynchronize(b->ev1));
                 for (int k = 0; k < BATCH_BUCKETS; ++k) {
-                    if (b->bucket_begin[k + 1] <= b->bucket_begin[k]) continue;
+                    if (!bucket_busy(b, k)) continue;
                     float ms = 0.f;
                     const cudaError_t e = cudaEventElapsedTime(&ms, b->bev[k][0], b->bev[k][1]);
                     if (e != cudaSuccess) {
@@ -675,7 +721,7 @@ extern "C" gm_status gm_batch_autotune(gm_batch* b, gm_stream stream, int32_t* b
         }
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         for (int k = 0; k < BATCH_BUCKETS; ++k)
-            if (b->bucket_begin[k + 1] > b->bucket_begin[k]) g_tune[keys[k]] = best[k];
+            if (bucket_busy(b, k)) g_tune[keys[k]] = best[k];
         tune_store_locked();
     }
     for (int k = 0; k < BATCH_BUCKETS; ++k) b->bflags[k] = best[k] >= 0 ? best[k] : b->flags;
@@ -699,10 +745,10 @@ extern "C" gm_status gm_batch_buckets(gm_batch* b, uint32_t* n_buckets, int32_t*
     for (int k = 0; k < BATCH_BUCKETS; ++k) {
         if (flags) flags[k] = b->bflags[k];
         if (sessions) sessions[k] = b->bucket_sessions[k];
-        if (work_items) work_items[k] = b->bucket_begin[k + 1] - b->bucket_begin[k];
+        if (work_items) work_items[k] = bucket_items(b, k);
         if (last_ms) {
             last_ms[k] = 0.f;
-            if (done && b->bucket_begin[k + 1] > b->bucket_begin[k] &&
+            if (done && bucket_busy(b, k) &&
                 cudaEventElapsedTime(&last_ms[k], b->bev[k][0], b->bev[k][1]) != cudaSuccess) {
                 cudaGetLastError();
                 last_ms[k] = 0.f;
@@ -733,16 +779,30 @@ extern "C" gm_status gm_autotune_accumulate(gm_scene* sc, gm_samples* sm, const 
     gm_fixations sub = *fx;
     sub.n = std::min<uint32_t>(fx->n, std::max<uint32_t>(256, fx->n / 16));
     constexpr int kTileFlags = GM_F_TILE_CONSECUTIVE | GM_F_STATIC_TILES;
-    constexpr int kShapeFlags = GM_F_BLOCK128 | GM_F_BLOCK512 | GM_F_SPT1 | GM_F_SPT2 | GM_F_GRID64 | GM_F_EYE_GRID;
+    constexpr int kShapeFlags = GM_F_BLOCK128 | GM_F_BLOCK512 | GM_F_SPT1 | GM_F_SPT2 | GM_F_SPT4 | GM_F_GRID64 |
+                                GM_F_EYE_GRID | GM_F_FIX_L1;
     std::vector<int> cand;
-    // BVH: the three kernel variants of the batched search, times the warp-tile shape (four spread
-    // 32-sample runs or 128 consecutive samples) and the scheduling (persistent or one tile per warp);
-    // then 128-thread blocks for the two ray-queue binary-tree variants (80- and 64-register caps)
-    for (int code = 0; code < 40; ++code) {
-        const int v = code < 32 ? (code & 7) : ((code & 1) ? 5 : 1);
-        const int shape = code < 32 ? code >> 3 : (code - 32) >> 1;
-        cand.push_back(flags_of_code(v) | ((shape & 1) ? GM_F_TILE_CONSECUTIVE : 0) |
-                       ((shape & 2) ? GM_F_STATIC_TILES : 0) | (code >= 32 ? GM_F_BLOCK128 : 0));
+    // BVH: the eight kernel variants (in place or ray queue, binary or 4-wide tree, 80- or
+    // 64-register cap), the ray-queue binary tree with 4, 2 or 1 samples per thread (1 takes 64
+    // registers either way), times the warp-tile shape (spread runs or consecutive samples) and the
+    // scheduling (persistent or one tile per warp); then 128-thread blocks of the ray-queue binary
+    // tree (4 samples per thread with either cap, or 1) and 512-thread blocks (1 sample per thread)
+    for (int shape = 0; shape < 4; ++shape) {
+        const int sf = ((shape & 1) ? GM_F_TILE_CONSECUTIVE : 0) | ((shape & 2) ? GM_F_STATIC_TILES : 0);
+        for (int v = 0; v < 8; ++v) {
+            const int vf = ((v & 1) ? 0 : GM_F_NO_COMPACT) | ((v & 2) ? GM_F_WIDE_BVH : 0) | ((v & 4) ? GM_F_REGCAP64 : 0);
+            if ((v & 3) != 1) {
+                cand.push_back(vf | sf);
+                continue;
+            }
+            cand.push_back(vf | sf | GM_F_SPT4);
+            cand.push_back(vf | sf | GM_F_SPT2);
+            if (v == 1) cand.push_back(vf | sf);
+        }
+        cand.push_back(sf | GM_F_BLOCK128 | GM_F_SPT4);
+        cand.push_back(sf | GM_F_BLOCK128 | GM_F_SPT4 | GM_F_REGCAP64);
+        cand.push_back(sf | GM_F_BLOCK128);
+        cand.push_back(sf | GM_F_BLOCK512);
     }
     // eye grid: 128 or 64 cells a side, samples per thread and block size, spread or consecutive tiles
     const int grid_shapes[7] = {0, GM_F_SPT2, GM_F_SPT1, GM_F_BLOCK128, GM_F_BLOCK128 | GM_F_SPT2,

@@ -268,8 +268,8 @@ __global__ void __launch_bounds__(256) k_field_query(const float* __restrict__ x
 // point t's 64 features into row t of its A tile (bf16, K-major core-matrix layout: 8 x 8 blocks
 // of 128 bytes); per layer one thread issues four tcgen05.mma (M 128, N 64, K 16, bf16 x bf16 ->
 // FP32 in tensor memory, columns 64 h .. 64 h + 63 for half h) and commits them to the half's
-// mbarrier; every thread then reads its row of the accumulator with tcgen05.ld (the bias was
-// stored there first), applies ReLU, rounds to bf16 and writes the next A row. The output layer is
+// mbarrier; every thread then reads its row of the accumulator with tcgen05.ld, adds the bias,
+// applies ReLU, rounds to bf16 and writes the next A row. The output layer is
 // a fifth product with N = 16 whose B rows are the three bf16 parts of w5. Waits are bounded: on a
 // timeout the block records GM_DEV_WAIT_TIMEOUT, drains its own copies, frees its tensor memory and
 // returns.
@@ -352,21 +352,6 @@ __device__ __forceinline__ void bulk_load(float* dst, const float* src, uint32_t
 __device__ __forceinline__ void half_sync(int h) {
     if (h == 0) asm volatile("bar.sync 1, 128;" ::: "memory");
     else asm volatile("bar.sync 2, 128;" ::: "memory");
-}
-
-// The bias of a layer into this thread's accumulator row (the products then add onto it, as the
-// warp-level kernel starts its accumulators from the bias).
-__device__ __forceinline__ void tmem_st_bias(uint32_t taddr, const float* bias) {
-#pragma unroll
-    for (int c0 = 0; c0 < FW; c0 += 16) {
-        const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
-        const float4 q0 = b4[0], q1 = b4[1], q2 = b4[2], q3 = b4[3];
-        asm volatile(
-            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::
-                "r"(taddr + c0),
-            "f"(q0.x), "f"(q0.y), "f"(q0.z), "f"(q0.w), "f"(q1.x), "f"(q1.y), "f"(q1.z), "f"(q1.w), "f"(q2.x),
-            "f"(q2.y), "f"(q2.z), "f"(q2.w), "f"(q3.x), "f"(q3.y), "f"(q3.z), "f"(q3.w));
-    }
 }
 
 // Row t of an A tile: 64 values as bf16, eight 16-byte stores into the core-matrix layout.
@@ -507,11 +492,11 @@ __global__ void __launch_bounds__(TQ_THREADS, 3) k_field_query_tc(const float* _
         float v[FW];
         features_fast(xt, v);
         store_a_row(A, t, v);
-        tmem_st_bias(row_addr, S.bias);   // layer 0's bias (the previous tile's last read is complete)
         // four hidden layers, then the output layer (l == FD) as one more product: A = h4, B = the
-        // three parts of w5, so z5 - b5 is the sum of the first three accumulator columns
+        // three parts of w5, so z5 - b5 is the sum of the first three accumulator columns. Each
+        // product starts a fresh accumulator (the previous tile's last read is complete); the bias
+        // is added to the 64 sums as they are read back.
         for (int l = 0; l <= FD; ++l) {
-            asm volatile("tcgen05.wait::st.sync.aligned;");   // the bias is in the accumulator
             asm volatile("fence.proxy.async.shared::cta;");   // this thread's A row, visible to the MMA
             asm volatile("tcgen05.fence::before_thread_sync;");
             half_sync(h);
@@ -530,7 +515,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 3) k_field_query_tc(const float* _
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_h),
-                            "l"(da), "l"(db), "r"(kQueryIdesc), "r"(1u));
+                            "l"(da), "l"(db), "r"(kQueryIdesc), "r"(s > 0 ? 1u : 0u));
                     }
                 } else {
                     const uint32_t w5_addr = smem_addr(S.W5);
@@ -557,7 +542,8 @@ __global__ void __launch_bounds__(TQ_THREADS, 3) k_field_query_tc(const float* _
                 if (i < n) out[i] = softplusf(((v[0] + v[1]) + v[2]) + S.w5[FW]);
                 break;
             }
-            // 32 columns at a time: read, ReLU and round to bf16, write the next A row
+            // 32 columns at a time: read, add the bias, ReLU and round to bf16, write the next A row
+            const float* bl = S.bias + l * FW;
 #pragma unroll
             for (int c0 = 0; c0 < FW; c0 += 32) {
                 float va[32];
@@ -566,7 +552,8 @@ __global__ void __launch_bounds__(TQ_THREADS, 3) k_field_query_tc(const float* _
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
                 uint32_t pk[16];
 #pragma unroll
-                for (int c = 0; c < 32; c += 2) pk[c / 2] = pack_bf16_relu(va[c], va[c + 1]);
+                for (int c = 0; c < 32; c += 2)
+                    pk[c / 2] = pack_bf16_relu(va[c] + bl[c0 + c], va[c + 1] + bl[c0 + c + 1]);
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
                     const int kg = c0 / 8 + g;
@@ -574,7 +561,6 @@ __global__ void __launch_bounds__(TQ_THREADS, 3) k_field_query_tc(const float* _
                         make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
                 }
             }
-            if (l + 1 < FD) tmem_st_bias(row_addr, S.bias + (l + 1) * FW);   // next layer's start
         }
     }
     if (S.abort && t == 0) {

@@ -20,6 +20,7 @@ GM_F_TIMING, GM_F_DEBUG_PAIRS, GM_F_NO_REORDER, GM_F_NO_COMPACT, GM_F_WIDE_BVH =
 GM_F_REGCAP64, GM_F_TILE_CONSECUTIVE, GM_F_STATIC_TILES, GM_F_NO_TILE_CULL, GM_F_BLOCK128 = 32, 64, 128, 256, 512
 GM_F_EYE_GRID, GM_F_GRID64, GM_F_SPT1, GM_F_SPT2, GM_F_BLOCK512 = 1024, 2048, 4096, 8192, 16384
 GM_F_FIX_L1 = 32768
+GM_F_SPT4 = 65536
 GM_Q_SAMPLE, GM_Q_PLAIN, GM_Q_FIELD = 0, 1, 2
 
 

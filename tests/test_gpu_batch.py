@@ -107,17 +107,28 @@ def test_batch_session_against_oracle(env):
         G.gm_scene_free(sc)
 
 
+def _batch_variant_flags(G):
+    """The batched kernel variants: ray queue or in-place tracing, binary or 4-wide tree, 80- or
+    64-register cap; the ray-queue binary tree with 4, 2 or 1 samples per thread."""
+    out = []
+    for code in range(8):
+        f = ((0 if code & 1 else G.GM_F_NO_COMPACT) | (G.GM_F_WIDE_BVH if code & 2 else 0)
+             | (G.GM_F_REGCAP64 if code & 4 else 0))
+        if code & 3 == 1:
+            out += [f | G.GM_F_SPT4, f | G.GM_F_SPT2] + ([f] if code == 1 else [])
+        else:
+            out.append(f)
+    return out
+
+
 def test_batched_variants_agree_bit_for_bit(env):
-    """Every batched kernel variant (ray queue or in-place tracing, binary or 4-wide tree, 80- or
-    64-register cap) gives the same maps: the same additions per sample in the same order, each
-    weight rounded on its own before it enters the compensated sum."""
+    """Every batched kernel variant gives the same maps: the same additions per sample in the
+    same order, each weight rounded on its own before it enters the compensated sum."""
     G, pipe, ctx = env
     ws = _small_sessions(3)
     hs = _prepare(G, pipe, ctx, ws)
     ref = None
-    for code in range(8):
-        f = ((0 if code & 1 else G.GM_F_NO_COMPACT) | (G.GM_F_WIDE_BVH if code & 2 else 0)
-             | (G.GM_F_REGCAP64 if code & 4 else 0))
+    for code, f in enumerate(_batch_variant_flags(G)):
         b = G.gm_batch_create(ctx, hs, pipe.params_of(ws[0], normalize=False, flags=f))
         G.gm_batch_run(b)
         maps = []
@@ -145,7 +156,7 @@ def test_autotune_picks_a_variant_and_keeps_results(env, tmp_path, monkeypatch):
         G.gm_map_copy(G.gm_batch_map(b, i), 0, a)
         before.append(a)
     flags, ms = G.gm_batch_autotune(b)
-    assert flags & ~(G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64) == 0 and ms > 0
+    assert flags in _batch_variant_flags(G) and ms > 0
     assert G.gm_batch_info(b)["variant_flags"] == flags
     G.gm_batch_run(b)
     G.gm_sync(ctx)
@@ -158,7 +169,7 @@ def test_autotune_picks_a_variant_and_keeps_results(env, tmp_path, monkeypatch):
     assert [x["sessions"] for x in bk] == want
     assert sum(x["work_items"] for x in bk) == G.gm_batch_info(b)["n_work_items"]
     for x in bk:
-        assert x["flags"] & ~(G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64) == 0
+        assert x["flags"] in _batch_variant_flags(G)
         assert (x["ms"] > 0) == (x["work_items"] > 0)
     for i in range(len(ws)):
         a = np.empty_like(before[i])
@@ -167,14 +178,18 @@ def test_autotune_picks_a_variant_and_keeps_results(env, tmp_path, monkeypatch):
     G.gm_batch_free(b)
     fl2, _ = G.gm_autotune_accumulate(hs[0][0], hs[0][1], *hs[0][2:], prm)
     shape = (G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64 | G.GM_F_TILE_CONSECUTIVE | G.GM_F_STATIC_TILES
-             | G.GM_F_BLOCK128 | G.GM_F_EYE_GRID | G.GM_F_GRID64 | G.GM_F_SPT1 | G.GM_F_SPT2 | G.GM_F_BLOCK512)
+             | G.GM_F_BLOCK128 | G.GM_F_EYE_GRID | G.GM_F_GRID64 | G.GM_F_SPT1 | G.GM_F_SPT2 | G.GM_F_SPT4
+             | G.GM_F_BLOCK512)
     assert fl2 & ~shape == 0
     if not fl2 & G.GM_F_EYE_GRID:
-        assert not fl2 & (G.GM_F_GRID64 | G.GM_F_SPT1 | G.GM_F_SPT2 | G.GM_F_BLOCK512)
-        if fl2 & G.GM_F_BLOCK128:   # only offered for the ray-queue binary-tree kernels
+        assert not fl2 & (G.GM_F_GRID64 | G.GM_F_SPT1)
+        if fl2 & (G.GM_F_BLOCK128 | G.GM_F_BLOCK512 | G.GM_F_SPT2 | G.GM_F_SPT4):
+            # only offered for the ray-queue binary-tree kernels
             assert not fl2 & (G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH)
+        if fl2 & G.GM_F_BLOCK512:   # one sample per thread
+            assert not fl2 & (G.GM_F_SPT2 | G.GM_F_SPT4 | G.GM_F_BLOCK128)
     else:                            # eye-grid shapes only
-        assert not fl2 & (G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64 | G.GM_F_STATIC_TILES)
+        assert not fl2 & (G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH | G.GM_F_REGCAP64 | G.GM_F_STATIC_TILES | G.GM_F_SPT4)
     # the tuned variant gives the same map as the default one
     ref = G.gm_accumulate_fixations(hs[0][0], hs[0][1], *hs[0][2:], prm)
     p2 = pipe.params_of(ws[0], normalize=False, flags=fl2)

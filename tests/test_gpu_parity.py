@@ -344,21 +344,51 @@ def test_paper_scene_full_size_sampled(G, ctx, pipe):
     _check_density(gpu[which], d, amb, sens * dpos)
 
 
+# forms the recording (debug) kernel also takes: their recorded pairs are compared too
+_DEBUG_FORMS = {"in_place", "wide_tree", "tile_consecutive", "static_tiles", "no_tile_cull"}
+
+
+def _all_windows(G, pipe, h):
+    return np.stack([pipe.map_array(h, k)[0] for k in range(G.gm_map_info(h.map)[0])])
+
+
+def _variant_flag(G, other):
+    return {"in_place": G.GM_F_NO_COMPACT, "wide_tree": G.GM_F_WIDE_BVH, "tile_consecutive": G.GM_F_TILE_CONSECUTIVE,
+            "static_tiles": G.GM_F_STATIC_TILES, "no_tile_cull": G.GM_F_NO_TILE_CULL,
+            "block128": G.GM_F_BLOCK128, "block512": G.GM_F_BLOCK512, "fix_l1": G.GM_F_FIX_L1,
+            "spt2": G.GM_F_SPT2, "spt2_regcap64": G.GM_F_SPT2 | G.GM_F_REGCAP64, "spt4": G.GM_F_SPT4,
+            "spt4_regcap64": G.GM_F_SPT4 | G.GM_F_REGCAP64, "spt4_fix_l1": G.GM_F_SPT4 | G.GM_F_FIX_L1,
+            "spt4_block128": G.GM_F_SPT4 | G.GM_F_BLOCK128,
+            "spt4_block128_regcap64": G.GM_F_SPT4 | G.GM_F_BLOCK128 | G.GM_F_REGCAP64}[other]
+
+
 @pytest.mark.parametrize("other", ["in_place", "wide_tree", "tile_consecutive", "static_tiles", "no_tile_cull",
-                                   "block128", "block128_regcap64", "fix_l1"])
+                                   "block128", "block512", "fix_l1", "spt2", "spt2_regcap64", "spt4",
+                                   "spt4_regcap64", "spt4_fix_l1", "spt4_block128", "spt4_block128_regcap64"])
 def test_accumulate_variants_agree_bit_for_bit(G, ctx, pipe, other):
     """The per-warp ray queue only reorders which lane traces which ray, and the 4-wide tree
     only skips intermediate boxes (every box is conservative, so every hitting triangle is
-    reached either way); each sample still gets its additions in fixation order, so maps and
-    recorded pairs are identical."""
-    flag = {"in_place": G.GM_F_NO_COMPACT, "wide_tree": G.GM_F_WIDE_BVH, "tile_consecutive": G.GM_F_TILE_CONSECUTIVE,
-            "static_tiles": G.GM_F_STATIC_TILES, "no_tile_cull": G.GM_F_NO_TILE_CULL,
-            "block128": G.GM_F_BLOCK128, "block128_regcap64": G.GM_F_BLOCK128 | G.GM_F_REGCAP64,
-            "fix_l1": G.GM_F_FIX_L1}[other]
+    reached either way); the warp-tile size only regroups the samples. Each sample
+    still gets its additions in fixation order, so maps (every window of a 60-window city block
+    too) and the in-cone and visible counts are identical, and so are the recorded pairs of the
+    forms the recording kernel takes."""
+    flag = _variant_flag(G, other)
     s5 = synth.session(5)
     s5.fixations = s5.fixations.subset(slice(0, 150))
+    city = synth.city_block(n_fix=1500, n_samples=120_000, grid=3, boxes_per_block=4, n_spheres=2, sphere_lat=40,
+                            duration_s=60.0, window_s=1.0)
     cap = 4_000_000
-    for w in (synth.tiny_sphere(), s5):
+    for w in (synth.tiny_sphere(), s5, city):
+        a = pipe.run(ctx, w, normalize=False)
+        b = pipe.run(ctx, w, normalize=False, flags=flag)
+        va, vb = _all_windows(G, pipe, a), _all_windows(G, pipe, b)
+        sa, sb = G.gm_map_info(a.map)[2], G.gm_map_info(b.map)[2]
+        a.free()
+        b.free()
+        assert va.shape == vb.shape and np.array_equal(va.view(np.uint32), vb.view(np.uint32))
+        assert sa["in_cone"] == sb["in_cone"] > 0 and sa["visible"] == sb["visible"]
+        if other not in _DEBUG_FORMS or w is city:
+            continue
         a = pipe.run(ctx, w, normalize=False, flags=G.GM_F_DEBUG_PAIRS, debug_pair_cap=cap)
         b = pipe.run(ctx, w, normalize=False, flags=G.GM_F_DEBUG_PAIRS | flag, debug_pair_cap=cap)
         va, vb = pipe.map_array(a)[0], pipe.map_array(b)[0]
