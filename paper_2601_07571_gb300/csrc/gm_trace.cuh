@@ -372,6 +372,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                                           unsigned long long* __restrict__ dbg_cursor, const DebugOut& dbg,
                                           int* __restrict__ err, TileStats& st, float4* wfix = nullptr) {
     static_assert(!GRID || COMPACT, "the eye grid traces from the ray queue");
+    static_assert(!(GRID && FSM), "staged fixations are a form of the BVH kernels");
     // fixation ranges and sums carried across launches exist for the eye grid's chunks only; the
     // BVH kernels cover the whole list in one launch and keep none of that code
     constexpr bool CH = GRID;
@@ -460,29 +461,33 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
     const uint32_t i_beg = CH ? P.f0 : 0u;
     float4 nF0 = !FSM && i_beg < i_end ? __ldg(&fix[2 * i_beg]) : make_float4(0.f, 0.f, 0.f, 0.f);
     float4 nF1 = !FSM && i_beg < i_end ? __ldg(&fix[2 * i_beg + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    // the work of one fixation (window change, tile sphere test, cone tests, ray queue)
-    auto per_fixation = [&](const uint32_t i, const float4 F0, const float4 F1) {
+    // whether fixation (F0, F1)'s cone can reach the tile's bounding sphere (always, without one)
+    auto sphere_reach = [&](const float4 F0, const float4 F1) -> bool {
+        const float4 bs = *wbox;
+        if (bs.w < 0.f) return true;
+        // a point p = q + u with |u| <= R has d1 <= d1c + R and |p x r^| >= |q x r^| - R; it is
+        // in the cone only if |p x r^| <= tan(phi) d1. Compared squared (both sides are
+        // non-negative); the margin, from the L1 norm of q, covers FP32 rounding on both sides.
+        const float bR = bs.w;
+        const float qx = bs.x - F0.x, qy = bs.y - F0.y, qz = bs.z - F0.z;
+        const float d1c = fmaf(qx, F1.x, fmaf(qy, F1.y, qz * F1.z));
+        const float ux = fmaf(qy, F1.z, -qz * F1.y);
+        const float uy = fmaf(qz, F1.x, -qx * F1.z);
+        const float uz = fmaf(qx, F1.y, -qy * F1.x);
+        const float margin = 1e-4f * (fabsf(qx) + fabsf(qy) + fabsf(qz) + bR);
+        const float reach = d1c + bR;
+        const float lim = bR + fmaf(P.tanphi, fmaxf(reach, 0.f), margin);
+        return !(reach <= -margin || fmaf(ux, ux, fmaf(uy, uy, uz * uz)) > lim * lim);
+    };
+    // the work of one fixation (window change, tile sphere test unless `reached` says it was
+    // passed, cone tests, ray queue)
+    auto per_fixation = [&](const uint32_t i, const float4 F0, const float4 F1, const bool reached) {
         const uint32_t win = __float_as_uint(F1.w);
         if (win != cur) {
             if (cur != 0xffffffffu) flush(cur);
             cur = win;
         }
-        const float4 bs = *wbox;
-        if (bs.w >= 0.f) {
-            // a point p = q + u with |u| <= R has d1 <= d1c + R and |p x r^| >= |q x r^| - R; it is
-            // in the cone only if |p x r^| <= tan(phi) d1. Compared squared (both sides are
-            // non-negative); the margin, from the L1 norm of q, covers FP32 rounding on both sides.
-            const float bR = bs.w;
-            const float qx = bs.x - F0.x, qy = bs.y - F0.y, qz = bs.z - F0.z;
-            const float d1c = fmaf(qx, F1.x, fmaf(qy, F1.y, qz * F1.z));
-            const float ux = fmaf(qy, F1.z, -qz * F1.y);
-            const float uy = fmaf(qz, F1.x, -qx * F1.z);
-            const float uz = fmaf(qx, F1.y, -qy * F1.x);
-            const float margin = 1e-4f * (fabsf(qx) + fabsf(qy) + fabsf(qz) + bR);
-            const float reach = d1c + bR;
-            const float lim = bR + fmaf(P.tanphi, fmaxf(reach, 0.f), margin);
-            if (reach <= -margin || fmaf(ux, ux, fmaf(uy, uy, uz * uz)) > lim * lim) return;
-        }
+        if (!reached && !sphere_reach(F0, F1)) return;
         st.n_tested += live;
         if (COMPACT) {
             int tot = 0;
@@ -596,16 +601,27 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
         };
     if (FSM) {
         // fixations staged 32 at a time in the warp's shared-memory slot (one coalesced load per
-        // lane), then read from there
+        // lane); each lane tests its fixation against the tile's sphere, and the warp then visits
+        // only the fixations that reach it, in list order. Skipping a fixation never changes a
+        // sum; a window is written when the next visited fixation opens another one, or at the
+        // end, which writes the same values as writing it at the first fixation of the next window.
         for (uint32_t c0 = i_beg; c0 < i_end; c0 += 32) {
             const uint32_t m = min(32u, i_end - c0);
             __syncwarp();
+            bool pass = false;
             if ((uint32_t)lane < m) {
-                wfix[2 * lane] = __ldg(&fix[2 * (c0 + lane)]);
-                wfix[2 * lane + 1] = __ldg(&fix[2 * (c0 + lane) + 1]);
+                const float4 a = __ldg(&fix[2 * (c0 + lane)]), b = __ldg(&fix[2 * (c0 + lane) + 1]);
+                wfix[2 * lane] = a;
+                wfix[2 * lane + 1] = b;
+                pass = sphere_reach(a, b);
             }
+            unsigned pm = __ballot_sync(0xffffffffu, pass);
             __syncwarp();
-            for (uint32_t k = 0; k < m; ++k) per_fixation(c0 + k, wfix[2 * k], wfix[2 * k + 1]);
+            while (pm) {
+                const int k = __ffs(pm) - 1;
+                pm &= pm - 1u;
+                per_fixation(c0 + k, wfix[2 * k], wfix[2 * k + 1], true);
+            }
         }
     } else {
         // fixations read through L1 as warp-wide broadcasts, the next one in flight
@@ -615,7 +631,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
                 nF0 = __ldg(&fix[2 * (i + 1)]);
                 nF1 = __ldg(&fix[2 * (i + 1) + 1]);
             }
-            per_fixation(i, F0, F1);
+            per_fixation(i, F0, F1, false);
         }
     }
     if (CH && P.carry_out) {
