@@ -100,7 +100,8 @@ enum {
                                kernel only: with NO_COMPACT, WIDE_BVH or REGCAP64 the BVH is kept) */
     GM_F_GRID64 = 2048,     /* with GM_F_EYE_GRID: 64 x 64 cells per fixation instead of 128 x 128 */
     GM_F_SPT1 = 4096,       /* warp tiles of 32 samples (1 per thread); the default of the ray-queue
-                               binary-tree kernel (the eye grid's default is 4 per thread) */
+                               binary-tree kernel (the eye grid's default is 4 per thread); with
+                               GM_F_NO_COMPACT: one-sample tiles traced in place */
     GM_F_SPT2 = 8192,       /* warp tiles of 64 samples (2 per thread): ray-queue binary tree and eye grid */
     GM_F_BLOCK512 = 16384,  /* blocks of 512 threads: eye grid (1 or 2 samples per thread) and the
                                one-sample ray-queue binary-tree kernel */

@@ -492,6 +492,9 @@ gm_status accumulate_impl(gm_scene* sc, gm_samples* sm, const gm_fixations* fx, 
                     else if (b512) GM_LAUNCH_ACC_F(false, true, false, 2, 512, false, 1, true);
                     else if (prm->flags & GM_F_FIX_L1) GM_LAUNCH_ACC_F(false, true, false, 4, 256, false, 1, false);
                     else GM_LAUNCH_ACC_F(false, true, false, 4, 256, false, 1, true);
+                } else if ((code == 0 || code == 4) && (prm->flags & GM_F_SPT1)) {
+                    // one-sample tiles traced in place: a lane traces its own sample's ray
+                    GM_LAUNCH_ACC_F(false, false, false, 4, 256, false, 1, true);
                 } else if ((code == 1 || code == 5) && qspt == 2) {
                     if (code == 5) GM_LAUNCH_ACC_F(false, true, false, 4, 256, false, 2, true);
                     else GM_LAUNCH_ACC_F(false, true, false, 3, 256, false, 2, true);

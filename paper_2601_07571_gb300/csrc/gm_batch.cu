@@ -784,15 +784,17 @@ extern "C" gm_status gm_autotune_accumulate(gm_scene* sc, gm_samples* sm, const 
     std::vector<int> cand;
     // BVH: the eight kernel variants (in place or ray queue, binary or 4-wide tree, 80- or
     // 64-register cap), the ray-queue binary tree with 4, 2 or 1 samples per thread (1 takes 64
-    // registers either way), times the warp-tile shape (spread runs or consecutive samples) and the
-    // scheduling (persistent or one tile per warp); then 128-thread blocks of the ray-queue binary
-    // tree (4 samples per thread with either cap, or 1) and 512-thread blocks (1 sample per thread)
+    // registers either way) and the in-place binary tree also with 1, times the warp-tile shape
+    // (spread runs or consecutive samples) and the scheduling (persistent or one tile per warp);
+    // then 128-thread blocks of the ray-queue binary tree (4 samples per thread with either cap,
+    // or 1) and 512-thread blocks (1 sample per thread)
     for (int shape = 0; shape < 4; ++shape) {
         const int sf = ((shape & 1) ? GM_F_TILE_CONSECUTIVE : 0) | ((shape & 2) ? GM_F_STATIC_TILES : 0);
         for (int v = 0; v < 8; ++v) {
             const int vf = ((v & 1) ? 0 : GM_F_NO_COMPACT) | ((v & 2) ? GM_F_WIDE_BVH : 0) | ((v & 4) ? GM_F_REGCAP64 : 0);
             if ((v & 3) != 1) {
                 cand.push_back(vf | sf);
+                if (v == 0) cand.push_back(vf | sf | GM_F_SPT1);   // one-sample tiles traced in place
                 continue;
             }
             cand.push_back(vf | sf | GM_F_SPT4);

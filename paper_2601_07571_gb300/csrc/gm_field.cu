@@ -552,8 +552,11 @@ __global__ void __launch_bounds__(TQ_THREADS, 3) k_field_query_tc(const float* _
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
                 uint32_t pk[16];
 #pragma unroll
-                for (int c = 0; c < 32; c += 2)
-                    pk[c / 2] = pack_bf16_relu(va[c] + bl[c0 + c], va[c + 1] + bl[c0 + c + 1]);
+                for (int c = 0; c < 32; c += 4) {
+                    const float4 b4 = *reinterpret_cast<const float4*>(bl + c0 + c);   // one 16-byte broadcast
+                    pk[c / 2] = pack_bf16_relu(va[c] + b4.x, va[c + 1] + b4.y);
+                    pk[c / 2 + 1] = pack_bf16_relu(va[c + 2] + b4.z, va[c + 3] + b4.w);
+                }
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
                     const int kg = c0 / 8 + g;

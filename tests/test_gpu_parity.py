@@ -359,12 +359,14 @@ def _variant_flag(G, other):
             "spt2": G.GM_F_SPT2, "spt2_regcap64": G.GM_F_SPT2 | G.GM_F_REGCAP64, "spt4": G.GM_F_SPT4,
             "spt4_regcap64": G.GM_F_SPT4 | G.GM_F_REGCAP64, "spt4_fix_l1": G.GM_F_SPT4 | G.GM_F_FIX_L1,
             "spt4_block128": G.GM_F_SPT4 | G.GM_F_BLOCK128,
-            "spt4_block128_regcap64": G.GM_F_SPT4 | G.GM_F_BLOCK128 | G.GM_F_REGCAP64}[other]
+            "spt4_block128_regcap64": G.GM_F_SPT4 | G.GM_F_BLOCK128 | G.GM_F_REGCAP64,
+            "in_place_spt1": G.GM_F_NO_COMPACT | G.GM_F_SPT1}[other]
 
 
 @pytest.mark.parametrize("other", ["in_place", "wide_tree", "tile_consecutive", "static_tiles", "no_tile_cull",
                                    "block128", "block512", "fix_l1", "spt2", "spt2_regcap64", "spt4",
-                                   "spt4_regcap64", "spt4_fix_l1", "spt4_block128", "spt4_block128_regcap64"])
+                                   "spt4_regcap64", "spt4_fix_l1", "spt4_block128", "spt4_block128_regcap64",
+                                   "in_place_spt1"])
 def test_accumulate_variants_agree_bit_for_bit(G, ctx, pipe, other):
     """The per-warp ray queue only reorders which lane traces which ray, and the 4-wide tree
     only skips intermediate boxes (every box is conservative, so every hitting triangle is
