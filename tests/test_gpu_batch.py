@@ -182,7 +182,9 @@ def test_autotune_picks_a_variant_and_keeps_results(env, tmp_path, monkeypatch):
              | G.GM_F_BLOCK512)
     assert fl2 & ~shape == 0
     if not fl2 & G.GM_F_EYE_GRID:
-        assert not fl2 & (G.GM_F_GRID64 | G.GM_F_SPT1)
+        assert not fl2 & G.GM_F_GRID64
+        if fl2 & G.GM_F_SPT1:        # only as the in-place one-sample form (the ray-queue default needs no flag)
+            assert fl2 & G.GM_F_NO_COMPACT and not fl2 & (G.GM_F_WIDE_BVH | G.GM_F_BLOCK128 | G.GM_F_BLOCK512)
         if fl2 & (G.GM_F_BLOCK128 | G.GM_F_BLOCK512 | G.GM_F_SPT2 | G.GM_F_SPT4):
             # only offered for the ray-queue binary-tree kernels
             assert not fl2 & (G.GM_F_NO_COMPACT | G.GM_F_WIDE_BVH)
