@@ -498,6 +498,19 @@ def dynamic_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def normalize_roofline(ns: int, nonempty_windows: int, ms: float):
+    """HBM roofline of the map normalisation (Section 3.2.3): every value of a non-empty window
+    read and written once, 8 B per sample and window, over the kernel's CUDA-event time."""
+    peak, basis = measured_hbm_peak()
+    if ms <= 0:
+        return None
+    nbytes = 8.0 * ns * nonempty_windows
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "kernel": "k_normalize", "bytes": nbytes, "kernel_ms": ms, "peak_basis": basis,
+            "work_basis": f"8 B (read + write) per sample of each of {nonempty_windows} non-empty window(s)"}
+
+
 def measured_hbm_peak():
     """HBM copy rate (GB/s) measured by the driver, else the machine's fallback."""
     try:
@@ -824,7 +837,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    for _ in range(args.steps):
+    nonempty = 0
+    for it in range(args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         l0 = G.gm_ctx_launches(ctx)
@@ -839,6 +853,11 @@ def main():
         prep_ms.append(stats["prep_ms"])
         norm_ms.append(stats["normalize_ms"])
         grid_ms.append(stats["grid_ms"])
+        if it == args.steps - 1:
+            # windows the normalisation reads and writes (an empty window is skipped)
+            maxima = np.empty(max(1, stats["n_windows"]), np.float32)
+            G.gm_map_max(h[2], maxima)
+            nonempty = int((maxima > 0).sum())
         release(h)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -927,6 +946,7 @@ def main():
             ("grid_entries_per_ray" if grid_on else "nodes_per_ray"): stats["nodes_visited"] / max(1, stats["in_cone"]),
             "tris_per_ray": stats["tris_tested"] / max(1, stats["in_cone"]),
             "roofline": roof,
+            "normalize_roofline": normalize_roofline(ns, nonempty, sum(norm_ms) / len(norm_ms)),
             "e2e": {"value": total_pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(out.numel() * 4), "ms_per_step": e2e_s * 1e3},
             "gpu_launches": int(launches), "clocks": clk}

@@ -135,30 +135,53 @@ int acc_occupancy() {
     return b > 0 ? b : 1;
 }
 
-// v / max for every window: blockIdx.y = window - w0, float4 loads and stores over the window's
-// samples (a scalar tail when n_samples is not a multiple of 4); windows whose maximum is 0 stay 0.
-__global__ void k_normalize(float* __restrict__ v, uint64_t ns, const unsigned int* __restrict__ max_bits,
-                            uint32_t w0) {
-    const uint32_t win = w0 + blockIdx.y;
-    const float m = __uint_as_float(max_bits[win]);
-    if (!(m > 0.f)) return;
-    float* w = v + (size_t)win * ns;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if ((reinterpret_cast<uintptr_t>(w) & 15u) == 0) {
-        const uint64_t n4 = ns / 4;
-        float4* w4 = reinterpret_cast<float4*>(w);
-        for (uint64_t i = i0; i < n4; i += stride) {
-            float4 x = w4[i];
-            x.x = __fdiv_rn(x.x, m);
-            x.y = __fdiv_rn(x.y, m);
-            x.z = __fdiv_rn(x.z, m);
-            x.w = __fdiv_rn(x.w, m);
-            w4[i] = x;
+// v / max for every window, windows whose maximum is 0 left as they are (0). A persistent grid
+// (every resident block slot once) walks work items (window, chunk of NORM_ITEM float4): each
+// thread moves NORM_UNROLL float4 of the chunk, all its loads issued before the first division.
+// 32 registers a thread, so 8 blocks of 256 fit an SM. A window whose start is not
+// 16-byte aligned (W > 1, ns not a multiple of 4) has up to 3 head floats before its float4 body
+// and up to 3 tail floats after it; the window's first item does those one by one.
+constexpr int NORM_THREADS = 256;
+constexpr int NORM_UNROLL = 4;
+constexpr uint64_t NORM_ITEM = (uint64_t)NORM_THREADS * NORM_UNROLL;
+
+__global__ void __launch_bounds__(NORM_THREADS, 8) k_normalize(float* __restrict__ v, uint64_t ns,
+                                                            const unsigned int* __restrict__ max_bits, uint64_t W,
+                                                            uint64_t items_per_win) {
+    const uint64_t n_items = W * items_per_win;
+    for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const uint64_t win = it / items_per_win;
+        const uint64_t c = it - win * items_per_win;
+        const float m = __uint_as_float(max_bits[win]);
+        if (!(m > 0.f)) continue;
+        float* w = v + win * ns;
+        const uint64_t mis = ((16u - (reinterpret_cast<uintptr_t>(w) & 15u)) & 15u) / 4u;
+        const uint64_t head = mis < ns ? mis : ns;
+        const uint64_t n4 = (ns - head) / 4;
+        float4* w4 = reinterpret_cast<float4*>(w + head);
+        const uint64_t i0 = c * NORM_ITEM + threadIdx.x;
+        float4 x[NORM_UNROLL];
+#pragma unroll
+        for (int u = 0; u < NORM_UNROLL; ++u) {
+            const uint64_t i = i0 + (uint64_t)u * NORM_THREADS;
+            if (i < n4) x[u] = w4[i];
         }
-        for (uint64_t i = 4 * n4 + i0; i < ns; i += stride) w[i] = __fdiv_rn(w[i], m);
-    } else {
-        for (uint64_t i = i0; i < ns; i += stride) w[i] = __fdiv_rn(w[i], m);
+#pragma unroll
+        for (int u = 0; u < NORM_UNROLL; ++u) {
+            const uint64_t i = i0 + (uint64_t)u * NORM_THREADS;
+            if (i < n4) {
+                x[u].x = __fdiv_rn(x[u].x, m);
+                x[u].y = __fdiv_rn(x[u].y, m);
+                x[u].z = __fdiv_rn(x[u].z, m);
+                x[u].w = __fdiv_rn(x[u].w, m);
+                w4[i] = x[u];
+            }
+        }
+        if (c == 0 && threadIdx.x < 8) {
+            // threads 0..3: the head floats; threads 4..7: the floats after the float4 body
+            const uint64_t k = threadIdx.x < 4 ? threadIdx.x : head + 4 * n4 + (threadIdx.x - 4);
+            if (threadIdx.x < 4 ? k < head : k < ns) w[k] = __fdiv_rn(w[k], m);
+        }
     }
 }
 
@@ -188,16 +211,16 @@ __global__ void k_add_valid(unsigned long long* __restrict__ c, const uint32_t* 
 int launch_normalize(gm_map* mp, int n_sm, cudaStream_t s) {
     const uint64_t ns = mp->ns, W = mp->W;
     if (ns == 0) return 0;
-    // blocks per window: enough to cover the window with float4s, and ~8 waves overall
-    const uint64_t per_win = std::max<uint64_t>(1, std::min<uint64_t>(gm_div_up(ns, 1024),
-                                                                     (uint64_t)n_sm * 8 / std::max<uint64_t>(1, W) + 1));
-    int launches = 0;
-    for (uint64_t w0 = 0; w0 < W; w0 += 65535) {
-        dim3 grid((uint32_t)per_win, (uint32_t)std::min<uint64_t>(65535, W - w0));
-        k_normalize<<<grid, 256, 0, s>>>(mp->values, ns, mp->max_bits, (uint32_t)w0);
-        ++launches;
-    }
-    return launches;
+    const uint64_t items_per_win = std::max<uint64_t>(1, gm_div_up(ns / 4, NORM_ITEM));
+    // every resident block slot once, never more blocks than items
+    static const int per_sm = [] {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_normalize, NORM_THREADS, 0);
+        return b > 0 ? b : 1;
+    }();
+    const uint64_t grid = std::min<uint64_t>((uint64_t)n_sm * per_sm, W * items_per_win);
+    k_normalize<<<(uint32_t)grid, NORM_THREADS, 0, s>>>(mp->values, ns, mp->max_bits, W, items_per_win);
+    return 1;
 }
 
 gm_status n_windows_of(const gm_params* prm, uint64_t* W_out) {

@@ -184,6 +184,47 @@ def test_end_to_end_tiny_with_normalisation(G, ctx, pipe):
     assert np.all(np.abs(gn - on) <= tol)
 
 
+def test_normalisation_of_every_window_is_the_ieee_quotient(G, ctx, pipe):
+    """Section 3.2.3's division by the window's maximum, window by window, on a map whose windows
+    do not start on 16-byte boundaries (6645 samples, not a multiple of 4: head and tail floats
+    around each window's float4 body) and whose empty windows stay 0: bit-identical to the FP32
+    quotient numpy computes from the unnormalised map."""
+    w = synth.tiny_sphere(n_fix=300)
+    ts = w.fixations.timestamp_s
+    w.params = synth.Params(t_begin=0.0, t_end=float(ts.max()) + 40.0, window_s=4.0)
+    a = pipe.run(ctx, w, normalize=False)
+    b = pipe.run(ctx, w, normalize=True)
+    W, ns, _, _ = G.gm_map_info(a.map)
+    assert ns % 4 != 0 and W >= 8
+    empty = 0
+    for k in range(W):
+        raw, mx = pipe.map_array(a, k)
+        nrm, mxb = pipe.map_array(b, k)
+        assert mx == mxb
+        if mx > 0:
+            want = (raw / np.float32(mx)).astype(np.float32)
+        else:
+            empty += 1
+            want = np.zeros_like(raw)
+        assert np.array_equal(nrm.view(np.uint32), want.view(np.uint32)), k
+    a.free()
+    b.free()
+    assert empty >= 1   # the last windows lie after the last fixation
+
+
+def test_normalisation_spans_many_chunks(G, ctx, pipe):
+    """The same on one window of the paper-shaped scene's 2M samples (245 chunks of 2048 float4)."""
+    w = synth.paper_scene(n_fix=40)
+    a = pipe.run(ctx, w, normalize=False)
+    raw, mx = pipe.map_array(a)
+    assert mx > 0
+    G.gm_map_normalize(a.map)
+    nrm, _ = pipe.map_array(a)
+    a.free()
+    want = (raw / np.float32(mx)).astype(np.float32)
+    assert np.array_equal(nrm.view(np.uint32), want.view(np.uint32))
+
+
 def test_device_inputs_match_host_inputs_and_rerun_is_bit_identical(G, ctx, pipe):
     w = synth.tiny_sphere()
     a = pipe.run(ctx, w, normalize=False)
