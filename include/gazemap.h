@@ -87,15 +87,18 @@ enum {
     GM_F_TIMING = 1,        /* record CUDA events around each stage (gm_map_stats.*_ms) */
     GM_F_DEBUG_PAIRS = 2,   /* record in-cone pairs (sample, fixation, visible, weight) */
     GM_F_NO_REORDER = 4,    /* process samples in stored order (no spatial work order) */
-    GM_F_NO_COMPACT = 8,    /* trace each lane's in-cone rays in place (no per-warp ray queue) */
+    GM_F_NO_COMPACT = 8,    /* trace each lane's in-cone rays in place (no per-warp ray queue; 4
+                               samples per thread unless GM_F_SPT1) */
     GM_F_WIDE_BVH = 16,     /* traverse the 4-wide collapse of the tree instead of the binary tree */
-    GM_F_REGCAP64 = 32,     /* cap the accumulation kernel at 64 registers (4 blocks per SM) */
-    GM_F_TILE_CONSECUTIVE = 64, /* warp tiles of 128 consecutive samples (else four 32-sample runs over 1024) */
+    GM_F_REGCAP64 = 32,     /* cap the accumulation kernel at 64 registers (4 blocks per SM; the
+                               one-sample ray-queue kernel, the default, always fits 64) */
+    GM_F_TILE_CONSECUTIVE = 64, /* multi-sample warp tiles of consecutive samples (else runs of 32 spread
+                               over 8 tiles' span); a one-sample tile is one run of 32 either way */
     GM_F_STATIC_TILES = 128, /* one warp tile per warp of a full grid (else warps pull tiles from a counter) */
     GM_F_NO_TILE_CULL = 256, /* test every sample against every fixation (no warp-tile sphere test) */
-    GM_F_BLOCK128 = 512,    /* blocks of 128 threads (7 per SM, 72 registers; 8 per SM with GM_F_REGCAP64)
-                               for the ray-queue binary-tree variant, instead of 256 (3 or 4 per SM);
-                               with the eye grid: 128-thread blocks, 6 per SM */
+    GM_F_BLOCK128 = 512,    /* blocks of 128 threads instead of 256 for the ray-queue binary-tree
+                               kernel (one sample per thread: 8 per SM; with GM_F_SPT4: 7 per SM at
+                               72 registers, 8 with GM_F_REGCAP64); with the eye grid: 6 per SM */
     GM_F_EYE_GRID = 1024,   /* occlusion through per-fixation eye grids instead of the BVH (ray-queue
                                kernel only: with NO_COMPACT, WIDE_BVH or REGCAP64 the BVH is kept) */
     GM_F_GRID64 = 2048,     /* with GM_F_EYE_GRID: 64 x 64 cells per fixation instead of 128 x 128 */
