@@ -79,7 +79,7 @@ extern "C" gm_status gm_create(int device, gm_ctx** out) {
                                                     ", this library is built for sm_103a only");
     GM_TRY_CUDA(cudaSetDevice(device));
     // Keep freed stream-ordered allocations in the device's default pool instead of returning
-    // them to the driver at every synchronisation: the scene, sample and map buffers of
+    // them to the CUDA driver at every synchronisation: the scene, sample and map buffers of
     // successive calls then reuse the same memory without new mappings.
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
