@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(NT, MINB) k_accumulate(
     warp_stats_commit(st, counters);
 }
 
-// (The CUDA driver's default shared-memory carveout is kept: preferring the largest L1 leaves room for
+// (The driver's default shared-memory carveout is kept: preferring the largest L1 leaves room for
 // fewer blocks per SM and measured 316 vs 253 ms at the paper scene.)
 template <bool D, bool Cm, bool Wd, int Mb, int NT = ACC_THREADS, bool Gr = false, int S = SPT, bool Fs = false>
 int acc_occupancy() {
