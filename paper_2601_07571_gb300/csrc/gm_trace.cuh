@@ -316,6 +316,44 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
+// Whether the cone of fixation (F0: eye; F1: unit gaze r^) with half-angle tan(phi) = tanphi can
+// reach the sphere bs (centre, radius; a negative radius: no sphere, always true). A point
+// p = q + u with |u| <= R has d1 <= d1c + R and |p x r^| >= |q x r^| - R; it is in the cone only
+// if |p x r^| <= tan(phi) d1. Compared squared (both sides are non-negative); the margin, from the
+// L1 norm of q, covers FP32 rounding on both sides.
+__device__ __forceinline__ bool cone_reaches_sphere(const float4 bs, const float4 F0, const float4 F1,
+                                                    const float tanphi) {
+    if (bs.w < 0.f) return true;
+    const float bR = bs.w;
+    const float qx = bs.x - F0.x, qy = bs.y - F0.y, qz = bs.z - F0.z;
+    const float d1c = fmaf(qx, F1.x, fmaf(qy, F1.y, qz * F1.z));
+    const float ux = fmaf(qy, F1.z, -qz * F1.y);
+    const float uy = fmaf(qz, F1.x, -qx * F1.z);
+    const float uz = fmaf(qx, F1.y, -qy * F1.x);
+    const float margin = 1e-4f * (fabsf(qx) + fabsf(qy) + fabsf(qz) + bR);
+    const float reach = d1c + bR;
+    const float lim = bR + fmaf(tanphi, fmaxf(reach, 0.f), margin);
+    return !(reach <= -margin || fmaf(ux, ux, fmaf(uy, uy, uz * uz)) > lim * lim);
+}
+
+// The bounding sphere of a warp's points (centre of their box, half its diagonal, enlarged by
+// 1e-4 relative), the same in every lane; radius -1 when no lane holds a point.
+__device__ __forceinline__ float4 warp_bounding_sphere(const bool has, const float x, const float y, const float z) {
+    float lo[3] = {has ? x : INFINITY, has ? y : INFINITY, has ? z : INFINITY};
+    float hi[3] = {has ? x : -INFINITY, has ? y : -INFINITY, has ? z : -INFINITY};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+    }
+    if (!(lo[0] <= hi[0])) return make_float4(0.f, 0.f, 0.f, -1.f);
+    return make_float4(0.5f * (lo[0] + hi[0]), 0.5f * (lo[1] + hi[1]), 0.5f * (lo[2] + hi[2]),
+                       0.5f * sqrtf((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                                    (hi[2] - lo[2]) * (hi[2] - lo[2])) * 1.0001f);
+}
+
 constexpr int WARP_TILE = 32 * SPT;   // samples per warp tile
 
 // Compensated addition of g into a sample's (sum, compensation) slot.
@@ -463,21 +501,7 @@ __device__ __forceinline__ void warp_tile(uint32_t tile, const float4* __restric
     float4 nF1 = !FSM && i_beg < i_end ? __ldg(&fix[2 * i_beg + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
     // whether fixation (F0, F1)'s cone can reach the tile's bounding sphere (always, without one)
     auto sphere_reach = [&](const float4 F0, const float4 F1) -> bool {
-        const float4 bs = *wbox;
-        if (bs.w < 0.f) return true;
-        // a point p = q + u with |u| <= R has d1 <= d1c + R and |p x r^| >= |q x r^| - R; it is
-        // in the cone only if |p x r^| <= tan(phi) d1. Compared squared (both sides are
-        // non-negative); the margin, from the L1 norm of q, covers FP32 rounding on both sides.
-        const float bR = bs.w;
-        const float qx = bs.x - F0.x, qy = bs.y - F0.y, qz = bs.z - F0.z;
-        const float d1c = fmaf(qx, F1.x, fmaf(qy, F1.y, qz * F1.z));
-        const float ux = fmaf(qy, F1.z, -qz * F1.y);
-        const float uy = fmaf(qz, F1.x, -qx * F1.z);
-        const float uz = fmaf(qx, F1.y, -qy * F1.x);
-        const float margin = 1e-4f * (fabsf(qx) + fabsf(qy) + fabsf(qz) + bR);
-        const float reach = d1c + bR;
-        const float lim = bR + fmaf(P.tanphi, fmaxf(reach, 0.f), margin);
-        return !(reach <= -margin || fmaf(ux, ux, fmaf(uy, uy, uz * uz)) > lim * lim);
+        return cone_reaches_sphere(*wbox, F0, F1, P.tanphi);
     };
     // the work of one fixation (window change, tile sphere test unless `reached` says it was
     // passed, cone tests, ray queue)

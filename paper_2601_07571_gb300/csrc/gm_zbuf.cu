@@ -500,6 +500,7 @@ struct ZbAccParams {
     float C2, K, tmax, eps;
     uint32_t ns, W, nt, res;
     uint64_t dbg_cap;
+    float tanphi;   // cutoff tan theta, slightly enlarged (the warp-sphere test's cone)
 };
 
 // Visibility of a point in fixation F's z-buffer: inside the crop frustum (the NDC filter of
@@ -545,8 +546,30 @@ __global__ void __launch_bounds__(ZB_THREADS) k_zb_accumulate(
         sum = 0.f;
         cmp = 0.f;
     };
-    for (uint32_t i = f0; i < f1; ++i) {
-        const float4 F0 = __ldg(&fix[2 * i]), F1 = __ldg(&fix[2 * i + 1]);
+    // the warp's 32 samples (consecutive in the work order) as one sphere: each lane tests one of
+    // 32 fixations against it, and the warp visits, in list order, only the fixations whose cone
+    // reaches it; a skipped fixation changes no sum, and a window is written when the next visited
+    // fixation opens another one
+    const float4 bs = warp_bounding_sphere(valid, s.x, s.y, s.z);
+    __shared__ float4 wf[ZB_THREADS / 32][64];
+    float4* myf = wf[threadIdx.x >> 5];
+    for (uint32_t c0 = f0; c0 < f1; c0 += 32) {
+      const uint32_t m = min(32u, f1 - c0);
+      bool pass = false;
+      __syncwarp();
+      if ((uint32_t)lane < m) {
+          const float4 a = __ldg(&fix[2 * (c0 + lane)]), b = __ldg(&fix[2 * (c0 + lane) + 1]);
+          myf[2 * lane] = a;
+          myf[2 * lane + 1] = b;
+          pass = cone_reaches_sphere(bs, a, b, P.tanphi);
+      }
+      unsigned pm = __ballot_sync(0xffffffffu, pass);
+      __syncwarp();
+      while (pm) {
+        const int kk = __ffs(pm) - 1;
+        pm &= pm - 1u;
+        const uint32_t i = c0 + kk;
+        const float4 F0 = myf[2 * kk], F1 = myf[2 * kk + 1];
         const uint32_t win = __float_as_uint(F1.w);
         if (win != cur) {
             if (cur != NO_WINDOW) flush(cur);
@@ -589,11 +612,18 @@ __global__ void __launch_bounds__(ZB_THREADS) k_zb_accumulate(
                 dbg.g[q] = g;
             }
         }
+      }
     }
     if (last) {
         if (cur != NO_WINDOW) flush(cur);
-    } else if (valid) {
-        state[j] = make_float2(sum, cmp);
+    } else {
+        // the next chunk continues the window of fixation f1 - 1: sums of an earlier window (its
+        // last fixations were skipped here) are written now
+        if (f1 > f0) {
+            const uint32_t wl = __float_as_uint(__ldg(&fix[2 * (f1 - 1) + 1]).w);
+            if (cur != wl && cur != NO_WINDOW) flush(cur);
+        }
+        if (valid) state[j] = make_float2(sum, cmp);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -957,6 +987,7 @@ extern "C" gm_status gm_accumulate_zbuffer(gm_scene* sc, gm_samples* sm, const g
     P.nt = sc->n_tris;
     P.res = res;
     P.dbg_cap = mp->dbg_cap;
+    P.tanphi = (float)(std::sqrt((double)P.K) * 1.00001);
     DebugOut dbg{mp->dbg_sample, mp->dbg_fix, mp->dbg_vis, mp->dbg_g, orig};
     const bool reorder = sm->work_pos != nullptr;
     uint32_t* ident = nullptr;
